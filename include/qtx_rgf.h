@@ -1,0 +1,150 @@
+/*
+ * qtx_rgf.h -- C ABI of the GB300 (sm_103a) RGF selected-inversion library.
+ *
+ * What it computes (paper: Sec. II-A, Eq. 2 and Table I, G-row): for every energy E of a grid,
+ * independently, the diagonal and first off-diagonal blocks of
+ *     G^R(E) = M(E)^-1,   M(E) = z S - H - Sigma^R(E),   z = E + i eta,
+ *     G^<(E) = G^R Sigma^<(E) G^A,                       G^A = (G^R)^H,
+ *     G^>(E) = G^< + G^R - G^A
+ * for a block-tridiagonal (BT, Sec. II-A) complex device matrix with N_B slices of block size b,
+ * plus the observables of Sec. II-B (current per slice interface, electron density per slice,
+ * contact currents, transmission) and their energy integrals.  The solver is the block Gaussian
+ * elimination of Sec. IV-A (forward sweep of left-connected Green's functions g_i, g^<_i, then a
+ * backward sweep for the selected blocks); contact self-energies come from Sancho-Rubio
+ * decimation.  The broadening eta acts as an extra retarded self-energy -i eta S whose lesser part
+ * is 0, i.e. G^> above equals G^R (Sigma^> - 2 i eta S) G^A.
+ *
+ * Memory: every array pointer in qtx_rgf_inputs / qtx_rgf_outputs is a DEVICE pointer owned by
+ * the caller; the library never frees or retains it after qtx_rgf_solve returns.  Complex values
+ * are interleaved (re, im) double pairs (C99 double complex / cuDoubleComplex), blocks row-major.
+ * Block arrays have layout [energy][slice][row][col] (energy index outermost) unless noted.
+ * The plan owns its device workspace (allocated in qtx_rgf_plan, freed in qtx_rgf_destroy).
+ *
+ * Errors: every call returns a qtx_status.  A status other than QTX_OK from qtx_rgf_solve means
+ * nothing was enqueued, except QTX_ERR_CUDA for a failure after launch (message in
+ * qtx_rgf_last_error).  Numerical failures found on the device (singular pivot, decimation not
+ * converged, bounded wait expired) are written per energy to outputs->status_per_energy (if
+ * given) and returned by the next qtx_rgf_status() call; they never trap or abort a kernel.
+ * Nothing falls back to the CPU.
+ */
+#ifndef QTX_RGF_H
+#define QTX_RGF_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  QTX_OK = 0,
+  QTX_ERR_INVALID_ARG = 1,   /* bad shape, NULL required pointer, unknown enum value */
+  QTX_ERR_OOM = 2,           /* workspace allocation failed */
+  QTX_ERR_CUDA = 3,          /* a CUDA runtime call or kernel launch failed */
+  QTX_ERR_SINGULAR = 4,      /* a pivot of a block inverse was zero (per energy) */
+  QTX_ERR_NOT_CONVERGED = 5, /* lead decimation hit decim_max_iter (per energy) */
+  QTX_ERR_TIMEOUT = 6,       /* a bounded device-side wait expired (per energy / per launch) */
+  QTX_ERR_UNSUPPORTED = 7    /* valid request this build or GPU does not provide */
+} qtx_status;
+
+/* Arithmetic of the block products and inverses (Sec. IV, V-A of the paper: the solve of Eq. 2 is
+ * ZGEMM-dominated; lower precision is traded against accuracy).  Observables are always reduced
+ * in FP64 and the lead decimation always runs in FP64. */
+typedef enum {
+  QTX_FP64 = 0,   /* complex128 throughout (SIMT DFMA) -- the plain FP64 path */
+  QTX_FP32 = 1,   /* complex64 products and inverses (SIMT FFMA) */
+  QTX_BF16X3 = 2, /* products from 2 bf16 digit planes per operand, 3 digit products, tensor cores */
+  QTX_EMU64 = 3   /* emulated FP64: products from 5 bf16 integer digit planes per operand (15 exact
+                     digit products on tcgen05 tensor cores, Ozaki-style slicing), inverses in FP32
+                     refined with emulated-FP64 residuals */
+} qtx_precision;
+
+/* Output selection bits (qtx_rgf_desc.outputs).  A block is written only if its bit is set AND
+ * its pointer in qtx_rgf_outputs is non-NULL. */
+enum {
+  QTX_OUT_GR_DIAG = 1u << 0,   /* G^R_ii        [N_E][N_B][b][b]   */
+  QTX_OUT_GR_UPPER = 1u << 1,  /* G^R_{i,i+1}   [N_E][N_B-1][b][b] */
+  QTX_OUT_GR_LOWER = 1u << 2,  /* G^R_{i+1,i}   [N_E][N_B-1][b][b] */
+  QTX_OUT_GL_DIAG = 1u << 3,   /* G^<_ii        [N_E][N_B][b][b]   */
+  QTX_OUT_GL_UPPER = 1u << 4,  /* G^<_{i,i+1}   [N_E][N_B-1][b][b]; G^<_{i+1,i} = -(G^<_{i,i+1})^H */
+  QTX_OUT_GG_DIAG = 1u << 5,   /* G^>_ii        [N_E][N_B][b][b]   */
+  QTX_OUT_GG_UPPER = 1u << 6,  /* G^>_{i,i+1}   [N_E][N_B-1][b][b] */
+  QTX_OUT_CURRENT = 1u << 7,   /* I_i(E) = 2 Re Tr[(H_{i,i+1} - E S_{i,i+1}) G^<_{i+1,i}]  [N_E][N_B-1] */
+  QTX_OUT_DENSITY = 1u << 8,   /* n_i(E) = Im Tr G^<_ii  [N_E][N_B]                                    */
+  QTX_OUT_CONTACT = 1u << 9,   /* I_L,R(E) = Re Tr[Sigma^<_c G^>_kk - Sigma^>_c G^<_kk]  [N_E][2]      */
+  QTX_OUT_TRANSMISSION = 1u << 10, /* T(E) = Tr[Gam_L A_00] - Tr[Gam_L G_00 Gam_L G_00^H]  [N_E]    */
+  QTX_OUT_INTEGRALS = 1u << 11,    /* sum_E w_E I_i(E) [N_B-1],  sum_E w_E n_i(E)/(2 pi) [N_B]     */
+  QTX_OUT_ALL = (1u << 12) - 1u
+};
+
+/* Shapes and numerics, fixed for the life of a plan. */
+typedef struct {
+  int n_blocks;                /* N_B >= 1 */
+  int block_size;              /* b, 1 <= b <= 1024 */
+  int max_energies_in_flight;  /* energies solved concurrently; workspace scales with it (>= 1) */
+  qtx_precision precision;
+  int refine_max_iter;         /* Newton sweeps X += X (I - A X) per block inverse (QTX_EMU64) */
+  int has_S;                   /* 0: S = I (S pointers ignored) */
+  int has_scattering;          /* 0: no scattering self-energies (Sigma pointers ignored) */
+  int energy_dependent_sigma;  /* 0: one Sigma set [N_B][b][b] for all energies; 1: [N_E][N_B][b][b] */
+  int leads;                   /* 0: none; 1: Sancho-Rubio contacts on slices 0 and N_B-1 */
+  double decim_tol;            /* stop when max|alpha|,|beta| < decim_tol * max|H01| (e.g. 1e-13) */
+  int decim_max_iter;          /* decimation sweeps before QTX_ERR_NOT_CONVERGED (e.g. 100) */
+  unsigned outputs;            /* QTX_OUT_* mask */
+} qtx_rgf_desc;
+
+/* Device inputs (caller-owned, complex128 unless noted). */
+typedef struct {
+  const void *H_diag;    /* [N_B][b][b] Hermitian H_ii */
+  const void *H_upper;   /* [N_B-1][b][b] H_{i,i+1}; H_{i+1,i} = H_{i,i+1}^H (may be NULL if N_B == 1) */
+  const void *S_diag;    /* [N_B][b][b] overlap (has_S) */
+  const void *S_upper;   /* [N_B-1][b][b] (has_S) */
+  const void *SigR_diag; /* scattering Sigma^R_ii, [N_B][b][b] or [N_E][N_B][b][b] (has_scattering) */
+  const void *SigL_diag; /* scattering Sigma^<_ii, same layout; Sigma^> = Sigma^< + Sigma^R - Sigma^A */
+  const void *lead_H00_L, *lead_H01_L;  /* [b][b] each (leads): principal layer and the coupling */
+  const void *lead_H00_R, *lead_H01_R;  /* from a lead cell to the next one away from the device */
+  double eta, mu_L, mu_R, kT;           /* broadening, contact chemical potentials, temperature */
+  const double *energies;  /* [N_E] device array */
+  const double *weights;   /* [N_E] device array of quadrature weights, or NULL for the trapezoid rule */
+  int n_energies;          /* N_E >= 1 */
+} qtx_rgf_inputs;
+
+/* Device outputs (caller-owned; NULL = not produced).  Layouts as in QTX_OUT_*. */
+typedef struct {
+  void *GR_diag, *GR_upper, *GR_lower, *GL_diag, *GL_upper, *GG_diag, *GG_upper; /* complex128 */
+  double *current, *density, *contact, *transmission;
+  double *current_int, *density_int;
+  int *status_per_energy;  /* [N_E] qtx_status per energy */
+} qtx_rgf_outputs;
+
+typedef struct qtx_rgf_plan_s *qtx_rgf_plan;
+
+/* Validate desc, allocate the device workspace on the current device.  *out receives the plan. */
+qtx_status qtx_rgf_plan_create(const qtx_rgf_desc *desc, qtx_rgf_plan *out);
+
+/* Enqueue the solve of all n_energies on `stream` (a cudaStream_t; NULL = legacy default stream).
+ * Energies are processed in chunks of max_energies_in_flight.  Returns after enqueueing, except
+ * that lead decimation synchronises the stream once per few sweeps to test convergence. */
+qtx_status qtx_rgf_solve(qtx_rgf_plan plan, const qtx_rgf_inputs *in, const qtx_rgf_outputs *out,
+                         void *stream);
+
+/* Synchronise the plan's last stream and return the worst per-energy status of the last solve. */
+qtx_status qtx_rgf_status(qtx_rgf_plan plan);
+
+/* Free the workspace.  Safe on NULL. */
+qtx_status qtx_rgf_destroy(qtx_rgf_plan plan);
+
+/* Message for the last error on this plan (or the last failed plan creation if plan is NULL).
+ * The string is owned by the library and valid until the next call on the same plan. */
+const char *qtx_rgf_last_error(qtx_rgf_plan plan);
+
+/* Device workspace bytes a plan with this desc allocates (for admission by HBM footprint). */
+size_t qtx_rgf_footprint(const qtx_rgf_desc *desc);
+
+/* Library version string. */
+const char *qtx_rgf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QTX_RGF_H */

@@ -24,7 +24,7 @@ def fermi(E: float, mu: float, kT: float) -> float:
 
 
 def sancho_rubio(z: complex, H00: np.ndarray, H01: np.ndarray, tol: float = 1e-13,
-                 max_iter: int = 100):
+                 max_iter: int = 100, track_cond: bool = False):
     """Surface Green's function g_s = (z - H00 - H01 g_s H01^H)^-1 of a semi-infinite lead.
 
     Decimation: start from alpha = H01, beta = H01^H, eps_s = eps = H00; each sweep removes every
@@ -33,7 +33,9 @@ def sancho_rubio(z: complex, H00: np.ndarray, H01: np.ndarray, tol: float = 1e-1
         eps_s += alpha g beta
         eps   += alpha g beta + beta g alpha
         alpha  = alpha g alpha,   beta = beta g beta
-    until max|alpha|, max|beta| fall below tol * max|H01|.  Returns (g_s, sweeps, converged).
+    until max|alpha|, max|beta| fall below tol * max|H01|.  Returns (g_s, sweeps, converged), plus
+    the largest 2-norm condition number of the inverted blocks (z - eps) when ``track_cond``: the
+    paper's Eq. 6 error model (error ~ kappa * eps_m) applied to this iteration.
     """
     b = H00.shape[0]
     eye = np.eye(b, dtype=np.complex128)
@@ -44,7 +46,10 @@ def sancho_rubio(z: complex, H00: np.ndarray, H01: np.ndarray, tol: float = 1e-1
     scale = max(float(np.abs(H01).max()), 1e-300)
     converged = False
     it = 0
+    kappa = 0.0
     for it in range(1, max_iter + 1):
+        if track_cond:
+            kappa = max(kappa, float(np.linalg.cond(z * eye - eps)))
         g = np.linalg.inv(z * eye - eps)
         agb = alpha @ g @ beta
         bga = beta @ g @ alpha
@@ -55,14 +60,21 @@ def sancho_rubio(z: complex, H00: np.ndarray, H01: np.ndarray, tol: float = 1e-1
         if max(np.abs(alpha).max(), np.abs(beta).max()) < tol * scale:
             converged = True
             break
+    if track_cond:
+        kappa = max(kappa, float(np.linalg.cond(z * eye - eps_s)))
     g_s = np.linalg.inv(z * eye - eps_s)
+    if track_cond:
+        return g_s, it, converged, kappa
     return g_s, it, converged
 
 
 def lead_self_energy(E: float, eta: float, H00: np.ndarray, H01: np.ndarray,
-                     tol: float = 1e-13, max_iter: int = 100):
+                     tol: float = 1e-13, max_iter: int = 100, track_cond: bool = False):
     """Retarded self-energy Sigma^R = H01 g_s(E + i eta) H01^H on the device's end slice.
 
-    Returns (Sigma^R, sweeps, converged)."""
-    g_s, it, conv = sancho_rubio(E + 1j * eta, H00, H01, tol, max_iter)
-    return H01 @ g_s @ H01.conj().T, it, conv
+    Returns (Sigma^R, sweeps, converged) or, with ``track_cond``, also the decimation's largest
+    block condition number."""
+    r = sancho_rubio(E + 1j * eta, H00, H01, tol, max_iter, track_cond)
+    if track_cond:
+        return H01 @ r[0] @ H01.conj().T, r[1], r[2], r[3]
+    return H01 @ r[0] @ H01.conj().T, r[1], r[2]

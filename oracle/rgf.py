@@ -40,7 +40,7 @@ def _H(X):
     return X.conj().T
 
 
-def _contacts(E: float, dev: dict, decim_tol: float, decim_max_iter: int):
+def _contacts(E: float, dev: dict, decim_tol: float, decim_max_iter: int, track_cond=False):
     """Contact self-energies on the two end slices (None when the device has no leads)."""
     leads = dev.get("leads")
     if not leads:
@@ -48,12 +48,14 @@ def _contacts(E: float, dev: dict, decim_tol: float, decim_max_iter: int):
     eta, kT = dev["eta"], dev["kT"]
     out = {}
     for side, mu in (("L", dev["mu_L"]), ("R", dev["mu_R"])):
-        SR, it, conv = lead_self_energy(E, eta, leads["H00_" + side], leads["H01_" + side],
-                                        decim_tol, decim_max_iter)
+        r = lead_self_energy(E, eta, leads["H00_" + side], leads["H01_" + side], decim_tol,
+                             decim_max_iter, track_cond)
+        SR, it, conv = r[0], r[1], r[2]
+        kappa = r[3] if track_cond else None
         gam = 1j * (SR - _H(SR))
         f = fermi(E, mu, kT)
         out[side] = dict(SigR=SR, Gamma=gam, SigL=1j * f * gam, SigG=-1j * (1.0 - f) * gam,
-                         sweeps=it, converged=conv)
+                         sweeps=it, converged=conv, kappa=kappa)
     return out
 
 
@@ -65,7 +67,7 @@ def _scattering(dev: dict, key: str, e_index: int, i: int):
 
 
 def rgf_energy(E: float, dev: dict, e_index: int = 0, decim_tol: float = 1e-13,
-               decim_max_iter: int = 100) -> dict:
+               decim_max_iter: int = 100, track_cond: bool = False) -> dict:
     """Selected blocks and observables at one energy (see the module docstring for every formula)."""
     nb, b = dev["n_blocks"], dev["block_size"]
     eta = dev["eta"]
@@ -73,7 +75,7 @@ def rgf_energy(E: float, dev: dict, e_index: int = 0, decim_tol: float = 1e-13,
     eye = np.eye(b, dtype=np.complex128)
     Hd, Hu = dev["H_diag"], dev["H_upper"]
     Sd, Su = dev.get("S_diag"), dev.get("S_upper")
-    con = _contacts(E, dev, decim_tol, decim_max_iter)
+    con = _contacts(E, dev, decim_tol, decim_max_iter, track_cond)
 
     # Step 1: the block rows of M and the lesser self-energy on each slice.
     A, SigL = [], []
@@ -143,6 +145,8 @@ def rgf_energy(E: float, dev: dict, e_index: int = 0, decim_tol: float = 1e-13,
         out["lead_SigL"] = (con["L"]["SigL"], con["R"]["SigL"])
         out["decim_sweeps"] = (con["L"]["sweeps"], con["R"]["sweeps"])
         out["decim_converged"] = con["L"]["converged"] and con["R"]["converged"]
+        if track_cond:
+            out["decim_cond"] = max(con["L"]["kappa"], con["R"]["kappa"])
     return out
 
 
@@ -177,14 +181,15 @@ def integrate(current_E: np.ndarray, density_E: np.ndarray, weights: np.ndarray)
 
 
 def solve(dev: dict, energy_indices=None, weights=None, decim_tol: float = 1e-13,
-          decim_max_iter: int = 100, keep_blocks: bool = True) -> dict:
+          decim_max_iter: int = 100, keep_blocks: bool = True, track_cond: bool = False) -> dict:
     """Run ``rgf_energy`` over the device's energy grid (or the listed indices) and stack results.
 
     ``weights`` (per listed energy) default to the trapezoid rule on the full grid restricted to
     the listed indices."""
     energies = dev["energies"]
     idx = np.arange(energies.size) if energy_indices is None else np.asarray(energy_indices)
-    res = [rgf_energy(float(energies[k]), dev, int(k), decim_tol, decim_max_iter) for k in idx]
+    res = [rgf_energy(float(energies[k]), dev, int(k), decim_tol, decim_max_iter, track_cond)
+           for k in idx]
     out = {}
     keys = ["current", "density"] + (["contact", "transmission"] if dev.get("leads") else [])
     if keep_blocks:
@@ -197,4 +202,6 @@ def solve(dev: dict, energy_indices=None, weights=None, decim_tol: float = 1e-13
     out["current_int"], out["density_int"] = integrate(out["current"], out["density"], weights)
     if dev.get("leads"):
         out["decim_sweeps"] = np.array([r["decim_sweeps"] for r in res])
+        if track_cond:
+            out["decim_cond"] = np.array([r["decim_cond"] for r in res])
     return out

@@ -1,0 +1,248 @@
+"""Python binding of the GB300 RGF selected-inversion library (``libqtx_rgf.so``, C ABI in
+``include/qtx_rgf.h``).
+
+This module only marshals arguments: it builds the ctypes descriptors, hands device pointers
+(from torch CUDA tensors) and a CUDA stream to the library, and returns the output tensors.
+Every step of the solve runs in the library's CUDA kernels; there is no CPU path.  Importing works
+without a GPU (the library loads and its symbols resolve); solving needs one.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+__all__ = ["lib", "load", "Desc", "Inputs", "Outputs", "Plan", "QtxError", "PRECISION",
+           "OUT", "solve_device", "footprint", "EXPORTED"]
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libqtx_rgf.so")
+
+PRECISION = {"fp64": 0, "fp32": 1, "bf16x3": 2, "emu64": 3}
+STATUS = {0: "QTX_OK", 1: "QTX_ERR_INVALID_ARG", 2: "QTX_ERR_OOM", 3: "QTX_ERR_CUDA",
+          4: "QTX_ERR_SINGULAR", 5: "QTX_ERR_NOT_CONVERGED", 6: "QTX_ERR_TIMEOUT",
+          7: "QTX_ERR_UNSUPPORTED"}
+OUT = {"GR_diag": 1 << 0, "GR_upper": 1 << 1, "GR_lower": 1 << 2, "GL_diag": 1 << 3,
+       "GL_upper": 1 << 4, "GG_diag": 1 << 5, "GG_upper": 1 << 6, "current": 1 << 7,
+       "density": 1 << 8, "contact": 1 << 9, "transmission": 1 << 10, "integrals": 1 << 11}
+BLOCK_OUTPUTS = ("GR_diag", "GR_upper", "GR_lower", "GL_diag", "GL_upper", "GG_diag", "GG_upper")
+# Every function the C ABI exports (checked by the CPU tests against include/*.h).
+EXPORTED = ("qtx_rgf_plan_create", "qtx_rgf_solve", "qtx_rgf_status", "qtx_rgf_destroy",
+            "qtx_rgf_last_error", "qtx_rgf_footprint", "qtx_rgf_version")
+
+
+class QtxError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Desc(ctypes.Structure):
+    _fields_ = [("n_blocks", ctypes.c_int), ("block_size", ctypes.c_int),
+                ("max_energies_in_flight", ctypes.c_int), ("precision", ctypes.c_int),
+                ("refine_max_iter", ctypes.c_int), ("has_S", ctypes.c_int),
+                ("has_scattering", ctypes.c_int), ("energy_dependent_sigma", ctypes.c_int),
+                ("leads", ctypes.c_int), ("decim_tol", ctypes.c_double),
+                ("decim_max_iter", ctypes.c_int), ("outputs", ctypes.c_uint)]
+
+
+class Inputs(ctypes.Structure):
+    _fields_ = [("H_diag", ctypes.c_void_p), ("H_upper", ctypes.c_void_p),
+                ("S_diag", ctypes.c_void_p), ("S_upper", ctypes.c_void_p),
+                ("SigR_diag", ctypes.c_void_p), ("SigL_diag", ctypes.c_void_p),
+                ("lead_H00_L", ctypes.c_void_p), ("lead_H01_L", ctypes.c_void_p),
+                ("lead_H00_R", ctypes.c_void_p), ("lead_H01_R", ctypes.c_void_p),
+                ("eta", ctypes.c_double), ("mu_L", ctypes.c_double), ("mu_R", ctypes.c_double),
+                ("kT", ctypes.c_double), ("energies", ctypes.c_void_p),
+                ("weights", ctypes.c_void_p), ("n_energies", ctypes.c_int)]
+
+
+class Outputs(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_void_p) for n in BLOCK_OUTPUTS] + \
+               [(n, ctypes.c_void_p) for n in ("current", "density", "contact", "transmission",
+                                               "current_int", "density_int",
+                                               "status_per_energy")]
+
+
+_lib = None
+
+
+def load() -> ctypes.CDLL:
+    """Load ``libqtx_rgf.so`` (built in-tree by ``paper_2606_25595_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: run paper_2606_25595_gb300.build.build() "
+                          "(nvcc, sm_103a); there is no CPU fallback")
+    L = ctypes.CDLL(LIB_PATH)
+    L.qtx_rgf_plan_create.argtypes = [ctypes.POINTER(Desc), ctypes.POINTER(ctypes.c_void_p)]
+    L.qtx_rgf_plan_create.restype = ctypes.c_int
+    L.qtx_rgf_solve.argtypes = [ctypes.c_void_p, ctypes.POINTER(Inputs), ctypes.POINTER(Outputs),
+                                ctypes.c_void_p]
+    L.qtx_rgf_solve.restype = ctypes.c_int
+    L.qtx_rgf_status.argtypes = [ctypes.c_void_p]
+    L.qtx_rgf_status.restype = ctypes.c_int
+    L.qtx_rgf_destroy.argtypes = [ctypes.c_void_p]
+    L.qtx_rgf_destroy.restype = ctypes.c_int
+    L.qtx_rgf_last_error.argtypes = [ctypes.c_void_p]
+    L.qtx_rgf_last_error.restype = ctypes.c_char_p
+    L.qtx_rgf_footprint.argtypes = [ctypes.POINTER(Desc)]
+    L.qtx_rgf_footprint.restype = ctypes.c_size_t
+    L.qtx_rgf_version.argtypes = []
+    L.qtx_rgf_version.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def lib() -> ctypes.CDLL:
+    return load()
+
+
+def make_desc(n_blocks, block_size, precision="fp64", max_energies_in_flight=64,
+              refine_max_iter=2, has_S=False, has_scattering=True, energy_dependent_sigma=False,
+              leads=False, decim_tol=1e-13, decim_max_iter=100, outputs=None) -> Desc:
+    if outputs is None:
+        outputs = (1 << 12) - 1
+    elif not isinstance(outputs, int):
+        mask = 0
+        for name in outputs:
+            mask |= OUT[name]
+        outputs = mask
+    return Desc(int(n_blocks), int(block_size), int(max_energies_in_flight),
+                PRECISION[precision] if isinstance(precision, str) else int(precision),
+                int(refine_max_iter), int(bool(has_S)), int(bool(has_scattering)),
+                int(bool(energy_dependent_sigma)), int(bool(leads)), float(decim_tol),
+                int(decim_max_iter), int(outputs))
+
+
+def footprint(desc: Desc) -> int:
+    return int(load().qtx_rgf_footprint(ctypes.byref(desc)))
+
+
+class Plan:
+    """Owns a ``qtx_rgf_plan`` (device workspace for one shape / precision)."""
+
+    def __init__(self, desc: Desc):
+        L = load()
+        self.desc = desc
+        h = ctypes.c_void_p()
+        s = L.qtx_rgf_plan_create(ctypes.byref(desc), ctypes.byref(h))
+        if s != 0:
+            raise QtxError(s, L.qtx_rgf_last_error(None).decode())
+        self._h = h
+
+    def _check(self, s):
+        if s != 0:
+            raise QtxError(s, load().qtx_rgf_last_error(self._h).decode())
+
+    def solve(self, inputs: Inputs, outputs: Outputs, stream: int = 0) -> None:
+        self._check(load().qtx_rgf_solve(self._h, ctypes.byref(inputs), ctypes.byref(outputs),
+                                         ctypes.c_void_p(stream)))
+
+    def status(self) -> int:
+        return int(load().qtx_rgf_status(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().qtx_rgf_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def solve_device(dev: dict, precision: str = "fp64", outputs=None, max_energies_in_flight=64,
+                 refine_max_iter=2, weights=None, energies=None, stream=None, plan=None,
+                 device_inputs=None, keep_on_device=False):
+    """Solve a ``workloads``-style device dict on the GPU and return numpy arrays (or tensors).
+
+    Marshalling only: inputs are copied to torch CUDA tensors (complex128), the C ABI is called on
+    the current torch stream, and the requested outputs come back.  ``device_inputs`` reuses
+    already-uploaded tensors (see ``upload``).
+    """
+    import torch
+
+    nb, b = dev["n_blocks"], dev["block_size"]
+    E = np.asarray(dev["energies"] if energies is None else energies, dtype=np.float64)
+    ne = E.size
+    din = device_inputs if device_inputs is not None else upload(dev, E, weights)
+    want = list(outputs) if outputs is not None else list(OUT)
+    if not dev.get("leads"):
+        want = [w for w in want if w not in ("contact", "transmission")]
+    desc = make_desc(nb, b, precision, min(max_energies_in_flight, ne), refine_max_iter,
+                     has_S=dev.get("S_diag") is not None, has_scattering=dev.get("SigR") is not None,
+                     energy_dependent_sigma=dev.get("SigR") is not None and dev["SigR"].shape[0] > 1,
+                     leads=bool(dev.get("leads")), outputs=want)
+    P = plan if plan is not None else Plan(desc)
+    cdev = torch.device("cuda")
+    res = {}
+    shapes = {"GR_diag": (ne, nb, b, b), "GR_upper": (ne, nb - 1, b, b),
+              "GR_lower": (ne, nb - 1, b, b), "GL_diag": (ne, nb, b, b),
+              "GL_upper": (ne, nb - 1, b, b), "GG_diag": (ne, nb, b, b),
+              "GG_upper": (ne, nb - 1, b, b), "current": (ne, nb - 1), "density": (ne, nb),
+              "contact": (ne, 2), "transmission": (ne,), "integrals": None}
+    o = Outputs()
+    for k in want:
+        if k == "integrals":
+            res["current_int"] = torch.zeros(max(nb - 1, 0), dtype=torch.float64, device=cdev)
+            res["density_int"] = torch.zeros(nb, dtype=torch.float64, device=cdev)
+            o.current_int = res["current_int"].data_ptr() if nb > 1 else None
+            o.density_int = res["density_int"].data_ptr()
+            continue
+        shp = shapes[k]
+        if 0 in shp:
+            continue
+        dt = torch.complex128 if k in BLOCK_OUTPUTS else torch.float64
+        res[k] = torch.empty(shp, dtype=dt, device=cdev)
+        setattr(o, k, res[k].data_ptr())
+    res["status"] = torch.zeros(ne, dtype=torch.int32, device=cdev)
+    o.status_per_energy = res["status"].data_ptr()
+    st = torch.cuda.current_stream().cuda_stream if stream is None else stream
+    P.solve(din["_inputs"], o, st)
+    torch.cuda.current_stream().synchronize()
+    if keep_on_device:
+        return res
+    return {k: v.cpu().numpy() for k, v in res.items()}
+
+
+def upload(dev: dict, energies=None, weights=None) -> dict:
+    """Copy a device dict's blocks to torch CUDA tensors and build the ``Inputs`` struct."""
+    import torch
+
+    cdev = torch.device("cuda")
+
+    def T(x, dt=torch.complex128):
+        return None if x is None else torch.as_tensor(np.ascontiguousarray(x), dtype=dt).to(cdev)
+
+    E = np.asarray(dev["energies"] if energies is None else energies, dtype=np.float64)
+    d = {"H_diag": T(dev["H_diag"]), "H_upper": T(dev["H_upper"]) if dev["n_blocks"] > 1 else None,
+         "S_diag": T(dev.get("S_diag")), "S_upper": T(dev.get("S_upper")),
+         "SigR_diag": None, "SigL_diag": None, "energies": T(E, torch.float64),
+         "weights": T(weights, torch.float64) if weights is not None else None}
+    if dev.get("SigR") is not None:
+        SR, SL = dev["SigR"], dev["SigL"]
+        d["SigR_diag"] = T(SR[0] if SR.shape[0] == 1 else SR)
+        d["SigL_diag"] = T(SL[0] if SL.shape[0] == 1 else SL)
+    leads = dev.get("leads") or {}
+    for k in ("H00_L", "H01_L", "H00_R", "H01_R"):
+        d["lead_" + k] = T(leads.get(k))
+    inp = Inputs()
+    for k in ("H_diag", "H_upper", "S_diag", "S_upper", "SigR_diag", "SigL_diag", "lead_H00_L",
+              "lead_H01_L", "lead_H00_R", "lead_H01_R", "energies", "weights"):
+        setattr(inp, k, None if d[k] is None else d[k].data_ptr())
+    inp.eta = float(dev["eta"])
+    inp.mu_L = float(dev.get("mu_L", 0.0))
+    inp.mu_R = float(dev.get("mu_R", 0.0))
+    inp.kT = float(dev.get("kT", 0.025))
+    inp.n_energies = int(E.size)
+    d["_inputs"] = inp
+    return d

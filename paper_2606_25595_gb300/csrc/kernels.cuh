@@ -1,0 +1,96 @@
+// Launchers of the SIMT kernels (simt.cu) and of the tensor-core engine (tc_engine.cu), called by the
+// host orchestration (rgf.cu).  All launchers are asynchronous on `st` and return the launch status.
+#pragma once
+#include "common.cuh"
+
+namespace qtx {
+
+// ---- batched complex GEMM on the CUDA cores (T = double: DFMA, T = float: FFMA)
+template <typename T>
+cudaError_t gemm_simt(const GemmArgs<T>& g, cudaStream_t st);
+
+// ---- in-place inverse of n x n blocks (n <= kLeafMax) by Gauss-Jordan elimination with partial
+// (row) pivoting, one CTA per block.  A zero pivot stores QTX_ERR_SINGULAR into status[e].
+constexpr int kLeafMax = 64;
+template <typename T>
+cudaError_t leaf_inverse(cx<T>* A, long lda, long sA, int n, int batch, const int* active,
+                         int* status, cudaStream_t st);
+
+// ---- elementwise combination of b x b blocks (batched over energies):
+//   out[e] = sum_t alpha_t * op_t(X_t[e])  +  diag_coef * (E[e] + i eta) * I
+// op_t = OP_N or OP_C (conjugate transpose).  Up to 3 terms; a term with p == nullptr is skipped.
+template <typename T>
+struct Term {
+  const cx<T>* p = nullptr;
+  long s = 0;     // batch stride (complex elements); 0 shares one block
+  int op = OP_N;
+  double alpha = 0.0;
+};
+template <typename Tin, typename Tout>
+cudaError_t combine(cx<Tout>* out, long sOut, Term<Tin> t0, Term<Tin> t1, Term<Tin> t2, int b,
+                    int batch, const double* E, double eta, double diag_coef, const int* active,
+                    cudaStream_t st);
+
+// ---- assemble a diagonal block of M (step 1 of the sweep), in T precision from complex128 inputs:
+//   out[e] = (E[e] + i eta) S - H - SigR[e] - lead[e]     (S == nullptr => identity)
+template <typename T>
+cudaError_t assemble_diag(cx<T>* out, const cx<double>* H, const cx<double>* S,
+                          const cx<double>* SigR, long sSig, const cx<double>* lead, long sLead,
+                          const double* E, double eta, int b, int batch, cudaStream_t st);
+// out[e] = c1 * X[e] + c2 * Y[e]  with complex128 inputs (Y may be nullptr), converted to T
+template <typename T>
+cudaError_t axpby_from64(cx<T>* out, long sOut, const cx<double>* X, long sX, double c1,
+                         const cx<double>* Y, long sY, double c2, int b, int batch,
+                         cudaStream_t st);
+// off-diagonal rows of M: U[e] = z_e S_up - H_up,  V[e] = z_e S_up^H - H_up^H (S_up may be nullptr)
+template <typename T>
+cudaError_t assemble_offdiag(cx<T>* U, cx<T>* V, const cx<double>* Hup, const cx<double>* Sup,
+                             const double* E, double eta, int b, int batch, cudaStream_t st);
+
+// ---- observables, FP64 accumulation
+// cur[e * ldcur] = 2 Re Tr[(H_up - E S_up) G^<_{i+1,i}],  G^<_{i+1,i} = -(GLu)^H
+template <typename T>
+cudaError_t obs_current(double* cur, long ldcur, const cx<double>* Hup, const cx<double>* Sup,
+                        const cx<T>* GLu, long sG, const double* E, int b, int batch,
+                        cudaStream_t st);
+// den[e * ldden] = Im Tr GL[e]
+template <typename T>
+cudaError_t obs_density(double* den, long ldden, const cx<T>* GL, long sG, int b, int batch,
+                        cudaStream_t st);
+// out[e * ld] = scale * Part(Tr[X[e] Y[e]] - Tr[Z[e] W[e]])  (Z, W may be nullptr; X, Z complex128),
+// Part = Re for part == 0, Im for part == 1.
+template <typename T>
+cudaError_t obs_trace2(double* out, long ld, const cx<double>* X, long sX, const cx<T>* Y, long sY,
+                       const cx<double>* Z, long sZ, const cx<T>* Wm, long sW, int b, int batch,
+                       cudaStream_t st, int part = 0, double scale = 1.0);
+// out[e * ld] = Re Tr[X[e] op(Y[e])] with op = conj-transpose-conj, i.e. sum_jk X_jk conj(Y_jk),
+// scaled by `scale` and added to `add[e*ld]` if add != nullptr.
+cudaError_t obs_frob_dot(double* out, long ld, const cx<double>* X, long sX, const cx<double>* Y,
+                         long sY, double scale, int b, int batch, cudaStream_t st);
+
+// ---- lead post-processing: from Sigma^R (complex128) build Gamma, Sigma^<, Sigma^>
+cudaError_t lead_sigmas(const cx<double>* SR, cx<double>* Gam, cx<double>* SL, cx<double>* SG,
+                        const double* E, double mu, double kT, int b, int batch, cudaStream_t st);
+// per batch entry: if the largest modulus over X and Y is < tol, clear active[e]; count sweeps
+cudaError_t decim_converged(const cx<double>* X, const cx<double>* Y, int b, double tol,
+                            int* active, int* sweeps, int batch, cudaStream_t st);
+// set status[e] = code for entries still active (decimation not converged)
+cudaError_t flag_active(const int* active, int* status, int code, int batch, cudaStream_t st);
+
+// ---- energy integration: acc[i] += scale * sum_{e<batch} w[e] * val[e * ld + i]
+//      (w == nullptr: trapezoid weights of the full grid E[0..nE), entries e0 .. e0+batch)
+cudaError_t integrate_add(double* acc, const double* val, long ld, int n, const double* w,
+                          const double* E, int e0, int nE, int batch, double scale,
+                          cudaStream_t st);
+
+// ---- tensor-core engine (tc_engine.cu): emulated-precision batched complex GEMM on sm_103a
+struct TcConfig {
+  int digits;        // bf16 digit planes per operand
+  int max_order;     // keep digit products with i + j <= max_order (1-based digit indices)
+};
+cudaError_t gemm_tc(const GemmArgs<double>& g, const TcConfig& cfg, void* scratch,
+                    size_t scratch_bytes, int* err_flag, cudaStream_t st);
+size_t gemm_tc_scratch_bytes(int M, int N, int K, int batch, const TcConfig& cfg);
+bool tc_available();
+
+}  // namespace qtx

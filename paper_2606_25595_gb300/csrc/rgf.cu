@@ -1,0 +1,689 @@
+// Host orchestration and C ABI of the RGF selected inversion (declared in include/qtx_rgf.h).
+//
+// Per chunk of energies (all kernels batched over the chunk, one stream):
+//   1. contacts: Sancho-Rubio decimation in FP64 -> Sigma^R_L,R, Gamma, Sigma^<, Sigma^>
+//   2. forward sweep i = 0..N_B-1:  g_i = (A_i - V_{i-1} g_{i-1} U_{i-1})^-1,
+//                                   g^<_i = g_i (Sigma^<_i + V_{i-1} g^<_{i-1} V_{i-1}^H) g_i^H
+//   3. backward sweep i = N_B-2..0 for G^R, G^< blocks (formulas at `backward`), G^> = G^< + G^R - G^A
+//   4. FP64 observables and their energy integrals.
+// The sweep is the block Gaussian elimination of the paper's Sec. IV-A applied to Eq. 2 (Table I,
+// G-row); the block inverse is a recursive 2 x 2 Schur-complement inversion over leaf blocks of at
+// most 64 that are inverted with partial pivoting.  Elimination without pivoting between blocks is
+// safe here for the same reason it is safe between slices: the anti-Hermitian part of M,
+// eta S + Gamma/2, is positive definite, so every leading principal block and every Schur
+// complement is nonsingular.
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+
+using namespace qtx;
+
+namespace {
+thread_local std::string g_create_error;
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Byte-offset allocator for the single workspace allocation.
+struct Arena {
+  size_t off = 0;
+  size_t take(size_t bytes) {
+    const size_t o = off;
+    off = align_up(off + bytes, 256);
+    return o;
+  }
+};
+
+struct Layout {
+  size_t g, gl, tmp, inv_tmp, U, V, ident, ref, f32a, f32tmp, dec, lead, obs, flags, tc_scratch, total;
+  int n_tmp, n_dec;
+  size_t tc_bytes;
+};
+}  // namespace
+
+struct qtx_rgf_plan_s {
+  qtx_rgf_desc d{};
+  int b = 0, nb = 0, Ec = 0;
+  long bb = 0;
+  size_t esz = 0;  // bytes per complex element of the sweep workspace
+  Layout L{};
+  unsigned char* ws = nullptr;
+  std::string err;
+  cudaStream_t last = nullptr;
+  int* d_err_flag = nullptr;    // tensor-core engine wait/limit flag
+  int worst = 0;                // worst per-energy status after the last synchronising call
+  int* h_status = nullptr;      // pinned host copy of the chunk status
+  std::vector<int> status_host;
+  const int* out_status = nullptr;  // caller's per-energy status array of the last solve
+  int out_status_n = 0;
+};
+
+namespace {
+
+Layout make_layout(const qtx_rgf_desc& d) {
+  Layout L{};
+  const long b = d.block_size, nb = d.n_blocks, Ec = d.max_energies_in_flight;
+  const size_t bb = (size_t)b * b;
+  const size_t es = d.precision == QTX_FP32 ? sizeof(cx<float>) : sizeof(cx<double>);
+  Arena a;
+  L.n_tmp = 12;
+  L.g = a.take(nb * Ec * bb * es);
+  L.gl = a.take(nb * Ec * bb * es);
+  L.tmp = a.take((size_t)L.n_tmp * Ec * bb * es);
+  L.inv_tmp = a.take(Ec * bb * es + 4096);
+  const size_t ou = d.has_S ? (size_t)(nb > 1 ? nb - 1 : 0) * Ec * bb * es : (size_t)(nb > 1 ? nb - 1 : 0) * bb * es;
+  L.U = a.take(ou);
+  L.V = a.take(ou);
+  L.ident = a.take(bb * sizeof(cx<double>));
+  const bool mixed = d.precision == QTX_EMU64 || d.precision == QTX_BF16X3;
+  L.ref = a.take(mixed ? 3 * Ec * bb * sizeof(cx<double>) : 0);
+  L.f32a = a.take(mixed ? Ec * bb * sizeof(cx<float>) : 0);
+  L.f32tmp = a.take(mixed ? Ec * bb * sizeof(cx<float>) + 4096 : 0);
+  L.n_dec = 9;
+  L.dec = a.take(d.leads ? (size_t)L.n_dec * Ec * bb * sizeof(cx<double>) : 0);
+  L.lead = a.take(d.leads ? 8 * Ec * bb * sizeof(cx<double>) : 0);
+  // per-energy observables: current, density, contact(2), transmission, scratch(2)
+  L.obs = a.take((size_t)Ec * (2 * nb + 8) * sizeof(double));
+  L.flags = a.take((size_t)Ec * 3 * sizeof(int) + 64);
+  L.tc_bytes = 0;
+  if (mixed) L.tc_bytes = gemm_tc_scratch_bytes((int)b, (int)b, (int)b, (int)Ec, TcConfig{5, 6});
+  L.tc_scratch = a.take(L.tc_bytes);
+  L.total = a.off;
+  return L;
+}
+
+const char* cuda_msg(cudaError_t e) { return cudaGetErrorString(e); }
+
+#define QTX_CK(call)                                                      \
+  do {                                                                    \
+    cudaError_t e_ = (call);                                              \
+    if (e_ != cudaSuccess) {                                              \
+      P->err = std::string(#call) + ": " + cuda_msg(e_);                  \
+      return QTX_ERR_CUDA;                                                \
+    }                                                                     \
+  } while (0)
+
+// ----------------------------------------------------------------------------- solver context
+template <typename T>
+struct Ctx {
+  qtx_rgf_plan_s* P;
+  cudaStream_t st;
+  int ne;                 // energies in this chunk
+  const double* E;        // device energies of this chunk
+  int* status;            // device status of this chunk [ne]
+  long bb;
+  int b;
+
+  cx<T>* blk(size_t base, long i) const {
+    return reinterpret_cast<cx<T>*>(P->ws + base) + (size_t)i * P->Ec * bb;
+  }
+  cx<T>* tmp(int k) const { return blk(P->L.tmp, k); }
+  cx<T>* g(int i) const { return blk(P->L.g, i); }
+  cx<T>* gl(int i) const { return blk(P->L.gl, i); }
+};
+
+template <typename T>
+GemmArgs<T> gargs(int M, int N, int K, const cx<T>* A, long lda, long sA, int opA, const cx<T>* B,
+                  long ldb, long sB, int opB, const cx<T>* C0, long ldc0, long sC0, cx<T>* C, long ldc,
+                  long sC, T alpha, T beta, int batch, const int* active) {
+  GemmArgs<T> g;
+  g.M = M; g.N = N; g.K = K;
+  g.A = A; g.lda = lda; g.sA = sA; g.opA = opA;
+  g.B = B; g.ldb = ldb; g.sB = sB; g.opB = opB;
+  g.C0 = C0; g.ldc0 = ldc0; g.sC0 = sC0;
+  g.C = C; g.ldc = ldc; g.sC = sC;
+  g.alpha = alpha; g.beta = beta; g.batch = batch; g.active = active;
+  return g;
+}
+
+// GEMM dispatch by the plan's precision (FP32 and FP64: SIMT; EMU64 / BF16X3: tensor-core engine).
+template <typename T>
+qtx_status gemm(qtx_rgf_plan_s* P, const GemmArgs<T>& g, cudaStream_t st, bool force_simt = false);
+
+template <>
+qtx_status gemm<float>(qtx_rgf_plan_s* P, const GemmArgs<float>& g, cudaStream_t st, bool) {
+  QTX_CK(gemm_simt<float>(g, st));
+  return QTX_OK;
+}
+template <>
+qtx_status gemm<double>(qtx_rgf_plan_s* P, const GemmArgs<double>& g, cudaStream_t st, bool force_simt) {
+  if (force_simt || P->d.precision == QTX_FP64) {
+    QTX_CK(gemm_simt<double>(g, st));
+    return QTX_OK;
+  }
+  const TcConfig cfg = P->d.precision == QTX_EMU64 ? TcConfig{5, 6} : TcConfig{2, 3};
+  QTX_CK(gemm_tc(g, cfg, P->ws + P->L.tc_scratch, P->L.tc_bytes, P->d_err_flag, st));
+  return QTX_OK;
+}
+
+// Plain (non-refined) recursive inverse of n x n blocks stored with leading dimension lda.
+// T12/T21 scratch for each recursion level is carved from `scratch` (>= 0.7 n^2 per batch entry).
+template <typename T>
+qtx_status inverse_rec(qtx_rgf_plan_s* P, cx<T>* A, long lda, long sA, int n, int batch,
+                       const int* active, int* status, cx<T>* scratch, long sScr, cudaStream_t st,
+                       bool force_simt) {
+  if (n <= kLeafMax) {
+    QTX_CK(leaf_inverse<T>(A, lda, sA, n, batch, active, status, st));
+    return QTX_OK;
+  }
+  const int h = (n + 1) / 2, r = n - h;
+  cx<T>* A11 = A;
+  cx<T>* A12 = A + h;
+  cx<T>* A21 = A + (long)h * lda;
+  cx<T>* A22 = A + (long)h * lda + h;
+  cx<T>* T12 = scratch;              // h x r, ld r
+  cx<T>* T21 = scratch + (long)h * r; // r x h, ld h
+  cx<T>* next = scratch + 2L * h * r;
+  qtx_status s;
+  if ((s = inverse_rec<T>(P, A11, lda, sA, h, batch, active, status, next, sScr, st, force_simt))) return s;
+  // T12 = X11 A12 ; T21 = A21 X11
+  if ((s = gemm<T>(P, gargs<T>(h, r, h, A11, lda, sA, OP_N, A12, lda, sA, OP_N, nullptr, 0, 0, T12, r, sScr, T(1), T(0), batch, active), st, force_simt))) return s;
+  if ((s = gemm<T>(P, gargs<T>(r, h, h, A21, lda, sA, OP_N, A11, lda, sA, OP_N, nullptr, 0, 0, T21, h, sScr, T(1), T(0), batch, active), st, force_simt))) return s;
+  // A22 <- A22 - A21 T12 (Schur complement), then invert it in place
+  if ((s = gemm<T>(P, gargs<T>(r, r, h, A21, lda, sA, OP_N, T12, r, sScr, OP_N, A22, lda, sA, A22, lda, sA, T(-1), T(1), batch, active), st, force_simt))) return s;
+  if ((s = inverse_rec<T>(P, A22, lda, sA, r, batch, active, status, next, sScr, st, force_simt))) return s;
+  // A12 <- -T12 Y ; A21 <- -Y T21 ; A11 <- X11 - T12 A21
+  if ((s = gemm<T>(P, gargs<T>(h, r, r, T12, r, sScr, OP_N, A22, lda, sA, OP_N, nullptr, 0, 0, A12, lda, sA, T(-1), T(0), batch, active), st, force_simt))) return s;
+  if ((s = gemm<T>(P, gargs<T>(r, h, r, A22, lda, sA, OP_N, T21, h, sScr, OP_N, nullptr, 0, 0, A21, lda, sA, T(-1), T(0), batch, active), st, force_simt))) return s;
+  if ((s = gemm<T>(P, gargs<T>(h, h, r, T12, r, sScr, OP_N, A21, lda, sA, OP_N, A11, lda, sA, A11, lda, sA, T(-1), T(1), batch, active), st, force_simt))) return s;
+  return QTX_OK;
+}
+
+// Block inverse used by the sweep.  FP64 / FP32: recursive inverse in the sweep precision.
+// EMU64 / BF16X3: X0 from the recursive inverse in FP32, then Newton refinement
+// X <- X + X (I - A X) with both products on the tensor-core engine (the residual I - A X is
+// formed in emulated FP64 before it is rounded for the correction product).
+template <typename T>
+qtx_status block_inverse(qtx_rgf_plan_s* P, cx<T>* A, int n, int batch, const int* active,
+                         int* status, cudaStream_t st);
+
+template <>
+qtx_status block_inverse<float>(qtx_rgf_plan_s* P, cx<float>* A, int n, int batch, const int* active,
+                                int* status, cudaStream_t st) {
+  cx<float>* scr = reinterpret_cast<cx<float>*>(P->ws + P->L.inv_tmp);
+  return inverse_rec<float>(P, A, n, (long)n * n, n, batch, active, status, scr, (long)n * n, st, true);
+}
+
+template <>
+qtx_status block_inverse<double>(qtx_rgf_plan_s* P, cx<double>* A, int n, int batch, const int* active,
+                                 int* status, cudaStream_t st) {
+  const long nn = (long)n * n;
+  if (P->d.precision == QTX_FP64) {
+    cx<double>* scr = reinterpret_cast<cx<double>*>(P->ws + P->L.inv_tmp);
+    return inverse_rec<double>(P, A, n, nn, n, batch, active, status, scr, nn, st, true);
+  }
+  // mixed: A (complex128) -> FP32 copy -> inverse -> X0 (complex128) -> refinement
+  cx<float>* A32 = reinterpret_cast<cx<float>*>(P->ws + P->L.f32a);
+  cx<float>* scr32 = reinterpret_cast<cx<float>*>(P->ws + P->L.f32tmp);
+  cx<double>* Acopy = reinterpret_cast<cx<double>*>(P->ws + P->L.ref);
+  cx<double>* R = Acopy + (size_t)P->Ec * nn;
+  cx<double>* Xn = R + (size_t)P->Ec * nn;
+  const cx<double>* I = reinterpret_cast<cx<double>*>(P->ws + P->L.ident);
+  Term<double> tA; tA.p = A; tA.s = nn; tA.alpha = 1.0;
+  Term<double> none;
+  QTX_CK((combine<double, float>(A32, nn, tA, none, none, n, batch, nullptr, 0.0, 0.0, active, st)));
+  QTX_CK((combine<double, double>(Acopy, nn, tA, none, none, n, batch, nullptr, 0.0, 0.0, active, st)));
+  qtx_status s = inverse_rec<float>(P, A32, n, nn, n, batch, active, status, scr32, nn, st, true);
+  if (s) return s;
+  Term<float> tX; tX.p = A32; tX.s = nn; tX.alpha = 1.0;
+  Term<float> none32;
+  QTX_CK((combine<float, double>(A, nn, tX, none32, none32, n, batch, nullptr, 0.0, 0.0, active, st)));
+  for (int it = 0; it < P->d.refine_max_iter; ++it) {
+    // R = I - Acopy X ; Xn = X + X R ; X <- Xn
+    if ((s = gemm<double>(P, gargs<double>(n, n, n, Acopy, n, nn, OP_N, A, n, nn, OP_N, I, n, 0, R, n, nn, -1.0, 1.0, batch, active), st))) return s;
+    if ((s = gemm<double>(P, gargs<double>(n, n, n, A, n, nn, OP_N, R, n, nn, OP_N, A, n, nn, Xn, n, nn, 1.0, 1.0, batch, active), st))) return s;
+    Term<double> tXn; tXn.p = Xn; tXn.s = nn; tXn.alpha = 1.0;
+    QTX_CK((combine<double, double>(A, nn, tXn, none, none, n, batch, nullptr, 0.0, 0.0, active, st)));
+  }
+  return QTX_OK;
+}
+
+// ----------------------------------------------------------------------------- contacts
+// Batched Sancho-Rubio decimation for one contact (FP64); result Sigma^R = H01 g_s H01^H in SR.
+template <typename T>
+qtx_status contact(const Ctx<T>& c, const cx<double>* H00, const cx<double>* H01, double eta,
+                   cx<double>* SR) {
+  qtx_rgf_plan_s* P = c.P;
+  const int b = c.b, ne = c.ne;
+  const long bb = c.bb;
+  cudaStream_t st = c.st;
+  cx<double>* D = reinterpret_cast<cx<double>*>(P->ws + P->L.dec);
+  auto buf = [&](int k) { return D + (size_t)k * P->Ec * bb; };
+  cx<double>*alpha = buf(0), *beta = buf(1), *eps = buf(2), *eps_s = buf(3), *g = buf(4), *ag = buf(5),
+  *bg = buf(6), *t1 = buf(7), *t2 = buf(8);
+  int* flags = reinterpret_cast<int*>(P->ws + P->L.flags);
+  int* active = flags;
+  int* sweeps = flags + P->Ec;
+  cx<double>* inv_scr = reinterpret_cast<cx<double>*>(P->ws + P->L.inv_tmp);
+  std::vector<cx<double>> h(bb);
+  QTX_CK(cudaMemcpyAsync(h.data(), H01, bb * sizeof(cx<double>), cudaMemcpyDeviceToHost, st));
+  QTX_CK(cudaStreamSynchronize(st));
+  double scale = 0.0;
+  for (auto& v : h) scale = std::max(scale, std::hypot(v.re, v.im));
+  const double tol = P->d.decim_tol * (scale > 0 ? scale : 1.0);
+
+  Term<double> none;
+  Term<double> t01; t01.p = H01; t01.s = 0; t01.alpha = 1.0;
+  Term<double> t01h = t01; t01h.op = OP_C;
+  Term<double> t00; t00.p = H00; t00.s = 0; t00.alpha = 1.0;
+  QTX_CK((combine<double, double>(alpha, bb, t01, none, none, b, ne, nullptr, 0, 0, nullptr, st)));
+  QTX_CK((combine<double, double>(beta, bb, t01h, none, none, b, ne, nullptr, 0, 0, nullptr, st)));
+  QTX_CK((combine<double, double>(eps, bb, t00, none, none, b, ne, nullptr, 0, 0, nullptr, st)));
+  QTX_CK((combine<double, double>(eps_s, bb, t00, none, none, b, ne, nullptr, 0, 0, nullptr, st)));
+  std::vector<int> ones(ne, 1);
+  QTX_CK(cudaMemcpyAsync(active, ones.data(), ne * sizeof(int), cudaMemcpyHostToDevice, st));
+  QTX_CK(cudaMemsetAsync(sweeps, 0, ne * sizeof(int), st));
+  std::vector<int> act(ne);
+  qtx_status s;
+  auto G = [&](const cx<double>* A, const cx<double>* B, cx<double>* C) {
+    return gemm<double>(P, gargs<double>(b, b, b, A, b, bb, OP_N, B, b, bb, OP_N, nullptr, 0, 0, C, b, bb, 1.0, 0.0, ne, active), st, true);
+  };
+  for (int it = 1; it <= P->d.decim_max_iter; ++it) {
+    Term<double> te; te.p = eps; te.s = bb; te.alpha = -1.0;
+    QTX_CK((combine<double, double>(g, bb, te, none, none, b, ne, c.E, eta, 1.0, active, st)));  // z - eps
+    if ((s = inverse_rec<double>(P, g, b, bb, b, ne, active, c.status, inv_scr, bb, st, true))) return s;
+    if ((s = G(alpha, g, ag))) return s;
+    if ((s = G(beta, g, bg))) return s;
+    if ((s = G(ag, beta, t1))) return s;   // alpha g beta
+    if ((s = G(bg, alpha, t2))) return s;  // beta g alpha
+    Term<double> ts; ts.p = eps_s; ts.s = bb; ts.alpha = 1.0;
+    Term<double> ta; ta.p = t1; ta.s = bb; ta.alpha = 1.0;
+    Term<double> tb; tb.p = t2; tb.s = bb; tb.alpha = 1.0;
+    Term<double> tep; tep.p = eps; tep.s = bb; tep.alpha = 1.0;
+    QTX_CK((combine<double, double>(eps_s, bb, ts, ta, none, b, ne, nullptr, 0, 0, active, st)));
+    QTX_CK((combine<double, double>(eps, bb, tep, ta, tb, b, ne, nullptr, 0, 0, active, st)));
+    if ((s = G(ag, alpha, t1))) return s;  // alpha g alpha
+    if ((s = G(bg, beta, t2))) return s;   // beta g beta
+    Term<double> tt1; tt1.p = t1; tt1.s = bb; tt1.alpha = 1.0;
+    Term<double> tt2; tt2.p = t2; tt2.s = bb; tt2.alpha = 1.0;
+    QTX_CK((combine<double, double>(alpha, bb, tt1, none, none, b, ne, nullptr, 0, 0, active, st)));
+    QTX_CK((combine<double, double>(beta, bb, tt2, none, none, b, ne, nullptr, 0, 0, active, st)));
+    QTX_CK(decim_converged(alpha, beta, b, tol, active, sweeps, ne, st));
+    if (it % 4 == 0 || it == P->d.decim_max_iter) {
+      QTX_CK(cudaMemcpyAsync(act.data(), active, ne * sizeof(int), cudaMemcpyDeviceToHost, st));
+      QTX_CK(cudaStreamSynchronize(st));
+      bool any = false;
+      for (int v : act) any |= (v != 0);
+      if (!any) break;
+    }
+  }
+  QTX_CK(flag_active(active, c.status, (int)QTX_ERR_NOT_CONVERGED, ne, st));
+  Term<double> tes; tes.p = eps_s; tes.s = bb; tes.alpha = -1.0;
+  QTX_CK((combine<double, double>(g, bb, tes, none, none, b, ne, c.E, eta, 1.0, nullptr, st)));  // z - eps_s
+  if ((s = inverse_rec<double>(P, g, b, bb, b, ne, nullptr, c.status, inv_scr, bb, st, true))) return s;
+  // Sigma^R = H01 g_s H01^H
+  if ((s = gemm<double>(P, gargs<double>(b, b, b, H01, b, 0, OP_N, g, b, bb, OP_N, nullptr, 0, 0, t1, b, bb, 1.0, 0.0, ne, nullptr), st, true))) return s;
+  if ((s = gemm<double>(P, gargs<double>(b, b, b, t1, b, bb, OP_N, H01, b, 0, OP_C, nullptr, 0, 0, SR, b, bb, 1.0, 0.0, ne, nullptr), st, true))) return s;
+  return QTX_OK;
+}
+
+// Copy/convert a sweep block (batch stride bb) into a complex128 output [e][slice] layout.
+template <typename T>
+qtx_status emit(qtx_rgf_plan_s* P, void* out, long nslices, long slice, int e0, const cx<T>* src,
+                int b, int ne, cudaStream_t st, const cx<T>* plus = nullptr, const cx<T>* minus_h = nullptr) {
+  if (!out) return QTX_OK;
+  const long bb = (long)b * b;
+  cx<double>* o = reinterpret_cast<cx<double>*>(out) + ((long)e0 * nslices + slice) * bb;
+  Term<T> t0; t0.p = src; t0.s = bb; t0.alpha = 1.0;
+  Term<T> t1; t1.p = plus; t1.s = bb; t1.alpha = 1.0;
+  Term<T> t2; t2.p = minus_h; t2.s = bb; t2.alpha = -1.0; t2.op = OP_C;
+  QTX_CK((combine<T, double>(o, nslices * bb, t0, t1, t2, b, ne, nullptr, 0.0, 0.0, nullptr, st)));
+  return QTX_OK;
+}
+
+template <typename T>
+qtx_status solve_chunk(qtx_rgf_plan_s* P, const qtx_rgf_inputs* in, const qtx_rgf_outputs* out,
+                       int e0, int ne, int* status, cudaStream_t st) {
+  const qtx_rgf_desc& d = P->d;
+  const int b = P->b, nb = P->nb;
+  const long bb = P->bb;
+  Ctx<T> c{P, st, ne, in->energies + e0, status, bb, b};
+  const double eta = in->eta;
+  const cx<double>* Hd = reinterpret_cast<const cx<double>*>(in->H_diag);
+  const cx<double>* Hu = reinterpret_cast<const cx<double>*>(in->H_upper);
+  const cx<double>* Sd = d.has_S ? reinterpret_cast<const cx<double>*>(in->S_diag) : nullptr;
+  const cx<double>* Su = d.has_S ? reinterpret_cast<const cx<double>*>(in->S_upper) : nullptr;
+  const cx<double>* SRd = d.has_scattering ? reinterpret_cast<const cx<double>*>(in->SigR_diag) : nullptr;
+  const cx<double>* SLd = d.has_scattering ? reinterpret_cast<const cx<double>*>(in->SigL_diag) : nullptr;
+  const long sSig = d.energy_dependent_sigma ? (long)nb * bb : 0;
+  const long sigE0 = d.energy_dependent_sigma ? (long)e0 * nb * bb : 0;
+  auto sigR = [&](int i) { return SRd ? SRd + sigE0 + (long)i * bb : nullptr; };
+  auto sigL = [&](int i) { return SLd ? SLd + sigE0 + (long)i * bb : nullptr; };
+  qtx_status s;
+  Term<T> none;
+
+  // ---- 1. contacts
+  cx<double>* LB = reinterpret_cast<cx<double>*>(P->ws + P->L.lead);
+  auto lb = [&](int k) { return LB + (size_t)k * P->Ec * bb; };
+  cx<double>*SR_L = lb(0), *Gam_L = lb(1), *SL_L = lb(2), *SG_L = lb(3);
+  cx<double>*SR_R = lb(4), *Gam_R = lb(5), *SL_R = lb(6), *SG_R = lb(7);
+  if (d.leads) {
+    if ((s = contact<T>(c, (const cx<double>*)in->lead_H00_L, (const cx<double>*)in->lead_H01_L, eta, SR_L))) return s;
+    if ((s = contact<T>(c, (const cx<double>*)in->lead_H00_R, (const cx<double>*)in->lead_H01_R, eta, SR_R))) return s;
+    QTX_CK(lead_sigmas(SR_L, Gam_L, SL_L, SG_L, c.E, in->mu_L, in->kT, b, ne, st));
+    QTX_CK(lead_sigmas(SR_R, Gam_R, SL_R, SG_R, c.E, in->mu_R, in->kT, b, ne, st));
+  }
+
+  // ---- off-diagonal blocks of M
+  cx<T>* Ub = reinterpret_cast<cx<T>*>(P->ws + P->L.U);
+  cx<T>* Vb = reinterpret_cast<cx<T>*>(P->ws + P->L.V);
+  const long sUV = d.has_S ? bb : 0;
+  auto U = [&](int i) { return Ub + (size_t)i * (d.has_S ? P->Ec * bb : bb); };
+  auto V = [&](int i) { return Vb + (size_t)i * (d.has_S ? P->Ec * bb : bb); };
+  for (int i = 0; i + 1 < nb; ++i) {
+    if (d.has_S) QTX_CK(assemble_offdiag<T>(U(i), V(i), Hu + (long)i * bb, Su + (long)i * bb, c.E, eta, b, ne, st));
+    else QTX_CK(assemble_offdiag<T>(U(i), V(i), Hu + (long)i * bb, nullptr, nullptr, 0.0, b, 1, st));
+  }
+
+  // ---- 2. forward sweep
+  for (int i = 0; i < nb; ++i) {
+    cx<T>* gi = c.g(i);
+    const cx<double>* lead = nullptr;
+    if (d.leads && i == 0) lead = SR_L;
+    else if (d.leads && i == nb - 1) lead = SR_R;
+    QTX_CK(assemble_diag<T>(gi, Hd + (long)i * bb, Sd ? Sd + (long)i * bb : nullptr, sigR(i), sSig, lead, bb, c.E, eta, b, ne, st));
+    if (d.leads && nb == 1) {  // one slice touches both contacts
+      Term<T> tg; tg.p = gi; tg.s = bb; tg.alpha = 1.0;
+      QTX_CK((combine<T, T>(c.tmp(0), bb, tg, none, none, b, ne, nullptr, 0, 0, nullptr, st)));
+      QTX_CK(axpby_from64<T>(c.tmp(1), bb, SR_R, bb, -1.0, nullptr, 0, 0.0, b, ne, st));
+      Term<T> t0; t0.p = c.tmp(0); t0.s = bb; t0.alpha = 1.0;
+      Term<T> t1; t1.p = c.tmp(1); t1.s = bb; t1.alpha = 1.0;
+      QTX_CK((combine<T, T>(gi, bb, t0, t1, none, b, ne, nullptr, 0, 0, nullptr, st)));
+    }
+    if (i > 0) {
+      cx<T>* Tm = c.tmp(0);
+      if ((s = gemm<T>(P, gargs<T>(b, b, b, c.g(i - 1), b, bb, OP_N, U(i - 1), b, sUV, OP_N, nullptr, 0, 0, Tm, b, bb, T(1), T(0), ne, nullptr), st))) return s;
+      if ((s = gemm<T>(P, gargs<T>(b, b, b, V(i - 1), b, sUV, OP_N, Tm, b, bb, OP_N, gi, b, bb, gi, b, bb, T(-1), T(1), ne, nullptr), st))) return s;
+    }
+    if ((s = block_inverse<T>(P, gi, b, ne, nullptr, status, st))) return s;
+    // Sigma^<_ii (+ contacts), then the left-connected lesser function
+    cx<T>* SLi = c.tmp(1);
+    const cx<double>* sl = sigL(i);
+    const cx<double>* lsl = nullptr;
+    if (d.leads && i == 0) lsl = SL_L;
+    else if (d.leads && i == nb - 1) lsl = SL_R;
+    if (sl) QTX_CK(axpby_from64<T>(SLi, bb, sl, sSig, 1.0, lsl, bb, 1.0, b, ne, st));
+    else if (lsl) QTX_CK(axpby_from64<T>(SLi, bb, lsl, bb, 1.0, nullptr, 0, 0.0, b, ne, st));
+    else QTX_CK(cudaMemsetAsync(SLi, 0, (size_t)ne * bb * sizeof(cx<T>), st));
+    if (d.leads && nb == 1) {
+      QTX_CK(axpby_from64<T>(c.tmp(2), bb, SL_R, bb, 1.0, nullptr, 0, 0.0, b, ne, st));
+      Term<T> t0; t0.p = SLi; t0.s = bb; t0.alpha = 1.0;
+      Term<T> t1; t1.p = c.tmp(2); t1.s = bb; t1.alpha = 1.0;
+      QTX_CK((combine<T, T>(SLi, bb, t0, t1, none, b, ne, nullptr, 0, 0, nullptr, st)));
+    }
+    if (i > 0) {
+      cx<T>* X = c.tmp(0);
+      if ((s = gemm<T>(P, gargs<T>(b, b, b, V(i - 1), b, sUV, OP_N, c.gl(i - 1), b, bb, OP_N, nullptr, 0, 0, X, b, bb, T(1), T(0), ne, nullptr), st))) return s;
+      if ((s = gemm<T>(P, gargs<T>(b, b, b, X, b, bb, OP_N, V(i - 1), b, sUV, OP_C, SLi, b, bb, SLi, b, bb, T(1), T(1), ne, nullptr), st))) return s;
+    }
+    cx<T>* Y = c.tmp(0);
+    if ((s = gemm<T>(P, gargs<T>(b, b, b, gi, b, bb, OP_N, SLi, b, bb, OP_N, nullptr, 0, 0, Y, b, bb, T(1), T(0), ne, nullptr), st))) return s;
+    if ((s = gemm<T>(P, gargs<T>(b, b, b, Y, b, bb, OP_N, gi, b, bb, OP_C, nullptr, 0, 0, c.gl(i), b, bb, T(1), T(0), ne, nullptr), st))) return s;
+  }
+
+  // ---- 3. backward sweep.  With P = g_i U_i, Z = V_i g_i, Q = V_i g^<_i:
+  //   G_{i+1,i} = -G_{i+1,i+1} Z,  G_{i,i+1} = -P G_{i+1,i+1},  G_ii = g_i - P G_{i+1,i}
+  //   K = P G_{i+1,i+1} Q = -G_{i,i+1} Q
+  //   G^<_ii = g^<_i + (P G^<_{i+1,i+1}) P^H + K - K^H
+  //   G^<_{i,i+1} = -P G^<_{i+1,i+1} + (G_{i+1,i+1} Q)^H     [= -P G^< - g^< V^H G^A]
+  double* obs = reinterpret_cast<double*>(P->ws + P->L.obs);
+  const int ncur = nb > 1 ? nb - 1 : 1;
+  double* cur = obs;                           // [ne][nb-1]
+  double* den = cur + (size_t)P->Ec * ncur;    // [ne][nb]
+  double* con = den + (size_t)P->Ec * nb;      // [ne][2]
+  double* tra = con + (size_t)P->Ec * 2;       // [ne]
+  const unsigned m = d.outputs;
+  auto want = [&](unsigned bit, const void* p) { return (m & bit) && p; };
+  {
+    const int i = nb - 1;
+    if (want(QTX_OUT_GR_DIAG, out->GR_diag) && (s = emit<T>(P, out->GR_diag, nb, i, e0, c.g(i), b, ne, st))) return s;
+    if (want(QTX_OUT_GL_DIAG, out->GL_diag) && (s = emit<T>(P, out->GL_diag, nb, i, e0, c.gl(i), b, ne, st))) return s;
+    if (want(QTX_OUT_GG_DIAG, out->GG_diag) && (s = emit<T>(P, out->GG_diag, nb, i, e0, c.gl(i), b, ne, st, c.g(i), c.g(i)))) return s;
+    QTX_CK(obs_density<T>(den + i, nb, c.gl(i), bb, b, ne, st));
+    if (d.leads) {  // right contact current on slice N_B-1:  G^> = G^< + G^R - G^A
+      cx<T>* GG = c.tmp(0);
+      Term<T> t0; t0.p = c.gl(i); t0.s = bb; t0.alpha = 1.0;
+      Term<T> t1; t1.p = c.g(i); t1.s = bb; t1.alpha = 1.0;
+      Term<T> t2; t2.p = c.g(i); t2.s = bb; t2.alpha = -1.0; t2.op = OP_C;
+      QTX_CK((combine<T, T>(GG, bb, t0, t1, t2, b, ne, nullptr, 0, 0, nullptr, st)));
+      QTX_CK(obs_trace2<T>(con + 1, 2, SL_R, bb, GG, bb, SG_R, bb, c.gl(i), bb, b, ne, st));
+    }
+  }
+  for (int i = nb - 2; i >= 0; --i) {
+    cx<T>* GRn = c.g(i + 1);
+    cx<T>* GLn = c.gl(i + 1);
+    cx<T>* Pm = c.tmp(2);
+    cx<T>* Z = c.tmp(3);
+    cx<T>* GRl = c.tmp(4);
+    cx<T>* GRu = c.tmp(5);
+    cx<T>* Q = c.tmp(6);
+    cx<T>* K = c.tmp(7);
+    cx<T>* PGL = c.tmp(8);
+    cx<T>* X2 = c.tmp(9);
+    cx<T>* GLu = c.tmp(10);
+    cx<T>* gi = c.g(i);
+    cx<T>* gli = c.gl(i);
+    auto MM = [&](const cx<T>* A, long sA_, int opA, const cx<T>* B, long sB_, int opB, const cx<T>* C0, cx<T>* C, T al, T be) {
+      return gemm<T>(P, gargs<T>(b, b, b, A, b, sA_, opA, B, b, sB_, opB, C0, b, bb, C, b, bb, al, be, ne, nullptr), st);
+    };
+    if ((s = MM(gi, bb, OP_N, U(i), sUV, OP_N, nullptr, Pm, T(1), T(0)))) return s;
+    if ((s = MM(V(i), sUV, OP_N, gi, bb, OP_N, nullptr, Z, T(1), T(0)))) return s;
+    if ((s = MM(GRn, bb, OP_N, Z, bb, OP_N, nullptr, GRl, T(-1), T(0)))) return s;
+    if ((s = MM(Pm, bb, OP_N, GRn, bb, OP_N, nullptr, GRu, T(-1), T(0)))) return s;
+    if ((s = MM(Pm, bb, OP_N, GRl, bb, OP_N, gi, gi, T(-1), T(1)))) return s;   // g_i <- G_ii
+    if ((s = MM(V(i), sUV, OP_N, gli, bb, OP_N, nullptr, Q, T(1), T(0)))) return s;
+    if ((s = MM(GRu, bb, OP_N, Q, bb, OP_N, nullptr, K, T(-1), T(0)))) return s;
+    if ((s = MM(Pm, bb, OP_N, GLn, bb, OP_N, nullptr, PGL, T(1), T(0)))) return s;
+    if ((s = MM(PGL, bb, OP_N, Pm, bb, OP_C, gli, gli, T(1), T(1)))) return s;   // g^<_i + PGL P^H
+    if ((s = MM(GRn, bb, OP_N, Q, bb, OP_N, nullptr, X2, T(1), T(0)))) return s;
+    {
+      Term<T> t0; t0.p = gli; t0.s = bb; t0.alpha = 1.0;
+      Term<T> t1; t1.p = K; t1.s = bb; t1.alpha = 1.0;
+      Term<T> t2; t2.p = K; t2.s = bb; t2.alpha = -1.0; t2.op = OP_C;
+      QTX_CK((combine<T, T>(gli, bb, t0, t1, t2, b, ne, nullptr, 0, 0, nullptr, st)));   // G^<_ii
+      Term<T> u0; u0.p = PGL; u0.s = bb; u0.alpha = -1.0;
+      Term<T> u1; u1.p = X2; u1.s = bb; u1.alpha = 1.0; u1.op = OP_C;
+      QTX_CK((combine<T, T>(GLu, bb, u0, u1, none, b, ne, nullptr, 0, 0, nullptr, st)));  // G^<_{i,i+1}
+    }
+    if (want(QTX_OUT_GR_DIAG, out->GR_diag) && (s = emit<T>(P, out->GR_diag, nb, i, e0, gi, b, ne, st))) return s;
+    if (want(QTX_OUT_GR_UPPER, out->GR_upper) && (s = emit<T>(P, out->GR_upper, nb - 1, i, e0, GRu, b, ne, st))) return s;
+    if (want(QTX_OUT_GR_LOWER, out->GR_lower) && (s = emit<T>(P, out->GR_lower, nb - 1, i, e0, GRl, b, ne, st))) return s;
+    if (want(QTX_OUT_GL_DIAG, out->GL_diag) && (s = emit<T>(P, out->GL_diag, nb, i, e0, gli, b, ne, st))) return s;
+    if (want(QTX_OUT_GL_UPPER, out->GL_upper) && (s = emit<T>(P, out->GL_upper, nb - 1, i, e0, GLu, b, ne, st))) return s;
+    if (want(QTX_OUT_GG_DIAG, out->GG_diag) && (s = emit<T>(P, out->GG_diag, nb, i, e0, gli, b, ne, st, gi, gi))) return s;
+    if (want(QTX_OUT_GG_UPPER, out->GG_upper) && (s = emit<T>(P, out->GG_upper, nb - 1, i, e0, GLu, b, ne, st, GRu, GRl))) return s;
+    QTX_CK(obs_current<T>(cur + i, ncur, Hu + (long)i * bb, Su ? Su + (long)i * bb : nullptr, GLu, bb, c.E, b, ne, st));
+    QTX_CK(obs_density<T>(den + i, nb, gli, bb, b, ne, st));
+  }
+  if (d.leads) {  // left contact current and transmission on slice 0
+    cx<T>* GG = c.tmp(0);
+    Term<T> t0; t0.p = c.gl(0); t0.s = bb; t0.alpha = 1.0;
+    Term<T> t1; t1.p = c.g(0); t1.s = bb; t1.alpha = 1.0;
+    Term<T> t2; t2.p = c.g(0); t2.s = bb; t2.alpha = -1.0; t2.op = OP_C;
+    QTX_CK((combine<T, T>(GG, bb, t0, t1, t2, b, ne, nullptr, 0, 0, nullptr, st)));
+    QTX_CK(obs_trace2<T>(con, 2, SL_L, bb, GG, bb, SG_L, bb, c.gl(0), bb, b, ne, st));
+    // T = Tr[Gam A_00] - Tr[Gam G Gam G^H] with A = i (G - G^H): Tr[Gam A] = -Im Tr[Gam (G - G^H)],
+    // and Tr[Gam G Gam G^H] = sum_jk (Gam G)_jk conj((G Gam)_jk) since Gam is Hermitian (FP64).
+    cx<double>* D = reinterpret_cast<cx<double>*>(P->ws + P->L.dec);
+    cx<double>* G64 = D;
+    cx<double>* X1 = D + (size_t)P->Ec * bb;
+    cx<double>* X2 = X1 + (size_t)P->Ec * bb;
+    cx<double>* Dm = X2 + (size_t)P->Ec * bb;
+    Term<T> tg; tg.p = c.g(0); tg.s = bb; tg.alpha = 1.0;
+    QTX_CK((combine<T, double>(G64, bb, tg, none, none, b, ne, nullptr, 0, 0, nullptr, st)));
+    Term<double> a0; a0.p = G64; a0.s = bb; a0.alpha = 1.0;
+    Term<double> a1; a1.p = G64; a1.s = bb; a1.alpha = -1.0; a1.op = OP_C;
+    Term<double> nn;
+    QTX_CK((combine<double, double>(Dm, bb, a0, a1, nn, b, ne, nullptr, 0, 0, nullptr, st)));
+    QTX_CK(obs_trace2<double>(tra, 1, Gam_L, bb, Dm, bb, nullptr, 0, nullptr, 0, b, ne, st, 1, -1.0));
+    if ((s = gemm<double>(P, gargs<double>(b, b, b, Gam_L, b, bb, OP_N, G64, b, bb, OP_N, nullptr, 0, 0, X1, b, bb, 1.0, 0.0, ne, nullptr), st, true))) return s;
+    if ((s = gemm<double>(P, gargs<double>(b, b, b, G64, b, bb, OP_N, Gam_L, b, bb, OP_N, nullptr, 0, 0, X2, b, bb, 1.0, 0.0, ne, nullptr), st, true))) return s;
+    QTX_CK(obs_frob_dot(tra, 1, X1, bb, X2, bb, -1.0, b, ne, st));
+  }
+  // ---- 4. outputs of the per-energy observables and their integrals
+  const int nbm1 = nb - 1;
+  if (want(QTX_OUT_CURRENT, out->current) && nbm1 > 0)
+    QTX_CK(cudaMemcpyAsync(out->current + (size_t)e0 * nbm1, cur, (size_t)ne * nbm1 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  if (want(QTX_OUT_DENSITY, out->density))
+    QTX_CK(cudaMemcpyAsync(out->density + (size_t)e0 * nb, den, (size_t)ne * nb * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  if (d.leads && want(QTX_OUT_CONTACT, out->contact))
+    QTX_CK(cudaMemcpyAsync(out->contact + (size_t)e0 * 2, con, (size_t)ne * 2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  if (d.leads && want(QTX_OUT_TRANSMISSION, out->transmission))
+    QTX_CK(cudaMemcpyAsync(out->transmission + e0, tra, (size_t)ne * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  if (m & QTX_OUT_INTEGRALS) {
+    if (out->current_int && nbm1 > 0)
+      QTX_CK(integrate_add(out->current_int, cur, nbm1, nbm1, in->weights, in->energies, e0, in->n_energies, ne, 1.0, st));
+    if (out->density_int)
+      QTX_CK(integrate_add(out->density_int, den, nb, nb, in->weights, in->energies, e0, in->n_energies, ne, 1.0 / (2.0 * 3.14159265358979323846), st));
+  }
+  return QTX_OK;
+}
+
+template <typename T>
+qtx_status solve_all(qtx_rgf_plan_s* P, const qtx_rgf_inputs* in, const qtx_rgf_outputs* out, cudaStream_t st) {
+  const int nb = P->nb;
+  const unsigned m = P->d.outputs;
+  if ((m & QTX_OUT_INTEGRALS) && out->current_int && nb > 1)
+    QTX_CK(cudaMemsetAsync(out->current_int, 0, (size_t)(nb - 1) * sizeof(double), st));
+  if ((m & QTX_OUT_INTEGRALS) && out->density_int)
+    QTX_CK(cudaMemsetAsync(out->density_int, 0, (size_t)nb * sizeof(double), st));
+  int* chunk_status = reinterpret_cast<int*>(P->ws + P->L.flags) + 2 * P->Ec;
+  P->status_host.assign(in->n_energies, 0);
+  for (int e0 = 0; e0 < in->n_energies; e0 += P->Ec) {
+    const int ne = std::min(P->Ec, in->n_energies - e0);
+    int* status = out->status_per_energy ? out->status_per_energy + e0 : chunk_status;
+    QTX_CK(cudaMemsetAsync(status, 0, (size_t)ne * sizeof(int), st));
+    qtx_status s = solve_chunk<T>(P, in, out, e0, ne, status, st);
+    if (s) return s;
+    if (!out->status_per_energy) {
+      // keep the worst chunk status without a host sync: fold into the error flag word
+      QTX_CK(cudaMemcpyAsync(P->h_status, status, sizeof(int) * ne, cudaMemcpyDeviceToHost, st));
+      QTX_CK(cudaStreamSynchronize(st));
+      for (int k = 0; k < ne; ++k) P->worst = std::max(P->worst, P->h_status[k]);
+    }
+  }
+  return QTX_OK;
+}
+
+qtx_status validate(const qtx_rgf_desc* d, std::string& err) {
+  if (!d) { err = "desc is NULL"; return QTX_ERR_INVALID_ARG; }
+  if (d->n_blocks < 1) { err = "n_blocks must be >= 1"; return QTX_ERR_INVALID_ARG; }
+  if (d->block_size < 1 || d->block_size > 1024) { err = "block_size must be in [1, 1024]"; return QTX_ERR_INVALID_ARG; }
+  if (d->max_energies_in_flight < 1) { err = "max_energies_in_flight must be >= 1"; return QTX_ERR_INVALID_ARG; }
+  if (d->precision < QTX_FP64 || d->precision > QTX_EMU64) { err = "unknown precision"; return QTX_ERR_INVALID_ARG; }
+  if (d->leads && (d->decim_max_iter < 1 || !(d->decim_tol > 0))) { err = "leads need decim_max_iter >= 1 and decim_tol > 0"; return QTX_ERR_INVALID_ARG; }
+  if (d->refine_max_iter < 0) { err = "refine_max_iter must be >= 0"; return QTX_ERR_INVALID_ARG; }
+  if ((d->precision == QTX_EMU64 || d->precision == QTX_BF16X3) && !tc_available()) {
+    err = "tensor-core engine not available in this build";
+    return QTX_ERR_UNSUPPORTED;
+  }
+  return QTX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+qtx_status qtx_rgf_plan_create(const qtx_rgf_desc* desc, qtx_rgf_plan* out) {
+  if (!out) { g_create_error = "out is NULL"; return QTX_ERR_INVALID_ARG; }
+  *out = nullptr;
+  std::string err;
+  qtx_status s = validate(desc, err);
+  if (s) { g_create_error = err; return s; }
+  auto* P = new qtx_rgf_plan_s();
+  P->d = *desc;
+  P->b = desc->block_size;
+  P->nb = desc->n_blocks;
+  P->Ec = desc->max_energies_in_flight;
+  P->bb = (long)P->b * P->b;
+  P->esz = desc->precision == QTX_FP32 ? sizeof(cx<float>) : sizeof(cx<double>);
+  P->L = make_layout(*desc);
+  cudaError_t e = cudaMalloc(&P->ws, P->L.total);
+  if (e != cudaSuccess) {
+    g_create_error = std::string("workspace cudaMalloc(") + std::to_string(P->L.total) + "): " + cudaGetErrorString(e);
+    cudaGetLastError();
+    delete P;
+    return QTX_ERR_OOM;
+  }
+  e = cudaMalloc(&P->d_err_flag, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(P->d_err_flag, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMallocHost(&P->h_status, sizeof(int) * P->Ec);
+  // identity block for the refinement residual
+  if (e == cudaSuccess) {
+    std::vector<cx<double>> I((size_t)P->bb, mk<double>(0, 0));
+    for (int i = 0; i < P->b; ++i) I[(size_t)i * P->b + i] = mk<double>(1, 0);
+    e = cudaMemcpy(P->ws + P->L.ident, I.data(), I.size() * sizeof(cx<double>), cudaMemcpyHostToDevice);
+  }
+  if (e != cudaSuccess) {
+    g_create_error = std::string("plan setup: ") + cudaGetErrorString(e);
+    cudaFree(P->ws);
+    if (P->d_err_flag) cudaFree(P->d_err_flag);
+    if (P->h_status) cudaFreeHost(P->h_status);
+    delete P;
+    return QTX_ERR_CUDA;
+  }
+  *out = P;
+  return QTX_OK;
+}
+
+qtx_status qtx_rgf_solve(qtx_rgf_plan P, const qtx_rgf_inputs* in, const qtx_rgf_outputs* out, void* stream) {
+  if (!P) return QTX_ERR_INVALID_ARG;
+  if (!in || !out) { P->err = "inputs/outputs NULL"; return QTX_ERR_INVALID_ARG; }
+  if (in->n_energies < 1 || !in->energies) { P->err = "need n_energies >= 1 and an energies array"; return QTX_ERR_INVALID_ARG; }
+  if (!in->H_diag || (P->nb > 1 && !in->H_upper)) { P->err = "H_diag / H_upper missing"; return QTX_ERR_INVALID_ARG; }
+  if (P->d.has_S && (!in->S_diag || (P->nb > 1 && !in->S_upper))) { P->err = "has_S set but S pointers missing"; return QTX_ERR_INVALID_ARG; }
+  if (P->d.has_scattering && (!in->SigR_diag || !in->SigL_diag)) { P->err = "has_scattering set but Sigma pointers missing"; return QTX_ERR_INVALID_ARG; }
+  if (P->d.leads && (!in->lead_H00_L || !in->lead_H01_L || !in->lead_H00_R || !in->lead_H01_R)) { P->err = "leads set but lead blocks missing"; return QTX_ERR_INVALID_ARG; }
+  if (P->d.leads && !(in->kT > 0)) { P->err = "leads need kT > 0"; return QTX_ERR_INVALID_ARG; }
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  P->last = st;
+  P->worst = 0;
+  qtx_status s = P->d.precision == QTX_FP32 ? solve_all<float>(P, in, out, st) : solve_all<double>(P, in, out, st);
+  if (s == QTX_OK) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) { P->err = cudaGetErrorString(e); return QTX_ERR_CUDA; }
+  }
+  P->out_status = out->status_per_energy;
+  P->out_status_n = in->n_energies;
+  return s;
+}
+
+qtx_status qtx_rgf_status(qtx_rgf_plan P) {
+  if (!P) return QTX_ERR_INVALID_ARG;
+  cudaError_t e = cudaStreamSynchronize(P->last);
+  if (e != cudaSuccess) { P->err = cudaGetErrorString(e); return QTX_ERR_CUDA; }
+  int flag = 0;
+  e = cudaMemcpy(&flag, P->d_err_flag, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) { P->err = cudaGetErrorString(e); return QTX_ERR_CUDA; }
+  if (flag) { P->err = "tensor-core engine: bounded wait expired"; return QTX_ERR_TIMEOUT; }
+  if (P->out_status) {
+    P->status_host.assign(P->out_status_n, 0);
+    e = cudaMemcpy(P->status_host.data(), P->out_status, sizeof(int) * P->out_status_n, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) { P->err = cudaGetErrorString(e); return QTX_ERR_CUDA; }
+    for (int v : P->status_host) P->worst = std::max(P->worst, v);
+  }
+  return (qtx_status)P->worst;
+}
+
+qtx_status qtx_rgf_destroy(qtx_rgf_plan P) {
+  if (!P) return QTX_OK;
+  if (P->ws) cudaFree(P->ws);
+  if (P->d_err_flag) cudaFree(P->d_err_flag);
+  if (P->h_status) cudaFreeHost(P->h_status);
+  delete P;
+  return QTX_OK;
+}
+
+const char* qtx_rgf_last_error(qtx_rgf_plan P) { return P ? P->err.c_str() : g_create_error.c_str(); }
+
+size_t qtx_rgf_footprint(const qtx_rgf_desc* desc) {
+  std::string err;
+  if (validate(desc, err) && validate(desc, err) != QTX_ERR_UNSUPPORTED) return 0;
+  return make_layout(*desc).total;
+}
+
+const char* qtx_rgf_version(void) { return "qtx-rgf 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,591 @@
+// SIMT kernels of the RGF library (sm_103a): batched complex GEMM, batched leaf inverse by
+// Gauss-Jordan elimination with partial pivoting, elementwise block combinations, assembly of
+// the block rows of M, and the FP64 observable reductions of Sec. II-B.
+#include <cmath>
+
+#include "kernels.cuh"
+
+namespace qtx {
+
+// ============================================================================ batched GEMM
+// Tile BM x BN of C per CTA, K staged through shared memory BK at a time; each thread owns a
+// TM x TN sub-grid interleaved with stride (BM/TM, BN/TN) so smem reads of a warp are contiguous.
+template <typename T, int BM, int BN, int BK, int TM, int TN>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+    k_gemm(GemmArgs<T> g) {
+  constexpr int TX = BN / TN, TY = BM / TM, NT = TX * TY;
+  const int e = blockIdx.z;
+  if (g.active && !g.active[e]) return;
+  __shared__ cx<T> As[BK][BM + 1];
+  __shared__ cx<T> Bs[BK][BN + 1];
+  const int tid = threadIdx.x;
+  const int tx = tid % TX, ty = tid / TX;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const cx<T>* A = g.A + (long)e * g.sA;
+  const cx<T>* B = g.B + (long)e * g.sB;
+  cx<T> acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = mk<T>(0, 0);
+
+  for (int k0 = 0; k0 < g.K; k0 += BK) {
+    for (int idx = tid; idx < BM * BK; idx += NT) {
+      int mm, kk;
+      if (g.opA == OP_N) { kk = idx % BK; mm = idx / BK; }
+      else { mm = idx % BM; kk = idx / BM; }
+      const int m = m0 + mm, k = k0 + kk;
+      cx<T> v = mk<T>(0, 0);
+      if (m < g.M && k < g.K) v = (g.opA == OP_N) ? A[(long)m * g.lda + k] : conj(A[(long)k * g.lda + m]);
+      As[kk][mm] = v;
+    }
+    for (int idx = tid; idx < BK * BN; idx += NT) {
+      int kk, nn;
+      if (g.opB == OP_N) { nn = idx % BN; kk = idx / BN; }
+      else { kk = idx % BK; nn = idx / BK; }
+      const int k = k0 + kk, n = n0 + nn;
+      cx<T> v = mk<T>(0, 0);
+      if (k < g.K && n < g.N) v = (g.opB == OP_N) ? B[(long)k * g.ldb + n] : conj(B[(long)n * g.ldb + k]);
+      Bs[kk][nn] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      cx<T> a[TM], bb[TN];
+#pragma unroll
+      for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + i * TY];
+#pragma unroll
+      for (int j = 0; j < TN; ++j) bb[j] = Bs[kk][tx + j * TX];
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) cfma(acc[i][j], a[i], bb[j]);
+    }
+    __syncthreads();
+  }
+  cx<T>* C = g.C + (long)e * g.sC;
+  const cx<T>* C0 = g.C0 ? g.C0 + (long)e * g.sC0 : nullptr;
+#pragma unroll
+  for (int i = 0; i < TM; ++i) {
+    const int m = m0 + ty + i * TY;
+    if (m >= g.M) continue;
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      const int n = n0 + tx + j * TX;
+      if (n >= g.N) continue;
+      cx<T> r = g.alpha * acc[i][j];
+      if (C0 && g.beta != T(0)) r = r + g.beta * C0[(long)m * g.ldc0 + n];
+      C[(long)m * g.ldc + n] = r;
+    }
+  }
+}
+
+template <typename T, int BM, int BN, int BK, int TM, int TN>
+static cudaError_t launch_gemm(const GemmArgs<T>& g, cudaStream_t st) {
+  dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, g.batch);
+  k_gemm<T, BM, BN, BK, TM, TN><<<grid, (BM / TM) * (BN / TN), 0, st>>>(g);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t gemm_simt(const GemmArgs<T>& g, cudaStream_t st) {
+  if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return cudaSuccess;
+  if (g.M <= 32 && g.N <= 32) return launch_gemm<T, 32, 32, 16, 2, 2>(g, st);
+  if (sizeof(T) == 4 && g.M >= 128 && g.N >= 128) return launch_gemm<T, 128, 128, 8, 8, 8>(g, st);
+  return launch_gemm<T, 64, 64, 16, 4, 4>(g, st);
+}
+template cudaError_t gemm_simt<double>(const GemmArgs<double>&, cudaStream_t);
+template cudaError_t gemm_simt<float>(const GemmArgs<float>&, cudaStream_t);
+
+// ============================================================================ leaf inverse
+// In-place Gauss-Jordan inverse with partial row pivoting (pivot = first row of largest
+// |Re|+|Im| in the column); the row interchanges are undone as column interchanges at the end.
+template <typename T>
+__global__ void __launch_bounds__(256) k_leaf_inverse(cx<T>* Ag, long lda, long sA, int n,
+                                                      const int* active, int* status) {
+  extern __shared__ unsigned char smem_raw[];
+  const int e = blockIdx.x;
+  if (active && !active[e]) return;
+  const int ld = n + 1;
+  cx<T>* a = reinterpret_cast<cx<T>*>(smem_raw);
+  cx<T>* colk = a + n * ld;
+  int* piv = reinterpret_cast<int*>(colk + n);
+  __shared__ int s_p, s_bad;
+  __shared__ cx<T> s_r;
+  cx<T>* A = Ag + (long)e * sA;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int idx = tid; idx < n * n; idx += nt) {
+    const int i = idx / n, j = idx % n;
+    a[i * ld + j] = A[(long)i * lda + j];
+  }
+  if (tid == 0) s_bad = 0;
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    if (tid < 32) {  // pivot search by warp 0: largest |Re|+|Im| in column k, first on ties
+      T best = T(-1);
+      int bi = k;
+      for (int i = k + tid; i < n; i += 32) {
+        const T v = cabs1(a[i * ld + k]);
+        if (v > best) { best = v; bi = i; }
+      }
+      for (int off = 16; off > 0; off >>= 1) {
+        const T ov = __shfl_down_sync(0xffffffffu, best, off);
+        const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+        if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+      }
+      if (tid == 0) {
+        s_p = bi;
+        piv[k] = bi;
+        if (!(best > T(0)) || !isfinite(best)) s_bad = 1;
+      }
+    }
+    __syncthreads();
+    if (s_bad) break;
+    const int p = s_p;
+    if (p != k)
+      for (int j = tid; j < n; j += nt) {
+        const cx<T> t = a[k * ld + j];
+        a[k * ld + j] = a[p * ld + j];
+        a[p * ld + j] = t;
+      }
+    __syncthreads();
+    if (tid == 0) s_r = crecip(a[k * ld + k]);
+    __syncthreads();
+    const cx<T> r = s_r;
+    for (int j = tid; j < n; j += nt) a[k * ld + j] = (j == k) ? r : a[k * ld + j] * r;
+    for (int i = tid; i < n; i += nt) colk[i] = a[i * ld + k];
+    __syncthreads();
+    for (int idx = tid; idx < n * n; idx += nt) {
+      const int i = idx / n, j = idx % n;
+      if (i == k) continue;
+      const cx<T> f = colk[i];
+      if (j == k) a[i * ld + j] = mk<T>(-(f.re * r.re - f.im * r.im), -(f.re * r.im + f.im * r.re));
+      else {
+        cx<T> v = a[i * ld + j];
+        const cx<T> w = a[k * ld + j];
+        v.re = fma(-f.re, w.re, v.re);
+        v.re = fma(f.im, w.im, v.re);
+        v.im = fma(-f.re, w.im, v.im);
+        v.im = fma(-f.im, w.re, v.im);
+        a[i * ld + j] = v;
+      }
+    }
+    __syncthreads();
+  }
+  if (s_bad) {
+    if (tid == 0 && status) atomicCAS(status + e, 0, (int)QTX_ERR_SINGULAR);
+    return;
+  }
+  for (int k = n - 1; k >= 0; --k) {
+    const int p = piv[k];
+    if (p != k)
+      for (int i = tid; i < n; i += nt) {
+        const cx<T> t = a[i * ld + k];
+        a[i * ld + k] = a[i * ld + p];
+        a[i * ld + p] = t;
+      }
+    __syncthreads();
+  }
+  for (int idx = tid; idx < n * n; idx += nt) {
+    const int i = idx / n, j = idx % n;
+    A[(long)i * lda + j] = a[i * ld + j];
+  }
+}
+
+template <typename T>
+cudaError_t leaf_inverse(cx<T>* A, long lda, long sA, int n, int batch, const int* active,
+                         int* status, cudaStream_t st) {
+  if (n <= 0 || n > kLeafMax) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)n * (n + 1) * sizeof(cx<T>) + n * sizeof(cx<T>) + n * sizeof(int) + 16;
+  static bool attr_set[2] = {false, false};
+  const int which = sizeof(T) == 8 ? 0 : 1;
+  if (!attr_set[which]) {
+    cudaError_t err = cudaFuncSetAttribute(k_leaf_inverse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)((size_t)kLeafMax * (kLeafMax + 2) * sizeof(cx<T>) + 1024));
+    if (err != cudaSuccess) return err;
+    attr_set[which] = true;
+  }
+  const int threads = n <= 16 ? 64 : (n <= 32 ? 128 : 256);
+  k_leaf_inverse<T><<<batch, threads, smem, st>>>(A, lda, sA, n, active, status);
+  return cudaGetLastError();
+}
+template cudaError_t leaf_inverse<double>(cx<double>*, long, long, int, int, const int*, int*, cudaStream_t);
+template cudaError_t leaf_inverse<float>(cx<float>*, long, long, int, int, const int*, int*, cudaStream_t);
+
+// ============================================================================ elementwise
+// 32 x 32 output tiles; conjugate-transposed terms are staged through shared memory so that both
+// the read and the write stay coalesced.
+template <typename Tin, typename Tout>
+__global__ void __launch_bounds__(256) k_combine(cx<Tout>* out, long sOut, Term<Tin> t0, Term<Tin> t1,
+                                                 Term<Tin> t2, int b, const double* E, double eta,
+                                                 double diag_coef, const int* active) {
+  const int e = blockIdx.z;
+  if (active && !active[e]) return;
+  __shared__ cx<Tin> tile[32][33];
+  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;  // 32 x 8
+  double accr[4] = {0, 0, 0, 0}, acci[4] = {0, 0, 0, 0};
+  const Term<Tin> ts[3] = {t0, t1, t2};
+#pragma unroll
+  for (int t = 0; t < 3; ++t) {
+    const Term<Tin>& T_ = ts[t];
+    if (!T_.p) continue;
+    const cx<Tin>* X = T_.p + (long)e * T_.s;
+    if (T_.op == OP_N) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int r = r0 + ty + 8 * q, c = c0 + tx;
+        if (r < b && c < b) {
+          const cx<Tin> v = X[(long)r * b + c];
+          accr[q] += T_.alpha * (double)v.re;
+          acci[q] += T_.alpha * (double)v.im;
+        }
+      }
+    } else {
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {  // tile[cc][rr] = X[c0+cc][r0+rr]
+        const int rr = tx, cc = ty + 8 * q;
+        const int xr = c0 + cc, xc = r0 + rr;
+        tile[cc][rr] = (xr < b && xc < b) ? X[(long)xr * b + xc] : mk<Tin>(0, 0);
+      }
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {  // out(r, c) gets conj(X(c, r)) = conj(tile[c - c0][r - r0])
+        const cx<Tin> v = tile[tx][ty + 8 * q];
+        accr[q] += T_.alpha * (double)v.re;
+        acci[q] -= T_.alpha * (double)v.im;
+      }
+    }
+  }
+  const double zr = E ? diag_coef * E[e] : 0.0, zi = diag_coef * eta;
+  cx<Tout>* O = out + (long)e * sOut;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int r = r0 + ty + 8 * q, c = c0 + tx;
+    if (r < b && c < b) {
+      double vr = accr[q], vi = acci[q];
+      if (r == c && diag_coef != 0.0) { vr += zr; vi += zi; }
+      O[(long)r * b + c] = mk<Tout>((Tout)vr, (Tout)vi);
+    }
+  }
+}
+
+template <typename Tin, typename Tout>
+cudaError_t combine(cx<Tout>* out, long sOut, Term<Tin> t0, Term<Tin> t1, Term<Tin> t2, int b,
+                    int batch, const double* E, double eta, double diag_coef, const int* active,
+                    cudaStream_t st) {
+  dim3 grid((b + 31) / 32, (b + 31) / 32, batch);
+  k_combine<Tin, Tout><<<grid, 256, 0, st>>>(out, sOut, t0, t1, t2, b, E, eta, diag_coef, active);
+  return cudaGetLastError();
+}
+template cudaError_t combine<double, double>(cx<double>*, long, Term<double>, Term<double>, Term<double>, int, int, const double*, double, double, const int*, cudaStream_t);
+template cudaError_t combine<float, float>(cx<float>*, long, Term<float>, Term<float>, Term<float>, int, int, const double*, double, double, const int*, cudaStream_t);
+template cudaError_t combine<float, double>(cx<double>*, long, Term<float>, Term<float>, Term<float>, int, int, const double*, double, double, const int*, cudaStream_t);
+template cudaError_t combine<double, float>(cx<float>*, long, Term<double>, Term<double>, Term<double>, int, int, const double*, double, double, const int*, cudaStream_t);
+
+template <typename T>
+__global__ void k_assemble_diag(cx<T>* out, const cx<double>* H, const cx<double>* S,
+                                const cx<double>* SigR, long sSig, const cx<double>* lead,
+                                long sLead, const double* E, double eta, int b) {
+  const int e = blockIdx.y;
+  const long bb = (long)b * b;
+  const double Er = E[e];
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < bb; idx += (long)gridDim.x * blockDim.x) {
+    const int r = (int)(idx / b), c = (int)(idx % b);
+    cx<double> s = S ? S[idx] : mk<double>(r == c ? 1.0 : 0.0, 0.0);
+    cx<double> v = mk<double>(Er * s.re - eta * s.im, Er * s.im + eta * s.re) - H[idx];
+    if (SigR) v = v - SigR[(long)e * sSig + idx];
+    if (lead) v = v - lead[(long)e * sLead + idx];
+    out[(long)e * bb + idx] = cvt<T>(v);
+  }
+}
+template <typename T>
+cudaError_t assemble_diag(cx<T>* out, const cx<double>* H, const cx<double>* S,
+                          const cx<double>* SigR, long sSig, const cx<double>* lead, long sLead,
+                          const double* E, double eta, int b, int batch, cudaStream_t st) {
+  const long bb = (long)b * b;
+  dim3 grid((unsigned)((bb + 255) / 256 < 1024 ? (bb + 255) / 256 : 1024), batch);
+  k_assemble_diag<T><<<grid, 256, 0, st>>>(out, H, S, SigR, sSig, lead, sLead, E, eta, b);
+  return cudaGetLastError();
+}
+template cudaError_t assemble_diag<double>(cx<double>*, const cx<double>*, const cx<double>*, const cx<double>*, long, const cx<double>*, long, const double*, double, int, int, cudaStream_t);
+template cudaError_t assemble_diag<float>(cx<float>*, const cx<double>*, const cx<double>*, const cx<double>*, long, const cx<double>*, long, const double*, double, int, int, cudaStream_t);
+
+template <typename T>
+__global__ void k_axpby_from64(cx<T>* out, long sOut, const cx<double>* X, long sX, double c1,
+                               const cx<double>* Y, long sY, double c2, int b) {
+  const int e = blockIdx.y;
+  const long bb = (long)b * b;
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < bb; idx += (long)gridDim.x * blockDim.x) {
+    cx<double> v = c1 * X[(long)e * sX + idx];
+    if (Y) v = v + c2 * Y[(long)e * sY + idx];
+    out[(long)e * sOut + idx] = cvt<T>(v);
+  }
+}
+template <typename T>
+cudaError_t axpby_from64(cx<T>* out, long sOut, const cx<double>* X, long sX, double c1,
+                         const cx<double>* Y, long sY, double c2, int b, int batch, cudaStream_t st) {
+  const long bb = (long)b * b;
+  dim3 grid((unsigned)((bb + 255) / 256 < 1024 ? (bb + 255) / 256 : 1024), batch);
+  k_axpby_from64<T><<<grid, 256, 0, st>>>(out, sOut, X, sX, c1, Y, sY, c2, b);
+  return cudaGetLastError();
+}
+template cudaError_t axpby_from64<double>(cx<double>*, long, const cx<double>*, long, double, const cx<double>*, long, double, int, int, cudaStream_t);
+template cudaError_t axpby_from64<float>(cx<float>*, long, const cx<double>*, long, double, const cx<double>*, long, double, int, int, cudaStream_t);
+
+template <typename T>
+__global__ void k_assemble_offdiag(cx<T>* U, cx<T>* V, const cx<double>* Hup, const cx<double>* Sup,
+                                   const double* E, double eta, int b) {
+  const int e = blockIdx.z;
+  __shared__ cx<double> tile[32][33];
+  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
+  const double Er = E ? E[e] : 0.0, ei = E ? eta : 0.0;
+  const long bb = (long)b * b;
+  // U(r, c) = z S(r, c) - H(r, c)
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int r = r0 + ty + 8 * q, c = c0 + tx;
+    if (r < b && c < b) {
+      const cx<double> s = Sup ? Sup[(long)r * b + c] : mk<double>(0, 0);
+      const cx<double> h = Hup[(long)r * b + c];
+      U[(long)e * bb + (long)r * b + c] = cvt<T>(mk<double>(Er * s.re - ei * s.im - h.re, Er * s.im + ei * s.re - h.im));
+    }
+  }
+  // V(r, c) = z conj(S(c, r)) - conj(H(c, r))
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int cc = ty + 8 * q, rr = tx;
+    const int xr = c0 + cc, xc = r0 + rr;
+    if (xr < b && xc < b) {
+      const cx<double> s = Sup ? Sup[(long)xr * b + xc] : mk<double>(0, 0);
+      const cx<double> h = Hup[(long)xr * b + xc];
+      // z * conj(s) - conj(h)
+      tile[cc][rr] = mk<double>(Er * s.re + ei * s.im - h.re, -Er * s.im + ei * s.re + h.im);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int r = r0 + ty + 8 * q, c = c0 + tx;
+    if (r < b && c < b) V[(long)e * bb + (long)r * b + c] = cvt<T>(tile[tx][ty + 8 * q]);
+  }
+}
+template <typename T>
+cudaError_t assemble_offdiag(cx<T>* U, cx<T>* V, const cx<double>* Hup, const cx<double>* Sup,
+                             const double* E, double eta, int b, int batch, cudaStream_t st) {
+  dim3 grid((b + 31) / 32, (b + 31) / 32, batch);
+  k_assemble_offdiag<T><<<grid, 256, 0, st>>>(U, V, Hup, Sup, E, eta, b);
+  return cudaGetLastError();
+}
+template cudaError_t assemble_offdiag<double>(cx<double>*, cx<double>*, const cx<double>*, const cx<double>*, const double*, double, int, int, cudaStream_t);
+template cudaError_t assemble_offdiag<float>(cx<float>*, cx<float>*, const cx<double>*, const cx<double>*, const double*, double, int, int, cudaStream_t);
+
+// ============================================================================ observables
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double red[32];
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  const int w = threadIdx.x / 32, l = threadIdx.x % 32;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)(blockDim.x + 31) / 32; ++i) s += red[i];
+  return s;  // valid in thread 0
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_obs_current(double* cur, long ldcur, const cx<double>* Hup,
+                                                     const cx<double>* Sup, const cx<T>* GLu, long sG,
+                                                     const double* E, int b) {
+  const int e = blockIdx.x;
+  const long bb = (long)b * b;
+  const double Er = E[e];
+  const cx<T>* G = GLu + (long)e * sG;
+  double s = 0.0;
+  for (long idx = threadIdx.x; idx < bb; idx += blockDim.x) {
+    cx<double> x = Hup[idx];
+    if (Sup) x = x - Er * Sup[idx];
+    const cx<double> gg = cvt<double>(G[idx]);
+    s += x.re * gg.re + x.im * gg.im;  // Re(x * conj(g))
+  }
+  s = block_sum(s);
+  // 2 Re Tr[X (-GLu^H)] = -2 sum_jk Re(X_jk conj(GLu_jk))
+  if (threadIdx.x == 0) cur[(long)e * ldcur] = -2.0 * s;
+}
+template <typename T>
+cudaError_t obs_current(double* cur, long ldcur, const cx<double>* Hup, const cx<double>* Sup,
+                        const cx<T>* GLu, long sG, const double* E, int b, int batch, cudaStream_t st) {
+  k_obs_current<T><<<batch, 256, 0, st>>>(cur, ldcur, Hup, Sup, GLu, sG, E, b);
+  return cudaGetLastError();
+}
+template cudaError_t obs_current<double>(double*, long, const cx<double>*, const cx<double>*, const cx<double>*, long, const double*, int, int, cudaStream_t);
+template cudaError_t obs_current<float>(double*, long, const cx<double>*, const cx<double>*, const cx<float>*, long, const double*, int, int, cudaStream_t);
+
+template <typename T>
+__global__ void k_obs_density(double* den, long ldden, const cx<T>* GL, long sG, int b) {
+  const int e = blockIdx.x;
+  const cx<T>* G = GL + (long)e * sG;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < b; i += blockDim.x) s += (double)G[(long)i * b + i].im;
+  s = block_sum(s);
+  if (threadIdx.x == 0) den[(long)e * ldden] = s;
+}
+template <typename T>
+cudaError_t obs_density(double* den, long ldden, const cx<T>* GL, long sG, int b, int batch, cudaStream_t st) {
+  k_obs_density<T><<<batch, 128, 0, st>>>(den, ldden, GL, sG, b);
+  return cudaGetLastError();
+}
+template cudaError_t obs_density<double>(double*, long, const cx<double>*, long, int, int, cudaStream_t);
+template cudaError_t obs_density<float>(double*, long, const cx<float>*, long, int, int, cudaStream_t);
+
+// scale * Part Tr[X Y - Z W],  Part = Re (part 0) or Im (part 1);  Tr[X Y] = sum_jk X_jk Y_kj
+template <typename T>
+__global__ void __launch_bounds__(256) k_obs_trace2(double* out, long ld, const cx<double>* X, long sX,
+                                                    const cx<T>* Y, long sY, const cx<double>* Z, long sZ,
+                                                    const cx<T>* W, long sW, int b, int part, double scale) {
+  const int e = blockIdx.x;
+  const long bb = (long)b * b;
+  double s = 0.0;
+  for (long idx = threadIdx.x; idx < bb; idx += blockDim.x) {
+    const int j = (int)(idx / b), k = (int)(idx % b);
+    const cx<double> x = X[(long)e * sX + idx];
+    const cx<double> y = cvt<double>(Y[(long)e * sY + (long)k * b + j]);
+    s += part ? x.re * y.im + x.im * y.re : x.re * y.re - x.im * y.im;
+    if (Z) {
+      const cx<double> z = Z[(long)e * sZ + idx];
+      const cx<double> w = cvt<double>(W[(long)e * sW + (long)k * b + j]);
+      s -= part ? z.re * w.im + z.im * w.re : z.re * w.re - z.im * w.im;
+    }
+  }
+  s = block_sum(s);
+  if (threadIdx.x == 0) out[(long)e * ld] = scale * s;
+}
+template <typename T>
+cudaError_t obs_trace2(double* out, long ld, const cx<double>* X, long sX, const cx<T>* Y, long sY,
+                       const cx<double>* Z, long sZ, const cx<T>* Wm, long sW, int b, int batch,
+                       cudaStream_t st, int part, double scale) {
+  k_obs_trace2<T><<<batch, 256, 0, st>>>(out, ld, X, sX, Y, sY, Z, sZ, Wm, sW, b, part, scale);
+  return cudaGetLastError();
+}
+template cudaError_t obs_trace2<double>(double*, long, const cx<double>*, long, const cx<double>*, long, const cx<double>*, long, const cx<double>*, long, int, int, cudaStream_t, int, double);
+template cudaError_t obs_trace2<float>(double*, long, const cx<double>*, long, const cx<float>*, long, const cx<double>*, long, const cx<float>*, long, int, int, cudaStream_t, int, double);
+
+__global__ void __launch_bounds__(256) k_obs_frob_dot(double* out, long ld, const cx<double>* X, long sX,
+                                                      const cx<double>* Y, long sY, double scale, int b) {
+  const int e = blockIdx.x;
+  const long bb = (long)b * b;
+  double s = 0.0;
+  for (long idx = threadIdx.x; idx < bb; idx += blockDim.x) {
+    const cx<double> x = X[(long)e * sX + idx], y = Y[(long)e * sY + idx];
+    s += x.re * y.re + x.im * y.im;
+  }
+  s = block_sum(s);
+  if (threadIdx.x == 0) out[(long)e * ld] += scale * s;
+}
+cudaError_t obs_frob_dot(double* out, long ld, const cx<double>* X, long sX, const cx<double>* Y,
+                         long sY, double scale, int b, int batch, cudaStream_t st) {
+  k_obs_frob_dot<<<batch, 256, 0, st>>>(out, ld, X, sX, Y, sY, scale, b);
+  return cudaGetLastError();
+}
+
+// ============================================================================ leads
+__device__ __forceinline__ double fermi_dev(double E, double mu, double kT) {
+  const double x = (E - mu) / kT;
+  if (x > 0) {
+    const double ex = exp(-x);
+    return ex / (1.0 + ex);
+  }
+  return 1.0 / (1.0 + exp(x));
+}
+
+__global__ void k_lead_sigmas(const cx<double>* SR, cx<double>* Gam, cx<double>* SL, cx<double>* SG,
+                              const double* E, double mu, double kT, int b) {
+  const int e = blockIdx.y;
+  const long bb = (long)b * b;
+  const double f = fermi_dev(E[e], mu, kT);
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < bb; idx += (long)gridDim.x * blockDim.x) {
+    const int r = (int)(idx / b), c = (int)(idx % b);
+    const cx<double> s = SR[(long)e * bb + idx];
+    const cx<double> st = SR[(long)e * bb + (long)c * b + r];
+    // Gamma = i (S - S^H):  (S - S^H)(r,c) = s - conj(st)
+    const cx<double> d = mk<double>(s.re - st.re, s.im + st.im);
+    const cx<double> g = mk<double>(-d.im, d.re);
+    Gam[(long)e * bb + idx] = g;
+    SL[(long)e * bb + idx] = mk<double>(-f * g.im, f * g.re);                   // i f Gamma
+    SG[(long)e * bb + idx] = mk<double>((1.0 - f) * g.im, -(1.0 - f) * g.re);  // -i (1-f) Gamma
+  }
+}
+cudaError_t lead_sigmas(const cx<double>* SR, cx<double>* Gam, cx<double>* SL, cx<double>* SG,
+                        const double* E, double mu, double kT, int b, int batch, cudaStream_t st) {
+  const long bb = (long)b * b;
+  dim3 grid((unsigned)((bb + 255) / 256 < 1024 ? (bb + 255) / 256 : 1024), batch);
+  k_lead_sigmas<<<grid, 256, 0, st>>>(SR, Gam, SL, SG, E, mu, kT, b);
+  return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256) k_decim_converged(const cx<double>* X, const cx<double>* Y, int b,
+                                                         double tol, int* active, int* sweeps) {
+  const int e = blockIdx.x;
+  if (!active[e]) return;
+  const long bb = (long)b * b;
+  double m = 0.0;
+  for (long idx = threadIdx.x; idx < bb; idx += blockDim.x) {
+    const cx<double> x = X[(long)e * bb + idx], y = Y[(long)e * bb + idx];
+    m = fmax(m, fmax(hypot(x.re, x.im), hypot(y.re, y.im)));
+  }
+  for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, off));
+  __shared__ double red[8];
+  if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 1; i < (int)blockDim.x / 32; ++i) m = fmax(m, red[i]);
+    m = fmax(m, red[0]);
+    sweeps[e] += 1;
+    if (m < tol) active[e] = 0;
+  }
+}
+cudaError_t decim_converged(const cx<double>* X, const cx<double>* Y, int b, double tol, int* active,
+                            int* sweeps, int batch, cudaStream_t st) {
+  k_decim_converged<<<batch, 256, 0, st>>>(X, Y, b, tol, active, sweeps);
+  return cudaGetLastError();
+}
+
+__global__ void k_flag_active(const int* active, int* status, int code, int batch) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < batch && active[e]) atomicCAS(status + e, 0, code);
+}
+cudaError_t flag_active(const int* active, int* status, int code, int batch, cudaStream_t st) {
+  k_flag_active<<<(batch + 127) / 128, 128, 0, st>>>(active, status, code, batch);
+  return cudaGetLastError();
+}
+
+// ============================================================================ integration
+__global__ void k_integrate_add(double* acc, const double* val, long ld, int n, const double* w,
+                                const double* E, int e0, int nE, int batch, double scale) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double s = 0.0;
+  for (int e = 0; e < batch; ++e) {
+    double we;
+    const int g = e0 + e;
+    if (w) we = w[g];
+    else {
+      we = 0.0;
+      if (g + 1 < nE) we += 0.5 * (E[g + 1] - E[g]);
+      if (g > 0) we += 0.5 * (E[g] - E[g - 1]);
+    }
+    s += we * val[(long)e * ld + i];
+  }
+  acc[i] += scale * s;
+}
+cudaError_t integrate_add(double* acc, const double* val, long ld, int n, const double* w,
+                          const double* E, int e0, int nE, int batch, double scale, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_integrate_add<<<(n + 127) / 128, 128, 0, st>>>(acc, val, ld, n, w, E, e0, nE, batch, scale);
+  return cudaGetLastError();
+}
+
+}  // namespace qtx

@@ -1,0 +1,60 @@
+"""CPU checks of the C-ABI library: it builds for sm_103a, loads, and exports every function that
+include/*.h declares.  No compute call is made (there is no GPU here)."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w\s\*]*?\b(qtx_\w+)\s*\(", src, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_2606_25595_gb300 import build
+    return build.build()
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for fn in ("qtx_rgf_plan_create", "qtx_rgf_solve", "qtx_rgf_destroy"):
+        assert fn in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    L = ctypes.CDLL(libpath)
+    missing = [n for n in _declared_functions() if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_binding_lists_the_exports(libpath):
+    import paper_2606_25595_gb300 as q
+    assert set(q.EXPORTED) <= set(_declared_functions())
+    assert q.load().qtx_rgf_version().decode().startswith("qtx-rgf")
+
+
+def test_footprint_and_validation(libpath):
+    import paper_2606_25595_gb300 as q
+    d = q.make_desc(64, 256, "fp64", max_energies_in_flight=8)
+    fp = q.footprint(d)
+    # g and g^< alone: 2 * N_B * Ec * b^2 * 16 bytes
+    assert fp >= 2 * 64 * 8 * 256 * 256 * 16
+    d32 = q.make_desc(64, 256, "fp32", max_energies_in_flight=8)
+    assert q.footprint(d32) < fp
+    bad = q.make_desc(0, 16)
+    assert q.footprint(bad) == 0
+    h = ctypes.c_void_p()
+    s = q.load().qtx_rgf_plan_create(ctypes.byref(bad), ctypes.byref(h))
+    assert s == 1 and not h.value
+    assert b"n_blocks" in q.load().qtx_rgf_last_error(None)
