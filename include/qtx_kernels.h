@@ -1,0 +1,57 @@
+/*
+ * qtx_kernels.h -- component-level C ABI of the RGF library: the three building blocks of the sweep
+ * exposed on their own, on complex128 device arrays, for testing and for callers that assemble their
+ * own solvers.  Same conventions as qtx_rgf.h: device pointers owned by the caller, interleaved
+ * (re, im) doubles, row-major blocks, asynchronous on `stream` (a cudaStream_t), status codes from
+ * qtx_status.  Each call allocates its temporaries with stream-ordered cudaMallocAsync and frees them
+ * before returning.  Nothing falls back to the CPU.
+ */
+#ifndef QTX_KERNELS_H
+#define QTX_KERNELS_H
+
+#include "qtx_rgf.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Operand operations for qtx_zgemm_batched. */
+enum { QTX_OP_N = 0, QTX_OP_C = 1 /* conjugate transpose */ };
+
+/* Batched complex GEMM, the product kernel of the sweep (the paper's ZGEMM, Sec. IV):
+ *     C[e] = alpha * op(A[e]) * op(B[e]) + beta * C0[e],   e = 0 .. batch-1,
+ * op(A) is M x K, op(B) is K x N, C and C0 are M x N.  lda/ldb/ldc0/ldc are row strides and
+ * strideA/B/C0/C batch strides in complex elements (0 shares one matrix across the batch).
+ * precision: QTX_FP64 / QTX_FP32 on the CUDA cores; QTX_EMU64 / QTX_BF16X3 on the tcgen05 tensor cores
+ * with 5 / 2 bf16 digit planes per operand (Ozaki-style slicing, Sec. II-C), inputs and outputs
+ * rounded to df32 (hi + lo FP32 pairs) on the way in and out.  C0 may be NULL when beta == 0; C may
+ * alias C0 (same layout).  Errors: QTX_ERR_INVALID_ARG (sizes < 0, NULL operands),
+ * QTX_ERR_UNSUPPORTED (tensor-core modes on a GPU other than sm_103), QTX_ERR_CUDA, QTX_ERR_TIMEOUT
+ * (a bounded wait inside the tensor-core kernel expired; the context stays usable). */
+qtx_status qtx_zgemm_batched(int precision, int M, int N, int K, int opA, const void *A, long lda,
+                             long strideA, int opB, const void *B, long ldb, long strideB, double alpha,
+                             double beta, const void *C0, long ldc0, long strideC0, void *C, long ldc,
+                             long strideC, int batch, void *stream);
+
+/* Batched inverse of n x n complex blocks, in place (A[e] -> A[e]^-1, batch stride strideA), as used
+ * by the forward sweep (g_i = (A_i - V g U)^-1): Gauss-Jordan with partial pivoting on blocks of at
+ * most 64, a 2 x 2 Schur-complement recursion above that, plus one Newton step X += X (I - A X) for
+ * recursed FP32/FP64 blocks; QTX_EMU64 / QTX_BF16X3 start from the FP32 inverse and apply
+ * `refine_iter` Newton sweeps with tensor-core products.  status[e] (device, may be NULL) receives
+ * QTX_ERR_SINGULAR for a zero pivot. */
+qtx_status qtx_zinv_batched(int precision, int n, void *A, long strideA, int batch, int refine_iter,
+                            int *status, void *stream);
+
+/* Retarded contact self-energy Sigma^R(E) = H01 g_s H01^H of a semi-infinite lead by Sancho-Rubio
+ * decimation in FP64, batched over energies: H00, H01 are n x n (H01 couples a lead cell to the next
+ * one away from the device), energies[n_energies] a device array, z = E + i eta.  Output
+ * SigR[n_energies][n][n]; status[e] = QTX_ERR_NOT_CONVERGED when max|alpha|,|beta| did not fall below
+ * tol * max|H01| within max_iter sweeps.  Synchronises `stream` every few sweeps to test convergence. */
+qtx_status qtx_lead_self_energy(int n, const void *H00, const void *H01, const double *energies,
+                                int n_energies, double eta, double tol, int max_iter, void *SigR,
+                                int *status, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QTX_KERNELS_H */

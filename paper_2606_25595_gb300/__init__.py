@@ -29,7 +29,8 @@ OUT = {"GR_diag": 1 << 0, "GR_upper": 1 << 1, "GR_lower": 1 << 2, "GL_diag": 1 <
 BLOCK_OUTPUTS = ("GR_diag", "GR_upper", "GR_lower", "GL_diag", "GL_upper", "GG_diag", "GG_upper")
 # Every function the C ABI exports (checked by the CPU tests against include/*.h).
 EXPORTED = ("qtx_rgf_plan_create", "qtx_rgf_solve", "qtx_rgf_status", "qtx_rgf_destroy",
-            "qtx_rgf_last_error", "qtx_rgf_footprint", "qtx_rgf_version")
+            "qtx_rgf_last_error", "qtx_rgf_footprint", "qtx_rgf_version", "qtx_zgemm_batched",
+            "qtx_zinv_batched", "qtx_lead_self_energy")
 
 
 class QtxError(RuntimeError):
@@ -92,6 +93,13 @@ def load() -> ctypes.CDLL:
     L.qtx_rgf_footprint.restype = ctypes.c_size_t
     L.qtx_rgf_version.argtypes = []
     L.qtx_rgf_version.restype = ctypes.c_char_p
+    vp, i, l, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_long, ctypes.c_double
+    L.qtx_zgemm_batched.argtypes = [i, i, i, i, i, vp, l, l, i, vp, l, l, d, d, vp, l, l, vp, l, l, i, vp]
+    L.qtx_zgemm_batched.restype = i
+    L.qtx_zinv_batched.argtypes = [i, i, vp, l, i, i, vp, vp]
+    L.qtx_zinv_batched.restype = i
+    L.qtx_lead_self_energy.argtypes = [i, vp, vp, vp, i, d, d, i, vp, vp, vp]
+    L.qtx_lead_self_energy.restype = i
     _lib = L
     return L
 
@@ -246,3 +254,62 @@ def upload(dev: dict, energies=None, weights=None) -> dict:
     inp.n_energies = int(E.size)
     d["_inputs"] = inp
     return d
+
+
+def _stream(stream):
+    import torch
+    return torch.cuda.current_stream().cuda_stream if stream is None else stream
+
+
+def zgemm_batched(A, B, precision="emu64", opA="N", opB="N", alpha=1.0, beta=0.0, C0=None,
+                  stream=None):
+    """C[e] = alpha op(A[e]) op(B[e]) + beta C0[e] on complex128 CUDA tensors [batch, rows, cols]
+    (a 2-D tensor is shared by the whole batch).  Marshalling only; the product runs in the
+    library's kernels."""
+    import torch
+    ops = {"N": 0, "C": 1}
+    A3 = A if A.dim() == 3 else A.unsqueeze(0)
+    B3 = B if B.dim() == 3 else B.unsqueeze(0)
+    batch = max(A3.shape[0] if A.dim() == 3 else 1, B3.shape[0] if B.dim() == 3 else 1)
+    M = A3.shape[1] if opA == "N" else A3.shape[2]
+    K = A3.shape[2] if opA == "N" else A3.shape[1]
+    N = B3.shape[2] if opB == "N" else B3.shape[1]
+    C = torch.empty((batch, M, N), dtype=torch.complex128, device=A.device)
+    c0p, ldc0, sc0 = None, N, 0
+    if C0 is not None:
+        C03 = C0 if C0.dim() == 3 else C0.unsqueeze(0)
+        c0p, ldc0, sc0 = C03.data_ptr(), C03.shape[2], (C03.shape[1] * C03.shape[2] if C0.dim() == 3 else 0)
+    s = load().qtx_zgemm_batched(
+        PRECISION[precision], M, N, K, ops[opA], A3.data_ptr(), A3.shape[2],
+        A3.shape[1] * A3.shape[2] if A.dim() == 3 else 0, ops[opB], B3.data_ptr(), B3.shape[2],
+        B3.shape[1] * B3.shape[2] if B.dim() == 3 else 0, float(alpha), float(beta), c0p, ldc0, sc0,
+        C.data_ptr(), N, M * N, batch, ctypes.c_void_p(_stream(stream)))
+    if s != 0:
+        raise QtxError(s, "qtx_zgemm_batched")
+    return C
+
+
+def zinv_batched(A, precision="fp64", refine_iter=2, stream=None):
+    """In-place batched inverse of complex128 CUDA tensor A [batch, n, n]; returns (A, status)."""
+    import torch
+    status = torch.zeros(A.shape[0], dtype=torch.int32, device=A.device)
+    s = load().qtx_zinv_batched(PRECISION[precision], A.shape[1], A.data_ptr(), A.shape[1] * A.shape[2],
+                                A.shape[0], int(refine_iter), status.data_ptr(),
+                                ctypes.c_void_p(_stream(stream)))
+    if s != 0:
+        raise QtxError(s, "qtx_zinv_batched")
+    return A, status
+
+
+def lead_self_energy(H00, H01, energies, eta, tol=1e-13, max_iter=100, stream=None):
+    """Contact Sigma^R(E) [n_E, n, n] from CUDA tensors H00, H01 (complex128) and energies (float64)."""
+    import torch
+    n = H00.shape[0]
+    out = torch.empty((energies.shape[0], n, n), dtype=torch.complex128, device=H00.device)
+    status = torch.zeros(energies.shape[0], dtype=torch.int32, device=H00.device)
+    s = load().qtx_lead_self_energy(n, H00.data_ptr(), H01.data_ptr(), energies.data_ptr(),
+                                    energies.shape[0], float(eta), float(tol), int(max_iter),
+                                    out.data_ptr(), status.data_ptr(), ctypes.c_void_p(_stream(stream)))
+    if s != 0:
+        raise QtxError(s, "qtx_lead_self_energy")
+    return out, status

@@ -55,8 +55,36 @@ __device__ __forceinline__ cx<T> crecip(cx<T> a) {
 template <typename T>
 __device__ __forceinline__ T cabs1(cx<T> a) { return fabs(a.re) + fabs(a.im); }
 
+// "df32" real: the unevaluated sum hi + lo of two FP32 values (|lo| <= ulp(hi)/2); arithmetic in df32.cuh.
+struct df {
+  float hi, lo;
+};
+
+// Conversions through FP64 (used at the boundary of the sweep and in the observable reductions).
+__host__ __device__ __forceinline__ double to_d(float x) { return (double)x; }
+__host__ __device__ __forceinline__ double to_d(double x) { return x; }
+__host__ __device__ __forceinline__ double to_d(df x) { return (double)x.hi + (double)x.lo; }
+template <typename T>
+__host__ __device__ __forceinline__ T from_d(double x);
+template <>
+__host__ __device__ __forceinline__ float from_d<float>(double x) { return (float)x; }
+template <>
+__host__ __device__ __forceinline__ double from_d<double>(double x) { return x; }
+template <>
+__host__ __device__ __forceinline__ df from_d<df>(double x) {
+  df r;
+  r.hi = (float)x;
+  r.lo = (float)(x - (double)r.hi);
+  return r;
+}
+
 template <typename To, typename Ti>
-__host__ __device__ __forceinline__ cx<To> cvt(cx<Ti> a) { return mk<To>((To)a.re, (To)a.im); }
+__host__ __device__ __forceinline__ cx<To> cvt(cx<Ti> a) {
+  cx<To> z;
+  z.re = from_d<To>(to_d(a.re));
+  z.im = from_d<To>(to_d(a.im));
+  return z;
+}
 
 // Operation applied to a GEMM operand: as stored, or conjugate-transposed.
 enum Op : int { OP_N = 0, OP_C = 1 };
@@ -71,7 +99,19 @@ struct GemmArgs {
   const cx<T>* B; long ldb, sB; int opB;
   const cx<T>* C0; long ldc0, sC0;
   cx<T>* C; long ldc, sC;
-  T alpha, beta;
+  double alpha, beta;
+  int batch;
+  const int* active;
+};
+
+// Arguments of the tensor-core engine (complex df32 operands and result).
+struct TcArgs {
+  int M, N, K;
+  const cx<df>* A; long lda, sA; int opA;
+  const cx<df>* B; long ldb, sB; int opB;
+  const cx<df>* C0; long ldc0, sC0;
+  cx<df>* C; long ldc, sC;
+  float alpha, beta;
   int batch;
   const int* active;
 };

@@ -31,6 +31,15 @@ cudaError_t combine(cx<Tout>* out, long sOut, Term<Tin> t0, Term<Tin> t1, Term<T
                     int batch, const double* E, double eta, double diag_coef, const int* active,
                     cudaStream_t st);
 
+// out[e](r, c) = in[e](r, c) converted between storage types (row strides ldi/ldo, batch si/so)
+template <typename Tin, typename Tout>
+cudaError_t convert_strided(const cx<Tin>* in, long ldi, long si, cx<Tout>* out, long ldo, long so, int rows,
+                            int cols, int batch, cudaStream_t st);
+
+// X[e] += I
+template <typename T>
+cudaError_t add_identity(cx<T>* X, long sX, int n, int batch, const int* active, cudaStream_t st);
+
 // ---- assemble a diagonal block of M (step 1 of the sweep), in T precision from complex128 inputs:
 //   out[e] = (E[e] + i eta) S - H - SigR[e] - lead[e]     (S == nullptr => identity)
 template <typename T>
@@ -83,14 +92,12 @@ cudaError_t integrate_add(double* acc, const double* val, long ld, int n, const 
                           const double* E, int e0, int nE, int batch, double scale,
                           cudaStream_t st);
 
-// ---- tensor-core engine (tc_engine.cu): emulated-precision batched complex GEMM on sm_103a
-struct TcConfig {
-  int digits;        // bf16 digit planes per operand
-  int max_order;     // keep digit products with i + j <= max_order (1-based digit indices)
-};
-cudaError_t gemm_tc(const GemmArgs<double>& g, const TcConfig& cfg, void* scratch,
-                    size_t scratch_bytes, int* err_flag, cudaStream_t st);
-size_t gemm_tc_scratch_bytes(int M, int N, int K, int batch, const TcConfig& cfg);
+// ---- tensor-core engine (tc_engine.cu): emulated-precision batched complex GEMM on sm_103a.
+// `digits` bf16 digit planes per operand (6: ~41-bit products from 21 digit products; 2: ~13-bit
+// products from 3).  `scratch` holds the digit planes and scale exponents.
+cudaError_t gemm_tc(const TcArgs& a, int digits, void* scratch, size_t scratch_bytes, int* err_flag,
+                    cudaStream_t st);
+size_t gemm_tc_scratch_bytes(int M, int N, int K, int batch, int digits);
 bool tc_available();
 
 }  // namespace qtx

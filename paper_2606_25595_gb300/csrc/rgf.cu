@@ -15,8 +15,10 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
+#include "../../include/qtx_kernels.h"
 #include "kernels.cuh"
 
 using namespace qtx;
@@ -37,7 +39,7 @@ struct Arena {
 };
 
 struct Layout {
-  size_t g, gl, tmp, inv_tmp, U, V, ident, ref, f32a, f32tmp, dec, lead, obs, flags, tc_scratch, total;
+  size_t g, gl, tmp, inv_tmp, U, V, ident, ident_df, ref, f32a, f32tmp, dec, lead, obs, flags, tc_scratch, total;
   int n_tmp, n_dec;
   size_t tc_bytes;
 };
@@ -77,8 +79,9 @@ Layout make_layout(const qtx_rgf_desc& d) {
   L.U = a.take(ou);
   L.V = a.take(ou);
   L.ident = a.take(bb * sizeof(cx<double>));
+  L.ident_df = a.take(bb * sizeof(cx<double>));
   const bool mixed = d.precision == QTX_EMU64 || d.precision == QTX_BF16X3;
-  L.ref = a.take(mixed ? 3 * Ec * bb * sizeof(cx<double>) : 0);
+  L.ref = a.take((mixed || b > kLeafMax) ? 3 * Ec * bb * sizeof(cx<double>) : 0);
   L.f32a = a.take(mixed ? Ec * bb * sizeof(cx<float>) : 0);
   L.f32tmp = a.take(mixed ? Ec * bb * sizeof(cx<float>) + 4096 : 0);
   L.n_dec = 9;
@@ -88,7 +91,7 @@ Layout make_layout(const qtx_rgf_desc& d) {
   L.obs = a.take((size_t)Ec * (2 * nb + 8) * sizeof(double));
   L.flags = a.take((size_t)Ec * 3 * sizeof(int) + 64);
   L.tc_bytes = 0;
-  if (mixed) L.tc_bytes = gemm_tc_scratch_bytes((int)b, (int)b, (int)b, (int)Ec, TcConfig{5, 6});
+  if (mixed) L.tc_bytes = gemm_tc_scratch_bytes((int)b, (int)b, (int)b, (int)Ec, d.precision == QTX_EMU64 ? 6 : 2);
   L.tc_scratch = a.take(L.tc_bytes);
   L.total = a.off;
   return L;
@@ -127,7 +130,7 @@ struct Ctx {
 template <typename T>
 GemmArgs<T> gargs(int M, int N, int K, const cx<T>* A, long lda, long sA, int opA, const cx<T>* B,
                   long ldb, long sB, int opB, const cx<T>* C0, long ldc0, long sC0, cx<T>* C, long ldc,
-                  long sC, T alpha, T beta, int batch, const int* active) {
+                  long sC, double alpha, double beta, int batch, const int* active) {
   GemmArgs<T> g;
   g.M = M; g.N = N; g.K = K;
   g.A = A; g.lda = lda; g.sA = sA; g.opA = opA;
@@ -148,13 +151,22 @@ qtx_status gemm<float>(qtx_rgf_plan_s* P, const GemmArgs<float>& g, cudaStream_t
   return QTX_OK;
 }
 template <>
-qtx_status gemm<double>(qtx_rgf_plan_s* P, const GemmArgs<double>& g, cudaStream_t st, bool force_simt) {
-  if (force_simt || P->d.precision == QTX_FP64) {
-    QTX_CK(gemm_simt<double>(g, st));
-    return QTX_OK;
-  }
-  const TcConfig cfg = P->d.precision == QTX_EMU64 ? TcConfig{5, 6} : TcConfig{2, 3};
-  QTX_CK(gemm_tc(g, cfg, P->ws + P->L.tc_scratch, P->L.tc_bytes, P->d_err_flag, st));
+qtx_status gemm<double>(qtx_rgf_plan_s* P, const GemmArgs<double>& g, cudaStream_t st, bool) {
+  QTX_CK(gemm_simt<double>(g, st));
+  return QTX_OK;
+}
+inline int tc_digits(const qtx_rgf_desc& d) { return d.precision == QTX_EMU64 ? 6 : 2; }
+template <>
+qtx_status gemm<df>(qtx_rgf_plan_s* P, const GemmArgs<df>& g, cudaStream_t st, bool) {
+  TcArgs a;
+  a.M = g.M; a.N = g.N; a.K = g.K;
+  a.A = g.A; a.lda = g.lda; a.sA = g.sA; a.opA = g.opA;
+  a.B = g.B; a.ldb = g.ldb; a.sB = g.sB; a.opB = g.opB;
+  a.C0 = g.C0; a.ldc0 = g.ldc0; a.sC0 = g.sC0;
+  a.C = g.C; a.ldc = g.ldc; a.sC = g.sC;
+  a.alpha = (float)g.alpha; a.beta = (float)g.beta;
+  a.batch = g.batch; a.active = g.active;
+  QTX_CK(gemm_tc(a, tc_digits(P->d), P->ws + P->L.tc_scratch, P->L.tc_bytes, P->d_err_flag, st));
   return QTX_OK;
 }
 
@@ -179,16 +191,52 @@ qtx_status inverse_rec(qtx_rgf_plan_s* P, cx<T>* A, long lda, long sA, int n, in
   qtx_status s;
   if ((s = inverse_rec<T>(P, A11, lda, sA, h, batch, active, status, next, sScr, st, force_simt))) return s;
   // T12 = X11 A12 ; T21 = A21 X11
-  if ((s = gemm<T>(P, gargs<T>(h, r, h, A11, lda, sA, OP_N, A12, lda, sA, OP_N, nullptr, 0, 0, T12, r, sScr, T(1), T(0), batch, active), st, force_simt))) return s;
-  if ((s = gemm<T>(P, gargs<T>(r, h, h, A21, lda, sA, OP_N, A11, lda, sA, OP_N, nullptr, 0, 0, T21, h, sScr, T(1), T(0), batch, active), st, force_simt))) return s;
+  if ((s = gemm<T>(P, gargs<T>(h, r, h, A11, lda, sA, OP_N, A12, lda, sA, OP_N, nullptr, 0, 0, T12, r, sScr, 1.0, 0.0, batch, active), st, force_simt))) return s;
+  if ((s = gemm<T>(P, gargs<T>(r, h, h, A21, lda, sA, OP_N, A11, lda, sA, OP_N, nullptr, 0, 0, T21, h, sScr, 1.0, 0.0, batch, active), st, force_simt))) return s;
   // A22 <- A22 - A21 T12 (Schur complement), then invert it in place
-  if ((s = gemm<T>(P, gargs<T>(r, r, h, A21, lda, sA, OP_N, T12, r, sScr, OP_N, A22, lda, sA, A22, lda, sA, T(-1), T(1), batch, active), st, force_simt))) return s;
+  if ((s = gemm<T>(P, gargs<T>(r, r, h, A21, lda, sA, OP_N, T12, r, sScr, OP_N, A22, lda, sA, A22, lda, sA, -1.0, 1.0, batch, active), st, force_simt))) return s;
   if ((s = inverse_rec<T>(P, A22, lda, sA, r, batch, active, status, next, sScr, st, force_simt))) return s;
   // A12 <- -T12 Y ; A21 <- -Y T21 ; A11 <- X11 - T12 A21
-  if ((s = gemm<T>(P, gargs<T>(h, r, r, T12, r, sScr, OP_N, A22, lda, sA, OP_N, nullptr, 0, 0, A12, lda, sA, T(-1), T(0), batch, active), st, force_simt))) return s;
-  if ((s = gemm<T>(P, gargs<T>(r, h, r, A22, lda, sA, OP_N, T21, h, sScr, OP_N, nullptr, 0, 0, A21, lda, sA, T(-1), T(0), batch, active), st, force_simt))) return s;
-  if ((s = gemm<T>(P, gargs<T>(h, h, r, T12, r, sScr, OP_N, A21, lda, sA, OP_N, A11, lda, sA, A11, lda, sA, T(-1), T(1), batch, active), st, force_simt))) return s;
+  if ((s = gemm<T>(P, gargs<T>(h, r, r, T12, r, sScr, OP_N, A22, lda, sA, OP_N, nullptr, 0, 0, A12, lda, sA, -1.0, 0.0, batch, active), st, force_simt))) return s;
+  if ((s = gemm<T>(P, gargs<T>(r, h, r, A22, lda, sA, OP_N, T21, h, sScr, OP_N, nullptr, 0, 0, A21, lda, sA, -1.0, 0.0, batch, active), st, force_simt))) return s;
+  if ((s = gemm<T>(P, gargs<T>(h, h, r, T12, r, sScr, OP_N, A21, lda, sA, OP_N, A11, lda, sA, A11, lda, sA, -1.0, 1.0, batch, active), st, force_simt))) return s;
   return QTX_OK;
+}
+
+// Recursive inverse followed, when the recursion splits the block (n > kLeafMax), by one Newton
+// step X <- X + X (I - A X) in the same precision: elimination without pivoting between the two
+// halves can lose digits on ill-conditioned leading blocks (e.g. the decimation's z - eps), and one
+// step brings the result back to the accuracy of a pivoted inverse.
+template <typename T>
+qtx_status inverse_refined(qtx_rgf_plan_s* P, cx<T>* A, int n, int batch, const int* active,
+                           int* status, cudaStream_t st) {
+  const long nn = (long)n * n;
+  cx<T>* scr = reinterpret_cast<cx<T>*>(P->ws + P->L.inv_tmp);
+  if (n <= kLeafMax) return inverse_rec<T>(P, A, n, nn, n, batch, active, status, scr, nn, st, true);
+  cx<T>* Acopy = reinterpret_cast<cx<T>*>(P->ws + P->L.ref);
+  cx<T>* R = Acopy + (size_t)P->Ec * nn;
+  cx<T>* Xn = R + (size_t)P->Ec * nn;
+  Term<T> tA; tA.p = A; tA.s = nn; tA.alpha = 1.0;
+  Term<T> none;
+  QTX_CK((combine<T, T>(Acopy, nn, tA, none, none, n, batch, nullptr, 0.0, 0.0, active, st)));
+  qtx_status s = inverse_rec<T>(P, A, n, nn, n, batch, active, status, scr, nn, st, true);
+  if (s) return s;
+  // R = I - Acopy X  (identity via the diagonal term of combine), Xn = X + X R, X <- Xn
+  if ((s = gemm<T>(P, gargs<T>(n, n, n, Acopy, n, nn, OP_N, A, n, nn, OP_N, nullptr, 0, 0, R, n, nn, -1.0, 0.0, batch, active), st, true))) return s;
+  QTX_CK(add_identity<T>(R, nn, n, batch, active, st));
+  if ((s = gemm<T>(P, gargs<T>(n, n, n, A, n, nn, OP_N, R, n, nn, OP_N, A, n, nn, Xn, n, nn, 1.0, 1.0, batch, active), st, true))) return s;
+  Term<T> tX; tX.p = Xn; tX.s = nn; tX.alpha = 1.0;
+  QTX_CK((combine<T, T>(A, nn, tX, none, none, n, batch, nullptr, 0.0, 0.0, active, st)));
+  return QTX_OK;
+}
+
+// FP32 inverse used as the emulated modes' starting guess (the df32 Newton sweeps that follow only
+// need ||I - A X0|| < 1); its scratch lives in the FP32 area so the df32 buffers stay intact.
+qtx_status inverse_refined_f32(qtx_rgf_plan_s* P, cx<float>* A, int n, int batch, const int* active,
+                               int* status, cudaStream_t st) {
+  const long nn = (long)n * n;
+  cx<float>* scr = reinterpret_cast<cx<float>*>(P->ws + P->L.f32tmp);
+  return inverse_rec<float>(P, A, n, nn, n, batch, active, status, scr, nn, st, true);
 }
 
 // Block inverse used by the sweep.  FP64 / FP32: recursive inverse in the sweep precision.
@@ -202,40 +250,41 @@ qtx_status block_inverse(qtx_rgf_plan_s* P, cx<T>* A, int n, int batch, const in
 template <>
 qtx_status block_inverse<float>(qtx_rgf_plan_s* P, cx<float>* A, int n, int batch, const int* active,
                                 int* status, cudaStream_t st) {
-  cx<float>* scr = reinterpret_cast<cx<float>*>(P->ws + P->L.inv_tmp);
-  return inverse_rec<float>(P, A, n, (long)n * n, n, batch, active, status, scr, (long)n * n, st, true);
+  return inverse_refined<float>(P, A, n, batch, active, status, st);
 }
 
 template <>
 qtx_status block_inverse<double>(qtx_rgf_plan_s* P, cx<double>* A, int n, int batch, const int* active,
                                  int* status, cudaStream_t st) {
+  return inverse_refined<double>(P, A, n, batch, active, status, st);
+}
+
+// Emulated modes (df32 storage): X0 from the FP32 inverse of the leading parts, then Newton sweeps
+// X <- X + X (I - A X) with both products on the tensor-core engine; the residual I - A X is formed
+// by the engine's ~38-bit products with I added exactly in the epilogue.
+template <>
+qtx_status block_inverse<df>(qtx_rgf_plan_s* P, cx<df>* A, int n, int batch, const int* active,
+                             int* status, cudaStream_t st) {
   const long nn = (long)n * n;
-  if (P->d.precision == QTX_FP64) {
-    cx<double>* scr = reinterpret_cast<cx<double>*>(P->ws + P->L.inv_tmp);
-    return inverse_rec<double>(P, A, n, nn, n, batch, active, status, scr, nn, st, true);
-  }
-  // mixed: A (complex128) -> FP32 copy -> inverse -> X0 (complex128) -> refinement
   cx<float>* A32 = reinterpret_cast<cx<float>*>(P->ws + P->L.f32a);
-  cx<float>* scr32 = reinterpret_cast<cx<float>*>(P->ws + P->L.f32tmp);
-  cx<double>* Acopy = reinterpret_cast<cx<double>*>(P->ws + P->L.ref);
-  cx<double>* R = Acopy + (size_t)P->Ec * nn;
-  cx<double>* Xn = R + (size_t)P->Ec * nn;
-  const cx<double>* I = reinterpret_cast<cx<double>*>(P->ws + P->L.ident);
-  Term<double> tA; tA.p = A; tA.s = nn; tA.alpha = 1.0;
-  Term<double> none;
-  QTX_CK((combine<double, float>(A32, nn, tA, none, none, n, batch, nullptr, 0.0, 0.0, active, st)));
-  QTX_CK((combine<double, double>(Acopy, nn, tA, none, none, n, batch, nullptr, 0.0, 0.0, active, st)));
-  qtx_status s = inverse_rec<float>(P, A32, n, nn, n, batch, active, status, scr32, nn, st, true);
+  cx<df>* Acopy = reinterpret_cast<cx<df>*>(P->ws + P->L.ref);
+  cx<df>* R = Acopy + (size_t)P->Ec * nn;
+  cx<df>* Xn = R + (size_t)P->Ec * nn;
+  const cx<df>* I = reinterpret_cast<const cx<df>*>(P->ws + P->L.ident_df);
+  Term<df> tA; tA.p = A; tA.s = nn; tA.alpha = 1.0;
+  Term<df> none;
+  QTX_CK((combine<df, float>(A32, nn, tA, none, none, n, batch, nullptr, 0.0, 0.0, active, st)));
+  QTX_CK((combine<df, df>(Acopy, nn, tA, none, none, n, batch, nullptr, 0.0, 0.0, active, st)));
+  qtx_status s = inverse_refined_f32(P, A32, n, batch, active, status, st);
   if (s) return s;
   Term<float> tX; tX.p = A32; tX.s = nn; tX.alpha = 1.0;
   Term<float> none32;
-  QTX_CK((combine<float, double>(A, nn, tX, none32, none32, n, batch, nullptr, 0.0, 0.0, active, st)));
+  QTX_CK((combine<float, df>(A, nn, tX, none32, none32, n, batch, nullptr, 0.0, 0.0, active, st)));
   for (int it = 0; it < P->d.refine_max_iter; ++it) {
-    // R = I - Acopy X ; Xn = X + X R ; X <- Xn
-    if ((s = gemm<double>(P, gargs<double>(n, n, n, Acopy, n, nn, OP_N, A, n, nn, OP_N, I, n, 0, R, n, nn, -1.0, 1.0, batch, active), st))) return s;
-    if ((s = gemm<double>(P, gargs<double>(n, n, n, A, n, nn, OP_N, R, n, nn, OP_N, A, n, nn, Xn, n, nn, 1.0, 1.0, batch, active), st))) return s;
-    Term<double> tXn; tXn.p = Xn; tXn.s = nn; tXn.alpha = 1.0;
-    QTX_CK((combine<double, double>(A, nn, tXn, none, none, n, batch, nullptr, 0.0, 0.0, active, st)));
+    if ((s = gemm<df>(P, gargs<df>(n, n, n, Acopy, n, nn, OP_N, A, n, nn, OP_N, I, n, 0, R, n, nn, -1.0, 1.0, batch, active), st))) return s;
+    if ((s = gemm<df>(P, gargs<df>(n, n, n, A, n, nn, OP_N, R, n, nn, OP_N, A, n, nn, Xn, n, nn, 1.0, 1.0, batch, active), st))) return s;
+    Term<df> tXn; tXn.p = Xn; tXn.s = nn; tXn.alpha = 1.0;
+    QTX_CK((combine<df, df>(A, nn, tXn, none, none, n, batch, nullptr, 0.0, 0.0, active, st)));
   }
   return QTX_OK;
 }
@@ -256,7 +305,6 @@ qtx_status contact(const Ctx<T>& c, const cx<double>* H00, const cx<double>* H01
   int* flags = reinterpret_cast<int*>(P->ws + P->L.flags);
   int* active = flags;
   int* sweeps = flags + P->Ec;
-  cx<double>* inv_scr = reinterpret_cast<cx<double>*>(P->ws + P->L.inv_tmp);
   std::vector<cx<double>> h(bb);
   QTX_CK(cudaMemcpyAsync(h.data(), H01, bb * sizeof(cx<double>), cudaMemcpyDeviceToHost, st));
   QTX_CK(cudaStreamSynchronize(st));
@@ -283,7 +331,7 @@ qtx_status contact(const Ctx<T>& c, const cx<double>* H00, const cx<double>* H01
   for (int it = 1; it <= P->d.decim_max_iter; ++it) {
     Term<double> te; te.p = eps; te.s = bb; te.alpha = -1.0;
     QTX_CK((combine<double, double>(g, bb, te, none, none, b, ne, c.E, eta, 1.0, active, st)));  // z - eps
-    if ((s = inverse_rec<double>(P, g, b, bb, b, ne, active, c.status, inv_scr, bb, st, true))) return s;
+    if ((s = inverse_refined<double>(P, g, b, ne, active, c.status, st))) return s;
     if ((s = G(alpha, g, ag))) return s;
     if ((s = G(beta, g, bg))) return s;
     if ((s = G(ag, beta, t1))) return s;   // alpha g beta
@@ -312,7 +360,7 @@ qtx_status contact(const Ctx<T>& c, const cx<double>* H00, const cx<double>* H01
   QTX_CK(flag_active(active, c.status, (int)QTX_ERR_NOT_CONVERGED, ne, st));
   Term<double> tes; tes.p = eps_s; tes.s = bb; tes.alpha = -1.0;
   QTX_CK((combine<double, double>(g, bb, tes, none, none, b, ne, c.E, eta, 1.0, nullptr, st)));  // z - eps_s
-  if ((s = inverse_rec<double>(P, g, b, bb, b, ne, nullptr, c.status, inv_scr, bb, st, true))) return s;
+  if ((s = inverse_refined<double>(P, g, b, ne, nullptr, c.status, st))) return s;
   // Sigma^R = H01 g_s H01^H
   if ((s = gemm<double>(P, gargs<double>(b, b, b, H01, b, 0, OP_N, g, b, bb, OP_N, nullptr, 0, 0, t1, b, bb, 1.0, 0.0, ne, nullptr), st, true))) return s;
   if ((s = gemm<double>(P, gargs<double>(b, b, b, t1, b, bb, OP_N, H01, b, 0, OP_C, nullptr, 0, 0, SR, b, bb, 1.0, 0.0, ne, nullptr), st, true))) return s;
@@ -394,8 +442,8 @@ qtx_status solve_chunk(qtx_rgf_plan_s* P, const qtx_rgf_inputs* in, const qtx_rg
     }
     if (i > 0) {
       cx<T>* Tm = c.tmp(0);
-      if ((s = gemm<T>(P, gargs<T>(b, b, b, c.g(i - 1), b, bb, OP_N, U(i - 1), b, sUV, OP_N, nullptr, 0, 0, Tm, b, bb, T(1), T(0), ne, nullptr), st))) return s;
-      if ((s = gemm<T>(P, gargs<T>(b, b, b, V(i - 1), b, sUV, OP_N, Tm, b, bb, OP_N, gi, b, bb, gi, b, bb, T(-1), T(1), ne, nullptr), st))) return s;
+      if ((s = gemm<T>(P, gargs<T>(b, b, b, c.g(i - 1), b, bb, OP_N, U(i - 1), b, sUV, OP_N, nullptr, 0, 0, Tm, b, bb, 1.0, 0.0, ne, nullptr), st))) return s;
+      if ((s = gemm<T>(P, gargs<T>(b, b, b, V(i - 1), b, sUV, OP_N, Tm, b, bb, OP_N, gi, b, bb, gi, b, bb, -1.0, 1.0, ne, nullptr), st))) return s;
     }
     if ((s = block_inverse<T>(P, gi, b, ne, nullptr, status, st))) return s;
     // Sigma^<_ii (+ contacts), then the left-connected lesser function
@@ -415,12 +463,12 @@ qtx_status solve_chunk(qtx_rgf_plan_s* P, const qtx_rgf_inputs* in, const qtx_rg
     }
     if (i > 0) {
       cx<T>* X = c.tmp(0);
-      if ((s = gemm<T>(P, gargs<T>(b, b, b, V(i - 1), b, sUV, OP_N, c.gl(i - 1), b, bb, OP_N, nullptr, 0, 0, X, b, bb, T(1), T(0), ne, nullptr), st))) return s;
-      if ((s = gemm<T>(P, gargs<T>(b, b, b, X, b, bb, OP_N, V(i - 1), b, sUV, OP_C, SLi, b, bb, SLi, b, bb, T(1), T(1), ne, nullptr), st))) return s;
+      if ((s = gemm<T>(P, gargs<T>(b, b, b, V(i - 1), b, sUV, OP_N, c.gl(i - 1), b, bb, OP_N, nullptr, 0, 0, X, b, bb, 1.0, 0.0, ne, nullptr), st))) return s;
+      if ((s = gemm<T>(P, gargs<T>(b, b, b, X, b, bb, OP_N, V(i - 1), b, sUV, OP_C, SLi, b, bb, SLi, b, bb, 1.0, 1.0, ne, nullptr), st))) return s;
     }
     cx<T>* Y = c.tmp(0);
-    if ((s = gemm<T>(P, gargs<T>(b, b, b, gi, b, bb, OP_N, SLi, b, bb, OP_N, nullptr, 0, 0, Y, b, bb, T(1), T(0), ne, nullptr), st))) return s;
-    if ((s = gemm<T>(P, gargs<T>(b, b, b, Y, b, bb, OP_N, gi, b, bb, OP_C, nullptr, 0, 0, c.gl(i), b, bb, T(1), T(0), ne, nullptr), st))) return s;
+    if ((s = gemm<T>(P, gargs<T>(b, b, b, gi, b, bb, OP_N, SLi, b, bb, OP_N, nullptr, 0, 0, Y, b, bb, 1.0, 0.0, ne, nullptr), st))) return s;
+    if ((s = gemm<T>(P, gargs<T>(b, b, b, Y, b, bb, OP_N, gi, b, bb, OP_C, nullptr, 0, 0, c.gl(i), b, bb, 1.0, 0.0, ne, nullptr), st))) return s;
   }
 
   // ---- 3. backward sweep.  With P = g_i U_i, Z = V_i g_i, Q = V_i g^<_i:
@@ -465,19 +513,19 @@ qtx_status solve_chunk(qtx_rgf_plan_s* P, const qtx_rgf_inputs* in, const qtx_rg
     cx<T>* GLu = c.tmp(10);
     cx<T>* gi = c.g(i);
     cx<T>* gli = c.gl(i);
-    auto MM = [&](const cx<T>* A, long sA_, int opA, const cx<T>* B, long sB_, int opB, const cx<T>* C0, cx<T>* C, T al, T be) {
+    auto MM = [&](const cx<T>* A, long sA_, int opA, const cx<T>* B, long sB_, int opB, const cx<T>* C0, cx<T>* C, double al, double be) {
       return gemm<T>(P, gargs<T>(b, b, b, A, b, sA_, opA, B, b, sB_, opB, C0, b, bb, C, b, bb, al, be, ne, nullptr), st);
     };
-    if ((s = MM(gi, bb, OP_N, U(i), sUV, OP_N, nullptr, Pm, T(1), T(0)))) return s;
-    if ((s = MM(V(i), sUV, OP_N, gi, bb, OP_N, nullptr, Z, T(1), T(0)))) return s;
-    if ((s = MM(GRn, bb, OP_N, Z, bb, OP_N, nullptr, GRl, T(-1), T(0)))) return s;
-    if ((s = MM(Pm, bb, OP_N, GRn, bb, OP_N, nullptr, GRu, T(-1), T(0)))) return s;
-    if ((s = MM(Pm, bb, OP_N, GRl, bb, OP_N, gi, gi, T(-1), T(1)))) return s;   // g_i <- G_ii
-    if ((s = MM(V(i), sUV, OP_N, gli, bb, OP_N, nullptr, Q, T(1), T(0)))) return s;
-    if ((s = MM(GRu, bb, OP_N, Q, bb, OP_N, nullptr, K, T(-1), T(0)))) return s;
-    if ((s = MM(Pm, bb, OP_N, GLn, bb, OP_N, nullptr, PGL, T(1), T(0)))) return s;
-    if ((s = MM(PGL, bb, OP_N, Pm, bb, OP_C, gli, gli, T(1), T(1)))) return s;   // g^<_i + PGL P^H
-    if ((s = MM(GRn, bb, OP_N, Q, bb, OP_N, nullptr, X2, T(1), T(0)))) return s;
+    if ((s = MM(gi, bb, OP_N, U(i), sUV, OP_N, nullptr, Pm, 1.0, 0.0))) return s;
+    if ((s = MM(V(i), sUV, OP_N, gi, bb, OP_N, nullptr, Z, 1.0, 0.0))) return s;
+    if ((s = MM(GRn, bb, OP_N, Z, bb, OP_N, nullptr, GRl, -1.0, 0.0))) return s;
+    if ((s = MM(Pm, bb, OP_N, GRn, bb, OP_N, nullptr, GRu, -1.0, 0.0))) return s;
+    if ((s = MM(Pm, bb, OP_N, GRl, bb, OP_N, gi, gi, -1.0, 1.0))) return s;   // g_i <- G_ii
+    if ((s = MM(V(i), sUV, OP_N, gli, bb, OP_N, nullptr, Q, 1.0, 0.0))) return s;
+    if ((s = MM(GRu, bb, OP_N, Q, bb, OP_N, nullptr, K, -1.0, 0.0))) return s;
+    if ((s = MM(Pm, bb, OP_N, GLn, bb, OP_N, nullptr, PGL, 1.0, 0.0))) return s;
+    if ((s = MM(PGL, bb, OP_N, Pm, bb, OP_C, gli, gli, 1.0, 1.0))) return s;   // g^<_i + PGL P^H
+    if ((s = MM(GRn, bb, OP_N, Q, bb, OP_N, nullptr, X2, 1.0, 0.0))) return s;
     {
       Term<T> t0; t0.p = gli; t0.s = bb; t0.alpha = 1.0;
       Term<T> t1; t1.p = K; t1.s = bb; t1.alpha = 1.0;
@@ -615,6 +663,11 @@ qtx_status qtx_rgf_plan_create(const qtx_rgf_desc* desc, qtx_rgf_plan* out) {
     std::vector<cx<double>> I((size_t)P->bb, mk<double>(0, 0));
     for (int i = 0; i < P->b; ++i) I[(size_t)i * P->b + i] = mk<double>(1, 0);
     e = cudaMemcpy(P->ws + P->L.ident, I.data(), I.size() * sizeof(cx<double>), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+      std::vector<float> Idf((size_t)P->bb * 4, 0.f);  // (re.hi, re.lo, im.hi, im.lo)
+      for (int i = 0; i < P->b; ++i) Idf[((size_t)i * P->b + i) * 4] = 1.f;
+      e = cudaMemcpy(P->ws + P->L.ident_df, Idf.data(), Idf.size() * sizeof(float), cudaMemcpyHostToDevice);
+    }
   }
   if (e != cudaSuccess) {
     g_create_error = std::string("plan setup: ") + cudaGetErrorString(e);
@@ -640,7 +693,10 @@ qtx_status qtx_rgf_solve(qtx_rgf_plan P, const qtx_rgf_inputs* in, const qtx_rgf
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   P->last = st;
   P->worst = 0;
-  qtx_status s = P->d.precision == QTX_FP32 ? solve_all<float>(P, in, out, st) : solve_all<double>(P, in, out, st);
+  qtx_status s;
+  if (P->d.precision == QTX_FP32) s = solve_all<float>(P, in, out, st);
+  else if (P->d.precision == QTX_FP64) s = solve_all<double>(P, in, out, st);
+  else s = solve_all<df>(P, in, out, st);
   if (s == QTX_OK) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) { P->err = cudaGetErrorString(e); return QTX_ERR_CUDA; }
@@ -685,5 +741,180 @@ size_t qtx_rgf_footprint(const qtx_rgf_desc* desc) {
 }
 
 const char* qtx_rgf_version(void) { return "qtx-rgf 0.1 (sm_103a)"; }
+
+}  // extern "C"
+
+// ============================================================================ component ABI
+namespace {
+
+template <typename T>
+qtx_status zgemm_via(int precision, int M, int N, int K, int opA, const void* A, long lda, long sA, int opB,
+                     const void* B, long ldb, long sB, double alpha, double beta, const void* C0, long ldc0,
+                     long sC0, void* C, long ldc, long sC, int batch, cudaStream_t st, std::string& err) {
+  const int rA = opA == OP_N ? M : K, cA = opA == OP_N ? K : M;
+  const int rB = opB == OP_N ? K : N, cB = opB == OP_N ? N : K;
+  const int nA = sA ? batch : 1, nB = sB ? batch : 1, nC0 = (C0 && beta != 0.0) ? (sC0 ? batch : 1) : 0;
+  const size_t es = sizeof(cx<T>);
+  void *a = nullptr, *b = nullptr, *c0 = nullptr, *c = nullptr, *scr = nullptr;
+  int* flag = nullptr;
+  const int digits = precision == QTX_EMU64 ? 6 : 2;
+  const size_t scr_bytes = std::is_same<T, df>::value ? gemm_tc_scratch_bytes(M, N, K, batch, digits) : 0;
+  cudaError_t e = cudaSuccess;
+  qtx_status s = QTX_OK;
+  auto CK = [&](cudaError_t x) {
+    if (x != cudaSuccess && e == cudaSuccess) e = x;
+    return x == cudaSuccess;
+  };
+  CK(cudaMallocAsync(&a, es * (size_t)nA * rA * cA, st));
+  CK(cudaMallocAsync(&b, es * (size_t)nB * rB * cB, st));
+  if (nC0) CK(cudaMallocAsync(&c0, es * (size_t)nC0 * M * N, st));
+  CK(cudaMallocAsync(&c, es * (size_t)batch * M * N, st));
+  if (scr_bytes) CK(cudaMallocAsync(&scr, scr_bytes, st));
+  CK(cudaMallocAsync((void**)&flag, sizeof(int), st));
+  if (e == cudaSuccess) {
+    CK(cudaMemsetAsync(flag, 0, sizeof(int), st));
+    CK(convert_strided<double, T>((const cx<double>*)A, lda, sA, (cx<T>*)a, cA, (long)rA * cA, rA, cA, nA, st));
+    CK(convert_strided<double, T>((const cx<double>*)B, ldb, sB, (cx<T>*)b, cB, (long)rB * cB, rB, cB, nB, st));
+    if (nC0) CK(convert_strided<double, T>((const cx<double>*)C0, ldc0, sC0, (cx<T>*)c0, N, (long)M * N, M, N, nC0, st));
+  }
+  if (e == cudaSuccess) {
+    if constexpr (std::is_same<T, df>::value) {
+      TcArgs t;
+      t.M = M; t.N = N; t.K = K;
+      t.A = (const cx<df>*)a; t.lda = cA; t.sA = nA > 1 ? (long)rA * cA : 0; t.opA = opA;
+      t.B = (const cx<df>*)b; t.ldb = cB; t.sB = nB > 1 ? (long)rB * cB : 0; t.opB = opB;
+      t.C0 = nC0 ? (const cx<df>*)c0 : nullptr; t.ldc0 = N; t.sC0 = nC0 > 1 ? (long)M * N : 0;
+      t.C = (cx<df>*)c; t.ldc = N; t.sC = (long)M * N;
+      t.alpha = (float)alpha; t.beta = nC0 ? (float)beta : 0.f;
+      t.batch = batch; t.active = nullptr;
+      CK(gemm_tc(t, digits, scr, scr_bytes, flag, st));
+    } else {
+      GemmArgs<T> g;
+      g.M = M; g.N = N; g.K = K;
+      g.A = (const cx<T>*)a; g.lda = cA; g.sA = nA > 1 ? (long)rA * cA : 0; g.opA = opA;
+      g.B = (const cx<T>*)b; g.ldb = cB; g.sB = nB > 1 ? (long)rB * cB : 0; g.opB = opB;
+      g.C0 = nC0 ? (const cx<T>*)c0 : nullptr; g.ldc0 = N; g.sC0 = nC0 > 1 ? (long)M * N : 0;
+      g.C = (cx<T>*)c; g.ldc = N; g.sC = (long)M * N;
+      g.alpha = alpha; g.beta = nC0 ? beta : 0.0;
+      g.batch = batch; g.active = nullptr;
+      CK(gemm_simt<T>(g, st));
+    }
+    CK(convert_strided<T, double>((const cx<T>*)c, N, (long)M * N, (cx<double>*)C, ldc, sC, M, N, batch, st));
+  }
+  int hflag = 0;
+  if (e == cudaSuccess) CK(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  for (void* p : {a, b, c0, c, scr, (void*)flag})
+    if (p) cudaFreeAsync(p, st);
+  if (e == cudaSuccess) CK(cudaStreamSynchronize(st));
+  if (e != cudaSuccess) {
+    err = cudaGetErrorString(e);
+    cudaGetLastError();
+    return QTX_ERR_CUDA;
+  }
+  if (hflag) { err = "tensor-core engine: bounded wait expired"; s = QTX_ERR_TIMEOUT; }
+  return s;
+}
+
+template <typename T>
+qtx_status zinv_via(qtx_rgf_plan_s* P, int n, void* A, long sA, int batch, int* status, cudaStream_t st) {
+  cx<T>* X = reinterpret_cast<cx<T>*>(P->ws + P->L.g);
+  const long nn = (long)n * n;
+  QTX_CK((convert_strided<double, T>((const cx<double>*)A, n, sA, X, n, nn, n, n, batch, st)));
+  qtx_status s = block_inverse<T>(P, X, n, batch, nullptr, status, st);
+  if (s) return s;
+  QTX_CK((convert_strided<T, double>(X, n, nn, (cx<double>*)A, n, sA, n, n, batch, st)));
+  return QTX_OK;
+}
+template <>
+qtx_status zinv_via<double>(qtx_rgf_plan_s* P, int n, void* A, long sA, int batch, int* status, cudaStream_t st) {
+  cx<double>* X = reinterpret_cast<cx<double>*>(P->ws + P->L.g);
+  const long nn = (long)n * n;
+  QTX_CK(cudaMemcpy2DAsync(X, nn * sizeof(cx<double>), A, sA * sizeof(cx<double>), nn * sizeof(cx<double>), batch,
+                           cudaMemcpyDeviceToDevice, st));
+  qtx_status s = block_inverse<double>(P, X, n, batch, nullptr, status, st);
+  if (s) return s;
+  QTX_CK(cudaMemcpy2DAsync(A, sA * sizeof(cx<double>), X, nn * sizeof(cx<double>), nn * sizeof(cx<double>), batch,
+                           cudaMemcpyDeviceToDevice, st));
+  return QTX_OK;
+}
+
+thread_local std::string g_kernel_error;
+
+}  // namespace
+
+extern "C" {
+
+qtx_status qtx_zgemm_batched(int precision, int M, int N, int K, int opA, const void* A, long lda, long sA, int opB,
+                             const void* B, long ldb, long sB, double alpha, double beta, const void* C0, long ldc0,
+                             long sC0, void* C, long ldc, long sC, int batch, void* stream) {
+  if (M < 0 || N < 0 || K < 0 || batch < 1 || !A || !B || !C || (beta != 0.0 && !C0) ||
+      (opA != OP_N && opA != OP_C) || (opB != OP_N && opB != OP_C)) {
+    g_kernel_error = "qtx_zgemm_batched: invalid argument";
+    return QTX_ERR_INVALID_ARG;
+  }
+  if (M == 0 || N == 0) return QTX_OK;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  switch (precision) {
+    case QTX_FP64: return zgemm_via<double>(precision, M, N, K, opA, A, lda, sA, opB, B, ldb, sB, alpha, beta, C0, ldc0, sC0, C, ldc, sC, batch, st, g_kernel_error);
+    case QTX_FP32: return zgemm_via<float>(precision, M, N, K, opA, A, lda, sA, opB, B, ldb, sB, alpha, beta, C0, ldc0, sC0, C, ldc, sC, batch, st, g_kernel_error);
+    case QTX_EMU64:
+    case QTX_BF16X3:
+      if (!tc_available()) { g_kernel_error = "tensor-core engine needs an sm_103 GPU"; return QTX_ERR_UNSUPPORTED; }
+      return zgemm_via<df>(precision, M, N, K, opA, A, lda, sA, opB, B, ldb, sB, alpha, beta, C0, ldc0, sC0, C, ldc, sC, batch, st, g_kernel_error);
+    default:
+      g_kernel_error = "unknown precision";
+      return QTX_ERR_INVALID_ARG;
+  }
+}
+
+qtx_status qtx_zinv_batched(int precision, int n, void* A, long sA, int batch, int refine_iter, int* status, void* stream) {
+  if (n < 1 || n > 1024 || batch < 1 || !A || refine_iter < 0) return QTX_ERR_INVALID_ARG;
+  qtx_rgf_desc d{};
+  d.n_blocks = 1;
+  d.block_size = n;
+  d.max_energies_in_flight = batch;
+  d.precision = (qtx_precision)precision;
+  d.refine_max_iter = refine_iter;
+  qtx_rgf_plan P = nullptr;
+  qtx_status s = qtx_rgf_plan_create(&d, &P);
+  if (s) return s;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  int* stat = status;
+  if (!stat) stat = reinterpret_cast<int*>(P->ws + P->L.flags);
+  if (!status) cudaMemsetAsync(stat, 0, sizeof(int) * batch, st);
+  if (precision == QTX_FP32) s = zinv_via<float>(P, n, A, sA, batch, stat, st);
+  else if (precision == QTX_FP64) s = zinv_via<double>(P, n, A, sA, batch, stat, st);
+  else s = zinv_via<df>(P, n, A, sA, batch, stat, st);
+  cudaError_t e = cudaStreamSynchronize(st);
+  qtx_rgf_destroy(P);
+  if (s == QTX_OK && e != cudaSuccess) s = QTX_ERR_CUDA;
+  return s;
+}
+
+qtx_status qtx_lead_self_energy(int n, const void* H00, const void* H01, const double* energies, int n_energies,
+                                double eta, double tol, int max_iter, void* SigR, int* status, void* stream) {
+  if (n < 1 || n > 1024 || n_energies < 1 || !H00 || !H01 || !energies || !SigR || max_iter < 1 || !(tol > 0))
+    return QTX_ERR_INVALID_ARG;
+  qtx_rgf_desc d{};
+  d.n_blocks = 1;
+  d.block_size = n;
+  d.max_energies_in_flight = n_energies;
+  d.precision = QTX_FP64;
+  d.leads = 1;
+  d.decim_tol = tol;
+  d.decim_max_iter = max_iter;
+  qtx_rgf_plan P = nullptr;
+  qtx_status s = qtx_rgf_plan_create(&d, &P);
+  if (s) return s;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  int* stat = status ? status : reinterpret_cast<int*>(P->ws + P->L.flags) + 2 * P->Ec;
+  cudaMemsetAsync(stat, 0, sizeof(int) * n_energies, st);
+  Ctx<double> c{P, st, n_energies, energies, stat, (long)n * n, n};
+  s = contact<double>(c, (const cx<double>*)H00, (const cx<double>*)H01, eta, (cx<double>*)SigR);
+  cudaError_t e = cudaStreamSynchronize(st);
+  qtx_rgf_destroy(P);
+  if (s == QTX_OK && e != cudaSuccess) s = QTX_ERR_CUDA;
+  return s;
+}
 
 }  // extern "C"

@@ -73,8 +73,8 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
     for (int j = 0; j < TN; ++j) {
       const int n = n0 + tx + j * TX;
       if (n >= g.N) continue;
-      cx<T> r = g.alpha * acc[i][j];
-      if (C0 && g.beta != T(0)) r = r + g.beta * C0[(long)m * g.ldc0 + n];
+      cx<T> r = T(g.alpha) * acc[i][j];
+      if (C0 && g.beta != 0.0) r = r + T(g.beta) * C0[(long)m * g.ldc0 + n];
       C[(long)m * g.ldc + n] = r;
     }
   }
@@ -237,8 +237,8 @@ __global__ void __launch_bounds__(256) k_combine(cx<Tout>* out, long sOut, Term<
         const int r = r0 + ty + 8 * q, c = c0 + tx;
         if (r < b && c < b) {
           const cx<Tin> v = X[(long)r * b + c];
-          accr[q] += T_.alpha * (double)v.re;
-          acci[q] += T_.alpha * (double)v.im;
+          accr[q] += T_.alpha * to_d(v.re);
+          acci[q] += T_.alpha * to_d(v.im);
         }
       }
     } else {
@@ -247,14 +247,14 @@ __global__ void __launch_bounds__(256) k_combine(cx<Tout>* out, long sOut, Term<
       for (int q = 0; q < 4; ++q) {  // tile[cc][rr] = X[c0+cc][r0+rr]
         const int rr = tx, cc = ty + 8 * q;
         const int xr = c0 + cc, xc = r0 + rr;
-        tile[cc][rr] = (xr < b && xc < b) ? X[(long)xr * b + xc] : mk<Tin>(0, 0);
+        tile[cc][rr] = (xr < b && xc < b) ? X[(long)xr * b + xc] : cvt<Tin>(mk<double>(0, 0));
       }
       __syncthreads();
 #pragma unroll
       for (int q = 0; q < 4; ++q) {  // out(r, c) gets conj(X(c, r)) = conj(tile[c - c0][r - r0])
         const cx<Tin> v = tile[tx][ty + 8 * q];
-        accr[q] += T_.alpha * (double)v.re;
-        acci[q] -= T_.alpha * (double)v.im;
+        accr[q] += T_.alpha * to_d(v.re);
+        acci[q] -= T_.alpha * to_d(v.im);
       }
     }
   }
@@ -266,7 +266,10 @@ __global__ void __launch_bounds__(256) k_combine(cx<Tout>* out, long sOut, Term<
     if (r < b && c < b) {
       double vr = accr[q], vi = acci[q];
       if (r == c && diag_coef != 0.0) { vr += zr; vi += zi; }
-      O[(long)r * b + c] = mk<Tout>((Tout)vr, (Tout)vi);
+      cx<Tout> o;
+      o.re = from_d<Tout>(vr);
+      o.im = from_d<Tout>(vi);
+      O[(long)r * b + c] = o;
     }
   }
 }
@@ -283,6 +286,11 @@ template cudaError_t combine<double, double>(cx<double>*, long, Term<double>, Te
 template cudaError_t combine<float, float>(cx<float>*, long, Term<float>, Term<float>, Term<float>, int, int, const double*, double, double, const int*, cudaStream_t);
 template cudaError_t combine<float, double>(cx<double>*, long, Term<float>, Term<float>, Term<float>, int, int, const double*, double, double, const int*, cudaStream_t);
 template cudaError_t combine<double, float>(cx<float>*, long, Term<double>, Term<double>, Term<double>, int, int, const double*, double, double, const int*, cudaStream_t);
+template cudaError_t combine<df, df>(cx<df>*, long, Term<df>, Term<df>, Term<df>, int, int, const double*, double, double, const int*, cudaStream_t);
+template cudaError_t combine<df, double>(cx<double>*, long, Term<df>, Term<df>, Term<df>, int, int, const double*, double, double, const int*, cudaStream_t);
+template cudaError_t combine<df, float>(cx<float>*, long, Term<df>, Term<df>, Term<df>, int, int, const double*, double, double, const int*, cudaStream_t);
+template cudaError_t combine<float, df>(cx<df>*, long, Term<float>, Term<float>, Term<float>, int, int, const double*, double, double, const int*, cudaStream_t);
+template cudaError_t combine<double, df>(cx<df>*, long, Term<double>, Term<double>, Term<double>, int, int, const double*, double, double, const int*, cudaStream_t);
 
 template <typename T>
 __global__ void k_assemble_diag(cx<T>* out, const cx<double>* H, const cx<double>* S,
@@ -311,6 +319,7 @@ cudaError_t assemble_diag(cx<T>* out, const cx<double>* H, const cx<double>* S,
 }
 template cudaError_t assemble_diag<double>(cx<double>*, const cx<double>*, const cx<double>*, const cx<double>*, long, const cx<double>*, long, const double*, double, int, int, cudaStream_t);
 template cudaError_t assemble_diag<float>(cx<float>*, const cx<double>*, const cx<double>*, const cx<double>*, long, const cx<double>*, long, const double*, double, int, int, cudaStream_t);
+template cudaError_t assemble_diag<df>(cx<df>*, const cx<double>*, const cx<double>*, const cx<double>*, long, const cx<double>*, long, const double*, double, int, int, cudaStream_t);
 
 template <typename T>
 __global__ void k_axpby_from64(cx<T>* out, long sOut, const cx<double>* X, long sX, double c1,
@@ -333,6 +342,7 @@ cudaError_t axpby_from64(cx<T>* out, long sOut, const cx<double>* X, long sX, do
 }
 template cudaError_t axpby_from64<double>(cx<double>*, long, const cx<double>*, long, double, const cx<double>*, long, double, int, int, cudaStream_t);
 template cudaError_t axpby_from64<float>(cx<float>*, long, const cx<double>*, long, double, const cx<double>*, long, double, int, int, cudaStream_t);
+template cudaError_t axpby_from64<df>(cx<df>*, long, const cx<double>*, long, double, const cx<double>*, long, double, int, int, cudaStream_t);
 
 template <typename T>
 __global__ void k_assemble_offdiag(cx<T>* U, cx<T>* V, const cx<double>* Hup, const cx<double>* Sup,
@@ -381,6 +391,46 @@ cudaError_t assemble_offdiag(cx<T>* U, cx<T>* V, const cx<double>* Hup, const cx
 }
 template cudaError_t assemble_offdiag<double>(cx<double>*, cx<double>*, const cx<double>*, const cx<double>*, const double*, double, int, int, cudaStream_t);
 template cudaError_t assemble_offdiag<float>(cx<float>*, cx<float>*, const cx<double>*, const cx<double>*, const double*, double, int, int, cudaStream_t);
+template cudaError_t assemble_offdiag<df>(cx<df>*, cx<df>*, const cx<double>*, const cx<double>*, const double*, double, int, int, cudaStream_t);
+
+template <typename T>
+__global__ void k_add_identity(cx<T>* X, long sX, int n, const int* active) {
+  const int e = blockIdx.y;
+  if (active && !active[e]) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) X[(long)e * sX + (long)i * n + i].re += T(1);
+}
+template <typename T>
+cudaError_t add_identity(cx<T>* X, long sX, int n, int batch, const int* active, cudaStream_t st) {
+  dim3 grid((n + 127) / 128, batch);
+  k_add_identity<T><<<grid, 128, 0, st>>>(X, sX, n, active);
+  return cudaGetLastError();
+}
+template cudaError_t add_identity<double>(cx<double>*, long, int, int, const int*, cudaStream_t);
+template cudaError_t add_identity<float>(cx<float>*, long, int, int, const int*, cudaStream_t);
+
+// ============================================================================ strided conversion
+template <typename Tin, typename Tout>
+__global__ void k_convert(const cx<Tin>* in, long ldi, long si, cx<Tout>* out, long ldo, long so, int rows,
+                          int cols) {
+  const int e = blockIdx.z;
+  const int r = blockIdx.y;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < cols; c += gridDim.x * blockDim.x)
+    out[(long)e * so + (long)r * ldo + c] = cvt<Tout>(in[(long)e * si + (long)r * ldi + c]);
+}
+template <typename Tin, typename Tout>
+cudaError_t convert_strided(const cx<Tin>* in, long ldi, long si, cx<Tout>* out, long ldo, long so, int rows,
+                            int cols, int batch, cudaStream_t st) {
+  if (rows <= 0 || cols <= 0 || batch <= 0) return cudaSuccess;
+  dim3 grid((cols + 127) / 128 < 8 ? (cols + 127) / 128 : 8, rows, batch);
+  k_convert<Tin, Tout><<<grid, 128, 0, st>>>(in, ldi, si, out, ldo, so, rows, cols);
+  return cudaGetLastError();
+}
+template cudaError_t convert_strided<double, double>(const cx<double>*, long, long, cx<double>*, long, long, int, int, int, cudaStream_t);
+template cudaError_t convert_strided<double, float>(const cx<double>*, long, long, cx<float>*, long, long, int, int, int, cudaStream_t);
+template cudaError_t convert_strided<float, double>(const cx<float>*, long, long, cx<double>*, long, long, int, int, int, cudaStream_t);
+template cudaError_t convert_strided<double, df>(const cx<double>*, long, long, cx<df>*, long, long, int, int, int, cudaStream_t);
+template cudaError_t convert_strided<df, double>(const cx<df>*, long, long, cx<double>*, long, long, int, int, int, cudaStream_t);
 
 // ============================================================================ observables
 __device__ __forceinline__ double block_sum(double v) {
@@ -423,13 +473,14 @@ cudaError_t obs_current(double* cur, long ldcur, const cx<double>* Hup, const cx
 }
 template cudaError_t obs_current<double>(double*, long, const cx<double>*, const cx<double>*, const cx<double>*, long, const double*, int, int, cudaStream_t);
 template cudaError_t obs_current<float>(double*, long, const cx<double>*, const cx<double>*, const cx<float>*, long, const double*, int, int, cudaStream_t);
+template cudaError_t obs_current<df>(double*, long, const cx<double>*, const cx<double>*, const cx<df>*, long, const double*, int, int, cudaStream_t);
 
 template <typename T>
 __global__ void k_obs_density(double* den, long ldden, const cx<T>* GL, long sG, int b) {
   const int e = blockIdx.x;
   const cx<T>* G = GL + (long)e * sG;
   double s = 0.0;
-  for (int i = threadIdx.x; i < b; i += blockDim.x) s += (double)G[(long)i * b + i].im;
+  for (int i = threadIdx.x; i < b; i += blockDim.x) s += to_d(G[(long)i * b + i].im);
   s = block_sum(s);
   if (threadIdx.x == 0) den[(long)e * ldden] = s;
 }
@@ -440,6 +491,7 @@ cudaError_t obs_density(double* den, long ldden, const cx<T>* GL, long sG, int b
 }
 template cudaError_t obs_density<double>(double*, long, const cx<double>*, long, int, int, cudaStream_t);
 template cudaError_t obs_density<float>(double*, long, const cx<float>*, long, int, int, cudaStream_t);
+template cudaError_t obs_density<df>(double*, long, const cx<df>*, long, int, int, cudaStream_t);
 
 // scale * Part Tr[X Y - Z W],  Part = Re (part 0) or Im (part 1);  Tr[X Y] = sum_jk X_jk Y_kj
 template <typename T>
@@ -472,6 +524,7 @@ cudaError_t obs_trace2(double* out, long ld, const cx<double>* X, long sX, const
 }
 template cudaError_t obs_trace2<double>(double*, long, const cx<double>*, long, const cx<double>*, long, const cx<double>*, long, const cx<double>*, long, int, int, cudaStream_t, int, double);
 template cudaError_t obs_trace2<float>(double*, long, const cx<double>*, long, const cx<float>*, long, const cx<double>*, long, const cx<float>*, long, int, int, cudaStream_t, int, double);
+template cudaError_t obs_trace2<df>(double*, long, const cx<double>*, long, const cx<df>*, long, const cx<double>*, long, const cx<df>*, long, int, int, cudaStream_t, int, double);
 
 __global__ void __launch_bounds__(256) k_obs_frob_dot(double* out, long ld, const cx<double>* X, long sX,
                                                       const cx<double>* Y, long sY, double scale, int b) {

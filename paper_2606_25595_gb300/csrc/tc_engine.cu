@@ -1,10 +1,561 @@
-// Tensor-core engine (sm_103a tcgen05): emulated-precision batched complex GEMM.
+// Tensor-core engine for sm_103a: batched complex GEMM with emulated precision on tcgen05.
+//
+// C[e] = alpha * op(A[e]) * op(B[e]) + beta * C0[e]   (complex, df32 storage, e = batch index)
+//
+// Method (Ozaki-style slicing, paper Sec. II-C: operands are split into lower-precision slices whose
+// partial products are recombined): every row of op(A) and every column of op(B) is scaled by a
+// power of two 2^(P - e) (e: exponent of its largest entry) and rounded to a P-bit integer v, which is
+// written as S balanced base-128 digits  v = sum_i d_i 128^(S-i),  |d_1| <= 2^(l1-1), |d_i| <= 64.
+// Digit i is stored pre-scaled as d_i * 2^(-7(i-1)) in a bf16 "digit plane" (exact: <= 7 significant
+// bits).  The products of digit planes i, j with i + j <= S + 1 run on the tensor cores (kind::f16,
+// bf16 inputs, FP32 accumulation in TMEM) into five accumulators (480 of the 512 TMEM columns):
+//     acc0..acc3: i + j = 2, 3, 4, 5,     acc4: i + j >= 6.
+// acc0..acc3 hold integers times 2^(-7 (i+j-2)) whose magnitudes stay below 2^24 units (the bound l1
+// of the leading digit shrinks with K to guarantee it), so their FP32 sums are exact whatever
+// rounding the tensor core's accumulator applies; only acc4, at ~2^-24 of the product, is rounded
+// (the accumulation truncates, so its error grows with the number of MMA steps: ~2^-38 at K = 256).
+// The epilogue adds the five in 64-bit fixed point, applies the row/column scales and writes df32.
+// With S = 6 digits (21 digit products) the products carry ~41 bits for K <= 256 (the "emulated FP64"
+// mode); with S = 2 (3 digit products) they carry ~13 bits ("BF16x3").
+//
+// Complex arithmetic uses the real embedding (4M form):
+//     [D_re | D_im] = [A_re | A_im] * [[B_re, B_im], [-B_im, B_re]]
+// so one MMA chain with N = 96 real columns produces 48 complex columns.  The right operand's
+// digit planes are stored transposed (N x K, K-major) with rows permuted so that the 48 "re" rows
+// and the 48 "im" rows of each CTA tile are contiguous.
+//
+// Kernel structure (one CTA per 128 x 48 complex output tile, 6 warps):
+//   warp 0   TMA producer: 3-D tiled loads (32 K-elements x 128 rows x 1 plane, 64B swizzle) of the
+//            S A-planes and S B-planes of one K-stage into shared memory, mbarrier expect-tx;
+//   warp 1   allocates 512 TMEM columns; one thread issues the tcgen05.mma's (2 K16 steps x pairs)
+//            and tcgen05.commit's the stage back to the producer;
+//   warps 2-5 epilogue: tcgen05.ld of the three accumulators, fixed-point recombination, df32 store.
+// Every mbarrier wait is bounded (2 s of %globaltimer); on expiry the kernel sets *err and unwinds.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <cstring>
+#include <mutex>
+
+
+#include "df32.cuh"
 #include "kernels.cuh"
 
 namespace qtx {
-bool tc_available() { return false; }
-size_t gemm_tc_scratch_bytes(int, int, int, int, const TcConfig&) { return 0; }
-cudaError_t gemm_tc(const GemmArgs<double>&, const TcConfig&, void*, size_t, int*, cudaStream_t) {
-  return cudaErrorNotSupported;
+namespace tc {
+
+constexpr int BM = 128;        // output rows per CTA (TMEM lanes)
+constexpr int BNC = 48;        // complex output columns per CTA
+constexpr int BNR = 2 * BNC;   // real (embedded) columns per CTA = MMA N
+constexpr int BKS = 32;        // bf16 K elements per stage (64-byte rows, 64B swizzle)
+constexpr int TILE_A = BM * BKS * 2;   // bytes of one A-plane tile (128 rows)
+constexpr int TILE_B = BNR * BKS * 2;  // bytes of one B-plane tile (96 rows)
+constexpr int ACC_COLS = BNR;  // TMEM columns per accumulator
+constexpr int FIX = 40;        // fractional bits of the fixed-point recombination
+constexpr int DW = 7;          // bits per digit below the leading one
+
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t n) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(n) : "memory");
 }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(su32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Bounded wait: gives up after ~2 s, raising *err.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, int* err) {
+  if (mbar_try(b, parity)) return true;
+  const uint64_t t0 = gtimer();
+  while (true) {
+    for (int i = 0; i < 64; ++i)
+      if (mbar_try(b, parity)) return true;
+    if (*((volatile int*)err)) return false;
+    if (gtimer() - t0 > 2000000000ull) {
+      atomicExch(err, 1);
+      return false;
+    }
+    __nanosleep(128);
+  }
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];"
+      ::"r"(su32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(su32(bar)), "r"(x), "r"(y), "r"(z)
+      : "memory");
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: K-major, 64-byte swizzle, 8-row groups 512 bytes apart.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1u << 16;            // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(512u >> 4) << 32;   // stride byte offset
+  d |= (uint64_t)1u << 46;            // descriptor version for tcgen05
+  d |= (uint64_t)4u << 61;            // 64-byte swizzle
+  return d;
+}
+// Instruction descriptor: kind::f16, D = F32, A = B = BF16, both K-major, M = 128, N = 96.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BNR >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ void mma(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+      ::"r"(dtmem), "l"(ad), "l"(bd), "r"(kIdesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar)) : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// accumulator of digit pair (i, j): exact groups i + j = 2..5, then one rounded group
+__host__ __device__ constexpr int acc_of(int i, int j) { return (i + j <= 5) ? (i + j - 2) : 4; }
+__host__ __device__ constexpr int n_acc(int S) { return S + 1 >= 6 ? 5 : S; }
+
+// ------------------------------------------------------------------------------ GEMM kernel
+struct TcParams {
+  const int* eA;   // [batch][M_pad] row exponents of op(A)
+  const int* eB;   // [batch][N_pad] column exponents of op(B)
+  int M_pad, N_pad, nks;  // nks: K-stages of 32 over the embedded K (2 * K_pad)
+  int M, N;
+  cx<df>* C; long ldc, sC;
+  const cx<df>* C0; long ldc0, sC0;
+  float alpha, beta;
+  int escale;      // total exponent shift: (2 l1 - 2) + FIX
+  int a_batched, b_batched;  // 0: the operand is shared by the whole batch (digitized once)
+  const int* active;
+  int* err;
+};
+
+template <int S, int NST>
+__global__ void __launch_bounds__(192, 1)
+    k_tc_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, TcParams p) {
+  constexpr int STAGE = S * (TILE_A + TILE_B);
+  constexpr int NACC = n_acc(S);
+  extern __shared__ unsigned char smem_raw[];
+  const int e = blockIdx.z;
+  if (p.active && !p.active[e]) return;
+  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(base + NST * STAGE);
+  uint64_t* empty = full + NST;
+  uint64_t* accb = empty + NST;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(accb + 1);
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int nblk = blockIdx.x, mblk = blockIdx.y;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NST; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accb, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)), "r"(512) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tslot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      for (int ks = 0; ks < p.nks; ++ks) {
+        const int s = ks % NST;
+        const uint32_t ph = (uint32_t)(ks / NST) & 1u;
+        if (!mbar_wait(&empty[s], ph ^ 1u, p.err)) break;
+        mbar_expect_tx(&full[s], STAGE);
+        unsigned char* st = base + s * STAGE;
+        for (int d = 0; d < S; ++d) {
+          tma_load_3d(st + d * TILE_A, &mapA, &full[s], ks * BKS, mblk * BM, (p.a_batched ? e : 0) * S + d);
+          tma_load_3d(st + S * TILE_A + d * TILE_B, &mapB, &full[s], ks * BKS, nblk * BNR, (p.b_batched ? e : 0) * S + d);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      uint32_t started = 0;  // bit g set once accumulator g has been written
+      bool ok = true;
+      for (int ks = 0; ks < p.nks && ok; ++ks) {
+        const int s = ks % NST;
+        const uint32_t ph = (uint32_t)(ks / NST) & 1u;
+        if (!mbar_wait(&full[s], ph, p.err)) { ok = false; break; }
+        fence_after();
+        const uint32_t sa = su32(base + s * STAGE);
+#pragma unroll
+        for (int kk = 0; kk < 2; ++kk) {
+#pragma unroll
+          for (int i = 1; i <= S; ++i) {
+#pragma unroll
+            for (int j = 1; j <= S + 1 - i; ++j) {
+              const int g = acc_of(i, j);
+              const uint64_t ad = sdesc(sa + (i - 1) * TILE_A + kk * 32);
+              const uint64_t bd = sdesc(sa + S * TILE_A + (j - 1) * TILE_B + kk * 32);
+              mma(tmem + g * ACC_COLS, ad, bd, (started >> g) & 1u);
+              started |= 1u << g;
+            }
+          }
+        }
+        mma_commit(&empty[s]);
+      }
+      mma_commit(accb);
+    }
+  } else {
+    // epilogue: warps 2..5 -> TMEM lane quarters 2, 3, 0, 1
+    const int q = warp & 3;
+    const int r = q * 32 + lane;
+    const int m = mblk * BM + r;
+    const bool got = mbar_wait(accb, 0, p.err);
+    fence_after();
+    if (got) {
+      const int eAm = p.eA[(long)(p.a_batched ? e : 0) * p.M_pad + m];
+      const int* eBrow = p.eB + (long)(p.b_batched ? e : 0) * p.N_pad;
+      const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16);
+      cx<df>* Crow = p.C + (long)e * p.sC + (long)m * p.ldc;
+      const cx<df>* C0row = p.C0 ? p.C0 + (long)e * p.sC0 + (long)m * p.ldc0 : nullptr;
+#pragma unroll 1
+      for (int c0 = 0; c0 < BNC; c0 += 16) {
+        float hv[2][16], lv[2][16];
+#pragma unroll
+        for (int part = 0; part < 2; ++part) {  // 0: real columns, 1: imaginary columns
+          long long I[16];
+#pragma unroll
+          for (int c = 0; c < 16; ++c) I[c] = 0;
+#pragma unroll
+          for (int g = 0; g < NACC; ++g) {
+            uint32_t v[16];
+            tmem_ld16(trow + g * ACC_COLS + part * BNC + c0, v);
+            tmem_wait_ld();
+#pragma unroll
+            for (int c = 0; c < 16; ++c) I[c] += f2fix(__uint_as_float(v[c]), FIX);
+          }
+#pragma unroll
+          for (int c = 0; c < 16; ++c) {
+            hv[part][c] = __ll2float_rn(I[c]);
+            lv[part][c] = __ll2float_rn(I[c] - __float2ll_rz(hv[part][c]));
+          }
+        }
+        if (m < p.M) {
+#pragma unroll
+          for (int c = 0; c < 16; ++c) {
+            const int n = nblk * BNC + c0 + c;
+            if (n >= p.N) break;
+            const int Es = eAm + eBrow[n] - p.escale;
+            df vr = mkdf(scale2(hv[0][c], Es) * p.alpha, scale2(lv[0][c], Es) * p.alpha);
+            df vi = mkdf(scale2(hv[1][c], Es) * p.alpha, scale2(lv[1][c], Es) * p.alpha);
+            if (C0row && p.beta != 0.f) {
+              const cx<df> c0v = C0row[n];
+              vr = df_add(vr, df_mulf(c0v.re, p.beta));
+              vi = df_add(vi, df_mulf(c0v.im, p.beta));
+            }
+            cx<df> o;
+            o.re = vr;
+            o.im = vi;
+            Crow[n] = o;
+          }
+        }
+      }
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+  }
+}
+
+// ------------------------------------------------------------------------------ digitizer
+// Per-row exponent of the logical operand L (R x K): L(r, k) = X[r][k] (direct) or X[k][r]
+// (transposed).  e[r] = max over k of the exponent of max(|Re|, |Im|) (hi parts).
+__global__ void k_row_expo(const cx<df>* X, long ldx, long sX, int R, int K, int R_pad, int transposed,
+                           int* eout, const int* active) {
+  const int e = blockIdx.y;
+  if (active && !active[e]) return;
+  const cx<df>* Xe = X + (long)e * sX;
+  if (!transposed) {  // one warp per row
+    const int r = blockIdx.x * 8 + threadIdx.x / 32, lane = threadIdx.x % 32;
+    if (r >= R_pad) return;
+    int mx = -1000;
+    if (r < R)
+      for (int k = lane; k < K; k += 32) {
+        const cx<df> v = Xe[(long)r * ldx + k];
+        mx = max(mx, max(df_expo(v.re.hi), df_expo(v.im.hi)));
+      }
+    for (int off = 16; off > 0; off >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    if (lane == 0) eout[(long)e * R_pad + r] = mx;
+  } else {  // one thread per logical row (a column of X): coalesced across threads
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R_pad) return;
+    int mx = -1000;
+    if (r < R)
+      for (int k = 0; k < K; ++k) {
+        const cx<df> v = Xe[(long)k * ldx + r];
+        mx = max(mx, max(df_expo(v.re.hi), df_expo(v.im.hi)));
+      }
+    eout[(long)e * R_pad + r] = mx;
+  }
+}
+
+// v = round((hi + lo) * 2^sh), then S balanced base-128 digits (d_1 most significant).
+template <int S>
+__device__ __forceinline__ void digits_of(df x, int sh, int (&d)[S]) {
+  long long t = f2fix(x.hi, sh) + f2fix(x.lo, sh);
+#pragma unroll
+  for (int i = S - 1; i >= 1; --i) {
+    const int di = (int)((t + 64) & 127) - 64;
+    d[i] = di;
+    t = (t - di) >> DW;
+  }
+  d[0] = (int)t;
+}
+
+// Digit planes of one operand.  side 0 (left, A = op(X), M x K): plane[e][i][r][k] = digit_i(Re L),
+// plane[e][i][r][K_pad + k] = digit_i(Im L).  side 1 (right, B = op(X), K x N, logical row r = column
+// n of B): rows re = (n/64)*128 + n%64 and im = re + 64 of the embedded, transposed operand:
+//   [re row] = [ Re B(:,n) | -Im B(:,n) ],   [im row] = [ Im B(:,n) | Re B(:,n) ].
+template <int S>
+__global__ void __launch_bounds__(256) k_digitize(const cx<df>* X, long ldx, long sX, int R, int K,
+                                                  int R_pad, int K_pad, int transposed, int conj_,
+                                                  int side, const int* eR, int P, __nv_bfloat16* planes,
+                                                  long rows_plane, const int* active) {
+  const int e = blockIdx.z;
+  if (active && !active[e]) return;
+  __shared__ cx<df> tile[32][33];
+  const int k0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
+  const cx<df>* Xe = X + (long)e * sX;
+  const cx<df> zero = {mkdf(0.f, 0.f), mkdf(0.f, 0.f)};
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int a = ty + 8 * q;
+    if (!transposed) {  // tile[a][tx] = L(r0 + a, k0 + tx) = X[r0 + a][k0 + tx]
+      const int r = r0 + a, k = k0 + tx;
+      tile[a][tx] = (r < R && k < K) ? Xe[(long)r * ldx + k] : zero;
+    } else {            // tile[tx][a] = L(r0 + tx, k0 + a) = X[k0 + a][r0 + tx]
+      const int r = r0 + tx, k = k0 + a;
+      tile[tx][a] = (r < R && k < K) ? Xe[(long)k * ldx + r] : zero;
+    }
+  }
+  __syncthreads();
+  const long plane_elems = rows_plane * (2L * K_pad);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int rr = ty + 8 * q, r = r0 + rr, k = k0 + tx;
+    if (r >= R_pad) continue;
+    cx<df> v = tile[rr][tx];
+    if (conj_) v.im = df_neg(v.im);
+    const int sh = P - eR[(long)e * R_pad + r];
+    int dr[S], di[S];
+    digits_of<S>(v.re, sh, dr);
+    digits_of<S>(v.im, sh, di);
+    __nv_bfloat16* pe = planes + (long)e * S * plane_elems;
+#pragma unroll
+    for (int i = 0; i < S; ++i) {
+      const float sc = __int_as_float((127 - DW * i) << 23);  // 2^(-7 i)
+      __nv_bfloat16* pl = pe + (long)i * plane_elems;
+      if (side == 0) {
+        pl[(long)r * 2 * K_pad + k] = __float2bfloat16_rn((float)dr[i] * sc);
+        pl[(long)r * 2 * K_pad + K_pad + k] = __float2bfloat16_rn((float)di[i] * sc);
+      } else {
+        const long rre = (long)(r / BNC) * BNR + (r % BNC), rim = rre + BNC;
+        pl[rre * 2 * K_pad + k] = __float2bfloat16_rn((float)dr[i] * sc);
+        pl[rre * 2 * K_pad + K_pad + k] = __float2bfloat16_rn(-(float)di[i] * sc);
+        pl[rim * 2 * K_pad + k] = __float2bfloat16_rn((float)di[i] * sc);
+        pl[rim * 2 * K_pad + K_pad + k] = __float2bfloat16_rn((float)dr[i] * sc);
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------ host side
+struct Dims {
+  int M_pad, N_pad, K_pad, l1, P;
+};
+inline Dims dims_of(int M, int N, int K, int S) {
+  Dims d;
+  d.M_pad = (M + BM - 1) / BM * BM;
+  d.N_pad = (N + BNC - 1) / BNC * BNC;
+  d.K_pad = (K + 31) / 32 * 32;
+  // Leading digit bound L = 2^(l1-1), others 64: per K term the exact groups are bounded by
+  //   i+j=2: L^2,  3: 2 L 64,  4: 2 L 64 + 64^2,  5: 2 L 64 + 2 * 64^2
+  // units, so with Keff = 2 K_pad terms they stay below 2^24 for l1 = 7 up to Keff = 512 and
+  // l1 = 6 up to Keff = 1024.  Beyond that (b > 512) i+j = 5 is no longer guaranteed exact.
+  const int Keff = 2 * d.K_pad;
+  d.l1 = Keff <= 512 ? 7 : (Keff <= 1024 ? 6 : 5);
+  d.P = DW * (S - 1) + d.l1 - 1;
+  return d;
+}
+struct Scratch {
+  __nv_bfloat16 *pa, *pb;
+  int *ea, *eb;
+  size_t bytes;
+};
+inline Scratch carve(void* base, const Dims& d, int batch, int S) {
+  auto al = [](size_t x) { return (x + 1023) & ~size_t(1023); };
+  Scratch s;
+  unsigned char* p = reinterpret_cast<unsigned char*>(base);
+  const size_t a = al((size_t)batch * S * d.M_pad * 2 * d.K_pad * sizeof(__nv_bfloat16));
+  const size_t b = al((size_t)batch * S * 2 * d.N_pad * 2 * d.K_pad * sizeof(__nv_bfloat16));  // 2 N_pad rows
+  const size_t ea = al((size_t)batch * d.M_pad * sizeof(int));
+  const size_t eb = al((size_t)batch * d.N_pad * sizeof(int));
+  s.pa = reinterpret_cast<__nv_bfloat16*>(p);
+  s.pb = reinterpret_cast<__nv_bfloat16*>(p + a);
+  s.ea = reinterpret_cast<int*>(p + a + b);
+  s.eb = reinterpret_cast<int*>(p + a + b + ea);
+  s.bytes = a + b + ea + eb;
+  return s;
+}
+
+typedef CUresult (*EncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                             const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                             CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeFn encode_fn() {
+  static EncodeFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeFn>(f);
+  });
+  return fn;
+}
+
+// 3-D map over digit planes: x = 2*K_pad (contiguous), y = plane rows, z = batch*S planes; box
+// 32 x box_rows x 1.
+bool make_map(CUtensorMap* m, void* ptr, int K2, int rows, int zdim, int box_rows) {
+  EncodeFn fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t gdim[3] = {(cuuint64_t)K2, (cuuint64_t)rows, (cuuint64_t)zdim};
+  cuuint64_t gstr[2] = {(cuuint64_t)K2 * 2, (cuuint64_t)K2 * 2 * rows};
+  cuuint32_t box[3] = {(cuuint32_t)BKS, (cuuint32_t)box_rows, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, ptr, gdim, gstr, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int S>
+cudaError_t digitize(const cx<df>* X, long ldx, long sX, int opX, int side, int R, int K, const Dims& d,
+                     int* eout, __nv_bfloat16* planes, int batch, const int* active, cudaStream_t st) {
+  // logical row r of the operand: left A = op(X): row r of op(X); right B = op(X): column r of op(X)
+  //   left  N: X[r][k] direct      left  H: conj(X[k][r]) transposed
+  //   right N: X[k][r] transposed  right H: conj(X[r][k]) direct
+  const int transposed = (side == 0) ? (opX == OP_C) : (opX == OP_N);
+  const int cj = opX == OP_C;
+  const int R_pad = side == 0 ? d.M_pad : d.N_pad;
+  if (!transposed) {
+    dim3 g((R_pad + 7) / 8, batch);
+    k_row_expo<<<g, 256, 0, st>>>(X, ldx, sX, R, K, R_pad, 0, eout, active);
+  } else {
+    dim3 g((R_pad + 127) / 128, batch);
+    k_row_expo<<<g, 128, 0, st>>>(X, ldx, sX, R, K, R_pad, 1, eout, active);
+  }
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  const long rows_plane = side == 0 ? d.M_pad : 2L * d.N_pad;
+  dim3 g(d.K_pad / 32, (R_pad + 31) / 32, batch);
+  k_digitize<S><<<g, 256, 0, st>>>(X, ldx, sX, R, K, R_pad, d.K_pad, transposed, cj, side, eout, d.P, planes,
+                                   rows_plane, active);
+  return cudaGetLastError();
+}
+
+template <int S, int NST>
+cudaError_t launch(const TcArgs& a, void* scratch, size_t scratch_bytes, int* err_flag, cudaStream_t st) {
+  const Dims d = dims_of(a.M, a.N, a.K, S);
+  Scratch s = carve(scratch, d, a.batch, S);
+  if (s.bytes > scratch_bytes) return cudaErrorInvalidValue;
+  cudaError_t e;
+  const int ab = a.sA != 0, bb_ = a.sB != 0;
+  if ((e = digitize<S>(a.A, a.lda, a.sA, a.opA, 0, a.M, a.K, d, s.ea, s.pa, ab ? a.batch : 1, ab ? a.active : nullptr, st))) return e;
+  if ((e = digitize<S>(a.B, a.ldb, a.sB, a.opB, 1, a.N, a.K, d, s.eb, s.pb, bb_ ? a.batch : 1, bb_ ? a.active : nullptr, st))) return e;
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, s.pa, 2 * d.K_pad, d.M_pad, (ab ? a.batch : 1) * S, BM)) return cudaErrorInvalidConfiguration;
+  if (!make_map(&mb, s.pb, 2 * d.K_pad, 2 * d.N_pad, (bb_ ? a.batch : 1) * S, BNR)) return cudaErrorInvalidConfiguration;
+  TcParams p;
+  p.eA = s.ea;
+  p.eB = s.eb;
+  p.M_pad = d.M_pad;
+  p.N_pad = d.N_pad;
+  p.nks = 2 * d.K_pad / BKS;
+  p.M = a.M;
+  p.N = a.N;
+  p.C = a.C;
+  p.ldc = a.ldc;
+  p.sC = a.sC;
+  p.C0 = a.C0;
+  p.ldc0 = a.ldc0;
+  p.sC0 = a.sC0;
+  p.alpha = a.alpha;
+  p.beta = a.beta;
+  p.escale = (2 * d.l1 - 2) + FIX;
+  p.a_batched = ab;
+  p.b_batched = bb_;
+  p.active = a.active;
+  p.err = err_flag;
+  const size_t smem = (size_t)NST * S * (TILE_A + TILE_B) + 1024 + 256;
+  static bool attr = false;
+  if (!attr) {
+    if ((e = cudaFuncSetAttribute(k_tc_gemm<S, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
+    attr = true;
+  }
+  dim3 grid(d.N_pad / BNC, d.M_pad / BM, a.batch);
+  k_tc_gemm<S, NST><<<grid, 192, smem, st>>>(ma, mb, p);
+  return cudaGetLastError();
+}
+
+}  // namespace tc
+
+bool tc_available() {
+  int dev = 0, major = 0, minor = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  return major == 10 && minor == 3 && tc::encode_fn() != nullptr;
+}
+
+size_t gemm_tc_scratch_bytes(int M, int N, int K, int batch, int digits) {
+  const tc::Dims d = tc::dims_of(M, N, K, digits);
+  return tc::carve(nullptr, d, batch, digits).bytes + 4096;
+}
+
+cudaError_t gemm_tc(const TcArgs& a, int digits, void* scratch, size_t scratch_bytes, int* err_flag,
+                    cudaStream_t st) {
+  if (a.M <= 0 || a.N <= 0 || a.batch <= 0) return cudaSuccess;
+  if (digits == 6) return tc::launch<6, 2>(a, scratch, scratch_bytes, err_flag, st);
+  if (digits == 2) return tc::launch<2, 4>(a, scratch, scratch_bytes, err_flag, st);
+  return cudaErrorInvalidValue;
+}
+
 }  // namespace qtx

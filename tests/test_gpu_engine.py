@@ -1,0 +1,124 @@
+"""GPU checks of the building blocks through the component C ABI (include/qtx_kernels.h):
+the tensor-core GEMM engine (emulated FP64 and BF16x3), the batched block inverse with
+refinement, and the Sancho-Rubio contact self-energy."""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def q():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_2606_25595_gb300 import build
+    build.build()
+    import paper_2606_25595_gb300 as q
+    q.load()
+    return q
+
+
+def _t(x):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=torch.complex128).cuda()
+
+
+def _op(X, op):
+    return X if op == "N" else np.conj(np.swapaxes(X, -1, -2))
+
+
+SHAPES = [(128, 64, 32, 1), (130, 70, 50, 3), (16, 16, 16, 4), (256, 256, 256, 2), (33, 200, 300, 2)]
+
+
+@pytest.mark.parametrize("M,N,K,batch", SHAPES)
+@pytest.mark.parametrize("opA,opB", [("N", "N"), ("C", "N"), ("N", "C"), ("C", "C")])
+def test_emu64_integer_inputs_are_exact(q, M, N, K, batch, opA, opB):
+    """Integer operands: every digit product is exact, so the result equals the integer product
+    bit for bit (pins digits, scales, the complex embedding, the TMA/UMMA layouts and the epilogue)."""
+    rng = np.random.default_rng(M * 7 + N * 3 + K)
+    sa = (batch, M, K) if opA == "N" else (batch, K, M)
+    sb = (batch, K, N) if opB == "N" else (batch, N, K)
+    A = rng.integers(-500, 501, sa) + 1j * rng.integers(-500, 501, sa)
+    B = rng.integers(-500, 501, sb) + 1j * rng.integers(-500, 501, sb)
+    C0 = rng.integers(-1000, 1001, (batch, M, N)) + 1j * rng.integers(-1000, 1001, (batch, M, N))
+    ref = -(_op(A, opA) @ _op(B, opB)) + C0
+    got = q.zgemm_batched(_t(A), _t(B), "emu64", opA, opB, alpha=-1.0, beta=1.0, C0=_t(C0)).cpu().numpy()
+    assert np.array_equal(got, ref)
+
+
+def test_emu64_shared_operand_and_zero_rows(q):
+    """A 2-D operand is shared across the batch (digitised once); an all-zero row stays zero."""
+    rng = np.random.default_rng(5)
+    A = rng.standard_normal((3, 96, 80)) + 1j * rng.standard_normal((3, 96, 80))
+    A[1, 7, :] = 0
+    B = rng.standard_normal((80, 72)) + 1j * rng.standard_normal((80, 72))
+    got = q.zgemm_batched(_t(A), _t(B), "emu64").cpu().numpy()
+    ref = A @ B
+    assert np.all(got[1, 7] == 0)
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-10
+
+
+@pytest.mark.parametrize("M,N,K,batch", [(256, 256, 256, 3), (130, 70, 50, 2), (64, 192, 128, 2)])
+def test_emu64_random_error_bound(q, M, N, K, batch):
+    """Random FP64 data: |C - C_ref| <= 2^-36 * (|A| |B|) elementwise (~41-bit digit products with
+    row/column scaling; the rounded accumulator and the df32 rounding of inputs sit below that)."""
+    rng = np.random.default_rng(M + N + K)
+    A = (rng.standard_normal((batch, M, K)) + 1j * rng.standard_normal((batch, M, K))) * \
+        np.exp(rng.uniform(-3, 3, (batch, M, 1)))
+    B = rng.standard_normal((batch, K, N)) + 1j * rng.standard_normal((batch, K, N))
+    got = q.zgemm_batched(_t(A), _t(B), "emu64").cpu().numpy()
+    ref = A @ B
+    bound = (np.abs(A.real) + np.abs(A.imag)) @ (np.abs(B.real) + np.abs(B.imag))
+    assert np.all(np.abs(got - ref) <= 2.0 ** -36 * bound)
+
+
+def test_bf16x3_error_bound(q):
+    """Two digit planes (~13-bit products): |C - C_ref| <= 2^-11 * (|A| |B|)."""
+    rng = np.random.default_rng(11)
+    A = rng.standard_normal((2, 128, 96)) + 1j * rng.standard_normal((2, 128, 96))
+    B = rng.standard_normal((2, 96, 64)) + 1j * rng.standard_normal((2, 96, 64))
+    got = q.zgemm_batched(_t(A), _t(B), "bf16x3").cpu().numpy()
+    ref = A @ B
+    bound = (np.abs(A.real) + np.abs(A.imag)) @ (np.abs(B.real) + np.abs(B.imag))
+    assert np.all(np.abs(got - ref) <= 2.0 ** -11 * bound)
+
+
+# relative error bound per mode, as a multiple of kappa(A): FP64 / FP32 unit roundoff, and for the
+# emulated mode the ~2^-36 of its tensor-core products (Eq. 6: error ~ kappa * eps_m)
+INV_EPS = {"fp64": 2.0 ** -53, "fp32": 2.0 ** -24, "emu64": 2.0 ** -38}
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "emu64"])
+@pytest.mark.parametrize("n", [16, 64, 100, 256])
+def test_block_inverse(q, prec, n):
+    """Batched inverse of accretive blocks (E + i eta - H - Sigma^R) against LAPACK:
+    relative error <= 64 kappa(A) eps_mode."""
+    dev = W.random_device(n, 3, n_energies=1, seed=n)
+    A = np.stack([(0.37 + 1e-6j) * np.eye(n) - dev["H_diag"][i] - dev["SigR"][0, i] for i in range(3)])
+    ref = np.linalg.inv(A)
+    X, st = q.zinv_batched(_t(A), prec, refine_iter=2)
+    X = X.cpu().numpy()
+    assert np.all(st.cpu().numpy() == 0)
+    for e in range(3):
+        kap = np.linalg.cond(A[e])
+        err = np.linalg.norm(X[e] - ref[e]) / np.linalg.norm(ref[e])
+        assert err < 64 * kap * INV_EPS[prec], (err, kap)
+
+
+def test_lead_self_energy_matches_oracle(q):
+    import torch
+    s = W.strip(n_blocks=2, disorder=0.0)
+    E = np.linspace(-3.5, 3.5, 17)
+    eta = 1e-3
+    SR, st = q.lead_self_energy(_t(s["leads"]["H00_L"]), _t(s["leads"]["H01_L"]),
+                                torch.as_tensor(E).cuda(), eta)
+    SR = SR.cpu().numpy()
+    assert np.all(st.cpu().numpy() == 0)
+    for k, e in enumerate(E):
+        ref, _, _, kap = O.lead_self_energy(e, eta, s["leads"]["H00_L"], s["leads"]["H01_L"],
+                                           track_cond=True)
+        assert np.linalg.norm(SR[k] - ref) / np.linalg.norm(ref) < max(1e-12, 1e4 * kap * 2.0 ** -53)
