@@ -1,0 +1,372 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the RGF selected inversion on GB300: prints ONE JSON line.
+
+Workload (default): the batched mixed-precision device -- b = 256 complex blocks, N_B = 64 slices,
+N_E = 512 energies on [-2, 2], dense random Hermitian diagonal blocks, coupling blocks of variance
+0.3/b, block-diagonal scattering self-energies (seeded synthetic data, see ``workloads``).  One
+step = one ``qtx_rgf_solve`` of all 512 energies (forward and backward sweeps, G^R/G^< diagonal
+blocks kept resident in HBM, per-slice current and density and their energy integrals), in the
+emulated-FP64 mode (tensor-core digit products) unless ``--precision`` says otherwise.
+
+Also measured in the same run: the plain FP64 path on a subset of the same energies, the
+product kernel's live duration (CUDA events on the solve stream) for the roofline, the end-to-end
+rate through the C ABI with host buffers, the CPU FP64 oracle on a bounded sample (and the error of
+the GPU result at those energies), and the SM clocks during the timed region.
+
+``--impl reference`` times the CPU FP64 oracle instead (bounded sample per step).
+Multi-GPU (torchrun): every rank solves its own 512-energy batch on its own GPU with no
+collective in the data path (weak scaling); timing is max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "RGF energy-points/s vs FP64 path at <=1e-6 rel. current error; p50/p99 latency"
+UNIT = "energy-points/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="emu64", choices=["emu64", "fp32", "bf16x3", "fp64"])
+    ap.add_argument("--chunk", type=int, default=128, help="energies in flight per chunk")
+    ap.add_argument("--block", type=int, default=256)
+    ap.add_argument("--slices", type=int, default=64)
+    ap.add_argument("--energies", type=int, default=512)
+    ap.add_argument("--fp64-energies", type=int, default=16, help="energies for the FP64 comparison (0 = skip)")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU oracle sample")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 1, 0
+    import torch
+    import torch.distributed as dist
+    lr = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(lr)
+    dist.init_process_group("nccl")
+    return dist.get_rank(), ws, lr
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, ws):
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", self.uuid, f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        out, _ = self.p.communicate(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def cpu_oracle_sample(dev, budget_s, idx_pool):
+    """Time the FP64 oracle on host cores for as many energies of the pool as fit the budget."""
+    import oracle as O
+    t0 = time.perf_counter()
+    done, res = [], {}
+    for k in idx_pool:
+        r = O.rgf_energy(float(dev["energies"][k]), dev, int(k))
+        res[int(k)] = (r["current"], r["density"])
+        done.append(int(k))
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return done, res, dt
+
+
+def run_reference(args):
+    import workloads as W
+    dev = W.random_device(args.block, args.slices, n_energies=args.energies, seed=0)
+    per_step = 2
+    import numpy as np
+    pool = list(np.linspace(0, args.energies - 1, per_step * (args.steps + args.warmup)).astype(int))
+    for w in range(args.warmup):
+        cpu_oracle_sample(dev, 1e9, pool[w * per_step:(w + 1) * per_step])
+    t = 0.0
+    n = 0
+    for s in range(args.steps):
+        sl = pool[(args.warmup + s) * per_step:(args.warmup + s + 1) * per_step]
+        done, _, dt = cpu_oracle_sample(dev, 1e9, sl)
+        t += dt
+        n += len(done)
+    value = n / t
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"random BT device b={args.block} N_B={args.slices} "
+                                   f"N_E={args.energies} on [-2,2], scattering self-energies",
+                       "global_batch": args.energies, "precision": "fp64-oracle"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{per_step} energies of the {args.energies}-energy grid per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, ws, lr = dist_init()
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args)
+        return
+    import numpy as np
+    import torch
+
+    from paper_2606_25595_gb300 import build as qbuild
+    qbuild.build()
+    import paper_2606_25595_gb300 as q
+    import workloads as W
+
+    torch.cuda.set_device(lr)
+    dev = W.random_device(args.block, args.slices, n_energies=args.energies, seed=0)
+    nb, b, ne = args.slices, args.block, args.energies
+    din = q.upload(dev)
+    outs = ["GR_diag", "GL_diag", "current", "density", "integrals"]
+    desc = q.make_desc(nb, b, args.precision, min(args.chunk, ne), refine_max_iter=2,
+                       has_scattering=True, outputs=outs)
+    plan = q.Plan(desc)
+    cd = torch.device("cuda")
+    GR = torch.empty((ne, nb, b, b), dtype=torch.complex128, device=cd)
+    GL = torch.empty((ne, nb, b, b), dtype=torch.complex128, device=cd)
+    cur = torch.empty((ne, nb - 1), dtype=torch.float64, device=cd)
+    den = torch.empty((ne, nb), dtype=torch.float64, device=cd)
+    cint = torch.empty(nb - 1, dtype=torch.float64, device=cd)
+    dint = torch.empty(nb, dtype=torch.float64, device=cd)
+    stat = torch.zeros(ne, dtype=torch.int32, device=cd)
+    o = q.Outputs()
+    o.GR_diag, o.GL_diag = GR.data_ptr(), GL.data_ptr()
+    o.current, o.density = cur.data_ptr(), den.data_ptr()
+    o.current_int, o.density_int = cint.data_ptr(), dint.data_ptr()
+    o.status_per_energy = stat.data_ptr()
+    stream = torch.cuda.current_stream()
+
+    def step():
+        plan.solve(din["_inputs"], o, stream.cuda_stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    # ---------------------------------------------------------------- timed region (device)
+    sampler = ClockSampler(str(torch.cuda.get_device_properties(lr).uuid)
+                           if str(torch.cuda.get_device_properties(lr).uuid).startswith("GPU-")
+                           else "GPU-" + str(torch.cuda.get_device_properties(lr).uuid))
+    plan.set_profiling(True)
+    barrier(ws)
+    torch.cuda.synchronize()
+    sampler.start()
+    l0 = q.kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    launches = q.kernel_launches() - l0
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    prof = plan.gemm_profile()
+    plan.set_profiling(False)
+    ms_max = max_over_ranks(ms, ws)
+    status_ok = bool(torch.all(stat == 0).item())
+    value = ws * ne * args.steps / (ms_max / 1e3)
+
+    # ---------------------------------------------------------------- roofline of the product kernel
+    peaks, peak_src = measured_peaks()
+    if args.precision in ("emu64", "bf16x3"):
+        peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+        bound, kernel = "tensor", "k_tc_gemm (tcgen05 bf16 digit products)"
+    elif args.precision == "fp32":
+        peak, bound, kernel = 69.7, "alu", "k_gemm<float> (SIMT FFMA)"
+    else:
+        peak, bound, kernel = 1.1, "alu", "k_gemm<double> (SIMT DFMA)"
+    avg_ms = prof["ms"] / max(prof["launches"], 1)
+    achieved = (prof["pipe_flops"] / max(prof["launches"], 1)) / (avg_ms / 1e3) / 1e12 if prof["launches"] else None
+    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "kernel": kernel, "launches": prof["launches"], "avg_launch_ms": avg_ms,
+                "share_of_step": prof["ms"] / ms if ms else None,
+                "useful_fp64_equiv_tflops": (prof["useful_flops"] / (prof["ms"] / 1e3) / 1e12) if prof["ms"] else None,
+                "peak_source": f"{peak_src} ({'bf16 sustained' if bound == 'tensor' else 'cuBLAS/torch matmul on this GPU'})"}
+
+    # ---------------------------------------------------------------- end to end (host buffers)
+    e2e = None
+    if not args.no_e2e:
+        host = {k: v.cpu().pin_memory() for k, v in din.items()
+                if isinstance(v, torch.Tensor)}
+        hc = torch.empty_like(cur, device="cpu").pin_memory()
+        hd = torch.empty_like(den, device="cpu").pin_memory()
+        hci = torch.empty_like(cint, device="cpu").pin_memory()
+        hdi = torch.empty_like(dint, device="cpu").pin_memory()
+        h2d = sum(t.numel() * t.element_size() for t in host.values())
+        d2h = sum(t.numel() * t.element_size() for t in (hc, hd, hci, hdi))
+
+        def e2e_step():
+            for k, t in host.items():
+                din[k].copy_(t, non_blocking=True)
+            step()
+            hc.copy_(cur, non_blocking=True)
+            hd.copy_(den, non_blocking=True)
+            hci.copy_(cint, non_blocking=True)
+            hdi.copy_(dint, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        barrier(ws)
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        f1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = max_over_ranks(f0.elapsed_time(f1), ws)
+        e2e = {"value": ws * ne * args.steps / (e2e_ms / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+    # ---------------------------------------------------------------- FP64 path on a subset
+    fp64 = None
+    if args.fp64_energies > 0 and args.precision != "fp64":
+        nsub = min(args.fp64_energies, ne)
+        idx = np.linspace(0, ne - 1, nsub).astype(int)
+        Esub = dev["energies"][idx]
+        p64 = q.Plan(q.make_desc(nb, b, "fp64", nsub, has_scattering=True,
+                                 outputs=["current", "density"]))
+        din64 = q.upload(dev, Esub)
+        c64 = torch.empty((nsub, nb - 1), dtype=torch.float64, device=cd)
+        d64 = torch.empty((nsub, nb), dtype=torch.float64, device=cd)
+        o64 = q.Outputs()
+        o64.current, o64.density = c64.data_ptr(), d64.data_ptr()
+        p64.solve(din64["_inputs"], o64, stream.cuda_stream)  # warm-up
+        torch.cuda.synchronize()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        p64.solve(din64["_inputs"], o64, stream.cuda_stream)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        t64 = g0.elapsed_time(g1) / 1e3
+        c_h, d_h = cur[idx].cpu().numpy(), den[idx].cpu().numpy()
+        c64n, d64n = c64.cpu().numpy(), d64.cpu().numpy()
+        fp64 = {"value": ws * nsub / t64, "unit": UNIT, "energies_timed": int(nsub),
+                "speedup_of_headline": value / (ws * nsub / t64),
+                "headline_vs_fp64_gpu": {
+                    "current": float(np.abs(c_h - c64n).max() / np.abs(c64n).max()),
+                    "density": float(np.abs(d_h - d64n).max() / np.abs(d64n).max())}}
+        del p64
+
+    # ---------------------------------------------------------------- CPU oracle sample + error
+    cpu = None
+    err = None
+    if rank == 0 and ws == 1:
+        pool = list(np.linspace(0, ne - 1, 64).astype(int))
+        rng = np.random.default_rng(7)
+        rng.shuffle(pool)
+        done, res, dt = cpu_oracle_sample(dev, args.cpu_seconds, pool)
+        cpu = {"value": len(done) / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{len(done)} of the {ne} energies (numpy complex128, LAPACK inv, "
+                         f"{dt:.1f} s)"}
+        c_g, d_g = cur.cpu().numpy(), den.cpu().numpy()
+        cr = np.stack([res[k][0] for k in done])
+        dr = np.stack([res[k][1] for k in done])
+        err = {"energies": len(done),
+               "current": float(np.abs(c_g[done] - cr).max() / np.abs(cr).max()),
+               "density": float(np.abs(d_g[done] - dr).max() / np.abs(dr).max())}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": {"emu64": "bf16-digits(tcgen05)+df32", "bf16x3": "bf16-digits(tcgen05)+df32",
+                          "fp32": "c64", "fp64": "c128"}[args.precision],
+                "data": "synthetic",
+                "config": {"workload": f"random BT device b={b} N_B={nb} N_E={ne} on [-2,2], "
+                                       f"block-diagonal scattering self-energies (seed 0)",
+                           "global_batch": ne * ws, "precision": args.precision,
+                           "energies_in_flight": min(args.chunk, ne),
+                           "l2": "inputs and working set (>= 16 GB) larger than L2; no flush"},
+                "status_ok": status_ok,
+                "gpu_launches": int(launches),
+                "clocks": clocks, "roofline": roofline, "e2e": e2e, "fp64_path": fp64,
+                "cpu_baseline": cpu, "error_vs_oracle": err}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

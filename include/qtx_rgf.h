@@ -53,10 +53,11 @@ typedef enum {
 typedef enum {
   QTX_FP64 = 0,   /* complex128 throughout (SIMT DFMA) -- the plain FP64 path */
   QTX_FP32 = 1,   /* complex64 products and inverses (SIMT FFMA) */
-  QTX_BF16X3 = 2, /* products from 2 bf16 digit planes per operand, 3 digit products, tensor cores */
-  QTX_EMU64 = 3   /* emulated FP64: products from 5 bf16 integer digit planes per operand (15 exact
-                     digit products on tcgen05 tensor cores, Ozaki-style slicing), inverses in FP32
-                     refined with emulated-FP64 residuals */
+  QTX_BF16X3 = 2, /* products from 2 bf16 digit planes per operand (3 digit products, ~13-bit
+                     products) on the tcgen05 tensor cores; df32 storage; refined inverses */
+  QTX_EMU64 = 3   /* emulated FP64: products from 6 bf16 digit planes per operand (21 digit products
+                     on the tcgen05 tensor cores, Ozaki-style slicing, ~41-bit products), df32 storage,
+                     inverses in FP32 refined by Newton sweeps with emulated residuals */
 } qtx_precision;
 
 /* Output selection bits (qtx_rgf_desc.outputs).  A block is written only if its bit is set AND
@@ -83,7 +84,8 @@ typedef struct {
   int block_size;              /* b, 1 <= b <= 1024 */
   int max_energies_in_flight;  /* energies solved concurrently; workspace scales with it (>= 1) */
   qtx_precision precision;
-  int refine_max_iter;         /* Newton sweeps X += X (I - A X) per block inverse (QTX_EMU64) */
+  int refine_max_iter;         /* Newton sweeps X += X (I - A X) per block inverse (QTX_EMU64,
+                                  QTX_BF16X3; FP32/FP64 apply one step to recursed blocks > 64) */
   int has_S;                   /* 0: S = I (S pointers ignored) */
   int has_scattering;          /* 0: no scattering self-energies (Sigma pointers ignored) */
   int energy_dependent_sigma;  /* 0: one Sigma set [N_B][b][b] for all energies; 1: [N_E][N_B][b][b] */
@@ -143,6 +145,20 @@ size_t qtx_rgf_footprint(const qtx_rgf_desc *desc);
 
 /* Library version string. */
 const char *qtx_rgf_version(void);
+
+/* Profiling of the block products (the ZGEMM-class kernel that dominates the solve, Sec. IV).
+ * When enabled, every later product-kernel launch of this plan is bracketed by a pair of CUDA events
+ * recorded on the solve's stream (for the tensor-core modes, around the tcgen05 GEMM kernel itself,
+ * not the digit-plane preparation).  qtx_rgf_gemm_profile synchronises on those events and returns,
+ * since enabling or the previous query: the number of launches, their summed device time in
+ * milliseconds, the tensor-pipe (or FP pipe) flops issued, and the FP64-equivalent useful flops
+ * (8 M N K per complex product), then resets the counters.  Any output pointer may be NULL. */
+qtx_status qtx_rgf_set_profiling(qtx_rgf_plan plan, int enable);
+qtx_status qtx_rgf_gemm_profile(qtx_rgf_plan plan, long long *launches, double *ms,
+                                double *pipe_flops, double *useful_flops);
+
+/* Number of kernel launches this library has issued in this process (monotonic). */
+long long qtx_kernel_launches(void);
 
 #ifdef __cplusplus
 }

@@ -30,7 +30,8 @@ BLOCK_OUTPUTS = ("GR_diag", "GR_upper", "GR_lower", "GL_diag", "GL_upper", "GG_d
 # Every function the C ABI exports (checked by the CPU tests against include/*.h).
 EXPORTED = ("qtx_rgf_plan_create", "qtx_rgf_solve", "qtx_rgf_status", "qtx_rgf_destroy",
             "qtx_rgf_last_error", "qtx_rgf_footprint", "qtx_rgf_version", "qtx_zgemm_batched",
-            "qtx_zinv_batched", "qtx_lead_self_energy")
+            "qtx_zinv_batched", "qtx_lead_self_energy", "qtx_rgf_set_profiling",
+            "qtx_rgf_gemm_profile", "qtx_kernel_launches")
 
 
 class QtxError(RuntimeError):
@@ -100,6 +101,13 @@ def load() -> ctypes.CDLL:
     L.qtx_zinv_batched.restype = i
     L.qtx_lead_self_energy.argtypes = [i, vp, vp, vp, i, d, d, i, vp, vp, vp]
     L.qtx_lead_self_energy.restype = i
+    L.qtx_rgf_set_profiling.argtypes = [vp, i]
+    L.qtx_rgf_set_profiling.restype = i
+    L.qtx_rgf_gemm_profile.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(d),
+                                       ctypes.POINTER(d), ctypes.POINTER(d)]
+    L.qtx_rgf_gemm_profile.restype = i
+    L.qtx_kernel_launches.argtypes = []
+    L.qtx_kernel_launches.restype = ctypes.c_longlong
     _lib = L
     return L
 
@@ -123,6 +131,10 @@ def make_desc(n_blocks, block_size, precision="fp64", max_energies_in_flight=64,
                 int(refine_max_iter), int(bool(has_S)), int(bool(has_scattering)),
                 int(bool(energy_dependent_sigma)), int(bool(leads)), float(decim_tol),
                 int(decim_max_iter), int(outputs))
+
+
+def kernel_launches() -> int:
+    return int(load().qtx_kernel_launches())
 
 
 def footprint(desc: Desc) -> int:
@@ -151,6 +163,15 @@ class Plan:
 
     def status(self) -> int:
         return int(load().qtx_rgf_status(self._h))
+
+    def set_profiling(self, on: bool = True) -> None:
+        self._check(load().qtx_rgf_set_profiling(self._h, int(bool(on))))
+
+    def gemm_profile(self) -> dict:
+        n, ms, pf, uf = ctypes.c_longlong(), ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        self._check(load().qtx_rgf_gemm_profile(self._h, ctypes.byref(n), ctypes.byref(ms),
+                                                ctypes.byref(pf), ctypes.byref(uf)))
+        return dict(launches=n.value, ms=ms.value, pipe_flops=pf.value, useful_flops=uf.value)
 
     def close(self):
         if getattr(self, "_h", None):

@@ -1,9 +1,15 @@
 // Launchers of the SIMT kernels (simt.cu) and of the tensor-core engine (tc_engine.cu), called by the
 // host orchestration (rgf.cu).  All launchers are asynchronous on `st` and return the launch status.
 #pragma once
+#include <atomic>
+
 #include "common.cuh"
 
 namespace qtx {
+
+// Running count of kernel launches issued by this library (read by qtx_kernel_launches()).
+extern std::atomic<long long> g_launches;
+inline void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 // ---- batched complex GEMM on the CUDA cores (T = double: DFMA, T = float: FFMA)
 template <typename T>
@@ -95,8 +101,11 @@ cudaError_t integrate_add(double* acc, const double* val, long ld, int n, const 
 // ---- tensor-core engine (tc_engine.cu): emulated-precision batched complex GEMM on sm_103a.
 // `digits` bf16 digit planes per operand (6: ~41-bit products from 21 digit products; 2: ~13-bit
 // products from 3).  `scratch` holds the digit planes and scale exponents.
+// `ev` (optional, two events) brackets the tensor-core GEMM kernel itself (not the digitiser).
 cudaError_t gemm_tc(const TcArgs& a, int digits, void* scratch, size_t scratch_bytes, int* err_flag,
-                    cudaStream_t st);
+                    cudaStream_t st, cudaEvent_t* ev = nullptr);
+// digit products (pairs i + j <= digits + 1) the engine issues per real product
+inline int tc_pairs(int digits) { return digits * (digits + 1) / 2; }
 size_t gemm_tc_scratch_bytes(int M, int N, int K, int batch, int digits);
 bool tc_available();
 

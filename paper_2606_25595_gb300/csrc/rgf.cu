@@ -60,6 +60,23 @@ struct qtx_rgf_plan_s {
   std::vector<int> status_host;
   const int* out_status = nullptr;  // caller's per-energy status array of the last solve
   int out_status_n = 0;
+  // GEMM profiling (qtx_rgf_set_profiling): event pairs around each product-kernel launch
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  double pipe_flops = 0.0, useful_flops = 0.0;
+  cudaEvent_t* next_events() {
+    if (ev_used + 2 > ev_pool.size()) {
+      for (int k = 0; k < 256; ++k) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        ev_pool.push_back(e);
+      }
+    }
+    cudaEvent_t* r = &ev_pool[ev_used];
+    ev_used += 2;
+    return r;
+  }
 };
 
 namespace {
@@ -145,15 +162,26 @@ GemmArgs<T> gargs(int M, int N, int K, const cx<T>* A, long lda, long sA, int op
 template <typename T>
 qtx_status gemm(qtx_rgf_plan_s* P, const GemmArgs<T>& g, cudaStream_t st, bool force_simt = false);
 
-template <>
-qtx_status gemm<float>(qtx_rgf_plan_s* P, const GemmArgs<float>& g, cudaStream_t st, bool) {
-  QTX_CK(gemm_simt<float>(g, st));
+template <typename T>
+qtx_status gemm_simt_prof(qtx_rgf_plan_s* P, const GemmArgs<T>& g, cudaStream_t st) {
+  cudaEvent_t* ev = P->prof ? P->next_events() : nullptr;
+  if (ev) cudaEventRecord(ev[0], st);
+  QTX_CK(gemm_simt<T>(g, st));
+  if (ev) {
+    cudaEventRecord(ev[1], st);
+    const double f = 8.0 * g.M * g.N * g.K * g.batch;
+    P->pipe_flops += f;
+    P->useful_flops += f;
+  }
   return QTX_OK;
 }
 template <>
+qtx_status gemm<float>(qtx_rgf_plan_s* P, const GemmArgs<float>& g, cudaStream_t st, bool) {
+  return gemm_simt_prof<float>(P, g, st);
+}
+template <>
 qtx_status gemm<double>(qtx_rgf_plan_s* P, const GemmArgs<double>& g, cudaStream_t st, bool) {
-  QTX_CK(gemm_simt<double>(g, st));
-  return QTX_OK;
+  return gemm_simt_prof<double>(P, g, st);
 }
 inline int tc_digits(const qtx_rgf_desc& d) { return d.precision == QTX_EMU64 ? 6 : 2; }
 template <>
@@ -166,7 +194,13 @@ qtx_status gemm<df>(qtx_rgf_plan_s* P, const GemmArgs<df>& g, cudaStream_t st, b
   a.C = g.C; a.ldc = g.ldc; a.sC = g.sC;
   a.alpha = (float)g.alpha; a.beta = (float)g.beta;
   a.batch = g.batch; a.active = g.active;
-  QTX_CK(gemm_tc(a, tc_digits(P->d), P->ws + P->L.tc_scratch, P->L.tc_bytes, P->d_err_flag, st));
+  cudaEvent_t* ev = P->prof ? P->next_events() : nullptr;
+  QTX_CK(gemm_tc(a, tc_digits(P->d), P->ws + P->L.tc_scratch, P->L.tc_bytes, P->d_err_flag, st, ev));
+  if (ev) {
+    const double f = 8.0 * g.M * g.N * g.K * g.batch;
+    P->pipe_flops += f * tc_pairs(tc_digits(P->d));
+    P->useful_flops += f;
+  }
   return QTX_OK;
 }
 
@@ -723,8 +757,39 @@ qtx_status qtx_rgf_status(qtx_rgf_plan P) {
   return (qtx_status)P->worst;
 }
 
+qtx_status qtx_rgf_set_profiling(qtx_rgf_plan P, int enable) {
+  if (!P) return QTX_ERR_INVALID_ARG;
+  P->prof = enable != 0;
+  P->ev_used = 0;
+  P->pipe_flops = P->useful_flops = 0.0;
+  return QTX_OK;
+}
+
+qtx_status qtx_rgf_gemm_profile(qtx_rgf_plan P, long long* launches, double* ms, double* pipe_flops,
+                                double* useful_flops) {
+  if (!P) return QTX_ERR_INVALID_ARG;
+  double tot = 0.0;
+  for (size_t k = 0; k + 1 < P->ev_used; k += 2) {
+    cudaError_t e = cudaEventSynchronize(P->ev_pool[k + 1]);
+    float t = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, P->ev_pool[k], P->ev_pool[k + 1]);
+    if (e != cudaSuccess) { P->err = cudaGetErrorString(e); return QTX_ERR_CUDA; }
+    tot += t;
+  }
+  if (launches) *launches = (long long)(P->ev_used / 2);
+  if (ms) *ms = tot;
+  if (pipe_flops) *pipe_flops = P->pipe_flops;
+  if (useful_flops) *useful_flops = P->useful_flops;
+  P->ev_used = 0;
+  P->pipe_flops = P->useful_flops = 0.0;
+  return QTX_OK;
+}
+
+long long qtx_kernel_launches(void) { return g_launches.load(); }
+
 qtx_status qtx_rgf_destroy(qtx_rgf_plan P) {
   if (!P) return QTX_OK;
+  for (cudaEvent_t e : P->ev_pool) cudaEventDestroy(e);
   if (P->ws) cudaFree(P->ws);
   if (P->d_err_flag) cudaFree(P->d_err_flag);
   if (P->h_status) cudaFreeHost(P->h_status);

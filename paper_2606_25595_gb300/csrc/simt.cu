@@ -7,6 +7,8 @@
 
 namespace qtx {
 
+std::atomic<long long> g_launches{0};
+
 // ============================================================================ batched GEMM
 // Tile BM x BN of C per CTA, K staged through shared memory BK at a time; each thread owns a
 // TM x TN sub-grid interleaved with stride (BM/TM, BN/TN) so smem reads of a warp are contiguous.
@@ -84,6 +86,7 @@ template <typename T, int BM, int BN, int BK, int TM, int TN>
 static cudaError_t launch_gemm(const GemmArgs<T>& g, cudaStream_t st) {
   dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, g.batch);
   k_gemm<T, BM, BN, BK, TM, TN><<<grid, (BM / TM) * (BN / TN), 0, st>>>(g);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -207,6 +210,7 @@ cudaError_t leaf_inverse(cx<T>* A, long lda, long sA, int n, int batch, const in
   }
   const int threads = n <= 16 ? 64 : (n <= 32 ? 128 : 256);
   k_leaf_inverse<T><<<batch, threads, smem, st>>>(A, lda, sA, n, active, status);
+  count_launch();
   return cudaGetLastError();
 }
 template cudaError_t leaf_inverse<double>(cx<double>*, long, long, int, int, const int*, int*, cudaStream_t);
@@ -280,6 +284,7 @@ cudaError_t combine(cx<Tout>* out, long sOut, Term<Tin> t0, Term<Tin> t1, Term<T
                     cudaStream_t st) {
   dim3 grid((b + 31) / 32, (b + 31) / 32, batch);
   k_combine<Tin, Tout><<<grid, 256, 0, st>>>(out, sOut, t0, t1, t2, b, E, eta, diag_coef, active);
+  count_launch();
   return cudaGetLastError();
 }
 template cudaError_t combine<double, double>(cx<double>*, long, Term<double>, Term<double>, Term<double>, int, int, const double*, double, double, const int*, cudaStream_t);
@@ -315,6 +320,7 @@ cudaError_t assemble_diag(cx<T>* out, const cx<double>* H, const cx<double>* S,
   const long bb = (long)b * b;
   dim3 grid((unsigned)((bb + 255) / 256 < 1024 ? (bb + 255) / 256 : 1024), batch);
   k_assemble_diag<T><<<grid, 256, 0, st>>>(out, H, S, SigR, sSig, lead, sLead, E, eta, b);
+  count_launch();
   return cudaGetLastError();
 }
 template cudaError_t assemble_diag<double>(cx<double>*, const cx<double>*, const cx<double>*, const cx<double>*, long, const cx<double>*, long, const double*, double, int, int, cudaStream_t);
@@ -338,6 +344,7 @@ cudaError_t axpby_from64(cx<T>* out, long sOut, const cx<double>* X, long sX, do
   const long bb = (long)b * b;
   dim3 grid((unsigned)((bb + 255) / 256 < 1024 ? (bb + 255) / 256 : 1024), batch);
   k_axpby_from64<T><<<grid, 256, 0, st>>>(out, sOut, X, sX, c1, Y, sY, c2, b);
+  count_launch();
   return cudaGetLastError();
 }
 template cudaError_t axpby_from64<double>(cx<double>*, long, const cx<double>*, long, double, const cx<double>*, long, double, int, int, cudaStream_t);
@@ -387,6 +394,7 @@ cudaError_t assemble_offdiag(cx<T>* U, cx<T>* V, const cx<double>* Hup, const cx
                              const double* E, double eta, int b, int batch, cudaStream_t st) {
   dim3 grid((b + 31) / 32, (b + 31) / 32, batch);
   k_assemble_offdiag<T><<<grid, 256, 0, st>>>(U, V, Hup, Sup, E, eta, b);
+  count_launch();
   return cudaGetLastError();
 }
 template cudaError_t assemble_offdiag<double>(cx<double>*, cx<double>*, const cx<double>*, const cx<double>*, const double*, double, int, int, cudaStream_t);
@@ -404,6 +412,7 @@ template <typename T>
 cudaError_t add_identity(cx<T>* X, long sX, int n, int batch, const int* active, cudaStream_t st) {
   dim3 grid((n + 127) / 128, batch);
   k_add_identity<T><<<grid, 128, 0, st>>>(X, sX, n, active);
+  count_launch();
   return cudaGetLastError();
 }
 template cudaError_t add_identity<double>(cx<double>*, long, int, int, const int*, cudaStream_t);
@@ -424,6 +433,7 @@ cudaError_t convert_strided(const cx<Tin>* in, long ldi, long si, cx<Tout>* out,
   if (rows <= 0 || cols <= 0 || batch <= 0) return cudaSuccess;
   dim3 grid((cols + 127) / 128 < 8 ? (cols + 127) / 128 : 8, rows, batch);
   k_convert<Tin, Tout><<<grid, 128, 0, st>>>(in, ldi, si, out, ldo, so, rows, cols);
+  count_launch();
   return cudaGetLastError();
 }
 template cudaError_t convert_strided<double, double>(const cx<double>*, long, long, cx<double>*, long, long, int, int, int, cudaStream_t);
@@ -469,6 +479,7 @@ template <typename T>
 cudaError_t obs_current(double* cur, long ldcur, const cx<double>* Hup, const cx<double>* Sup,
                         const cx<T>* GLu, long sG, const double* E, int b, int batch, cudaStream_t st) {
   k_obs_current<T><<<batch, 256, 0, st>>>(cur, ldcur, Hup, Sup, GLu, sG, E, b);
+  count_launch();
   return cudaGetLastError();
 }
 template cudaError_t obs_current<double>(double*, long, const cx<double>*, const cx<double>*, const cx<double>*, long, const double*, int, int, cudaStream_t);
@@ -487,6 +498,7 @@ __global__ void k_obs_density(double* den, long ldden, const cx<T>* GL, long sG,
 template <typename T>
 cudaError_t obs_density(double* den, long ldden, const cx<T>* GL, long sG, int b, int batch, cudaStream_t st) {
   k_obs_density<T><<<batch, 128, 0, st>>>(den, ldden, GL, sG, b);
+  count_launch();
   return cudaGetLastError();
 }
 template cudaError_t obs_density<double>(double*, long, const cx<double>*, long, int, int, cudaStream_t);
@@ -520,6 +532,7 @@ cudaError_t obs_trace2(double* out, long ld, const cx<double>* X, long sX, const
                        const cx<double>* Z, long sZ, const cx<T>* Wm, long sW, int b, int batch,
                        cudaStream_t st, int part, double scale) {
   k_obs_trace2<T><<<batch, 256, 0, st>>>(out, ld, X, sX, Y, sY, Z, sZ, Wm, sW, b, part, scale);
+  count_launch();
   return cudaGetLastError();
 }
 template cudaError_t obs_trace2<double>(double*, long, const cx<double>*, long, const cx<double>*, long, const cx<double>*, long, const cx<double>*, long, int, int, cudaStream_t, int, double);
@@ -541,6 +554,7 @@ __global__ void __launch_bounds__(256) k_obs_frob_dot(double* out, long ld, cons
 cudaError_t obs_frob_dot(double* out, long ld, const cx<double>* X, long sX, const cx<double>* Y,
                          long sY, double scale, int b, int batch, cudaStream_t st) {
   k_obs_frob_dot<<<batch, 256, 0, st>>>(out, ld, X, sX, Y, sY, scale, b);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -576,6 +590,7 @@ cudaError_t lead_sigmas(const cx<double>* SR, cx<double>* Gam, cx<double>* SL, c
   const long bb = (long)b * b;
   dim3 grid((unsigned)((bb + 255) / 256 < 1024 ? (bb + 255) / 256 : 1024), batch);
   k_lead_sigmas<<<grid, 256, 0, st>>>(SR, Gam, SL, SG, E, mu, kT, b);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -603,6 +618,7 @@ __global__ void __launch_bounds__(256) k_decim_converged(const cx<double>* X, co
 cudaError_t decim_converged(const cx<double>* X, const cx<double>* Y, int b, double tol, int* active,
                             int* sweeps, int batch, cudaStream_t st) {
   k_decim_converged<<<batch, 256, 0, st>>>(X, Y, b, tol, active, sweeps);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -612,6 +628,7 @@ __global__ void k_flag_active(const int* active, int* status, int code, int batc
 }
 cudaError_t flag_active(const int* active, int* status, int code, int batch, cudaStream_t st) {
   k_flag_active<<<(batch + 127) / 128, 128, 0, st>>>(active, status, code, batch);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -638,6 +655,7 @@ cudaError_t integrate_add(double* acc, const double* val, long ld, int n, const 
                           const double* E, int e0, int nE, int batch, double scale, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   k_integrate_add<<<(n + 127) / 128, 128, 0, st>>>(acc, val, ld, n, w, E, e0, nE, batch, scale);
+  count_launch();
   return cudaGetLastError();
 }
 

@@ -478,9 +478,11 @@ cudaError_t digitize(const cx<df>* X, long ldx, long sX, int opX, int side, int 
   if (!transposed) {
     dim3 g((R_pad + 7) / 8, batch);
     k_row_expo<<<g, 256, 0, st>>>(X, ldx, sX, R, K, R_pad, 0, eout, active);
+    count_launch();
   } else {
     dim3 g((R_pad + 127) / 128, batch);
     k_row_expo<<<g, 128, 0, st>>>(X, ldx, sX, R, K, R_pad, 1, eout, active);
+    count_launch();
   }
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
@@ -488,11 +490,13 @@ cudaError_t digitize(const cx<df>* X, long ldx, long sX, int opX, int side, int 
   dim3 g(d.K_pad / 32, (R_pad + 31) / 32, batch);
   k_digitize<S><<<g, 256, 0, st>>>(X, ldx, sX, R, K, R_pad, d.K_pad, transposed, cj, side, eout, d.P, planes,
                                    rows_plane, active);
+  count_launch();
   return cudaGetLastError();
 }
 
 template <int S, int NST>
-cudaError_t launch(const TcArgs& a, void* scratch, size_t scratch_bytes, int* err_flag, cudaStream_t st) {
+cudaError_t launch(const TcArgs& a, void* scratch, size_t scratch_bytes, int* err_flag, cudaStream_t st,
+                   cudaEvent_t* ev) {
   const Dims d = dims_of(a.M, a.N, a.K, S);
   Scratch s = carve(scratch, d, a.batch, S);
   if (s.bytes > scratch_bytes) return cudaErrorInvalidValue;
@@ -531,7 +535,10 @@ cudaError_t launch(const TcArgs& a, void* scratch, size_t scratch_bytes, int* er
     attr = true;
   }
   dim3 grid(d.N_pad / BNC, d.M_pad / BM, a.batch);
+  if (ev) cudaEventRecord(ev[0], st);
   k_tc_gemm<S, NST><<<grid, 192, smem, st>>>(ma, mb, p);
+  count_launch();
+  if (ev) cudaEventRecord(ev[1], st);
   return cudaGetLastError();
 }
 
@@ -551,10 +558,10 @@ size_t gemm_tc_scratch_bytes(int M, int N, int K, int batch, int digits) {
 }
 
 cudaError_t gemm_tc(const TcArgs& a, int digits, void* scratch, size_t scratch_bytes, int* err_flag,
-                    cudaStream_t st) {
+                    cudaStream_t st, cudaEvent_t* ev) {
   if (a.M <= 0 || a.N <= 0 || a.batch <= 0) return cudaSuccess;
-  if (digits == 6) return tc::launch<6, 2>(a, scratch, scratch_bytes, err_flag, st);
-  if (digits == 2) return tc::launch<2, 4>(a, scratch, scratch_bytes, err_flag, st);
+  if (digits == 6) return tc::launch<6, 2>(a, scratch, scratch_bytes, err_flag, st, ev);
+  if (digits == 2) return tc::launch<2, 4>(a, scratch, scratch_bytes, err_flag, st, ev);
   return cudaErrorInvalidValue;
 }
 
