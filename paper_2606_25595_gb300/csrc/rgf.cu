@@ -162,9 +162,13 @@ GemmArgs<T> gargs(int M, int N, int K, const cx<T>* A, long lda, long sA, int op
 template <typename T>
 qtx_status gemm(qtx_rgf_plan_s* P, const GemmArgs<T>& g, cudaStream_t st, bool force_simt = false);
 
+// The profiled product kernel is the plan's own: the SIMT GEMM in the FP64 / FP32 modes, the
+// tensor-core GEMM in the emulated modes (whose FP32 starting-guess inverse also calls SIMT GEMMs,
+// which are not counted).
 template <typename T>
 qtx_status gemm_simt_prof(qtx_rgf_plan_s* P, const GemmArgs<T>& g, cudaStream_t st) {
-  cudaEvent_t* ev = P->prof ? P->next_events() : nullptr;
+  const bool mine = P->d.precision == QTX_FP64 || P->d.precision == QTX_FP32;
+  cudaEvent_t* ev = (P->prof && mine) ? P->next_events() : nullptr;
   if (ev) cudaEventRecord(ev[0], st);
   QTX_CK(gemm_simt<T>(g, st));
   if (ev) {

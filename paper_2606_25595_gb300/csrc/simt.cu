@@ -3,6 +3,7 @@
 // the block rows of M, and the FP64 observable reductions of Sec. II-B.
 #include <cmath>
 
+#include "df32.cuh"
 #include "kernels.cuh"
 
 namespace qtx {
@@ -217,18 +218,87 @@ template cudaError_t leaf_inverse<double>(cx<double>*, long, long, int, int, con
 template cudaError_t leaf_inverse<float>(cx<float>*, long, long, int, int, const int*, int*, cudaStream_t);
 
 // ============================================================================ elementwise
+// Accumulator of a combination: FP64 when FP64 data is involved, df32 (error-free FP32 steps) when
+// df32 data is, FP32 otherwise -- so the emulated and FP32 sweeps never touch the FP64 pipe here.
+template <typename Tin, typename Tout>
+struct AccSel {
+  using type = float;
+};
+template <typename Tout>
+struct AccSel<double, Tout> {
+  using type = double;
+};
+template <>
+struct AccSel<float, double> {
+  using type = double;
+};
+template <>
+struct AccSel<df, double> {
+  using type = double;
+};
+template <>
+struct AccSel<df, df> {
+  using type = df;
+};
+template <>
+struct AccSel<df, float> {
+  using type = df;
+};
+template <>
+struct AccSel<float, df> {
+  using type = df;
+};
+
+__device__ __forceinline__ void acc_zero(double& a) { a = 0.0; }
+__device__ __forceinline__ void acc_zero(float& a) { a = 0.f; }
+__device__ __forceinline__ void acc_zero(df& a) { a = mkdf(0.f, 0.f); }
+__device__ __forceinline__ df as_df(float x) { return mkdf(x, 0.f); }
+__device__ __forceinline__ df as_df(df x) { return x; }
+__device__ __forceinline__ df as_df(double x) { return from_d<df>(x); }
+template <typename X>
+__device__ __forceinline__ void acc_axpy(double& a, double alpha, X x) { a += alpha * to_d(x); }
+template <typename X>
+__device__ __forceinline__ void acc_axpy(float& a, double alpha, X x) { a = fmaf((float)alpha, (float)to_d(x), a); }
+__device__ __forceinline__ void acc_axpy(float& a, double alpha, float x) { a = fmaf((float)alpha, x, a); }
+template <typename X>
+__device__ __forceinline__ void acc_axpy(df& a, double alpha, X x) {
+  const df v = as_df(x);
+  a = df_add(a, alpha == 1.0 ? v : (alpha == -1.0 ? df_neg(v) : df_mulf(v, (float)alpha)));
+}
+__device__ __forceinline__ void acc_add_d(double& a, double z) { a += z; }
+__device__ __forceinline__ void acc_add_d(float& a, double z) { a += (float)z; }
+__device__ __forceinline__ void acc_add_d(df& a, double z) { a = df_add(a, from_d<df>(z)); }
+template <typename Tout>
+__device__ __forceinline__ Tout acc_out(double a) { return from_d<Tout>(a); }
+template <typename Tout>
+__device__ __forceinline__ Tout acc_out(float a);
+template <>
+__device__ __forceinline__ float acc_out<float>(float a) { return a; }
+template <typename Tout>
+__device__ __forceinline__ Tout acc_out(df a);
+template <>
+__device__ __forceinline__ df acc_out<df>(df a) { return a; }
+template <>
+__device__ __forceinline__ float acc_out<float>(df a) { return a.hi + a.lo; }
+
 // 32 x 32 output tiles; conjugate-transposed terms are staged through shared memory so that both
 // the read and the write stay coalesced.
 template <typename Tin, typename Tout>
 __global__ void __launch_bounds__(256) k_combine(cx<Tout>* out, long sOut, Term<Tin> t0, Term<Tin> t1,
                                                  Term<Tin> t2, int b, const double* E, double eta,
                                                  double diag_coef, const int* active) {
+  using Acc = typename AccSel<Tin, Tout>::type;
   const int e = blockIdx.z;
   if (active && !active[e]) return;
   __shared__ cx<Tin> tile[32][33];
   const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
   const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;  // 32 x 8
-  double accr[4] = {0, 0, 0, 0}, acci[4] = {0, 0, 0, 0};
+  Acc accr[4], acci[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    acc_zero(accr[q]);
+    acc_zero(acci[q]);
+  }
   const Term<Tin> ts[3] = {t0, t1, t2};
 #pragma unroll
   for (int t = 0; t < 3; ++t) {
@@ -241,8 +311,8 @@ __global__ void __launch_bounds__(256) k_combine(cx<Tout>* out, long sOut, Term<
         const int r = r0 + ty + 8 * q, c = c0 + tx;
         if (r < b && c < b) {
           const cx<Tin> v = X[(long)r * b + c];
-          accr[q] += T_.alpha * to_d(v.re);
-          acci[q] += T_.alpha * to_d(v.im);
+          acc_axpy(accr[q], T_.alpha, v.re);
+          acc_axpy(acci[q], T_.alpha, v.im);
         }
       }
     } else {
@@ -251,28 +321,32 @@ __global__ void __launch_bounds__(256) k_combine(cx<Tout>* out, long sOut, Term<
       for (int q = 0; q < 4; ++q) {  // tile[cc][rr] = X[c0+cc][r0+rr]
         const int rr = tx, cc = ty + 8 * q;
         const int xr = c0 + cc, xc = r0 + rr;
-        tile[cc][rr] = (xr < b && xc < b) ? X[(long)xr * b + xc] : cvt<Tin>(mk<double>(0, 0));
+        if (xr < b && xc < b) tile[cc][rr] = X[(long)xr * b + xc];
       }
       __syncthreads();
 #pragma unroll
       for (int q = 0; q < 4; ++q) {  // out(r, c) gets conj(X(c, r)) = conj(tile[c - c0][r - r0])
-        const cx<Tin> v = tile[tx][ty + 8 * q];
-        accr[q] += T_.alpha * to_d(v.re);
-        acci[q] -= T_.alpha * to_d(v.im);
+        const int r = r0 + ty + 8 * q, c = c0 + tx;
+        if (r < b && c < b) {
+          const cx<Tin> v = tile[tx][ty + 8 * q];
+          acc_axpy(accr[q], T_.alpha, v.re);
+          acc_axpy(acci[q], -T_.alpha, v.im);
+        }
       }
     }
   }
-  const double zr = E ? diag_coef * E[e] : 0.0, zi = diag_coef * eta;
   cx<Tout>* O = out + (long)e * sOut;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const int r = r0 + ty + 8 * q, c = c0 + tx;
     if (r < b && c < b) {
-      double vr = accr[q], vi = acci[q];
-      if (r == c && diag_coef != 0.0) { vr += zr; vi += zi; }
+      if (r == c && diag_coef != 0.0) {
+        acc_add_d(accr[q], E ? diag_coef * E[e] : 0.0);
+        acc_add_d(acci[q], diag_coef * eta);
+      }
       cx<Tout> o;
-      o.re = from_d<Tout>(vr);
-      o.im = from_d<Tout>(vi);
+      o.re = acc_out<Tout>(accr[q]);
+      o.im = acc_out<Tout>(acci[q]);
       O[(long)r * b + c] = o;
     }
   }

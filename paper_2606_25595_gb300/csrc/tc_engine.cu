@@ -14,7 +14,8 @@
 // of the leading digit shrinks with K to guarantee it), so their FP32 sums are exact whatever
 // rounding the tensor core's accumulator applies; only acc4, at ~2^-24 of the product, is rounded
 // (the accumulation truncates, so its error grows with the number of MMA steps: ~2^-38 at K = 256).
-// The epilogue adds the five in 64-bit fixed point, applies the row/column scales and writes df32.
+// The epilogue adds the five with error-free FP32 TwoSum steps (the exact groups are summed exactly up
+// to the final df32 rounding), applies the row/column scales and writes df32.
 // With S = 6 digits (21 digit products) the products carry ~41 bits for K <= 256 (the "emulated FP64"
 // mode); with S = 2 (3 digit products) they carry ~13 bits ("BF16x3").
 //
@@ -24,14 +25,16 @@
 // digit planes are stored transposed (N x K, K-major) with rows permuted so that the 48 "re" rows
 // and the 48 "im" rows of each CTA tile are contiguous.
 //
-// Kernel structure (one CTA per 128 x 48 complex output tile, 6 warps):
-//   warp 0   TMA producer: 3-D tiled loads (32 K-elements x 128 rows x 1 plane, 64B swizzle) of the
-//            S A-planes and S B-planes of one K-stage into shared memory, mbarrier expect-tx;
+// Kernel structure (one CTA per 128 x 48 complex output tile, 10 warps):
+//   warp 0   producer: one bulk asynchronous copy (cp.async.bulk, mbarrier complete-tx) per plane
+//            tile of one K-stage (16 K-elements; the digitiser stores every tile contiguously, already
+//            in the 32-byte-swizzled K-major layout the MMA descriptors expect), 5 stages deep;
 //   warp 1   allocates 512 TMEM columns; one thread issues the tcgen05.mma's (2 K16 steps x pairs)
 //            and tcgen05.commit's the stage back to the producer;
-//   warps 2-5 epilogue: tcgen05.ld of the three accumulators, fixed-point recombination, df32 store.
+//   warps 2-9 epilogue (two warps per TMEM lane quarter, one per column half): tcgen05.ld of the
+//            accumulators, TwoSum recombination into df32, row/column scaling, staging through the
+//            (then idle) pipeline shared memory, and coalesced stores with the beta * C0 term.
 // Every mbarrier wait is bounded (2 s of %globaltimer); on expiry the kernel sets *err and unwinds.
-#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include <cstring>
@@ -47,11 +50,11 @@ namespace tc {
 constexpr int BM = 128;        // output rows per CTA (TMEM lanes)
 constexpr int BNC = 48;        // complex output columns per CTA
 constexpr int BNR = 2 * BNC;   // real (embedded) columns per CTA = MMA N
-constexpr int BKS = 32;        // bf16 K elements per stage (64-byte rows, 64B swizzle)
-constexpr int TILE_A = BM * BKS * 2;   // bytes of one A-plane tile (128 rows)
-constexpr int TILE_B = BNR * BKS * 2;  // bytes of one B-plane tile (96 rows)
+constexpr int BKS = 16;        // bf16 K elements per stage (32-byte rows, 32B swizzle) = one MMA K
+constexpr int TILE_A = BM * BKS * 2;   // bytes of one A-plane tile (128 rows x 32 B)
+constexpr int TILE_B = BNR * BKS * 2;  // bytes of one B-plane tile (96 rows x 32 B)
 constexpr int ACC_COLS = BNR;  // TMEM columns per accumulator
-constexpr int FIX = 40;        // fractional bits of the fixed-point recombination
+constexpr int OUT_LD = BNC + 1;  // row stride (complex elements) of the epilogue's smem staging
 constexpr int DW = 7;          // bits per digit below the leading one
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -93,24 +96,30 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, int* err
     __nanosleep(128);
   }
 }
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z) {
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
   asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];"
-      ::"r"(su32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(su32(bar)), "r"(x), "r"(y), "r"(z)
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+      ::"r"(su32(dst)), "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(su32(bar))
       : "memory");
 }
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// Shared-memory matrix descriptor: K-major, 64-byte swizzle, 8-row groups 512 bytes apart.
+// Shared-memory matrix descriptor: K-major, 32-byte swizzle, 8-row groups 256 bytes apart.
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
   d |= (uint64_t)1u << 16;            // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)(512u >> 4) << 32;   // stride byte offset
+  d |= (uint64_t)(256u >> 4) << 32;   // stride byte offset
   d |= (uint64_t)1u << 46;            // descriptor version for tcgen05
-  d |= (uint64_t)4u << 61;            // 64-byte swizzle
+  d |= (uint64_t)6u << 61;            // 32-byte swizzle
   return d;
+}
+// Byte offset of element (row rr, k) inside a K-major tile with 32-byte rows and 32-byte swizzle:
+// the 16-byte half-row index is XORed with bit 2 of the row (address bit 4 ^= address bit 7).
+__host__ __device__ __forceinline__ uint32_t sw32_offset(uint32_t rr, uint32_t kk) {
+  const uint32_t o = rr * 32u + kk * 2u;
+  return o ^ (((o >> 7) & 1u) << 4);
 }
 // Instruction descriptor: kind::f16, D = F32, A = B = BF16, both K-major, M = 128, N = 96.
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BNR >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
@@ -134,6 +143,13 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
       : "r"(taddr)
       : "memory");
 }
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+      : "r"(taddr)
+      : "memory");
+}
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // accumulator of digit pair (i, j): exact groups i + j = 2..5, then one rounded group
@@ -142,6 +158,8 @@ __host__ __device__ constexpr int n_acc(int S) { return S + 1 >= 6 ? 5 : S; }
 
 // ------------------------------------------------------------------------------ GEMM kernel
 struct TcParams {
+  const unsigned char* pa;  // A plane tiles [batch'][S][M_pad/128][nks][TILE_A]
+  const unsigned char* pb;  // B plane tiles [batch'][S][2 N_pad/96][nks][TILE_B]
   const int* eA;   // [batch][M_pad] row exponents of op(A)
   const int* eB;   // [batch][N_pad] column exponents of op(B)
   int M_pad, N_pad, nks;  // nks: K-stages of 32 over the embedded K (2 * K_pad)
@@ -149,15 +167,30 @@ struct TcParams {
   cx<df>* C; long ldc, sC;
   const cx<df>* C0; long ldc0, sC0;
   float alpha, beta;
-  int escale;      // total exponent shift: (2 l1 - 2) + FIX
+  int escale;      // exponent shift of the recombined sum: 2 l1 - 2
   int a_batched, b_batched;  // 0: the operand is shared by the whole batch (digitized once)
   const int* active;
   int* err;
 };
 
+// Sum of the accumulators of one output value (acc0 largest) as df32, with TwoSum steps.
+template <int NACC>
+__device__ __forceinline__ df sum_acc(const uint32_t (&v)[NACC][8], int c) {
+  float s = __uint_as_float(v[0][c]), e = 0.f;
+#pragma unroll
+  for (int g = 1; g < NACC; ++g) {
+    const float x = __uint_as_float(v[g][c]);
+    const float t = s + x;
+    const float bv = t - s;
+    e += (s - (t - bv)) + (x - bv);
+    s = t;
+  }
+  const float h = s + e;
+  return mkdf(h, e - (h - s));
+}
+
 template <int S, int NST>
-__global__ void __launch_bounds__(192, 1)
-    k_tc_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, TcParams p) {
+__global__ void __launch_bounds__(320, 1) k_tc_gemm(TcParams p) {
   constexpr int STAGE = S * (TILE_A + TILE_B);
   constexpr int NACC = n_acc(S);
   extern __shared__ unsigned char smem_raw[];
@@ -196,12 +229,16 @@ __global__ void __launch_bounds__(192, 1)
         if (!mbar_wait(&empty[s], ph ^ 1u, p.err)) break;
         mbar_expect_tx(&full[s], STAGE);
         unsigned char* st = base + s * STAGE;
+        const long MB = p.M_pad / BM, NB = 2L * p.N_pad / BNR;
+        const long ea = p.a_batched ? e : 0, eb = p.b_batched ? e : 0;
         for (int d = 0; d < S; ++d) {
-          tma_load_3d(st + d * TILE_A, &mapA, &full[s], ks * BKS, mblk * BM, (p.a_batched ? e : 0) * S + d);
-          tma_load_3d(st + S * TILE_A + d * TILE_B, &mapB, &full[s], ks * BKS, nblk * BNR, (p.b_batched ? e : 0) * S + d);
+          bulk_load(st + d * TILE_A, p.pa + (((ea * S + d) * MB + mblk) * p.nks + ks) * (long)TILE_A, TILE_A, &full[s]);
+          bulk_load(st + S * TILE_A + d * TILE_B, p.pb + (((eb * S + d) * NB + nblk) * p.nks + ks) * (long)TILE_B,
+                    TILE_B, &full[s]);
         }
       }
     }
+    __syncwarp();  // reconverge before the CTA barrier (bar.sync counts whole warps)
   } else if (warp == 1) {
     if (lane == 0) {
       uint32_t started = 0;  // bit g set once accumulator g has been written
@@ -213,80 +250,81 @@ __global__ void __launch_bounds__(192, 1)
         fence_after();
         const uint32_t sa = su32(base + s * STAGE);
 #pragma unroll
-        for (int kk = 0; kk < 2; ++kk) {
+        for (int i = 1; i <= S; ++i) {
 #pragma unroll
-          for (int i = 1; i <= S; ++i) {
-#pragma unroll
-            for (int j = 1; j <= S + 1 - i; ++j) {
-              const int g = acc_of(i, j);
-              const uint64_t ad = sdesc(sa + (i - 1) * TILE_A + kk * 32);
-              const uint64_t bd = sdesc(sa + S * TILE_A + (j - 1) * TILE_B + kk * 32);
-              mma(tmem + g * ACC_COLS, ad, bd, (started >> g) & 1u);
-              started |= 1u << g;
-            }
+          for (int j = 1; j <= S + 1 - i; ++j) {
+            const int g = acc_of(i, j);
+            const uint64_t ad = sdesc(sa + (i - 1) * TILE_A);
+            const uint64_t bd = sdesc(sa + S * TILE_A + (j - 1) * TILE_B);
+            mma(tmem + g * ACC_COLS, ad, bd, (started >> g) & 1u);
+            started |= 1u << g;
           }
         }
         mma_commit(&empty[s]);
       }
       mma_commit(accb);
     }
+    __syncwarp();
   } else {
-    // epilogue: warps 2..5 -> TMEM lane quarters 2, 3, 0, 1
-    const int q = warp & 3;
+    // epilogue: warps 2..9; TMEM lane quarter = warp % 4, column half = (warp - 2) / 4
+    const int q = warp & 3, h = (warp - 2) >> 2;
     const int r = q * 32 + lane;
     const int m = mblk * BM + r;
-    const bool got = mbar_wait(accb, 0, p.err);
+    // one thread waits for the accumulators; the other epilogue threads sleep in a named barrier
+    // instead of polling shared memory while the tensor core reads its operands from it
+    __shared__ int s_got;
+    if (threadIdx.x == 64) s_got = mbar_wait(accb, 0, p.err) ? 1 : 0;
+    __syncwarp();
+    asm volatile("bar.sync 2, 256;" ::: "memory");
+    const bool got = s_got != 0;
     fence_after();
+    cx<df>* out = reinterpret_cast<cx<df>*>(base);  // [BM][OUT_LD] staging (pipeline smem is idle now)
     if (got) {
       const int eAm = p.eA[(long)(p.a_batched ? e : 0) * p.M_pad + m];
       const int* eBrow = p.eB + (long)(p.b_batched ? e : 0) * p.N_pad;
       const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16);
-      cx<df>* Crow = p.C + (long)e * p.sC + (long)m * p.ldc;
-      const cx<df>* C0row = p.C0 ? p.C0 + (long)e * p.sC0 + (long)m * p.ldc0 : nullptr;
 #pragma unroll 1
-      for (int c0 = 0; c0 < BNC; c0 += 16) {
-        float hv[2][16], lv[2][16];
+      for (int c0 = h * (BNC / 2); c0 < (h + 1) * (BNC / 2); c0 += 8) {
+        uint32_t vr[NACC][8], vi[NACC][8];
 #pragma unroll
-        for (int part = 0; part < 2; ++part) {  // 0: real columns, 1: imaginary columns
-          long long I[16];
-#pragma unroll
-          for (int c = 0; c < 16; ++c) I[c] = 0;
-#pragma unroll
-          for (int g = 0; g < NACC; ++g) {
-            uint32_t v[16];
-            tmem_ld16(trow + g * ACC_COLS + part * BNC + c0, v);
-            tmem_wait_ld();
-#pragma unroll
-            for (int c = 0; c < 16; ++c) I[c] += f2fix(__uint_as_float(v[c]), FIX);
-          }
-#pragma unroll
-          for (int c = 0; c < 16; ++c) {
-            hv[part][c] = __ll2float_rn(I[c]);
-            lv[part][c] = __ll2float_rn(I[c] - __float2ll_rz(hv[part][c]));
-          }
+        for (int g = 0; g < NACC; ++g) {
+          tmem_ld8(trow + g * ACC_COLS + c0, vr[g]);
+          tmem_ld8(trow + g * ACC_COLS + BNC + c0, vi[g]);
         }
-        if (m < p.M) {
+        tmem_wait_ld();
 #pragma unroll
-          for (int c = 0; c < 16; ++c) {
-            const int n = nblk * BNC + c0 + c;
-            if (n >= p.N) break;
-            const int Es = eAm + eBrow[n] - p.escale;
-            df vr = mkdf(scale2(hv[0][c], Es) * p.alpha, scale2(lv[0][c], Es) * p.alpha);
-            df vi = mkdf(scale2(hv[1][c], Es) * p.alpha, scale2(lv[1][c], Es) * p.alpha);
-            if (C0row && p.beta != 0.f) {
-              const cx<df> c0v = C0row[n];
-              vr = df_add(vr, df_mulf(c0v.re, p.beta));
-              vi = df_add(vi, df_mulf(c0v.im, p.beta));
-            }
-            cx<df> o;
-            o.re = vr;
-            o.im = vi;
-            Crow[n] = o;
+        for (int c = 0; c < 8; ++c) {
+          const int n = nblk * BNC + c0 + c;
+          const int Es = eAm + eBrow[n] - p.escale;
+          const df sr = sum_acc<NACC>(vr, c), si = sum_acc<NACC>(vi, c);
+          cx<df> o;
+          o.re = mkdf(scale2(sr.hi, Es) * p.alpha, scale2(sr.lo, Es) * p.alpha);
+          o.im = mkdf(scale2(si.hi, Es) * p.alpha, scale2(si.lo, Es) * p.alpha);
+          out[r * OUT_LD + c0 + c] = o;
+        }
+      }
+    }
+    __syncwarp();
+    asm volatile("bar.sync 1, 256;" ::: "memory");  // the eight epilogue warps
+    if (got) {
+      const cx<df>* C0e = p.C0 ? p.C0 + (long)e * p.sC0 : nullptr;
+      cx<df>* Ce = p.C + (long)e * p.sC;
+      for (int idx = threadIdx.x - 64; idx < BM * BNC; idx += 256) {
+        const int rr = idx / BNC, cc = idx % BNC;
+        const int mm = mblk * BM + rr, nn = nblk * BNC + cc;
+        if (mm < p.M && nn < p.N) {
+          cx<df> v = out[rr * OUT_LD + cc];
+          if (C0e && p.beta != 0.f) {
+            const cx<df> c0v = C0e[(long)mm * p.ldc0 + nn];
+            v.re = df_add(v.re, df_mulf(c0v.re, p.beta));
+            v.im = df_add(v.im, df_mulf(c0v.im, p.beta));
           }
+          Ce[(long)mm * p.ldc + nn] = v;
         }
       }
     }
   }
+  __syncwarp();
   fence_before();
   __syncthreads();
   if (warp == 1) {
@@ -297,33 +335,48 @@ __global__ void __launch_bounds__(192, 1)
 
 // ------------------------------------------------------------------------------ digitizer
 // Per-row exponent of the logical operand L (R x K): L(r, k) = X[r][k] (direct) or X[k][r]
-// (transposed).  e[r] = max over k of the exponent of max(|Re|, |Im|) (hi parts).
-__global__ void k_row_expo(const cx<df>* X, long ldx, long sX, int R, int K, int R_pad, int transposed,
-                           int* eout, const int* active) {
+// (transposed).  e[r] = max over k of the exponent of max(|Re|, |Im|) (hi parts).  One CTA per 32
+// logical rows: 8 warps stride over k, lanes over rows (transposed, coalesced along r) or over k
+// (direct, coalesced along k); partial maxima meet in shared memory.
+__global__ void __launch_bounds__(256) k_row_expo(const cx<df>* X, long ldx, long sX, int R, int K, int R_pad,
+                                                  int transposed, int* eout, const int* active) {
   const int e = blockIdx.y;
   if (active && !active[e]) return;
+  __shared__ int part[8][33];
   const cx<df>* Xe = X + (long)e * sX;
-  if (!transposed) {  // one warp per row
-    const int r = blockIdx.x * 8 + threadIdx.x / 32, lane = threadIdx.x % 32;
-    if (r >= R_pad) return;
+  const int r0 = blockIdx.x * 32, w = threadIdx.x / 32, lane = threadIdx.x % 32;
+  if (transposed) {
+    const int r = r0 + lane;
     int mx = -1000;
     if (r < R)
-      for (int k = lane; k < K; k += 32) {
-        const cx<df> v = Xe[(long)r * ldx + k];
-        mx = max(mx, max(df_expo(v.re.hi), df_expo(v.im.hi)));
-      }
-    for (int off = 16; off > 0; off >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-    if (lane == 0) eout[(long)e * R_pad + r] = mx;
-  } else {  // one thread per logical row (a column of X): coalesced across threads
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= R_pad) return;
-    int mx = -1000;
-    if (r < R)
-      for (int k = 0; k < K; ++k) {
+      for (int k = w; k < K; k += 8) {
         const cx<df> v = Xe[(long)k * ldx + r];
         mx = max(mx, max(df_expo(v.re.hi), df_expo(v.im.hi)));
       }
-    eout[(long)e * R_pad + r] = mx;
+    part[w][lane] = mx;
+  } else {
+    for (int q = 0; q < 4; ++q) {
+      const int rr = w + 8 * q, r = r0 + rr;
+      int mx = -1000;
+      if (r < R)
+        for (int k = lane; k < K; k += 32) {
+          const cx<df> v = Xe[(long)r * ldx + k];
+          mx = max(mx, max(df_expo(v.re.hi), df_expo(v.im.hi)));
+        }
+      for (int off = 16; off > 0; off >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+      if (lane == 0) part[q][w] = mx;  // row rr = w + 8 q
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int rr = threadIdx.x, r = r0 + rr;
+    int mx = -1000;
+    if (transposed) {
+      for (int ww = 0; ww < 8; ++ww) mx = max(mx, part[ww][rr]);
+    } else {
+      mx = part[rr / 8][rr % 8];
+    }
+    if (r < R_pad) eout[(long)e * R_pad + r] = mx;
   }
 }
 
@@ -347,7 +400,7 @@ __device__ __forceinline__ void digits_of(df x, int sh, int (&d)[S]) {
 template <int S>
 __global__ void __launch_bounds__(256) k_digitize(const cx<df>* X, long ldx, long sX, int R, int K,
                                                   int R_pad, int K_pad, int transposed, int conj_,
-                                                  int side, const int* eR, int P, __nv_bfloat16* planes,
+                                                  int side, const int* eR, int P, unsigned char* planes,
                                                   long rows_plane, const int* active) {
   const int e = blockIdx.z;
   if (active && !active[e]) return;
@@ -368,7 +421,16 @@ __global__ void __launch_bounds__(256) k_digitize(const cx<df>* X, long ldx, lon
     }
   }
   __syncthreads();
-  const long plane_elems = rows_plane * (2L * K_pad);
+  // plane tiles: [e][i][row_block][k_stage][tile], rows per block 128 (A) or 96 (B), 16 k per stage
+  const int rows_blk = side == 0 ? BM : BNR;
+  const long tile_bytes = (long)rows_blk * BKS * 2;
+  const long nks = 2L * K_pad / BKS;
+  const long plane_bytes = (rows_plane / rows_blk) * nks * tile_bytes;
+  auto put = [&](unsigned char* pl, long row, int kcol, float val) {
+    const long blk = row / rows_blk, rr = row % rows_blk, ks = kcol / BKS, kk = kcol % BKS;
+    *reinterpret_cast<__nv_bfloat16*>(pl + (blk * nks + ks) * tile_bytes + sw32_offset((uint32_t)rr, (uint32_t)kk)) =
+        __float2bfloat16_rn(val);
+  };
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const int rr = ty + 8 * q, r = r0 + rr, k = k0 + tx;
@@ -379,20 +441,20 @@ __global__ void __launch_bounds__(256) k_digitize(const cx<df>* X, long ldx, lon
     int dr[S], di[S];
     digits_of<S>(v.re, sh, dr);
     digits_of<S>(v.im, sh, di);
-    __nv_bfloat16* pe = planes + (long)e * S * plane_elems;
+    unsigned char* pe = planes + (long)e * S * plane_bytes;
 #pragma unroll
     for (int i = 0; i < S; ++i) {
       const float sc = __int_as_float((127 - DW * i) << 23);  // 2^(-7 i)
-      __nv_bfloat16* pl = pe + (long)i * plane_elems;
+      unsigned char* pl = pe + (long)i * plane_bytes;
       if (side == 0) {
-        pl[(long)r * 2 * K_pad + k] = __float2bfloat16_rn((float)dr[i] * sc);
-        pl[(long)r * 2 * K_pad + K_pad + k] = __float2bfloat16_rn((float)di[i] * sc);
+        put(pl, r, k, (float)dr[i] * sc);
+        put(pl, r, K_pad + k, (float)di[i] * sc);
       } else {
         const long rre = (long)(r / BNC) * BNR + (r % BNC), rim = rre + BNC;
-        pl[rre * 2 * K_pad + k] = __float2bfloat16_rn((float)dr[i] * sc);
-        pl[rre * 2 * K_pad + K_pad + k] = __float2bfloat16_rn(-(float)di[i] * sc);
-        pl[rim * 2 * K_pad + k] = __float2bfloat16_rn((float)di[i] * sc);
-        pl[rim * 2 * K_pad + K_pad + k] = __float2bfloat16_rn((float)dr[i] * sc);
+        put(pl, rre, k, (float)dr[i] * sc);
+        put(pl, rre, K_pad + k, -(float)di[i] * sc);
+        put(pl, rim, k, (float)di[i] * sc);
+        put(pl, rim, K_pad + k, (float)dr[i] * sc);
       }
     }
   }
@@ -417,7 +479,7 @@ inline Dims dims_of(int M, int N, int K, int S) {
   return d;
 }
 struct Scratch {
-  __nv_bfloat16 *pa, *pb;
+  unsigned char *pa, *pb;
   int *ea, *eb;
   size_t bytes;
 };
@@ -429,59 +491,26 @@ inline Scratch carve(void* base, const Dims& d, int batch, int S) {
   const size_t b = al((size_t)batch * S * 2 * d.N_pad * 2 * d.K_pad * sizeof(__nv_bfloat16));  // 2 N_pad rows
   const size_t ea = al((size_t)batch * d.M_pad * sizeof(int));
   const size_t eb = al((size_t)batch * d.N_pad * sizeof(int));
-  s.pa = reinterpret_cast<__nv_bfloat16*>(p);
-  s.pb = reinterpret_cast<__nv_bfloat16*>(p + a);
+  s.pa = p;
+  s.pb = p + a;
   s.ea = reinterpret_cast<int*>(p + a + b);
   s.eb = reinterpret_cast<int*>(p + a + b + ea);
   s.bytes = a + b + ea + eb;
   return s;
 }
 
-typedef CUresult (*EncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                             const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                             CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-EncodeFn encode_fn() {
-  static EncodeFn fn = nullptr;
-  static std::once_flag once;
-  std::call_once(once, [] {
-    void* f = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeFn>(f);
-  });
-  return fn;
-}
-
-// 3-D map over digit planes: x = 2*K_pad (contiguous), y = plane rows, z = batch*S planes; box
-// 32 x box_rows x 1.
-bool make_map(CUtensorMap* m, void* ptr, int K2, int rows, int zdim, int box_rows) {
-  EncodeFn fn = encode_fn();
-  if (!fn) return false;
-  cuuint64_t gdim[3] = {(cuuint64_t)K2, (cuuint64_t)rows, (cuuint64_t)zdim};
-  cuuint64_t gstr[2] = {(cuuint64_t)K2 * 2, (cuuint64_t)K2 * 2 * rows};
-  cuuint32_t box[3] = {(cuuint32_t)BKS, (cuuint32_t)box_rows, 1};
-  cuuint32_t estr[3] = {1, 1, 1};
-  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, ptr, gdim, gstr, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-            CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
 template <int S>
 cudaError_t digitize(const cx<df>* X, long ldx, long sX, int opX, int side, int R, int K, const Dims& d,
-                     int* eout, __nv_bfloat16* planes, int batch, const int* active, cudaStream_t st) {
+                     int* eout, unsigned char* planes, int batch, const int* active, cudaStream_t st) {
   // logical row r of the operand: left A = op(X): row r of op(X); right B = op(X): column r of op(X)
   //   left  N: X[r][k] direct      left  H: conj(X[k][r]) transposed
   //   right N: X[k][r] transposed  right H: conj(X[r][k]) direct
   const int transposed = (side == 0) ? (opX == OP_C) : (opX == OP_N);
   const int cj = opX == OP_C;
   const int R_pad = side == 0 ? d.M_pad : d.N_pad;
-  if (!transposed) {
-    dim3 g((R_pad + 7) / 8, batch);
-    k_row_expo<<<g, 256, 0, st>>>(X, ldx, sX, R, K, R_pad, 0, eout, active);
-    count_launch();
-  } else {
-    dim3 g((R_pad + 127) / 128, batch);
-    k_row_expo<<<g, 128, 0, st>>>(X, ldx, sX, R, K, R_pad, 1, eout, active);
+  {
+    dim3 g((R_pad + 31) / 32, batch);
+    k_row_expo<<<g, 256, 0, st>>>(X, ldx, sX, R, K, R_pad, transposed, eout, active);
     count_launch();
   }
   cudaError_t err = cudaGetLastError();
@@ -504,10 +533,9 @@ cudaError_t launch(const TcArgs& a, void* scratch, size_t scratch_bytes, int* er
   const int ab = a.sA != 0, bb_ = a.sB != 0;
   if ((e = digitize<S>(a.A, a.lda, a.sA, a.opA, 0, a.M, a.K, d, s.ea, s.pa, ab ? a.batch : 1, ab ? a.active : nullptr, st))) return e;
   if ((e = digitize<S>(a.B, a.ldb, a.sB, a.opB, 1, a.N, a.K, d, s.eb, s.pb, bb_ ? a.batch : 1, bb_ ? a.active : nullptr, st))) return e;
-  CUtensorMap ma, mb;
-  if (!make_map(&ma, s.pa, 2 * d.K_pad, d.M_pad, (ab ? a.batch : 1) * S, BM)) return cudaErrorInvalidConfiguration;
-  if (!make_map(&mb, s.pb, 2 * d.K_pad, 2 * d.N_pad, (bb_ ? a.batch : 1) * S, BNR)) return cudaErrorInvalidConfiguration;
   TcParams p;
+  p.pa = s.pa;
+  p.pb = s.pb;
   p.eA = s.ea;
   p.eB = s.eb;
   p.M_pad = d.M_pad;
@@ -523,7 +551,7 @@ cudaError_t launch(const TcArgs& a, void* scratch, size_t scratch_bytes, int* er
   p.sC0 = a.sC0;
   p.alpha = a.alpha;
   p.beta = a.beta;
-  p.escale = (2 * d.l1 - 2) + FIX;
+  p.escale = 2 * d.l1 - 2;
   p.a_batched = ab;
   p.b_batched = bb_;
   p.active = a.active;
@@ -536,7 +564,7 @@ cudaError_t launch(const TcArgs& a, void* scratch, size_t scratch_bytes, int* er
   }
   dim3 grid(d.N_pad / BNC, d.M_pad / BM, a.batch);
   if (ev) cudaEventRecord(ev[0], st);
-  k_tc_gemm<S, NST><<<grid, 192, smem, st>>>(ma, mb, p);
+  k_tc_gemm<S, NST><<<grid, 320, smem, st>>>(p);
   count_launch();
   if (ev) cudaEventRecord(ev[1], st);
   return cudaGetLastError();
@@ -549,7 +577,7 @@ bool tc_available() {
   if (cudaGetDevice(&dev) != cudaSuccess) return false;
   cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
   cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
-  return major == 10 && minor == 3 && tc::encode_fn() != nullptr;
+  return major == 10 && minor == 3;
 }
 
 size_t gemm_tc_scratch_bytes(int M, int N, int K, int batch, int digits) {
@@ -560,8 +588,8 @@ size_t gemm_tc_scratch_bytes(int M, int N, int K, int batch, int digits) {
 cudaError_t gemm_tc(const TcArgs& a, int digits, void* scratch, size_t scratch_bytes, int* err_flag,
                     cudaStream_t st, cudaEvent_t* ev) {
   if (a.M <= 0 || a.N <= 0 || a.batch <= 0) return cudaSuccess;
-  if (digits == 6) return tc::launch<6, 2>(a, scratch, scratch_bytes, err_flag, st, ev);
-  if (digits == 2) return tc::launch<2, 4>(a, scratch, scratch_bytes, err_flag, st, ev);
+  if (digits == 6) return tc::launch<6, 5>(a, scratch, scratch_bytes, err_flag, st, ev);
+  if (digits == 2) return tc::launch<2, 8>(a, scratch, scratch_bytes, err_flag, st, ev);
   return cudaErrorInvalidValue;
 }
 
