@@ -80,6 +80,29 @@ def max_over_ranks(x, ws):
     return float(t.item())
 
 
+def captured_traffic(energies_per_launch):
+    """DRAM bytes per product-kernel launch from the committed ncu capture, scaled by the energies a
+    launch processes (traffic grows in proportion: each energy's planes are read once).  None when
+    the kernel source changed since the capture."""
+    import hashlib
+    cap = os.path.join(ROOT, "profiles", "k_tc_gemm_emu64_b256_e64.txt")
+    src = os.path.join(ROOT, "paper_2606_25595_gb300", "csrc", "tc_engine.cu")
+    if not (os.path.exists(cap) and os.path.exists(src)):
+        return None, None
+    txt = open(cap).read()
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    per = None
+    same = False
+    for line in txt.splitlines():
+        if line.startswith("source_sha256_16:"):
+            same = line.split()[1] == h
+        if line.startswith("dram_bytes_per_energy:"):
+            per = float(line.split()[1])
+    if not same or per is None:
+        return None, per
+    return per * energies_per_launch, per
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -257,8 +280,10 @@ def main():
         peak, bound, kernel = 1.1, "alu", "k_gemm<double> (SIMT DFMA)"
     avg_ms = prof["ms"] / max(prof["launches"], 1)
     achieved = (prof["pipe_flops"] / max(prof["launches"], 1)) / (avg_ms / 1e3) / 1e12 if prof["launches"] else None
+    traffic, _ = captured_traffic(min(args.chunk, ne)) if args.precision == "emu64" and b == 256 else (None, None)
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                "traffic_unit": "bytes per launch (ncu dram read+write, scaled from a 64-energy capture)",
                 "kernel": kernel, "launches": prof["launches"], "avg_launch_ms": avg_ms,
                 "share_of_step": prof["ms"] / ms if ms else None,
                 "useful_fp64_equiv_tflops": (prof["useful_flops"] / (prof["ms"] / 1e3) / 1e12) if prof["ms"] else None,
