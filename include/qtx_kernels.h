@@ -51,6 +51,33 @@ qtx_status qtx_lead_self_energy(int n, const void *H00, const void *H01, const d
                                 int n_energies, double eta, double tol, int max_iter, void *SigR,
                                 int *status, void *stream);
 
+/* Size in bytes of the fixed device array behind qtx_zgemm_emu64_noalloc (48 MiB per GPU). */
+#define QTX_NOALLOC_SCRATCH_BYTES ((size_t)48 << 20)
+
+/* Allocation-free variant of qtx_zgemm_batched with precision QTX_EMU64 (same arguments and result,
+ * same tensor-core kernels).  The paper has no counterpart: this serves callers that must not allocate
+ * device memory while they run -- a latency-critical loop (cudaMalloc/cudaFree can synchronise the
+ * device), a plugin or progress thread inside another runtime that owns all device memory, or a process
+ * with a fixed memory budget.  All temporaries (df32 copies of A, B, C0 and of the result, the digit
+ * planes and exponents, a wait flag) live in one array of QTX_NOALLOC_SCRATCH_BYTES that is part of the
+ * library image; every GPU that loads the library holds it until the process exits.  No cudaMalloc,
+ * cudaFree or allocating library routine is called.
+ *   - The first call on each device (with that device current) resolves the array's device address
+ *     once with cudaGetSymbolAddress; make that first call outside any stream capture.
+ *   - Calls share the array and it keeps the last call's contents: the wait flag is cleared at the
+ *     start of every call and everything else is rewritten.  Calls that overlap on the GPU (other
+ *     streams, other host threads) race on it; serialise them.
+ *   - The call synchronises `stream` before returning (it reads the wait flag).
+ * Errors: QTX_ERR_OOM when the call needs more scratch than QTX_NOALLOC_SCRATCH_BYTES -- about
+ * 16 B x (M K + K N + 2 M N) + the digit planes (12 B x 6 planes x (M_pad K_pad + 2 N_pad K_pad) with
+ * M_pad = 128-multiple, N_pad = 48-multiple, K_pad = 32-multiple) per batch entry, e.g. at most 5
+ * entries of 256 x 256 x 256 -- nothing is enqueued then; QTX_ERR_INVALID_ARG, QTX_ERR_UNSUPPORTED,
+ * QTX_ERR_CUDA, QTX_ERR_TIMEOUT as for qtx_zgemm_batched. */
+qtx_status qtx_zgemm_emu64_noalloc(int M, int N, int K, int opA, const void *A, long lda, long strideA,
+                                   int opB, const void *B, long ldb, long strideB, double alpha,
+                                   double beta, const void *C0, long ldc0, long strideC0, void *C,
+                                   long ldc, long strideC, int batch, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -31,7 +31,7 @@ BLOCK_OUTPUTS = ("GR_diag", "GR_upper", "GR_lower", "GL_diag", "GL_upper", "GG_d
 EXPORTED = ("qtx_rgf_plan_create", "qtx_rgf_solve", "qtx_rgf_status", "qtx_rgf_destroy",
             "qtx_rgf_last_error", "qtx_rgf_footprint", "qtx_rgf_version", "qtx_zgemm_batched",
             "qtx_zinv_batched", "qtx_lead_self_energy", "qtx_rgf_set_profiling",
-            "qtx_rgf_gemm_profile", "qtx_kernel_launches")
+            "qtx_rgf_gemm_profile", "qtx_kernel_launches", "qtx_zgemm_emu64_noalloc")
 
 
 class QtxError(RuntimeError):
@@ -108,6 +108,8 @@ def load() -> ctypes.CDLL:
     L.qtx_rgf_gemm_profile.restype = i
     L.qtx_kernel_launches.argtypes = []
     L.qtx_kernel_launches.restype = ctypes.c_longlong
+    L.qtx_zgemm_emu64_noalloc.argtypes = [i, i, i, i, vp, l, l, i, vp, l, l, d, d, vp, l, l, vp, l, l, i, vp]
+    L.qtx_zgemm_emu64_noalloc.restype = i
     _lib = L
     return L
 
