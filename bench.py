@@ -49,6 +49,11 @@ def parse():
     ap.add_argument("--fp64-energies", type=int, default=16, help="energies for the FP64 comparison (0 = skip)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU oracle sample")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default="mixed", choices=["mixed", "strip", "uneven", "ozaki", "serving"],
+                    help="mixed: b=256 N_B=64 N_E=512 (default); strip: W=16 strip FP64 with contacts; "
+                         "uneven: 8 devices x 128 energies in one CUDA graph; ozaki: b=1024 N_B=32 "
+                         "emulated FP64 (subset of the 256 energies); serving: Poisson request stream")
+    ap.add_argument("--requests", type=int, default=40)
     return ap.parse_args()
 
 
@@ -200,12 +205,209 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def _line(args, metric_value, ms_per_step, workload, precision, extra):
+    line = {"metric": METRIC, "value": metric_value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {"emu64": "bf16-digits(tcgen05)+df32", "fp32": "c64",
+                                           "fp64": "c128", "bf16x3": "bf16-digits(tcgen05)+df32"}[precision],
+            "data": "synthetic", "config": {"workload": workload, "precision": precision}}
+    line.update(extra)
+    print(json.dumps(line), flush=True)
+
+
+def _solve_setup(q, dev, precision, chunk, outs, energies=None):
+    import torch
+    E = dev["energies"] if energies is None else energies
+    din = q.upload(dev, E)
+    nb, b, ne = dev["n_blocks"], dev["block_size"], len(E)
+    want = [o for o in outs if not (o in ("contact", "transmission") and not dev.get("leads"))]
+    desc = q.make_desc(nb, b, precision, min(chunk, ne), 2, has_S=dev.get("S_diag") is not None,
+                       has_scattering=dev.get("SigR") is not None, leads=bool(dev.get("leads")), outputs=want)
+    plan = q.Plan(desc)
+    o = q.Outputs()
+    bufs = {}
+    shapes = {"current": (ne, max(nb - 1, 1)), "density": (ne, nb), "contact": (ne, 2), "transmission": (ne,)}
+    for k in want:
+        if k == "integrals":
+            bufs["current_int"] = torch.zeros(max(nb - 1, 1), dtype=torch.float64, device="cuda")
+            bufs["density_int"] = torch.zeros(nb, dtype=torch.float64, device="cuda")
+            o.current_int, o.density_int = bufs["current_int"].data_ptr(), bufs["density_int"].data_ptr()
+        elif k in shapes:
+            bufs[k] = torch.empty(shapes[k], dtype=torch.float64, device="cuda")
+            setattr(o, k, bufs[k].data_ptr())
+        else:
+            shp = (ne, nb if "diag" in k else nb - 1, b, b)
+            bufs[k] = torch.empty(shp, dtype=torch.complex128, device="cuda")
+            setattr(o, k, bufs[k].data_ptr())
+    bufs["status"] = torch.zeros(ne, dtype=torch.int32, device="cuda")
+    o.status_per_energy = bufs["status"].data_ptr()
+    return plan, din, o, bufs
+
+
+def _timed(step, steps, warmup):
+    import torch
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(steps):
+        step()
+    e1.record(st)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def run_strip(args, q, W):
+    """W=16 strip, b=16, N_B=32, 64 energies, Sancho-Rubio contacts, plain FP64."""
+    import numpy as np
+    import torch
+    import oracle as O
+    dev = W.strip(**W.STRIP_CFG)
+    prec = args.precision if args.precision != "emu64" else "fp64"
+    plan, din, o, bufs = _solve_setup(q, dev, prec, 64, ["GR_diag", "GL_diag", "current", "density",
+                                                         "contact", "transmission", "integrals"])
+    st = torch.cuda.current_stream()
+    launches0 = q.kernel_launches()
+    ms = _timed(lambda: plan.solve(din["_inputs"], o, st.cuda_stream), args.steps, args.warmup)
+    launches = (q.kernel_launches() - launches0) * args.steps // (args.steps + args.warmup)
+    value = 64 * args.steps / (ms / 1e3)
+    t0 = time.perf_counter()
+    ref = O.solve(dev, keep_blocks=False)
+    tc = time.perf_counter() - t0
+    err = {k: float(np.abs(bufs[k].cpu().numpy() - ref[k]).max() / np.abs(ref[k]).max())
+           for k in ("current", "density", "contact", "transmission")}
+    _line(args, value, ms / args.steps, "W=16 strip b=16 N_B=32 N_E=64 [-3.5,3.5] eta=1e-6, Sancho-Rubio "
+          "contacts, onsite U[-0.25,0.25]", prec,
+          {"gpu_launches": int(launches), "status_ok": bool(torch.all(bufs["status"] == 0).item()),
+           "cpu_baseline": {"value": 64 / tc, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                            "sample": "all 64 energies"},
+           "error_vs_oracle": err})
+
+
+def run_ozaki(args, q, W):
+    """b=1024, N_B=32 (blocks as in the mixed workload), emulated FP64, a subset of the 256 energies."""
+    import numpy as np
+    import torch
+    cfg = W.OZAKI_CFG
+    ne = args.energies if args.energies != 512 else 32
+    dev = W.random_device(cfg["b"], cfg["n_blocks"], n_energies=cfg["n_energies"], seed=0)
+    idx = np.linspace(0, cfg["n_energies"] - 1, ne).astype(int)
+    plan, din, o, bufs = _solve_setup(q, dev, args.precision, min(args.chunk, 16), ["current", "density", "integrals"],
+                                      energies=dev["energies"][idx])
+    st = torch.cuda.current_stream()
+    plan.set_profiling(True)
+    ms = _timed(lambda: plan.solve(din["_inputs"], o, st.cuda_stream), args.steps, args.warmup)
+    prof = plan.gemm_profile()
+    value = ne * args.steps / (ms / 1e3)
+    peaks, _ = measured_peaks()
+    ach = prof["pipe_flops"] / (prof["ms"] / 1e3) / 1e12 if prof["ms"] else None
+    _line(args, value, ms / args.steps, f"random BT device b=1024 N_B=32, {ne} of 256 energies on [-2,2]",
+          args.precision, {"status_ok": bool(torch.all(bufs["status"] == 0).item()),
+                           "roofline": {"bound": "tensor", "achieved": ach, "unit": "TFLOP/s",
+                                        "peak": peaks.get("bf16_tflops_sustained"),
+                                        "frac": ach / peaks.get("bf16_tflops_sustained") if ach else None}})
+
+
+def run_uneven(args, q, W):
+    """8 devices (N_B in 16..128, b in 128..512), 128 energies each, all solves captured in one CUDA
+    graph (one stream per device), energies in flight per device from the autotuner."""
+    import torch
+    from paper_2606_25595_gb300 import autotune
+    prec = args.precision if args.precision != "emu64" else "fp32"
+    devs = W.uneven_batch(n_energies=128)
+    setups, chunks = [], []
+    for dev in devs:
+        din = q.upload(dev)
+        ec = autotune.best_chunk(din, dev["block_size"], dev["n_blocks"], prec, 128,
+                                 budget_bytes=24 << 30)
+        chunks.append(ec)
+        del din
+        setups.append(_solve_setup(q, dev, prec, ec, ["current", "density", "integrals"]))
+    streams = [torch.cuda.Stream() for _ in devs]
+    cap = torch.cuda.Stream()
+
+    def launch_all():
+        for k, s in enumerate(streams):
+            s.wait_stream(torch.cuda.current_stream())
+            plan, din, o, _ = setups[k]
+            plan.solve(din["_inputs"], o, s.cuda_stream)
+        for s in streams:
+            torch.cuda.current_stream().wait_stream(s)
+
+    launch_all()
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    captured = True
+    try:
+        with torch.cuda.graph(graph, stream=cap):
+            launch_all()
+    except Exception as ex:  # capture refused: fall back to direct launches, say so
+        captured = False
+        sys.stderr.write(f"graph capture failed: {ex}\n")
+    torch.cuda.synchronize()
+    step = graph.replay if captured else launch_all
+    ms = _timed(step, args.steps, args.warmup)
+    ne_total = 128 * len(devs)
+    ok = all(bool(torch.all(s[3]["status"] == 0).item()) for s in setups)
+    _line(args, ne_total * args.steps / (ms / 1e3), ms / args.steps,
+          "8 random BT devices (N_B, b) = " + ", ".join(f"({d['n_blocks']},{d['block_size']})" for d in devs)
+          + ", 128 energies each", prec,
+          {"status_ok": ok, "cuda_graph": captured, "energies_in_flight": chunks})
+
+
+def run_serving(args, q, W):
+    """Poisson request stream (mean 200/s): b in {64,128,256,512}, N_B ~ U[16,96], N_E in {32,64,128},
+    complex64 / emulated-FP64 tags; then the same at 0.7 x the measured capacity."""
+    import numpy as np
+    from paper_2606_25595_gb300 import serve
+    models = {}
+    for b in (64, 128, 256, 512):
+        models[f"b{b}"] = serve.DeviceModel(W.random_device(b, 96, n_energies=1, seed=500 + b), f"b{b}")
+
+    def reqs(n, rate, seed):
+        out = []
+        for r in W.serving_requests(n, rate_hz=rate, seed=seed):
+            E = np.linspace(-2.0, 2.0, r["n_energies"])
+            out.append(serve.Request(len(out), f"b{r['b']}", r["n_blocks"], E,
+                                     "emu64" if r["precision"] == "emu64" else "fp32", 0.0, 0.0,
+                                     r["t_arrival"] - 0.0))
+        t0 = out[0].t_arrival if out else 0.0
+        for r in out:
+            r.t_arrival -= t0
+        return out
+
+    srv = serve.Server(models, slots=4)
+    srv.warm(("emu64", "fp32"))
+    # warm every kernel once
+    srv.run([serve.Request(0, "b64", 16, np.linspace(-1, 1, 4), "emu64"),
+             serve.Request(1, "b64", 16, np.linspace(-1, 1, 4), "fp32")])
+    sat = srv.run(reqs(args.requests, 200.0, 1))
+    lam = max(0.7 * sat["requests_per_s"], 0.05)
+    srv2 = serve.Server(models, slots=4)
+    srv2.warm(("emu64", "fp32"))
+    sub = srv2.run(reqs(max(args.requests // 2, 10), lam, 2))
+    _line(args, sat["energy_points_per_s"], 1e3 * sat["wall_s"],
+          "served RGF requests: Poisson arrivals, b in {64,128,256,512}, N_B~U[16,96], N_E in "
+          "{32,64,128}, complex64/emulated-FP64 tags", "emu64",
+          {"serving": {"saturated_200_per_s": sat, f"at_0.7_capacity_{lam:.2f}_per_s": sub,
+                       "slots": 4}})
+
+
 def main():
     args = parse()
     rank, ws, lr = dist_init()
     if args.impl == "reference":
         if rank == 0:
             run_reference(args)
+        return
+    if args.workload != "mixed":
+        from paper_2606_25595_gb300 import build as qbuild
+        qbuild.build()
+        import paper_2606_25595_gb300 as q
+        import workloads as W
+        {"strip": run_strip, "uneven": run_uneven, "ozaki": run_ozaki, "serving": run_serving}[args.workload](args, q, W)
         return
     import numpy as np
     import torch

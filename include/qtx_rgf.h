@@ -109,6 +109,9 @@ typedef struct {
   const double *energies;  /* [N_E] device array */
   const double *weights;   /* [N_E] device array of quadrature weights, or NULL for the trapezoid rule */
   int n_energies;          /* N_E >= 1 */
+  int n_blocks;            /* slices of this solve: 0 = the plan's n_blocks, else 1..plan's n_blocks (a
+                              plan sized for N_B slices serves any shorter device; block arrays are
+                              then laid out with this N_B) */
 } qtx_rgf_inputs;
 
 /* Device outputs (caller-owned; NULL = not produced).  Layouts as in QTX_OUT_*. */

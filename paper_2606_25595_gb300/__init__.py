@@ -57,7 +57,8 @@ class Inputs(ctypes.Structure):
                 ("lead_H00_R", ctypes.c_void_p), ("lead_H01_R", ctypes.c_void_p),
                 ("eta", ctypes.c_double), ("mu_L", ctypes.c_double), ("mu_R", ctypes.c_double),
                 ("kT", ctypes.c_double), ("energies", ctypes.c_void_p),
-                ("weights", ctypes.c_void_p), ("n_energies", ctypes.c_int)]
+                ("weights", ctypes.c_void_p), ("n_energies", ctypes.c_int),
+                ("n_blocks", ctypes.c_int)]
 
 
 class Outputs(ctypes.Structure):

@@ -728,13 +728,17 @@ qtx_status qtx_rgf_solve(qtx_rgf_plan P, const qtx_rgf_inputs* in, const qtx_rgf
   if (P->d.has_scattering && (!in->SigR_diag || !in->SigL_diag)) { P->err = "has_scattering set but Sigma pointers missing"; return QTX_ERR_INVALID_ARG; }
   if (P->d.leads && (!in->lead_H00_L || !in->lead_H01_L || !in->lead_H00_R || !in->lead_H01_R)) { P->err = "leads set but lead blocks missing"; return QTX_ERR_INVALID_ARG; }
   if (P->d.leads && !(in->kT > 0)) { P->err = "leads need kT > 0"; return QTX_ERR_INVALID_ARG; }
+  if (in->n_blocks < 0 || in->n_blocks > P->d.n_blocks) { P->err = "inputs->n_blocks exceeds the plan's n_blocks"; return QTX_ERR_INVALID_ARG; }
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   P->last = st;
   P->worst = 0;
+  // the workspace is laid out for the plan's n_blocks; a shorter device uses its first slices
+  P->nb = in->n_blocks ? in->n_blocks : P->d.n_blocks;
   qtx_status s;
   if (P->d.precision == QTX_FP32) s = solve_all<float>(P, in, out, st);
   else if (P->d.precision == QTX_FP64) s = solve_all<double>(P, in, out, st);
   else s = solve_all<df>(P, in, out, st);
+  P->nb = P->d.n_blocks;
   if (s == QTX_OK) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) { P->err = cudaGetErrorString(e); return QTX_ERR_CUDA; }
