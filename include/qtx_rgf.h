@@ -56,7 +56,8 @@ typedef enum {
   QTX_BF16X3 = 2, /* products from 2 bf16 digit planes per operand (3 digit products, ~13-bit
                      products) on the tcgen05 tensor cores; df32 storage; refined inverses */
   QTX_EMU64 = 3   /* emulated FP64: products from 6 bf16 digit planes per operand (21 digit products
-                     on the tcgen05 tensor cores, Ozaki-style slicing, ~41-bit products), df32 storage,
+                     on the tcgen05 tensor cores, Ozaki-style slicing, ~41-bit products; 7 planes and
+                     28 digit products for blocks larger than 512), df32 storage,
                      inverses in FP32 refined by Newton sweeps with emulated residuals */
 } qtx_precision;
 

@@ -102,115 +102,173 @@ template cudaError_t gemm_simt<double>(const GemmArgs<double>&, cudaStream_t);
 template cudaError_t gemm_simt<float>(const GemmArgs<float>&, cudaStream_t);
 
 // ============================================================================ leaf inverse
-// In-place Gauss-Jordan inverse with partial row pivoting (pivot = first row of largest
-// |Re|+|Im| in the column); the row interchanges are undone as column interchanges at the end.
-template <typename T>
-__global__ void __launch_bounds__(256) k_leaf_inverse(cx<T>* Ag, long lda, long sA, int n,
-                                                      const int* active, int* status) {
-  extern __shared__ unsigned char smem_raw[];
+// In-place Gauss-Jordan inverse with partial pivoting (pivot = first row of largest |Re|+|Im| among
+// the rows not yet used, in the current column), one CTA per block, the block held in registers.
+//
+// Rows are not moved: step k pivots on (p_k, k) wherever row p_k sits.  With P the permutation
+// (PA)[k] = A[p_k], the in-place sweep leaves B with B[p_k] = row k of (PA)^-1 = A^-1 P^T, i.e.
+//     A^-1[k][p_j] = B[p_k][j],
+// so each thread scatters its values to (step of its row, pivot row of its column's step).
+//
+// Layout: NMAX/8 warps; warp w owns rows w + (NMAX/8) m, m = 0..7; lane l owns columns l + 32 c,
+// c < NMAX/32.  Entries outside the n x n block are zero and stay zero.  Each step needs one CTA
+// barrier: at the end of step k every warp publishes, for column k+1, its best unused row already
+// scaled by the inverse of its pivot entry (double-buffered in shared memory); after the barrier
+// every thread picks the same winner (largest value, smallest row on ties) and reads the pivot row
+// straight from the winner's slot.
+template <typename T, int NMAX>
+__global__ void __launch_bounds__(NMAX * 4) k_leaf_inverse(cx<T>* Ag, long lda, long sA, int n,
+                                                          const int* active, int* status) {
+  constexpr int WARPS = NMAX / 8, C = NMAX / 32;
   const int e = blockIdx.x;
   if (active && !active[e]) return;
-  const int ld = n + 1;
-  cx<T>* a = reinterpret_cast<cx<T>*>(smem_raw);
-  cx<T>* colk = a + n * ld;
-  int* piv = reinterpret_cast<int*>(colk + n);
-  __shared__ int s_p, s_bad;
-  __shared__ cx<T> s_r;
+  __shared__ T s_val[2][WARPS];
+  __shared__ int s_row[2][WARPS];
+  __shared__ cx<T> s_prow[2][WARPS][NMAX];
   cx<T>* A = Ag + (long)e * sA;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  for (int idx = tid; idx < n * n; idx += nt) {
-    const int i = idx / n, j = idx % n;
-    a[i * ld + j] = A[(long)i * lda + j];
+  const int w = threadIdx.x / 32, lane = threadIdx.x % 32;
+  cx<T> a[8][C];
+  int rowstep[8], colpiv[C];
+  unsigned used = 0;
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const int i = w + WARPS * m;
+    rowstep[m] = 0;
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      const int j = lane + 32 * c;
+      a[m][c] = (i < n && j < n) ? A[(long)i * lda + j] : mk<T>(T(0), T(0));
+    }
   }
-  if (tid == 0) s_bad = 0;
+#pragma unroll
+  for (int c = 0; c < C; ++c) colpiv[c] = 0;
+
+  // publish this warp's pivot candidate for column kk into buffer b
+  auto publish = [&](int kk, int b) {
+    const int cc = kk / 32, owner = kk % 32;
+    T best = T(-1);
+    int bm = -1;
+    if (lane == owner) {
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+        const int i = w + WARPS * m;
+        const cx<T> v = cc == 0 ? a[m][0] : a[m][C - 1];
+        const T av = cabs1(v);
+        if (i < n && !((used >> m) & 1u) && av > best) {
+          best = av;
+          bm = m;
+        }
+      }
+    }
+    best = __shfl_sync(0xffffffffu, best, owner);
+    bm = __shfl_sync(0xffffffffu, bm, owner);
+    if (bm >= 0) {
+      cx<T> row[C];
+#pragma unroll
+      for (int c = 0; c < C; ++c) row[c] = mk<T>(T(0), T(0));
+#pragma unroll
+      for (int m = 0; m < 8; ++m)
+        if (m == bm)
+#pragma unroll
+          for (int c = 0; c < C; ++c) row[c] = a[m][c];
+      cx<T> pv = cc == 0 ? row[0] : row[C - 1];
+      pv.re = __shfl_sync(0xffffffffu, pv.re, owner);
+      pv.im = __shfl_sync(0xffffffffu, pv.im, owner);
+      const cx<T> r = crecip(pv);
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        const int j = lane + 32 * c;
+        s_prow[b][w][j] = (j == kk) ? r : row[c] * r;
+      }
+    }
+    if (lane == 0) {
+      s_val[b][w] = best;
+      s_row[b][w] = bm >= 0 ? w + WARPS * bm : -1;
+    }
+  };
+
+  bool bad = false;
+  if (n > 0) publish(0, 0);
   __syncthreads();
   for (int k = 0; k < n; ++k) {
-    if (tid < 32) {  // pivot search by warp 0: largest |Re|+|Im| in column k, first on ties
-      T best = T(-1);
-      int bi = k;
-      for (int i = k + tid; i < n; i += 32) {
-        const T v = cabs1(a[i * ld + k]);
-        if (v > best) { best = v; bi = i; }
-      }
-      for (int off = 16; off > 0; off >>= 1) {
-        const T ov = __shfl_down_sync(0xffffffffu, best, off);
-        const int oi = __shfl_down_sync(0xffffffffu, bi, off);
-        if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
-      }
-      if (tid == 0) {
-        s_p = bi;
-        piv[k] = bi;
-        if (!(best > T(0)) || !isfinite(best)) s_bad = 1;
+    const int b = k & 1;
+    T best = T(-1);
+    int p = -1, ww = 0;
+#pragma unroll
+    for (int q = 0; q < WARPS; ++q) {
+      const T v = s_val[b][q];
+      const int ri = s_row[b][q];
+      if (ri >= 0 && (v > best || (v == best && ri < p))) {
+        best = v;
+        p = ri;
+        ww = q;
       }
     }
-    __syncthreads();
-    if (s_bad) break;
-    const int p = s_p;
-    if (p != k)
-      for (int j = tid; j < n; j += nt) {
-        const cx<T> t = a[k * ld + j];
-        a[k * ld + j] = a[p * ld + j];
-        a[p * ld + j] = t;
-      }
-    __syncthreads();
-    if (tid == 0) s_r = crecip(a[k * ld + k]);
-    __syncthreads();
-    const cx<T> r = s_r;
-    for (int j = tid; j < n; j += nt) a[k * ld + j] = (j == k) ? r : a[k * ld + j] * r;
-    for (int i = tid; i < n; i += nt) colk[i] = a[i * ld + k];
-    __syncthreads();
-    for (int idx = tid; idx < n * n; idx += nt) {
-      const int i = idx / n, j = idx % n;
-      if (i == k) continue;
-      const cx<T> f = colk[i];
-      if (j == k) a[i * ld + j] = mk<T>(-(f.re * r.re - f.im * r.im), -(f.re * r.im + f.im * r.re));
-      else {
-        cx<T> v = a[i * ld + j];
-        const cx<T> w = a[k * ld + j];
-        v.re = fma(-f.re, w.re, v.re);
-        v.re = fma(f.im, w.im, v.re);
-        v.im = fma(-f.re, w.im, v.im);
-        v.im = fma(-f.im, w.re, v.im);
-        a[i * ld + j] = v;
+    if (!(best > T(0)) || !isfinite(best)) {
+      bad = true;
+      break;
+    }
+    const cx<T> r = s_prow[b][ww][k];
+    cx<T> prow[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      prow[c] = s_prow[b][ww][lane + 32 * c];
+      if (lane + 32 * c == k) colpiv[c] = p;
+    }
+    const int cc = k / 32, owner = k % 32;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const int i = w + WARPS * m;
+      cx<T> f = cc == 0 ? a[m][0] : a[m][C - 1];
+      f.re = __shfl_sync(0xffffffffu, f.re, owner);
+      f.im = __shfl_sync(0xffffffffu, f.im, owner);
+      if (i == p) {
+#pragma unroll
+        for (int c = 0; c < C; ++c) a[m][c] = prow[c];
+        used |= 1u << m;
+        rowstep[m] = k;
+      } else {
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          if (lane + 32 * c == k) {
+            a[m][c] = mk<T>(-(f.re * r.re - f.im * r.im), -(f.re * r.im + f.im * r.re));
+          } else {
+            cx<T> v = a[m][c];
+            v.re = fma(-f.re, prow[c].re, v.re);
+            v.re = fma(f.im, prow[c].im, v.re);
+            v.im = fma(-f.re, prow[c].im, v.im);
+            v.im = fma(-f.im, prow[c].re, v.im);
+            a[m][c] = v;
+          }
+        }
       }
     }
+    if (k + 1 < n) publish(k + 1, b ^ 1);
     __syncthreads();
   }
-  if (s_bad) {
-    if (tid == 0 && status) atomicCAS(status + e, 0, (int)QTX_ERR_SINGULAR);
+  if (bad) {
+    if (threadIdx.x == 0 && status) atomicCAS(status + e, 0, (int)QTX_ERR_SINGULAR);
     return;
   }
-  for (int k = n - 1; k >= 0; --k) {
-    const int p = piv[k];
-    if (p != k)
-      for (int i = tid; i < n; i += nt) {
-        const cx<T> t = a[i * ld + k];
-        a[i * ld + k] = a[i * ld + p];
-        a[i * ld + p] = t;
-      }
-    __syncthreads();
-  }
-  for (int idx = tid; idx < n * n; idx += nt) {
-    const int i = idx / n, j = idx % n;
-    A[(long)i * lda + j] = a[i * ld + j];
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const int i = w + WARPS * m;
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      const int j = lane + 32 * c;
+      if (i < n && j < n) A[(long)rowstep[m] * lda + colpiv[c]] = a[m][c];
+    }
   }
 }
 
 template <typename T>
-cudaError_t leaf_inverse(cx<T>* A, long lda, long sA, int n, int batch, const int* active,
-                         int* status, cudaStream_t st) {
+cudaError_t leaf_inverse(cx<T>* A, long lda, long sA, int n, int batch, const int* active, int* status,
+                         cudaStream_t st) {
   if (n <= 0 || n > kLeafMax) return cudaErrorInvalidValue;
-  const size_t smem = (size_t)n * (n + 1) * sizeof(cx<T>) + n * sizeof(cx<T>) + n * sizeof(int) + 16;
-  static bool attr_set[2] = {false, false};
-  const int which = sizeof(T) == 8 ? 0 : 1;
-  if (!attr_set[which]) {
-    cudaError_t err = cudaFuncSetAttribute(k_leaf_inverse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)((size_t)kLeafMax * (kLeafMax + 2) * sizeof(cx<T>) + 1024));
-    if (err != cudaSuccess) return err;
-    attr_set[which] = true;
-  }
-  const int threads = n <= 16 ? 64 : (n <= 32 ? 128 : 256);
-  k_leaf_inverse<T><<<batch, threads, smem, st>>>(A, lda, sA, n, active, status);
+  if (n <= 32)
+    k_leaf_inverse<T, 32><<<batch, 128, 0, st>>>(A, lda, sA, n, active, status);
+  else
+    k_leaf_inverse<T, 64><<<batch, 256, 0, st>>>(A, lda, sA, n, active, status);
   count_launch();
   return cudaGetLastError();
 }

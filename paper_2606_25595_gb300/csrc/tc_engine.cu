@@ -17,7 +17,8 @@
 // The epilogue adds the five with error-free FP32 TwoSum steps (the exact groups are summed exactly up
 // to the final df32 rounding), applies the row/column scales and writes df32.
 // With S = 6 digits (21 digit products) the products carry ~41 bits for K <= 256 (the "emulated FP64"
-// mode); with S = 2 (3 digit products) they carry ~13 bits ("BF16x3").
+// mode); for K > 512, where l1 = 5, that mode takes S = 7 (28 digit products, ~44 bits) instead.
+// With S = 2 (3 digit products) they carry ~13 bits ("BF16x3").
 //
 // Complex arithmetic uses the real embedding (4M form):
 //     [D_re | D_im] = [A_re | A_im] * [[B_re, B_im], [-B_im, B_re]]
@@ -28,7 +29,7 @@
 // Kernel structure (one CTA per 128 x 48 complex output tile, 10 warps):
 //   warp 0   producer: one bulk asynchronous copy (cp.async.bulk, mbarrier complete-tx) per plane
 //            tile of one K-stage (16 K-elements; the digitiser stores every tile contiguously, already
-//            in the 32-byte-swizzled K-major layout the MMA descriptors expect), 5 stages deep;
+//            in the 32-byte-swizzled K-major layout the MMA descriptors expect), 4-8 stages deep;
 //   warp 1   allocates 512 TMEM columns; one thread issues the tcgen05.mma's (2 K16 steps x pairs)
 //            and tcgen05.commit's the stage back to the producer;
 //   warps 2-9 epilogue (two warps per TMEM lane quarter, one per column half): tcgen05.ld of the
@@ -395,7 +396,7 @@ __device__ __forceinline__ void digits_of(df x, int sh, int (&d)[S]) {
 
 // Digit planes of one operand.  side 0 (left, A = op(X), M x K): plane[e][i][r][k] = digit_i(Re L),
 // plane[e][i][r][K_pad + k] = digit_i(Im L).  side 1 (right, B = op(X), K x N, logical row r = column
-// n of B): rows re = (n/64)*128 + n%64 and im = re + 64 of the embedded, transposed operand:
+// n of B): rows re = (n/48)*96 + n%48 and im = re + 48 of the embedded, transposed operand:
 //   [re row] = [ Re B(:,n) | -Im B(:,n) ],   [im row] = [ Im B(:,n) | Re B(:,n) ].
 template <int S>
 __global__ void __launch_bounds__(256) k_digitize(const cx<df>* X, long ldx, long sX, int R, int K,
@@ -460,6 +461,133 @@ __global__ void __launch_bounds__(256) k_digitize(const cx<df>* X, long ldx, lon
   }
 }
 
+// Fused exponent + digit pass over RPC whole logical rows per CTA (used whenever a strip of RPC
+// rows fits in shared memory, i.e. K up to ~11000): the strip is read from global memory once into
+// shared memory (coalesced along k for direct rows, along r for transposed ones), the row exponents
+// are reduced on the way in, and every thread then turns one (row, 8 complex k) item into the S
+// digit planes with 16-byte stores -- one swizzled half-row chunk per plane and part.  The strip is
+// skewed by one element per 8 so that the threads' 128-byte item reads fall in distinct banks.
+// Item layout as k_digitize: A rows [Re | Im]; B re row [Re | -Im], im row [Im | Re] (a bf16 sign
+// flip, exact).  Rows r >= R and k >= K are written as zero digits, with exponent -1000.
+__host__ __device__ constexpr int strip_skew(int k) { return k + (k >> 3); }
+
+template <int S, int RPC>
+__global__ void __launch_bounds__(256) k_digitize_rows(const cx<df>* X, long ldx, long sX, int R, int K, int R_pad,
+                                                       int K_pad, int transposed, int conj_, int side, int* eout,
+                                                       int P, unsigned char* planes, long rows_plane,
+                                                       const int* active) {
+  const int e = blockIdx.y;
+  if (active && !active[e]) return;
+  extern __shared__ __align__(16) unsigned char dsm[];
+  const int ldS = strip_skew(K_pad) + 1;  // complex elements per strip row
+  cx<df>* strip = reinterpret_cast<cx<df>*>(dsm);
+  __shared__ int s_ex[RPC];
+  const cx<df>* Xe = X + (long)e * sX;
+  const int r0 = blockIdx.x * RPC, t = threadIdx.x;
+  if (t < RPC) s_ex[t] = -1000;
+  __syncthreads();
+  const cx<df> zero = {mkdf(0.f, 0.f), mkdf(0.f, 0.f)};
+  // ---- load the strip (zero beyond R, K) and reduce the row exponents
+  if (!transposed) {
+#pragma unroll 1
+    for (int rr = 0; rr < RPC; ++rr) {
+      const int r = r0 + rr;
+      int mx = -1000;
+      for (int k = t; k < K_pad; k += 256) {
+        cx<df> v = zero;
+        if (r < R && k < K) {
+          v = Xe[(long)r * ldx + k];
+          mx = max(mx, max(df_expo(v.re.hi), df_expo(v.im.hi)));
+        }
+        strip[rr * ldS + strip_skew(k)] = v;
+      }
+      for (int off = 16; off > 0; off >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+      if ((t & 31) == 0 && mx > -1000) atomicMax(&s_ex[rr], mx);
+    }
+  } else {
+    const int rr = t % RPC, r = r0 + rr;
+    int mx = -1000;
+    for (int k = t / RPC; k < K_pad; k += 256 / RPC) {
+      cx<df> v = zero;
+      if (r < R && k < K) {
+        v = Xe[(long)k * ldx + r];
+        mx = max(mx, max(df_expo(v.re.hi), df_expo(v.im.hi)));
+      }
+      strip[rr * ldS + strip_skew(k)] = v;
+    }
+    if (mx > -1000) atomicMax(&s_ex[rr], mx);
+  }
+  __syncthreads();
+  if (t < RPC && r0 + t < R_pad) eout[(long)e * R_pad + r0 + t] = s_ex[t];
+  // ---- digits: item = (row rr, complex k = 8 kc .. 8 kc + 7)
+  const int rows_blk = side == 0 ? BM : BNR;
+  const long tile_bytes = (long)rows_blk * BKS * 2;
+  const long nks = 2L * K_pad / BKS;
+  const long plane_bytes = (rows_plane / rows_blk) * nks * tile_bytes;
+  unsigned char* pe = planes + (long)e * S * plane_bytes;
+  const int nkc = K_pad / 8;
+  // byte offset of the 16-byte chunk holding embedded k' .. k' + 7 (k' a multiple of 8) of plane row
+  auto chunk_off = [&](long row, int kp) -> long {
+    const long blk = row / rows_blk, rr_ = row % rows_blk, ks = kp / BKS, kk = kp % BKS;
+    return (blk * nks + ks) * tile_bytes + sw32_offset((uint32_t)rr_, (uint32_t)kk);
+  };
+#pragma unroll 1
+  for (int item = t; item < RPC * nkc; item += 256) {
+    const int rr = item / nkc, kc = item % nkc, r = r0 + rr;
+    if (r >= R_pad) continue;
+    const int sh = P - s_ex[rr];
+    uint32_t wre[S][4], wim[S][4];
+#pragma unroll
+    for (int j = 0; j < 8; j += 2) {
+      int d0r[S], d0i[S], d1r[S], d1i[S];
+      cx<df> v0 = strip[rr * ldS + strip_skew(8 * kc + j)];
+      cx<df> v1 = strip[rr * ldS + strip_skew(8 * kc + j + 1)];
+      if (conj_) {
+        v0.im = df_neg(v0.im);
+        v1.im = df_neg(v1.im);
+      }
+      digits_of<S>(v0.re, sh, d0r);
+      digits_of<S>(v0.im, sh, d0i);
+      digits_of<S>(v1.re, sh, d1r);
+      digits_of<S>(v1.im, sh, d1i);
+#pragma unroll
+      for (int i = 0; i < S; ++i) {
+        const float sc = __int_as_float((127 - DW * i) << 23);  // 2^(-7 i)
+        const uint32_t lo_r = __bfloat16_as_ushort(__float2bfloat16_rn((float)d0r[i] * sc));
+        const uint32_t hi_r = __bfloat16_as_ushort(__float2bfloat16_rn((float)d1r[i] * sc));
+        const uint32_t lo_i = __bfloat16_as_ushort(__float2bfloat16_rn((float)d0i[i] * sc));
+        const uint32_t hi_i = __bfloat16_as_ushort(__float2bfloat16_rn((float)d1i[i] * sc));
+        wre[i][j / 2] = lo_r | (hi_r << 16);
+        wim[i][j / 2] = lo_i | (hi_i << 16);
+      }
+    }
+    const int k8 = 8 * kc;
+    if (side == 0) {
+      const long o_re = chunk_off(r, k8), o_im = chunk_off(r, K_pad + k8);
+#pragma unroll
+      for (int i = 0; i < S; ++i) {
+        unsigned char* pl = pe + (long)i * plane_bytes;
+        *reinterpret_cast<uint4*>(pl + o_re) = make_uint4(wre[i][0], wre[i][1], wre[i][2], wre[i][3]);
+        *reinterpret_cast<uint4*>(pl + o_im) = make_uint4(wim[i][0], wim[i][1], wim[i][2], wim[i][3]);
+      }
+    } else {
+      const long rre = (long)(r / BNC) * BNR + (r % BNC), rim = rre + BNC;
+      const long o1 = chunk_off(rre, k8), o2 = chunk_off(rre, K_pad + k8);
+      const long o3 = chunk_off(rim, k8), o4 = chunk_off(rim, K_pad + k8);
+      const uint32_t SGN = 0x80008000u;  // bf16 sign bits of both halves
+#pragma unroll
+      for (int i = 0; i < S; ++i) {
+        unsigned char* pl = pe + (long)i * plane_bytes;
+        *reinterpret_cast<uint4*>(pl + o1) = make_uint4(wre[i][0], wre[i][1], wre[i][2], wre[i][3]);
+        *reinterpret_cast<uint4*>(pl + o2) =
+            make_uint4(wim[i][0] ^ SGN, wim[i][1] ^ SGN, wim[i][2] ^ SGN, wim[i][3] ^ SGN);
+        *reinterpret_cast<uint4*>(pl + o3) = make_uint4(wim[i][0], wim[i][1], wim[i][2], wim[i][3]);
+        *reinterpret_cast<uint4*>(pl + o4) = make_uint4(wre[i][0], wre[i][1], wre[i][2], wre[i][3]);
+      }
+    }
+  }
+}
+
 // ------------------------------------------------------------------------------ host side
 struct Dims {
   int M_pad, N_pad, K_pad, l1, P;
@@ -508,6 +636,34 @@ cudaError_t digitize(const cx<df>* X, long ldx, long sX, int opX, int side, int 
   const int transposed = (side == 0) ? (opX == OP_C) : (opX == OP_N);
   const int cj = opX == OP_C;
   const int R_pad = side == 0 ? d.M_pad : d.N_pad;
+  const long rows_plane = side == 0 ? d.M_pad : 2L * d.N_pad;
+  // fused pass: RPC rows per CTA, the largest of 8, 4, 2, 1 whose strip stays within 48 KB of shared
+  // memory (a few CTAs per SM), or a single row up to the 200 KB the kernel is allowed
+  const size_t row_bytes = (size_t)(strip_skew(d.K_pad) + 1) * sizeof(cx<df>);
+  int rpc = 8;
+  while (rpc > 1 && rpc * row_bytes > 48 * 1024) rpc /= 2;
+  if (rpc * row_bytes <= 200 * 1024) {
+    static bool attr = false;
+    if (!attr) {
+      cudaError_t ea = cudaSuccess;
+      ea = cudaFuncSetAttribute(k_digitize_rows<S, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      if (ea == cudaSuccess) ea = cudaFuncSetAttribute(k_digitize_rows<S, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      if (ea == cudaSuccess) ea = cudaFuncSetAttribute(k_digitize_rows<S, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      if (ea == cudaSuccess) ea = cudaFuncSetAttribute(k_digitize_rows<S, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      if (ea != cudaSuccess) return ea;
+      attr = true;
+    }
+    const size_t smem = rpc * row_bytes;
+    dim3 g(R_pad / rpc, batch);
+    switch (rpc) {
+      case 8: k_digitize_rows<S, 8><<<g, 256, smem, st>>>(X, ldx, sX, R, K, R_pad, d.K_pad, transposed, cj, side, eout, d.P, planes, rows_plane, active); break;
+      case 4: k_digitize_rows<S, 4><<<g, 256, smem, st>>>(X, ldx, sX, R, K, R_pad, d.K_pad, transposed, cj, side, eout, d.P, planes, rows_plane, active); break;
+      case 2: k_digitize_rows<S, 2><<<g, 256, smem, st>>>(X, ldx, sX, R, K, R_pad, d.K_pad, transposed, cj, side, eout, d.P, planes, rows_plane, active); break;
+      default: k_digitize_rows<S, 1><<<g, 256, smem, st>>>(X, ldx, sX, R, K, R_pad, d.K_pad, transposed, cj, side, eout, d.P, planes, rows_plane, active); break;
+    }
+    count_launch();
+    return cudaGetLastError();
+  }
   {
     dim3 g((R_pad + 31) / 32, batch);
     k_row_expo<<<g, 256, 0, st>>>(X, ldx, sX, R, K, R_pad, transposed, eout, active);
@@ -515,7 +671,6 @@ cudaError_t digitize(const cx<df>* X, long ldx, long sX, int opX, int side, int 
   }
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
-  const long rows_plane = side == 0 ? d.M_pad : 2L * d.N_pad;
   dim3 g(d.K_pad / 32, (R_pad + 31) / 32, batch);
   k_digitize<S><<<g, 256, 0, st>>>(X, ldx, sX, R, K, R_pad, d.K_pad, transposed, cj, side, eout, d.P, planes,
                                    rows_plane, active);
@@ -580,14 +735,21 @@ bool tc_available() {
   return major == 10 && minor == 3;
 }
 
+// Digits actually used: the emulated-FP64 mode takes a seventh digit when K > 512, where the
+// leading digit has shrunk to l1 = 5 bits (dims_of) and six digits would carry only 40 bits.
+static int effective_digits(int digits, int K) { return (digits == 6 && K > 512) ? 7 : digits; }
+
 size_t gemm_tc_scratch_bytes(int M, int N, int K, int batch, int digits) {
-  const tc::Dims d = tc::dims_of(M, N, K, digits);
-  return tc::carve(nullptr, d, batch, digits).bytes + 4096;
+  const int S = effective_digits(digits, K);
+  const tc::Dims d = tc::dims_of(M, N, K, S);
+  return tc::carve(nullptr, d, batch, S).bytes + 4096;
 }
 
 cudaError_t gemm_tc(const TcArgs& a, int digits, void* scratch, size_t scratch_bytes, int* err_flag,
                     cudaStream_t st, cudaEvent_t* ev) {
   if (a.M <= 0 || a.N <= 0 || a.batch <= 0) return cudaSuccess;
+  digits = effective_digits(digits, a.K);
+  if (digits == 7) return tc::launch<7, 4>(a, scratch, scratch_bytes, err_flag, st, ev);
   if (digits == 6) return tc::launch<6, 5>(a, scratch, scratch_bytes, err_flag, st, ev);
   if (digits == 2) return tc::launch<2, 8>(a, scratch, scratch_bytes, err_flag, st, ev);
   return cudaErrorInvalidValue;

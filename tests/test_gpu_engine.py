@@ -76,6 +76,24 @@ def test_emu64_random_error_bound(q, M, N, K, batch):
     assert np.all(np.abs(got - ref) <= 2.0 ** -36 * bound)
 
 
+@pytest.mark.parametrize("K,bits", [(512, 35), (1024, 36)])
+def test_emu64_random_error_bound_long_k(q, K, bits):
+    """Long contractions (b = 512, 1024 blocks): the leading digit shrinks to keep the exact
+    accumulators below 2^24 units (l1 = 6 for K <= 512, 5 for K <= 1024).  At K = 512 six digits
+    carry P = 7*5 + l1 - 1 = 40 bits, one less than at K <= 256, so the bound is 2^-35 (|A| |B|);
+    at K = 1024 the engine takes a seventh digit (P = 46) and the bound returns to 2^-36."""
+    rng = np.random.default_rng(K)
+    M, N, batch = 256, 144, 2
+    A = (rng.standard_normal((batch, M, K)) + 1j * rng.standard_normal((batch, M, K))) * \
+        np.exp(rng.uniform(-3, 3, (batch, M, 1)))
+    B = rng.standard_normal((batch, K, N)) + 1j * rng.standard_normal((batch, K, N))
+    got = q.zgemm_batched(_t(A), _t(B), "emu64").cpu().numpy()
+    ref = A @ B
+    bound = (np.abs(A.real) + np.abs(A.imag)) @ (np.abs(B.real) + np.abs(B.imag))
+    ratio = np.max(np.abs(got - ref) / bound)
+    assert ratio <= 2.0 ** -bits, np.log2(ratio)
+
+
 def test_bf16x3_error_bound(q):
     """Two digit planes (~13-bit products): |C - C_ref| <= 2^-11 * (|A| |B|)."""
     rng = np.random.default_rng(11)

@@ -253,6 +253,21 @@ def test_emu64_rgf_mixed_workload_sampled(q):
     _check(res, ref, 1e-7, 1e-6, keys=("GR_diag", "GL_diag"))
 
 
+def test_emu64_rgf_b1024_sampled(q):
+    """b=1024 blocks (the Ozaki-shaped workload: K = 1024 contractions, leading digit l1 = 5) on a
+    4-slice device at two energies of that workload's grid: current and density within 1e-6 of the
+    FP64 oracle, G blocks within 1e-7."""
+    dev = W.random_device(1024, 4, n_energies=W.OZAKI_CFG["n_energies"], seed=0)
+    idx = [37, 200]
+    ref = O.solve(dev, energy_indices=idx, keep_blocks=True)
+    res = q.solve_device(dev, "emu64", energies=dev["energies"][idx],
+                         outputs=["GR_diag", "GR_upper", "GL_diag", "GL_upper", "current", "density"])
+    assert np.all(res["status"] == 0)
+    e = _obs_errs(res, ref)
+    assert e["current"] < 1e-6 and e["density"] < 1e-6, e
+    _check(res, ref, 1e-7, 1e-6, keys=("GR_diag", "GR_upper", "GL_diag", "GL_upper"))
+
+
 def test_bf16x3_rgf_error_within_stated_bound(q):
     """Two digit planes (~13-bit products, 3 bf16 digit products per real product): the error
     follows kappa * 2^-13 and is large -- G blocks within 0.5, density within 0.2 on this
