@@ -461,6 +461,48 @@ __global__ void __launch_bounds__(256) k_digitize(const cx<df>* X, long ldx, lon
   }
 }
 
+// Digits of one df32 value in floating point (used by the fused pass).  With the row scaled so the
+// leading digit's unit is 1 (x' = x 2^(l1 - 1 - e_row), |x'| < 2^(l1-1)), digit i (0-based) is a
+// multiple of U_i = 2^(-7 i) -- exactly the pre-scaled plane value d_i 2^(-7 i).  Each digit is the
+// residual rounded to a multiple of U_i by adding and subtracting 1.5 * 2^23 * U_i (exact, round to
+// nearest), leaving an exact residual of at most U_i / 2 = 64 U_(i+1).  hi gives all S digits; lo
+// (|lo'| <= ulp(hi')/2 <= 2^-19) only reaches digits 3.. (0-based), which take the sum of both
+// parts; a bottom-up carry brings those back to |d_i| <= 64 U_i (digit 2 may end at 65 U_2).  The
+// represented value is within one unit U_(S-1) of x'.
+__device__ __forceinline__ float round_sigma(int i) { return 1.5f * __int_as_float((127 + 23 - DW * i) << 23); }
+template <int S>
+__device__ __forceinline__ void split_digits(df x, float f1, float f2, float (&d)[S]) {
+  float r = x.hi * f1 * f2;
+#pragma unroll
+  for (int i = 0; i < S; ++i) {
+    const float sg = round_sigma(i);
+    const float di = __fsub_rn(__fadd_rn(r, sg), sg);
+    d[i] = di;
+    r = __fsub_rn(r, di);
+  }
+  if constexpr (S >= 4) {
+    float t = x.lo * f1 * f2;
+#pragma unroll
+    for (int i = 3; i < S; ++i) {
+      const float sg = round_sigma(i);
+      const float di = __fsub_rn(__fadd_rn(t, sg), sg);
+      d[i] = __fadd_rn(d[i], di);
+      t = __fsub_rn(t, di);
+    }
+#pragma unroll
+    for (int i = S - 1; i >= 3; --i) {
+      const float sg = round_sigma(i - 1);
+      const float c = __fsub_rn(__fadd_rn(d[i], sg), sg);
+      d[i] = __fsub_rn(d[i], c);
+      d[i - 1] = __fadd_rn(d[i - 1], c);
+    }
+  }
+}
+__device__ __forceinline__ uint32_t bf16x2_bits(float lo_half, float hi_half) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(lo_half, hi_half);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+
 // Fused exponent + digit pass over RPC whole logical rows per CTA (used whenever a strip of RPC
 // rows fits in shared memory, i.e. K up to ~11000): the strip is read from global memory once into
 // shared memory (coalesced along k for direct rows, along r for transposed ones), the row exponents
@@ -472,7 +514,7 @@ __global__ void __launch_bounds__(256) k_digitize(const cx<df>* X, long ldx, lon
 __host__ __device__ constexpr int strip_skew(int k) { return k + (k >> 3); }
 
 template <int S, int RPC>
-__global__ void __launch_bounds__(256) k_digitize_rows(const cx<df>* X, long ldx, long sX, int R, int K, int R_pad,
+__global__ void __launch_bounds__(32 * RPC) k_digitize_rows(const cx<df>* X, long ldx, long sX, int R, int K, int R_pad,
                                                        int K_pad, int transposed, int conj_, int side, int* eout,
                                                        int P, unsigned char* planes, long rows_plane,
                                                        const int* active) {
@@ -482,38 +524,54 @@ __global__ void __launch_bounds__(256) k_digitize_rows(const cx<df>* X, long ldx
   const int ldS = strip_skew(K_pad) + 1;  // complex elements per strip row
   cx<df>* strip = reinterpret_cast<cx<df>*>(dsm);
   __shared__ int s_ex[RPC];
+  constexpr int NT = 32 * RPC;  // threads: one warp per strip row
   const cx<df>* Xe = X + (long)e * sX;
   const int r0 = blockIdx.x * RPC, t = threadIdx.x;
   if (t < RPC) s_ex[t] = -1000;
   __syncthreads();
   const cx<df> zero = {mkdf(0.f, 0.f), mkdf(0.f, 0.f)};
-  // ---- load the strip (zero beyond R, K) and reduce the row exponents
+  // ---- load the strip (zero beyond R, K) and reduce the row exponents; loads are batched (all
+  // rows of a direct strip, four k of a transposed one) before their first use
   if (!transposed) {
-#pragma unroll 1
-    for (int rr = 0; rr < RPC; ++rr) {
-      const int r = r0 + rr;
-      int mx = -1000;
-      for (int k = t; k < K_pad; k += 256) {
-        cx<df> v = zero;
-        if (r < R && k < K) {
-          v = Xe[(long)r * ldx + k];
-          mx = max(mx, max(df_expo(v.re.hi), df_expo(v.im.hi)));
-        }
-        strip[rr * ldS + strip_skew(k)] = v;
+    int mx[RPC];
+#pragma unroll
+    for (int rr = 0; rr < RPC; ++rr) mx[rr] = -1000;
+    for (int k = t; k < K_pad; k += NT) {
+      cx<df> v[RPC];
+#pragma unroll
+      for (int rr = 0; rr < RPC; ++rr) {
+        const int r = r0 + rr;
+        v[rr] = (r < R && k < K) ? Xe[(long)r * ldx + k] : zero;
       }
-      for (int off = 16; off > 0; off >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-      if ((t & 31) == 0 && mx > -1000) atomicMax(&s_ex[rr], mx);
+#pragma unroll
+      for (int rr = 0; rr < RPC; ++rr) {
+        strip[rr * ldS + strip_skew(k)] = v[rr];
+        if (r0 + rr < R && k < K) mx[rr] = max(mx[rr], max(df_expo(v[rr].re.hi), df_expo(v[rr].im.hi)));
+      }
+    }
+#pragma unroll
+    for (int rr = 0; rr < RPC; ++rr) {
+      int m = mx[rr];
+      for (int off = 16; off > 0; off >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, off));
+      if ((t & 31) == 0 && m > -1000) atomicMax(&s_ex[rr], m);
     }
   } else {
+    constexpr int KS = NT / RPC;  // k stride between a thread's elements
     const int rr = t % RPC, r = r0 + rr;
     int mx = -1000;
-    for (int k = t / RPC; k < K_pad; k += 256 / RPC) {
-      cx<df> v = zero;
-      if (r < R && k < K) {
-        v = Xe[(long)k * ldx + r];
-        mx = max(mx, max(df_expo(v.re.hi), df_expo(v.im.hi)));
+    for (int k0 = t / RPC; k0 < K_pad; k0 += 4 * KS) {
+      cx<df> v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int k = k0 + u * KS;
+        v[u] = (r < R && k < K) ? Xe[(long)k * ldx + r] : zero;
       }
-      strip[rr * ldS + strip_skew(k)] = v;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int k = k0 + u * KS;
+        if (k < K_pad) strip[rr * ldS + strip_skew(k)] = v[u];
+        if (r < R && k < K) mx = max(mx, max(df_expo(v[u].re.hi), df_expo(v[u].im.hi)));
+      }
     }
     if (mx > -1000) atomicMax(&s_ex[rr], mx);
   }
@@ -532,33 +590,31 @@ __global__ void __launch_bounds__(256) k_digitize_rows(const cx<df>* X, long ldx
     return (blk * nks + ks) * tile_bytes + sw32_offset((uint32_t)rr_, (uint32_t)kk);
   };
 #pragma unroll 1
-  for (int item = t; item < RPC * nkc; item += 256) {
+  for (int item = t; item < RPC * nkc; item += NT) {
     const int rr = item / nkc, kc = item % nkc, r = r0 + rr;
     if (r >= R_pad) continue;
-    const int sh = P - s_ex[rr];
+    // scale 2^(l1 - 1 - e_row) = 2^(P - 7 (S-1) - e_row), as two factors (e_row may be -1000)
+    int Es = P - DW * (S - 1) - s_ex[rr];
+    Es = Es < -250 ? -250 : (Es > 250 ? 250 : Es);
+    const float f1 = __int_as_float((Es / 2 + 127) << 23), f2 = __int_as_float((Es - Es / 2 + 127) << 23);
     uint32_t wre[S][4], wim[S][4];
 #pragma unroll
     for (int j = 0; j < 8; j += 2) {
-      int d0r[S], d0i[S], d1r[S], d1i[S];
+      float d0r[S], d0i[S], d1r[S], d1i[S];
       cx<df> v0 = strip[rr * ldS + strip_skew(8 * kc + j)];
       cx<df> v1 = strip[rr * ldS + strip_skew(8 * kc + j + 1)];
       if (conj_) {
         v0.im = df_neg(v0.im);
         v1.im = df_neg(v1.im);
       }
-      digits_of<S>(v0.re, sh, d0r);
-      digits_of<S>(v0.im, sh, d0i);
-      digits_of<S>(v1.re, sh, d1r);
-      digits_of<S>(v1.im, sh, d1i);
+      split_digits<S>(v0.re, f1, f2, d0r);
+      split_digits<S>(v0.im, f1, f2, d0i);
+      split_digits<S>(v1.re, f1, f2, d1r);
+      split_digits<S>(v1.im, f1, f2, d1i);
 #pragma unroll
       for (int i = 0; i < S; ++i) {
-        const float sc = __int_as_float((127 - DW * i) << 23);  // 2^(-7 i)
-        const uint32_t lo_r = __bfloat16_as_ushort(__float2bfloat16_rn((float)d0r[i] * sc));
-        const uint32_t hi_r = __bfloat16_as_ushort(__float2bfloat16_rn((float)d1r[i] * sc));
-        const uint32_t lo_i = __bfloat16_as_ushort(__float2bfloat16_rn((float)d0i[i] * sc));
-        const uint32_t hi_i = __bfloat16_as_ushort(__float2bfloat16_rn((float)d1i[i] * sc));
-        wre[i][j / 2] = lo_r | (hi_r << 16);
-        wim[i][j / 2] = lo_i | (hi_i << 16);
+        wre[i][j / 2] = bf16x2_bits(d0r[i], d1r[i]);
+        wim[i][j / 2] = bf16x2_bits(d0i[i], d1i[i]);
       }
     }
     const int k8 = 8 * kc;
@@ -637,30 +693,25 @@ cudaError_t digitize(const cx<df>* X, long ldx, long sX, int opX, int side, int 
   const int cj = opX == OP_C;
   const int R_pad = side == 0 ? d.M_pad : d.N_pad;
   const long rows_plane = side == 0 ? d.M_pad : 2L * d.N_pad;
-  // fused pass: RPC rows per CTA, the largest of 8, 4, 2, 1 whose strip stays within 48 KB of shared
-  // memory (a few CTAs per SM), or a single row up to the 200 KB the kernel is allowed
+  // fused pass: RPC rows per CTA with one warp per row -- two rows while the strip stays within
+  // 48 KB of shared memory (many small CTAs per SM, so loads, digit arithmetic and stores of
+  // different CTAs overlap), else a single row up to the 200 KB the kernel is allowed
   const size_t row_bytes = (size_t)(strip_skew(d.K_pad) + 1) * sizeof(cx<df>);
-  int rpc = 8;
-  while (rpc > 1 && rpc * row_bytes > 48 * 1024) rpc /= 2;
+  const int rpc = 2 * row_bytes <= 48 * 1024 ? 2 : 1;
   if (rpc * row_bytes <= 200 * 1024) {
     static bool attr = false;
     if (!attr) {
-      cudaError_t ea = cudaSuccess;
-      ea = cudaFuncSetAttribute(k_digitize_rows<S, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      if (ea == cudaSuccess) ea = cudaFuncSetAttribute(k_digitize_rows<S, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      if (ea == cudaSuccess) ea = cudaFuncSetAttribute(k_digitize_rows<S, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      cudaError_t ea = cudaFuncSetAttribute(k_digitize_rows<S, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
       if (ea == cudaSuccess) ea = cudaFuncSetAttribute(k_digitize_rows<S, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
       if (ea != cudaSuccess) return ea;
       attr = true;
     }
     const size_t smem = rpc * row_bytes;
     dim3 g(R_pad / rpc, batch);
-    switch (rpc) {
-      case 8: k_digitize_rows<S, 8><<<g, 256, smem, st>>>(X, ldx, sX, R, K, R_pad, d.K_pad, transposed, cj, side, eout, d.P, planes, rows_plane, active); break;
-      case 4: k_digitize_rows<S, 4><<<g, 256, smem, st>>>(X, ldx, sX, R, K, R_pad, d.K_pad, transposed, cj, side, eout, d.P, planes, rows_plane, active); break;
-      case 2: k_digitize_rows<S, 2><<<g, 256, smem, st>>>(X, ldx, sX, R, K, R_pad, d.K_pad, transposed, cj, side, eout, d.P, planes, rows_plane, active); break;
-      default: k_digitize_rows<S, 1><<<g, 256, smem, st>>>(X, ldx, sX, R, K, R_pad, d.K_pad, transposed, cj, side, eout, d.P, planes, rows_plane, active); break;
-    }
+    if (rpc == 2)
+      k_digitize_rows<S, 2><<<g, 64, smem, st>>>(X, ldx, sX, R, K, R_pad, d.K_pad, transposed, cj, side, eout, d.P, planes, rows_plane, active);
+    else
+      k_digitize_rows<S, 1><<<g, 32, smem, st>>>(X, ldx, sX, R, K, R_pad, d.K_pad, transposed, cj, side, eout, d.P, planes, rows_plane, active);
     count_launch();
     return cudaGetLastError();
   }
