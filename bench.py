@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="emu64", choices=["emu64", "fp32", "bf16x3", "fp64"])
-    ap.add_argument("--chunk", type=int, default=128, help="energies in flight per chunk")
+    ap.add_argument("--chunk", type=int, default=512, help="energies in flight per chunk (512: all 512 energies of the mixed workload in one chunk, 6144 product tiles = 40.4 waves on 152 SMs)")
     ap.add_argument("--block", type=int, default=256)
     ap.add_argument("--slices", type=int, default=64)
     ap.add_argument("--energies", type=int, default=512)

@@ -273,7 +273,14 @@ __global__ void __launch_bounds__(320, 1) k_tc_gemm(TcParams p) {
     const int m = mblk * BM + r;
     // one thread waits for the accumulators; the other epilogue threads sleep in a named barrier
     // instead of polling shared memory while the tensor core reads its operands from it
+    // The scale exponents are fetched while the mainloop runs: this row's into a register, the
+    // tile's 48 column exponents into shared memory (global loads in the epilogue's inner loop would
+    // put an L2 round trip on its critical path).
     __shared__ int s_got;
+    __shared__ int s_eB[BNC];
+    const int eAm = p.eA[(long)(p.a_batched ? e : 0) * p.M_pad + m];
+    if (threadIdx.x >= 64 && threadIdx.x < 64 + BNC)
+      s_eB[threadIdx.x - 64] = p.eB[(long)(p.b_batched ? e : 0) * p.N_pad + nblk * BNC + threadIdx.x - 64];
     if (threadIdx.x == 64) s_got = mbar_wait(accb, 0, p.err) ? 1 : 0;
     __syncwarp();
     asm volatile("bar.sync 2, 256;" ::: "memory");
@@ -281,8 +288,6 @@ __global__ void __launch_bounds__(320, 1) k_tc_gemm(TcParams p) {
     fence_after();
     cx<df>* out = reinterpret_cast<cx<df>*>(base);  // [BM][OUT_LD] staging (pipeline smem is idle now)
     if (got) {
-      const int eAm = p.eA[(long)(p.a_batched ? e : 0) * p.M_pad + m];
-      const int* eBrow = p.eB + (long)(p.b_batched ? e : 0) * p.N_pad;
       const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16);
 #pragma unroll 1
       for (int c0 = h * (BNC / 2); c0 < (h + 1) * (BNC / 2); c0 += 8) {
@@ -295,12 +300,14 @@ __global__ void __launch_bounds__(320, 1) k_tc_gemm(TcParams p) {
         tmem_wait_ld();
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
-          const int n = nblk * BNC + c0 + c;
-          const int Es = eAm + eBrow[n] - p.escale;
+          // 2^Es as two factors (as scale2), shared by the four parts of the output value
+          int Es = eAm + s_eB[c0 + c] - p.escale;
+          Es = Es < -250 ? -250 : (Es > 250 ? 250 : Es);
+          const float f1 = __int_as_float((Es / 2 + 127) << 23), f2 = __int_as_float((Es - Es / 2 + 127) << 23);
           const df sr = sum_acc<NACC>(vr, c), si = sum_acc<NACC>(vi, c);
           cx<df> o;
-          o.re = mkdf(scale2(sr.hi, Es) * p.alpha, scale2(sr.lo, Es) * p.alpha);
-          o.im = mkdf(scale2(si.hi, Es) * p.alpha, scale2(si.lo, Es) * p.alpha);
+          o.re = mkdf(sr.hi * f1 * f2 * p.alpha, sr.lo * f1 * f2 * p.alpha);
+          o.im = mkdf(si.hi * f1 * f2 * p.alpha, si.lo * f1 * f2 * p.alpha);
           out[r * OUT_LD + c0 + c] = o;
         }
       }
