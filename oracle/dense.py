@@ -28,10 +28,13 @@ def _full(diag: np.ndarray, upper: np.ndarray | None, hermitian_lower: bool = Tr
 
 
 def dense_selected(E: float, eta: float, H_diag, H_upper, S_diag=None, S_upper=None,
-                   SigR_diag=None, SigL_diag=None, lead_SigR=(None, None), lead_SigL=(None, None)):
+                   SigR_diag=None, SigL_diag=None, lead_SigR=(None, None), lead_SigL=(None, None),
+                   SigR_upper=None, SigR_lower=None, SigL_upper=None):
     """Selected blocks of G^R, G^<, G^> at one energy by dense inversion.
 
     ``SigR_diag``/``SigL_diag``: [N_B][b][b] scattering self-energies (or None);
+    ``SigR_upper``/``SigR_lower``/``SigL_upper``: [N_B-1][b][b] off-diagonal blocks Sigma^R_{i,i+1},
+    Sigma^R_{i+1,i}, Sigma^<_{i,i+1} of block-tridiagonal ones (Sigma^<_{i+1,i} = -(Sigma^<_{i,i+1})^H);
     ``lead_SigR``/``lead_SigL``: (left, right) contact blocks added on slices 0 and N_B-1.
     Returns dict with GR_diag [N_B], GR_upper [N_B-1] (G_{i,i+1}), GR_lower [N_B-1] (G_{i+1,i}),
     GL_diag, GL_upper, GG_diag, GG_upper.
@@ -49,6 +52,15 @@ def dense_selected(E: float, eta: float, H_diag, H_upper, S_diag=None, S_upper=N
         SR += _full(SigR_diag, None)
     if SigL_diag is not None:
         SL += _full(SigL_diag, None)
+    for i in range(nb - 1):
+        up, lo = slice(i * b, (i + 1) * b), slice((i + 1) * b, (i + 2) * b)
+        if SigR_upper is not None:
+            SR[up, lo] += SigR_upper[i]
+        if SigR_lower is not None:
+            SR[lo, up] += SigR_lower[i]
+        if SigL_upper is not None:
+            SL[up, lo] += SigL_upper[i]
+            SL[lo, up] -= SigL_upper[i].conj().T
     for k, sl in ((0, slice(0, b)), (1, slice(n - b, n))):
         if lead_SigR[k] is not None:
             SR[sl, sl] += lead_SigR[k]

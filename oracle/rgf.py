@@ -8,15 +8,24 @@ selected blocks); the blocks are those of the BT tiling of Sec. II-A.
 
 Notation (slice i = 0..N_B-1, block size b):
     A_i = M_ii = z S_ii - H_ii - Sigma^R_ii  (+ contact Sigma^R on slices 0 and N_B-1)
-    U_i = M_{i,i+1} = z S_{i,i+1} - H_{i,i+1},   V_i = M_{i+1,i} = z S_{i,i+1}^H - H_{i,i+1}^H
+    U_i = M_{i,i+1} = z S_{i,i+1} - H_{i,i+1} - Sigma^R_{i,i+1}
+    V_i = M_{i+1,i} = z S_{i,i+1}^H - H_{i,i+1}^H - Sigma^R_{i+1,i}
+The scattering self-energies may be block-diagonal or block-tridiagonal; their off-diagonal blocks
+Sigma^R_{i,i+1}, Sigma^R_{i+1,i}, L_i = Sigma^<_{i,i+1} (Sigma^<_{i+1,i} = -L_i^H) are zero in the
+first case.
 Forward (left-connected) sweep:
     g_0 = A_0^-1,                 g_i = (A_i - V_{i-1} g_{i-1} U_{i-1})^-1
-    g^<_0 = g_0 Sigma^<_0 g_0^H,  g^<_i = g_i (Sigma^<_i + V_{i-1} g^<_{i-1} V_{i-1}^H) g_i^H
+    g^<_0 = g_0 Sigma^<_0 g_0^H,
+    g^<_i = g_i (Sigma^<_i + V_{i-1} g^<_{i-1} V_{i-1}^H - Y_i + Y_i^H) g_i^H,  Y_i = V_{i-1} g_{i-1} L_{i-1}
 Backward sweep (G_{N-1,N-1} = g_{N-1}, G^<_{N-1,N-1} = g^<_{N-1}), with P = g_i U_i:
     G_{i,i+1} = -P G_{i+1,i+1},   G_{i+1,i} = -G_{i+1,i+1} V_i g_i,   G_ii = g_i - P G_{i+1,i}
-    K = P G_{i+1,i+1} V_i g^<_i
+    Q = V_i g^<_i + (g_i L_i)^H,  K = P G_{i+1,i+1} Q
     G^<_ii = g^<_i + P G^<_{i+1,i+1} P^H + K - K^H
-    G^<_{i,i+1} = -P G^<_{i+1,i+1} - g^<_i V_i^H (G_{i+1,i+1})^H
+    G^<_{i,i+1} = -P G^<_{i+1,i+1} + (G_{i+1,i+1} Q)^H
+(With L = 0, Q = V_i g^<_i and the last line is -P G^<_{i+1,i+1} - g^<_i V_i^H G_{i+1,i+1}^H.)
+The cross terms Y and (g L)^H come from splitting G^< = G Sigma^< G^H at the cut (i, i+1): the
+rows of G through slice i are g^(i) - P G_{i+1,.} (g^(i) the inverse of slices 0..i), and a
+block-tridiagonal Sigma^< couples the two sides only through L_i and -L_i^H.
 Greater function on the returned blocks: G^> = G^< + G^R - G^A (this is G^R Sigma^> G^A when
 Sigma^> - Sigma^< = Sigma^R - Sigma^A, with the broadening acting as Sigma^>_eta = -2 i eta S).
 
@@ -98,11 +107,21 @@ def rgf_energy(E: float, dev: dict, e_index: int = 0, decim_tol: float = 1e-13,
                 sl = sl + con["R"]["SigL"]
         A.append(a)
         SigL.append(sl)
-    U, V = [], []
+    U, V, L = [], [], []
     for i in range(nb - 1):
         Sup = np.zeros((b, b), dtype=np.complex128) if Su is None else Su[i]
-        U.append(z * Sup - Hu[i])
-        V.append(z * _H(Sup) - _H(Hu[i]))
+        u = z * Sup - Hu[i]
+        v = z * _H(Sup) - _H(Hu[i])
+        sru = _scattering(dev, "SigR_upper", e_index, i)
+        srl = _scattering(dev, "SigR_lower", e_index, i)
+        slu = _scattering(dev, "SigL_upper", e_index, i)
+        if sru is not None:
+            u = u - sru
+        if srl is not None:
+            v = v - srl
+        U.append(u)
+        V.append(v)
+        L.append(np.zeros((b, b), dtype=np.complex128) if slu is None else slu)
 
     # Step 2: forward sweep (retarded and lesser left-connected functions).
     g = [None] * nb
@@ -111,7 +130,8 @@ def rgf_energy(E: float, dev: dict, e_index: int = 0, decim_tol: float = 1e-13,
     gl[0] = g[0] @ SigL[0] @ _H(g[0])
     for i in range(1, nb):
         g[i] = np.linalg.inv(A[i] - V[i - 1] @ g[i - 1] @ U[i - 1])
-        gl[i] = g[i] @ (SigL[i] + V[i - 1] @ gl[i - 1] @ _H(V[i - 1])) @ _H(g[i])
+        Y = V[i - 1] @ g[i - 1] @ L[i - 1]
+        gl[i] = g[i] @ (SigL[i] + V[i - 1] @ gl[i - 1] @ _H(V[i - 1]) - Y + _H(Y)) @ _H(g[i])
 
     # Step 3: backward sweep for the selected blocks.
     GR = [None] * nb
@@ -126,9 +146,10 @@ def rgf_energy(E: float, dev: dict, e_index: int = 0, decim_tol: float = 1e-13,
         GRu[i] = -P @ GR[i + 1]
         GRl[i] = -GR[i + 1] @ V[i] @ g[i]
         GR[i] = g[i] - P @ GRl[i]
-        K = P @ GR[i + 1] @ V[i] @ gl[i]
+        Q = V[i] @ gl[i] + _H(g[i] @ L[i])
+        K = P @ GR[i + 1] @ Q
         GL[i] = gl[i] + P @ GL[i + 1] @ _H(P) + K - _H(K)
-        GLu[i] = -P @ GL[i + 1] - gl[i] @ _H(V[i]) @ _H(GR[i + 1])
+        GLu[i] = -P @ GL[i + 1] + _H(GR[i + 1] @ Q)
 
     # Step 4: greater function on the returned blocks.
     GG = [GL[i] + GR[i] - _H(GR[i]) for i in range(nb)]

@@ -1,7 +1,7 @@
 """Pins for the FP64 oracle: each test checks it against something other than itself.
 
 * brute-force dense inversion (Eq. 2 with Table I's G-row) on tiny random inputs, with overlap,
-  contacts, non-symmetric lead couplings and energy-dependent self-energies;
+  contacts, non-symmetric lead couplings, energy-dependent and block-tridiagonal self-energies;
 * the closed-form self-energy and Green's function of a clean tight-binding strip;
 * a long truncated lead solved densely (orientation of the lead coupling);
 * the clean strip's integer transmission and Landauer current;
@@ -45,15 +45,20 @@ def _with_leads_and_overlap(dev, rng, overlap=True):
     return dev
 
 
+def _at(dev, key, k):
+    X = dev.get(key)
+    return None if X is None else X[k if X.shape[0] > 1 else 0]
+
+
 def _dense_for(dev, E, k=0, r=None):
     if r is None:
         r = O.rgf_energy(E, dev, k)
-    SR = dev["SigR"][k if dev["SigR"].shape[0] > 1 else 0] if dev.get("SigR") is not None else None
-    SL = dev["SigL"][k if dev["SigL"].shape[0] > 1 else 0] if dev.get("SigL") is not None else None
     d = dense_selected(E, dev["eta"], dev["H_diag"], dev["H_upper"], dev.get("S_diag"),
-                       dev.get("S_upper"), SR, SL,
+                       dev.get("S_upper"), _at(dev, "SigR", k), _at(dev, "SigL", k),
                        lead_SigR=r.get("lead_SigR", (None, None)),
-                       lead_SigL=r.get("lead_SigL", (None, None)))
+                       lead_SigL=r.get("lead_SigL", (None, None)),
+                       SigR_upper=_at(dev, "SigR_upper", k), SigR_lower=_at(dev, "SigR_lower", k),
+                       SigL_upper=_at(dev, "SigL_upper", k))
     return r, d
 
 
@@ -80,6 +85,48 @@ def test_recursion_energy_dependent_sigma():
         for key in BLOCKS:
             assert _rel(r[key], d[key]) < 1e-11
     del rng
+
+
+@pytest.mark.parametrize("b,nb,seed", [(4, 5, 11), (3, 7, 12), (5, 2, 13), (4, 1, 14)])
+@pytest.mark.parametrize("parts", ["all", "lesser_only", "retarded_only"])
+def test_recursion_block_tridiagonal_sigma_matches_dense(b, nb, seed, parts):
+    """Block-tridiagonal scattering self-energies: every selected block equals the dense definition
+    with the full Sigma^R and Sigma^< matrices -- with only the lesser off-diagonal blocks (which
+    exercise the cross terms Y and (g L)^H alone), only the retarded ones (which enter U and V), or
+    both; with overlap and contacts."""
+    rng = np.random.default_rng(200 + seed)
+    dev = _with_leads_and_overlap(W.random_device(b, nb, n_energies=3, seed=seed, offdiag_sigma=True), rng)
+    if parts == "lesser_only":
+        dev["SigR_upper"] = dev["SigR_lower"] = None
+    elif parts == "retarded_only":
+        dev["SigL_upper"] = None
+    for E in (-1.1, 0.13, 0.8):
+        r, d = _dense_for(dev, E)
+        for key in BLOCKS:
+            if d[key].size:
+                assert _rel(r[key], d[key]) < 1e-11, (key, E)
+
+
+def test_block_tridiagonal_sigma_changes_the_result():
+    """The off-diagonal self-energy blocks matter at the level the pins resolve: dropping them
+    moves G^< by far more than the 1e-11 agreement above."""
+    dev = W.random_device(4, 5, n_energies=1, seed=21, offdiag_sigma=True)
+    full = O.rgf_energy(0.2, dev)
+    cut = dict(dev, SigL_upper=None, SigR_upper=None, SigR_lower=None)
+    part = O.rgf_energy(0.2, cut)
+    assert _rel(part["GL_diag"], full["GL_diag"]) > 1e-4
+    assert _rel(part["GL_upper"], full["GL_upper"]) > 1e-4
+
+
+def test_block_tridiagonal_sigma_energy_dependent():
+    """Per-energy off-diagonal self-energies are read at their own energy index."""
+    dev = W.random_device(3, 4, n_energies=3, seed=22, offdiag_sigma=True)
+    for key in ("SigR", "SigL", "SigR_upper", "SigR_lower", "SigL_upper"):
+        dev[key] = np.concatenate([dev[key] * (1.0 + 0.3 * k) for k in range(3)])
+    for k, E in enumerate(dev["energies"]):
+        r, d = _dense_for(dev, float(E), k)
+        for key in BLOCKS:
+            assert _rel(r[key], d[key]) < 1e-11
 
 
 def test_single_slice_is_plain_inverse():

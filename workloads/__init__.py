@@ -85,8 +85,16 @@ def _cgauss(rng: np.random.Generator, shape, var: float) -> np.ndarray:
 def random_device(b: int, n_blocks: int, n_energies: int = 8, e_lo: float = -2.0,
                   e_hi: float = 2.0, seed: int = 0, coupling_var: float = 0.3,
                   sigma_scale: float = 1e-2, eta: float = 1e-6, scattering: bool = True,
-                  energies: np.ndarray | None = None) -> dict:
-    """Dense random block-tridiagonal device with block-diagonal scattering self-energies."""
+                  energies: np.ndarray | None = None, offdiag_sigma: bool = False) -> dict:
+    """Dense random block-tridiagonal device with block-diagonal scattering self-energies.
+
+    ``offdiag_sigma``: block-tridiagonal self-energies instead.  Sigma^< = i s F F^H and
+    Sigma^> = -i s G G^H with F, G block-lower-bidiagonal (diagonal blocks as in the
+    block-diagonal case, sub-diagonal blocks complex Gaussian of variance 1/b from a second
+    generator), so both are block-tridiagonal, anti-Hermitian and of definite sign; Sigma^R =
+    (Sigma^> - Sigma^<) / 2 on every block.  Adds SigR_upper (Sigma^R_{i,i+1}), SigR_lower
+    (Sigma^R_{i+1,i}) and SigL_upper (Sigma^<_{i,i+1}; Sigma^<_{i+1,i} = -(Sigma^<_{i,i+1})^H),
+    each [1][N_B-1][b][b]."""
     rng = np.random.default_rng(seed)
     H_diag = np.empty((n_blocks, b, b), dtype=np.complex128)
     for i in range(n_blocks):
@@ -96,21 +104,43 @@ def random_device(b: int, n_blocks: int, n_energies: int = 8, e_lo: float = -2.0
     for i in range(n_blocks - 1):
         H_upper[i] = _cgauss(rng, (b, b), coupling_var / b)
     SigR = SigL = None
+    extra = {}
     if scattering:
         SigL = np.empty((1, n_blocks, b, b), dtype=np.complex128)
         SigG = np.empty((1, n_blocks, b, b), dtype=np.complex128)
+        FA, FB = [], []
         for i in range(n_blocks):
             A = _cgauss(rng, (b, b), 1.0 / b)
             B = _cgauss(rng, (b, b), 1.0 / b)
+            FA.append(A)
+            FB.append(B)
             SigL[0, i] = 1j * sigma_scale * (A @ A.conj().T)
             SigG[0, i] = -1j * sigma_scale * (B @ B.conj().T)
         SigR = (SigG - SigL) / 2.0
+        if offdiag_sigma:
+            rng2 = np.random.default_rng(seed + 104729)
+            nu = max(n_blocks - 1, 0)
+            SLu = np.empty((1, nu, b, b), dtype=np.complex128)
+            SGu = np.empty((1, nu, b, b), dtype=np.complex128)
+            for i in range(nu):
+                CA = _cgauss(rng2, (b, b), 1.0 / b)   # F_{i+1,i}
+                CB = _cgauss(rng2, (b, b), 1.0 / b)   # G_{i+1,i}
+                SigL[0, i + 1] += 1j * sigma_scale * (CA @ CA.conj().T)
+                SigG[0, i + 1] += -1j * sigma_scale * (CB @ CB.conj().T)
+                SLu[0, i] = 1j * sigma_scale * (FA[i] @ CA.conj().T)
+                SGu[0, i] = -1j * sigma_scale * (FB[i] @ CB.conj().T)
+            SigR = (SigG - SigL) / 2.0
+            SRu = (SGu - SLu) / 2.0
+            extra = dict(SigR_upper=SRu, SigR_lower=-np.conj(np.swapaxes(SRu, -1, -2)),
+                         SigL_upper=SLu)
     if energies is None:
         energies = np.linspace(e_lo, e_hi, n_energies)
-    return dict(n_blocks=n_blocks, block_size=b, H_diag=H_diag, H_upper=H_upper,
-                S_diag=None, S_upper=None, SigR=SigR, SigL=SigL, leads=None,
-                energies=np.asarray(energies, dtype=np.float64), eta=eta, mu_L=0.0, mu_R=0.0,
-                kT=0.025)
+    dev = dict(n_blocks=n_blocks, block_size=b, H_diag=H_diag, H_upper=H_upper,
+               S_diag=None, S_upper=None, SigR=SigR, SigL=SigL, leads=None,
+               energies=np.asarray(energies, dtype=np.float64), eta=eta, mu_L=0.0, mu_R=0.0,
+               kT=0.025)
+    dev.update(extra)
+    return dev
 
 
 def uneven_batch(n_energies: int = 128, seed: int = 0, nb_list=UNEVEN_NB, b_list=UNEVEN_B,
