@@ -49,8 +49,9 @@ def parse():
     ap.add_argument("--fp64-energies", type=int, default=16, help="energies for the FP64 comparison (0 = skip)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU oracle sample")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="mixed", choices=["mixed", "strip", "uneven", "ozaki", "serving"],
-                    help="mixed: b=256 N_B=64 N_E=512 (default); strip: W=16 strip FP64 with contacts; "
+    ap.add_argument("--workload", default="mixed", choices=["mixed", "mixed_bt", "strip", "uneven", "ozaki", "serving"],
+                    help="mixed: b=256 N_B=64 N_E=512 (default); mixed_bt: the same with block-tridiagonal "
+                         "scattering self-energies; strip: W=16 strip FP64 with contacts; "
                          "uneven: 8 devices x 128 energies in one CUDA graph; ozaki: b=1024 N_B=32 "
                          "emulated FP64 (subset of the 256 energies); serving: Poisson request stream")
     ap.add_argument("--requests", type=int, default=40)
@@ -177,7 +178,8 @@ def cpu_oracle_sample(dev, budget_s, idx_pool):
 
 def run_reference(args):
     import workloads as W
-    dev = W.random_device(args.block, args.slices, n_energies=args.energies, seed=0)
+    dev = W.random_device(args.block, args.slices, n_energies=args.energies, seed=0,
+                          offdiag_sigma=args.workload == "mixed_bt")
     per_step = 2
     import numpy as np
     pool = list(np.linspace(0, args.energies - 1, per_step * (args.steps + args.warmup)).astype(int))
@@ -402,7 +404,7 @@ def main():
         if rank == 0:
             run_reference(args)
         return
-    if args.workload != "mixed":
+    if args.workload not in ("mixed", "mixed_bt"):
         from paper_2606_25595_gb300 import build as qbuild
         qbuild.build()
         import paper_2606_25595_gb300 as q
@@ -418,12 +420,13 @@ def main():
     import workloads as W
 
     torch.cuda.set_device(lr)
-    dev = W.random_device(args.block, args.slices, n_energies=args.energies, seed=0)
+    bt = args.workload == "mixed_bt"
+    dev = W.random_device(args.block, args.slices, n_energies=args.energies, seed=0, offdiag_sigma=bt)
     nb, b, ne = args.slices, args.block, args.energies
     din = q.upload(dev)
     outs = ["GR_diag", "GL_diag", "current", "density", "integrals"]
     desc = q.make_desc(nb, b, args.precision, min(args.chunk, ne), refine_max_iter=2,
-                       has_scattering=True, outputs=outs)
+                       has_scattering=True, outputs=outs, offdiag_sigma=bt)
     plan = q.Plan(desc)
     cd = torch.device("cuda")
     GR = torch.empty((ne, nb, b, b), dtype=torch.complex128, device=cd)
@@ -532,7 +535,7 @@ def main():
         idx = np.linspace(0, ne - 1, nsub).astype(int)
         Esub = dev["energies"][idx]
         p64 = q.Plan(q.make_desc(nb, b, "fp64", nsub, has_scattering=True,
-                                 outputs=["current", "density"]))
+                                 outputs=["current", "density"], offdiag_sigma=bt))
         din64 = q.upload(dev, Esub)
         c64 = torch.empty((nsub, nb - 1), dtype=torch.float64, device=cd)
         d64 = torch.empty((nsub, nb), dtype=torch.float64, device=cd)
@@ -581,7 +584,8 @@ def main():
                           "fp32": "c64", "fp64": "c128"}[args.precision],
                 "data": "synthetic",
                 "config": {"workload": f"random BT device b={b} N_B={nb} N_E={ne} on [-2,2], "
-                                       f"block-diagonal scattering self-energies (seed 0)",
+                                       + ("block-tridiagonal" if bt else "block-diagonal")
+                                       + " scattering self-energies (seed 0)",
                            "global_batch": ne * ws, "precision": args.precision,
                            "energies_in_flight": min(args.chunk, ne),
                            "l2": "inputs and working set (>= 16 GB) larger than L2; no flush"},

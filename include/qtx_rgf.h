@@ -94,6 +94,11 @@ typedef struct {
   double decim_tol;            /* stop when max|alpha|,|beta| < decim_tol * max|H01| (e.g. 1e-13) */
   int decim_max_iter;          /* decimation sweeps before QTX_ERR_NOT_CONVERGED (e.g. 100) */
   unsigned outputs;            /* QTX_OUT_* mask */
+  int offdiag_sigma;           /* 1: block-tridiagonal scattering self-energies (needs has_scattering):
+                                  SigR_upper, SigR_lower, SigL_upper are read as well.  Sigma^R's
+                                  off-diagonal blocks enter M_{i,i+1}, M_{i+1,i}; Sigma^<'s add the
+                                  cross terms of the lesser recursions (forward: -V g L + (V g L)^H in
+                                  the bracket of g^<_i; backward: Q = V g^< + (g L)^H) */
 } qtx_rgf_desc;
 
 /* Device inputs (caller-owned, complex128 unless noted). */
@@ -113,6 +118,11 @@ typedef struct {
   int n_blocks;            /* slices of this solve: 0 = the plan's n_blocks, else 1..plan's n_blocks (a
                               plan sized for N_B slices serves any shorter device; block arrays are
                               then laid out with this N_B) */
+  const void *SigR_upper;  /* offdiag_sigma: Sigma^R_{i,i+1}, [N_B-1][b][b] or [N_E][N_B-1][b][b]
+                              (energy_dependent_sigma) */
+  const void *SigR_lower;  /* offdiag_sigma: Sigma^R_{i+1,i}, same layout */
+  const void *SigL_upper;  /* offdiag_sigma: Sigma^<_{i,i+1}, same layout; Sigma^<_{i+1,i} =
+                              -(Sigma^<_{i,i+1})^H (Sigma^< is anti-Hermitian) */
 } qtx_rgf_inputs;
 
 /* Device outputs (caller-owned; NULL = not produced).  Layouts as in QTX_OUT_*. */

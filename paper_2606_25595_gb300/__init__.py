@@ -46,7 +46,8 @@ class Desc(ctypes.Structure):
                 ("refine_max_iter", ctypes.c_int), ("has_S", ctypes.c_int),
                 ("has_scattering", ctypes.c_int), ("energy_dependent_sigma", ctypes.c_int),
                 ("leads", ctypes.c_int), ("decim_tol", ctypes.c_double),
-                ("decim_max_iter", ctypes.c_int), ("outputs", ctypes.c_uint)]
+                ("decim_max_iter", ctypes.c_int), ("outputs", ctypes.c_uint),
+                ("offdiag_sigma", ctypes.c_int)]
 
 
 class Inputs(ctypes.Structure):
@@ -58,7 +59,8 @@ class Inputs(ctypes.Structure):
                 ("eta", ctypes.c_double), ("mu_L", ctypes.c_double), ("mu_R", ctypes.c_double),
                 ("kT", ctypes.c_double), ("energies", ctypes.c_void_p),
                 ("weights", ctypes.c_void_p), ("n_energies", ctypes.c_int),
-                ("n_blocks", ctypes.c_int)]
+                ("n_blocks", ctypes.c_int), ("SigR_upper", ctypes.c_void_p),
+                ("SigR_lower", ctypes.c_void_p), ("SigL_upper", ctypes.c_void_p)]
 
 
 class Outputs(ctypes.Structure):
@@ -121,7 +123,8 @@ def lib() -> ctypes.CDLL:
 
 def make_desc(n_blocks, block_size, precision="fp64", max_energies_in_flight=64,
               refine_max_iter=2, has_S=False, has_scattering=True, energy_dependent_sigma=False,
-              leads=False, decim_tol=1e-13, decim_max_iter=100, outputs=None) -> Desc:
+              leads=False, decim_tol=1e-13, decim_max_iter=100, outputs=None,
+              offdiag_sigma=False) -> Desc:
     if outputs is None:
         outputs = (1 << 12) - 1
     elif not isinstance(outputs, int):
@@ -133,7 +136,7 @@ def make_desc(n_blocks, block_size, precision="fp64", max_energies_in_flight=64,
                 PRECISION[precision] if isinstance(precision, str) else int(precision),
                 int(refine_max_iter), int(bool(has_S)), int(bool(has_scattering)),
                 int(bool(energy_dependent_sigma)), int(bool(leads)), float(decim_tol),
-                int(decim_max_iter), int(outputs))
+                int(decim_max_iter), int(outputs), int(bool(offdiag_sigma)))
 
 
 def kernel_launches() -> int:
@@ -192,6 +195,11 @@ def _ptr(t):
     return None if t is None else ctypes.c_void_p(t.data_ptr())
 
 
+def has_offdiag_sigma(dev: dict) -> bool:
+    """True when a device dict carries block-tridiagonal scattering self-energies."""
+    return any(dev.get(k) is not None for k in ("SigR_upper", "SigR_lower", "SigL_upper"))
+
+
 def solve_device(dev: dict, precision: str = "fp64", outputs=None, max_energies_in_flight=64,
                  refine_max_iter=2, weights=None, energies=None, stream=None, plan=None,
                  device_inputs=None, keep_on_device=False):
@@ -213,7 +221,7 @@ def solve_device(dev: dict, precision: str = "fp64", outputs=None, max_energies_
     desc = make_desc(nb, b, precision, min(max_energies_in_flight, ne), refine_max_iter,
                      has_S=dev.get("S_diag") is not None, has_scattering=dev.get("SigR") is not None,
                      energy_dependent_sigma=dev.get("SigR") is not None and dev["SigR"].shape[0] > 1,
-                     leads=bool(dev.get("leads")), outputs=want)
+                     leads=bool(dev.get("leads")), outputs=want, offdiag_sigma=has_offdiag_sigma(dev))
     P = plan if plan is not None else Plan(desc)
     cdev = torch.device("cuda")
     res = {}
@@ -264,12 +272,16 @@ def upload(dev: dict, energies=None, weights=None) -> dict:
         SR, SL = dev["SigR"], dev["SigL"]
         d["SigR_diag"] = T(SR[0] if SR.shape[0] == 1 else SR)
         d["SigL_diag"] = T(SL[0] if SL.shape[0] == 1 else SL)
+    for k in ("SigR_upper", "SigR_lower", "SigL_upper"):
+        X = dev.get(k)
+        d[k] = None if X is None or X.size == 0 else T(X[0] if X.shape[0] == 1 else X)
     leads = dev.get("leads") or {}
     for k in ("H00_L", "H01_L", "H00_R", "H01_R"):
         d["lead_" + k] = T(leads.get(k))
     inp = Inputs()
     for k in ("H_diag", "H_upper", "S_diag", "S_upper", "SigR_diag", "SigL_diag", "lead_H00_L",
-              "lead_H01_L", "lead_H00_R", "lead_H01_R", "energies", "weights"):
+              "lead_H01_L", "lead_H00_R", "lead_H01_R", "energies", "weights", "SigR_upper",
+              "SigR_lower", "SigL_upper"):
         setattr(inp, k, None if d[k] is None else d[k].data_ptr())
     inp.eta = float(dev["eta"])
     inp.mu_L = float(dev.get("mu_L", 0.0))

@@ -57,10 +57,12 @@ template <typename T>
 cudaError_t axpby_from64(cx<T>* out, long sOut, const cx<double>* X, long sX, double c1,
                          const cx<double>* Y, long sY, double c2, int b, int batch,
                          cudaStream_t st);
-// off-diagonal rows of M: U[e] = z_e S_up - H_up,  V[e] = z_e S_up^H - H_up^H (S_up may be nullptr)
+// off-diagonal rows of M: U[e] = z_e S_up - H_up - SRu[e],  V[e] = z_e S_up^H - H_up^H - SRl[e]
+// (S_up, SRu, SRl may be nullptr; SRu/SRl advance by sSR per batch entry, 0 = shared)
 template <typename T>
 cudaError_t assemble_offdiag(cx<T>* U, cx<T>* V, const cx<double>* Hup, const cx<double>* Sup,
-                             const double* E, double eta, int b, int batch, cudaStream_t st);
+                             const double* E, double eta, int b, int batch, cudaStream_t st,
+                             const cx<double>* SRu = nullptr, const cx<double>* SRl = nullptr, long sSR = 0);
 
 // ---- observables, FP64 accumulation
 // cur[e * ldcur] = 2 Re Tr[(H_up - E S_up) G^<_{i+1,i}],  G^<_{i+1,i} = -(GLu)^H

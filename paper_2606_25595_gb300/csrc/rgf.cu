@@ -38,6 +38,9 @@ struct Arena {
   }
 };
 
+// U_i, V_i differ per energy when z multiplies an overlap block or Sigma^R_{i,i+1} depends on E.
+inline bool uv_per_energy(const qtx_rgf_desc& d) { return d.has_S || (d.offdiag_sigma && d.energy_dependent_sigma); }
+
 struct Layout {
   size_t g, gl, tmp, inv_tmp, U, V, ident, ident_df, ref, f32a, f32tmp, dec, lead, obs, flags, tc_scratch, total;
   int n_tmp, n_dec;
@@ -87,12 +90,12 @@ Layout make_layout(const qtx_rgf_desc& d) {
   const size_t bb = (size_t)b * b;
   const size_t es = d.precision == QTX_FP32 ? sizeof(cx<float>) : sizeof(cx<double>);
   Arena a;
-  L.n_tmp = 12;
+  L.n_tmp = d.offdiag_sigma ? 14 : 12;  // 12, 13: Sigma^<_{i,i+1} in the sweep's type and g_i Sigma^<_{i,i+1}
   L.g = a.take(nb * Ec * bb * es);
   L.gl = a.take(nb * Ec * bb * es);
   L.tmp = a.take((size_t)L.n_tmp * Ec * bb * es);
   L.inv_tmp = a.take(Ec * bb * es + 4096);
-  const size_t ou = d.has_S ? (size_t)(nb > 1 ? nb - 1 : 0) * Ec * bb * es : (size_t)(nb > 1 ? nb - 1 : 0) * bb * es;
+  const size_t ou = uv_per_energy(d) ? (size_t)(nb > 1 ? nb - 1 : 0) * Ec * bb * es : (size_t)(nb > 1 ? nb - 1 : 0) * bb * es;
   L.U = a.take(ou);
   L.V = a.take(ou);
   L.ident = a.take(bb * sizeof(cx<double>));
@@ -437,6 +440,21 @@ qtx_status solve_chunk(qtx_rgf_plan_s* P, const qtx_rgf_inputs* in, const qtx_rg
   const long sigE0 = d.energy_dependent_sigma ? (long)e0 * nb * bb : 0;
   auto sigR = [&](int i) { return SRd ? SRd + sigE0 + (long)i * bb : nullptr; };
   auto sigL = [&](int i) { return SLd ? SLd + sigE0 + (long)i * bb : nullptr; };
+  // off-diagonal scattering blocks [N_E or 1][N_B-1][b][b]
+  const bool odg = d.offdiag_sigma && nb > 1;
+  const long sSigU = d.energy_dependent_sigma ? (long)(nb - 1) * bb : 0;
+  const long sigUE0 = d.energy_dependent_sigma ? (long)e0 * (nb - 1) * bb : 0;
+  const cx<double>* SRu = odg ? reinterpret_cast<const cx<double>*>(in->SigR_upper) + sigUE0 : nullptr;
+  const cx<double>* SRl = odg ? reinterpret_cast<const cx<double>*>(in->SigR_lower) + sigUE0 : nullptr;
+  const cx<double>* SLu = odg ? reinterpret_cast<const cx<double>*>(in->SigL_upper) + sigUE0 : nullptr;
+  // Sigma^<_{i,i+1} in the sweep's type (tmp 12): one block shared by the chunk, or one per energy
+  const int nLt = d.energy_dependent_sigma ? ne : 1;
+  const long sLt = d.energy_dependent_sigma ? bb : 0;
+  auto load_L = [&](int i) -> cx<T>* {
+    cx<T>* Lt = c.tmp(12);
+    if (axpby_from64<T>(Lt, bb, SLu + (long)i * bb, sSigU, 1.0, nullptr, 0, 0.0, b, nLt, st) != cudaSuccess) return nullptr;
+    return Lt;
+  };
   qtx_status s;
   Term<T> none;
 
@@ -455,12 +473,15 @@ qtx_status solve_chunk(qtx_rgf_plan_s* P, const qtx_rgf_inputs* in, const qtx_rg
   // ---- off-diagonal blocks of M
   cx<T>* Ub = reinterpret_cast<cx<T>*>(P->ws + P->L.U);
   cx<T>* Vb = reinterpret_cast<cx<T>*>(P->ws + P->L.V);
-  const long sUV = d.has_S ? bb : 0;
-  auto U = [&](int i) { return Ub + (size_t)i * (d.has_S ? P->Ec * bb : bb); };
-  auto V = [&](int i) { return Vb + (size_t)i * (d.has_S ? P->Ec * bb : bb); };
+  const bool uvE = uv_per_energy(d);
+  const long sUV = uvE ? bb : 0;
+  auto U = [&](int i) { return Ub + (size_t)i * (uvE ? P->Ec * bb : bb); };
+  auto V = [&](int i) { return Vb + (size_t)i * (uvE ? P->Ec * bb : bb); };
   for (int i = 0; i + 1 < nb; ++i) {
-    if (d.has_S) QTX_CK(assemble_offdiag<T>(U(i), V(i), Hu + (long)i * bb, Su + (long)i * bb, c.E, eta, b, ne, st));
-    else QTX_CK(assemble_offdiag<T>(U(i), V(i), Hu + (long)i * bb, nullptr, nullptr, 0.0, b, 1, st));
+    const cx<double>* sru = SRu ? SRu + (long)i * bb : nullptr;
+    const cx<double>* srl = SRl ? SRl + (long)i * bb : nullptr;
+    if (uvE) QTX_CK(assemble_offdiag<T>(U(i), V(i), Hu + (long)i * bb, Su ? Su + (long)i * bb : nullptr, c.E, eta, b, ne, st, sru, srl, sSigU));
+    else QTX_CK(assemble_offdiag<T>(U(i), V(i), Hu + (long)i * bb, nullptr, nullptr, 0.0, b, 1, st, sru, srl, 0));
   }
 
   // ---- 2. forward sweep
@@ -503,6 +524,18 @@ qtx_status solve_chunk(qtx_rgf_plan_s* P, const qtx_rgf_inputs* in, const qtx_rg
       cx<T>* X = c.tmp(0);
       if ((s = gemm<T>(P, gargs<T>(b, b, b, V(i - 1), b, sUV, OP_N, c.gl(i - 1), b, bb, OP_N, nullptr, 0, 0, X, b, bb, 1.0, 0.0, ne, nullptr), st))) return s;
       if ((s = gemm<T>(P, gargs<T>(b, b, b, X, b, bb, OP_N, V(i - 1), b, sUV, OP_C, SLi, b, bb, SLi, b, bb, 1.0, 1.0, ne, nullptr), st))) return s;
+      if (odg) {  // block-tridiagonal Sigma^<: bracket += -Y + Y^H, Y = V_{i-1} g_{i-1} Sigma^<_{i-1,i}
+        cx<T>* Zf = c.tmp(2);
+        cx<T>* Yf = c.tmp(3);
+        cx<T>* Lt = load_L(i - 1);
+        if (!Lt) return QTX_ERR_CUDA;
+        if ((s = gemm<T>(P, gargs<T>(b, b, b, V(i - 1), b, sUV, OP_N, c.g(i - 1), b, bb, OP_N, nullptr, 0, 0, Zf, b, bb, 1.0, 0.0, ne, nullptr), st))) return s;
+        if ((s = gemm<T>(P, gargs<T>(b, b, b, Zf, b, bb, OP_N, Lt, b, sLt, OP_N, nullptr, 0, 0, Yf, b, bb, 1.0, 0.0, ne, nullptr), st))) return s;
+        Term<T> t0; t0.p = SLi; t0.s = bb; t0.alpha = 1.0;
+        Term<T> t1; t1.p = Yf; t1.s = bb; t1.alpha = -1.0;
+        Term<T> t2; t2.p = Yf; t2.s = bb; t2.alpha = 1.0; t2.op = OP_C;
+        QTX_CK((combine<T, T>(SLi, bb, t0, t1, t2, b, ne, nullptr, 0, 0, nullptr, st)));
+      }
     }
     cx<T>* Y = c.tmp(0);
     if ((s = gemm<T>(P, gargs<T>(b, b, b, gi, b, bb, OP_N, SLi, b, bb, OP_N, nullptr, 0, 0, Y, b, bb, 1.0, 0.0, ne, nullptr), st))) return s;
@@ -511,7 +544,7 @@ qtx_status solve_chunk(qtx_rgf_plan_s* P, const qtx_rgf_inputs* in, const qtx_rg
 
   // ---- 3. backward sweep.  With P = g_i U_i, Z = V_i g_i, Q = V_i g^<_i:
   //   G_{i+1,i} = -G_{i+1,i+1} Z,  G_{i,i+1} = -P G_{i+1,i+1},  G_ii = g_i - P G_{i+1,i}
-  //   K = P G_{i+1,i+1} Q = -G_{i,i+1} Q
+  //   K = P G_{i+1,i+1} Q = -G_{i,i+1} Q   (block-tridiagonal Sigma^<: Q += (g_i Sigma^<_{i,i+1})^H)
   //   G^<_ii = g^<_i + (P G^<_{i+1,i+1}) P^H + K - K^H
   //   G^<_{i,i+1} = -P G^<_{i+1,i+1} + (G_{i+1,i+1} Q)^H     [= -P G^< - g^< V^H G^A]
   double* obs = reinterpret_cast<double*>(P->ws + P->L.obs);
@@ -556,10 +589,21 @@ qtx_status solve_chunk(qtx_rgf_plan_s* P, const qtx_rgf_inputs* in, const qtx_rg
     };
     if ((s = MM(gi, bb, OP_N, U(i), sUV, OP_N, nullptr, Pm, 1.0, 0.0))) return s;
     if ((s = MM(V(i), sUV, OP_N, gi, bb, OP_N, nullptr, Z, 1.0, 0.0))) return s;
+    cx<T>* Rl = odg ? c.tmp(13) : nullptr;  // block-tridiagonal Sigma^<: g_i Sigma^<_{i,i+1} (g_i still left-connected)
+    if (odg) {
+      cx<T>* Lt = load_L(i);
+      if (!Lt) return QTX_ERR_CUDA;
+      if ((s = MM(gi, bb, OP_N, Lt, sLt, OP_N, nullptr, Rl, 1.0, 0.0))) return s;
+    }
     if ((s = MM(GRn, bb, OP_N, Z, bb, OP_N, nullptr, GRl, -1.0, 0.0))) return s;
     if ((s = MM(Pm, bb, OP_N, GRn, bb, OP_N, nullptr, GRu, -1.0, 0.0))) return s;
     if ((s = MM(Pm, bb, OP_N, GRl, bb, OP_N, gi, gi, -1.0, 1.0))) return s;   // g_i <- G_ii
     if ((s = MM(V(i), sUV, OP_N, gli, bb, OP_N, nullptr, Q, 1.0, 0.0))) return s;
+    if (odg) {  // Q = V_i g^<_i + (g_i Sigma^<_{i,i+1})^H
+      Term<T> t0; t0.p = Q; t0.s = bb; t0.alpha = 1.0;
+      Term<T> t1; t1.p = Rl; t1.s = bb; t1.alpha = 1.0; t1.op = OP_C;
+      QTX_CK((combine<T, T>(Q, bb, t0, t1, none, b, ne, nullptr, 0, 0, nullptr, st)));
+    }
     if ((s = MM(GRu, bb, OP_N, Q, bb, OP_N, nullptr, K, -1.0, 0.0))) return s;
     if ((s = MM(Pm, bb, OP_N, GLn, bb, OP_N, nullptr, PGL, 1.0, 0.0))) return s;
     if ((s = MM(PGL, bb, OP_N, Pm, bb, OP_C, gli, gli, 1.0, 1.0))) return s;   // g^<_i + PGL P^H
@@ -661,6 +705,7 @@ qtx_status validate(const qtx_rgf_desc* d, std::string& err) {
   if (d->precision < QTX_FP64 || d->precision > QTX_EMU64) { err = "unknown precision"; return QTX_ERR_INVALID_ARG; }
   if (d->leads && (d->decim_max_iter < 1 || !(d->decim_tol > 0))) { err = "leads need decim_max_iter >= 1 and decim_tol > 0"; return QTX_ERR_INVALID_ARG; }
   if (d->refine_max_iter < 0) { err = "refine_max_iter must be >= 0"; return QTX_ERR_INVALID_ARG; }
+  if (d->offdiag_sigma && !d->has_scattering) { err = "offdiag_sigma needs has_scattering"; return QTX_ERR_INVALID_ARG; }
   if ((d->precision == QTX_EMU64 || d->precision == QTX_BF16X3) && !tc_available()) {
     err = "tensor-core engine not available in this build";
     return QTX_ERR_UNSUPPORTED;
@@ -726,6 +771,8 @@ qtx_status qtx_rgf_solve(qtx_rgf_plan P, const qtx_rgf_inputs* in, const qtx_rgf
   if (!in->H_diag || (P->nb > 1 && !in->H_upper)) { P->err = "H_diag / H_upper missing"; return QTX_ERR_INVALID_ARG; }
   if (P->d.has_S && (!in->S_diag || (P->nb > 1 && !in->S_upper))) { P->err = "has_S set but S pointers missing"; return QTX_ERR_INVALID_ARG; }
   if (P->d.has_scattering && (!in->SigR_diag || !in->SigL_diag)) { P->err = "has_scattering set but Sigma pointers missing"; return QTX_ERR_INVALID_ARG; }
+  if (P->d.offdiag_sigma && (in->n_blocks ? in->n_blocks : P->d.n_blocks) > 1 &&
+      (!in->SigR_upper || !in->SigR_lower || !in->SigL_upper)) { P->err = "offdiag_sigma set but off-diagonal Sigma pointers missing"; return QTX_ERR_INVALID_ARG; }
   if (P->d.leads && (!in->lead_H00_L || !in->lead_H01_L || !in->lead_H00_R || !in->lead_H01_R)) { P->err = "leads set but lead blocks missing"; return QTX_ERR_INVALID_ARG; }
   if (P->d.leads && !(in->kT > 0)) { P->err = "leads need kT > 0"; return QTX_ERR_INVALID_ARG; }
   if (in->n_blocks < 0 || in->n_blocks > P->d.n_blocks) { P->err = "inputs->n_blocks exceeds the plan's n_blocks"; return QTX_ERR_INVALID_ARG; }

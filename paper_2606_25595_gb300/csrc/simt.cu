@@ -485,7 +485,8 @@ template cudaError_t axpby_from64<df>(cx<df>*, long, const cx<double>*, long, do
 
 template <typename T>
 __global__ void k_assemble_offdiag(cx<T>* U, cx<T>* V, const cx<double>* Hup, const cx<double>* Sup,
-                                   const double* E, double eta, int b) {
+                                   const double* E, double eta, int b, const cx<double>* SRu,
+                                   const cx<double>* SRl, long sSR) {
   const int e = blockIdx.z;
   __shared__ cx<double> tile[32][33];
   const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
@@ -498,7 +499,8 @@ __global__ void k_assemble_offdiag(cx<T>* U, cx<T>* V, const cx<double>* Hup, co
     const int r = r0 + ty + 8 * q, c = c0 + tx;
     if (r < b && c < b) {
       const cx<double> s = Sup ? Sup[(long)r * b + c] : mk<double>(0, 0);
-      const cx<double> h = Hup[(long)r * b + c];
+      cx<double> h = Hup[(long)r * b + c];
+      if (SRu) h = h + SRu[(long)e * sSR + (long)r * b + c];  // U = z S - H - Sigma^R_{i,i+1}
       U[(long)e * bb + (long)r * b + c] = cvt<T>(mk<double>(Er * s.re - ei * s.im - h.re, Er * s.im + ei * s.re - h.im));
     }
   }
@@ -518,20 +520,25 @@ __global__ void k_assemble_offdiag(cx<T>* U, cx<T>* V, const cx<double>* Hup, co
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const int r = r0 + ty + 8 * q, c = c0 + tx;
-    if (r < b && c < b) V[(long)e * bb + (long)r * b + c] = cvt<T>(tile[tx][ty + 8 * q]);
+    if (r < b && c < b) {
+      cx<double> v = tile[tx][ty + 8 * q];
+      if (SRl) v = v - SRl[(long)e * sSR + (long)r * b + c];  // V = z S^H - H^H - Sigma^R_{i+1,i}
+      V[(long)e * bb + (long)r * b + c] = cvt<T>(v);
+    }
   }
 }
 template <typename T>
 cudaError_t assemble_offdiag(cx<T>* U, cx<T>* V, const cx<double>* Hup, const cx<double>* Sup,
-                             const double* E, double eta, int b, int batch, cudaStream_t st) {
+                             const double* E, double eta, int b, int batch, cudaStream_t st,
+                             const cx<double>* SRu, const cx<double>* SRl, long sSR) {
   dim3 grid((b + 31) / 32, (b + 31) / 32, batch);
-  k_assemble_offdiag<T><<<grid, 256, 0, st>>>(U, V, Hup, Sup, E, eta, b);
+  k_assemble_offdiag<T><<<grid, 256, 0, st>>>(U, V, Hup, Sup, E, eta, b, SRu, SRl, sSR);
   count_launch();
   return cudaGetLastError();
 }
-template cudaError_t assemble_offdiag<double>(cx<double>*, cx<double>*, const cx<double>*, const cx<double>*, const double*, double, int, int, cudaStream_t);
-template cudaError_t assemble_offdiag<float>(cx<float>*, cx<float>*, const cx<double>*, const cx<double>*, const double*, double, int, int, cudaStream_t);
-template cudaError_t assemble_offdiag<df>(cx<df>*, cx<df>*, const cx<double>*, const cx<double>*, const double*, double, int, int, cudaStream_t);
+template cudaError_t assemble_offdiag<double>(cx<double>*, cx<double>*, const cx<double>*, const cx<double>*, const double*, double, int, int, cudaStream_t, const cx<double>*, const cx<double>*, long);
+template cudaError_t assemble_offdiag<float>(cx<float>*, cx<float>*, const cx<double>*, const cx<double>*, const double*, double, int, int, cudaStream_t, const cx<double>*, const cx<double>*, long);
+template cudaError_t assemble_offdiag<df>(cx<df>*, cx<df>*, const cx<double>*, const cx<double>*, const double*, double, int, int, cudaStream_t, const cx<double>*, const cx<double>*, long);
 
 template <typename T>
 __global__ void k_add_identity(cx<T>* X, long sX, int n, const int* active) {

@@ -156,6 +156,51 @@ def test_random_fp64_with_overlap_leads_ragged(q, b, nb, ne, chunk):
     _check_obs_kappa(res, ref)
 
 
+@pytest.mark.parametrize("b,nb,ne,chunk,energy_dep,contacts", [(48, 6, 3, 2, False, True),
+                                                               (37, 5, 3, 3, True, False),
+                                                               (70, 4, 2, 1, True, True),
+                                                               (16, 1, 2, 2, False, False)])
+def test_block_tridiagonal_sigma_fp64(q, b, nb, ne, chunk, energy_dep, contacts):
+    """Block-tridiagonal scattering self-energies (off-diagonal Sigma^R in U, V; the cross terms of
+    the lesser recursions), with overlap and contacts or per-energy self-energies, ragged sizes,
+    chunked energies, one-slice device: FP64 parity <= 1e-10 as above."""
+    rng = np.random.default_rng(b * 7 + nb)
+    dev = W.random_device(b, nb, n_energies=ne, seed=b + 3 * nb, offdiag_sigma=True)
+    if contacts:
+        dev["S_diag"] = np.stack([np.eye(b) + 0.05 * (lambda X: (X + X.conj().T) / 2)(
+            rng.standard_normal((b, b)) + 1j * rng.standard_normal((b, b))) for _ in range(nb)])
+        dev["S_upper"] = (0.03 * (rng.standard_normal((nb - 1, b, b)) + 1j * rng.standard_normal((nb - 1, b, b)))
+                          if nb > 1 else np.zeros((0, b, b), np.complex128))
+        X = rng.standard_normal((b, b)) + 1j * rng.standard_normal((b, b))
+        dev["leads"] = dict(H00_L=(X + X.conj().T) / 2, H01_L=0.4 * (rng.standard_normal((b, b)) + 1j * rng.standard_normal((b, b))),
+                            H00_R=(X + X.conj().T) / 3, H01_R=0.4 * (rng.standard_normal((b, b)) + 1j * rng.standard_normal((b, b))))
+        dev["eta"] = 1e-3
+        dev["mu_L"], dev["mu_R"], dev["kT"] = 0.3, -0.2, 0.05
+    if energy_dep:
+        for key in ("SigR", "SigL", "SigR_upper", "SigR_lower", "SigL_upper"):
+            dev[key] = np.concatenate([dev[key] * (1 + 0.15 * k) for k in range(ne)])
+    ref = O.solve(dev, track_cond=bool(contacts))
+    res = q.solve_device(dev, "fp64", max_energies_in_flight=chunk)
+    assert np.all(res["status"] == 0)
+    if contacts:
+        _check_blocks_kappa(res, ref, median=False)
+        _check_obs_kappa(res, ref)
+    else:
+        _check(res, ref, 1e-10, 1e-10)
+
+
+def test_block_tridiagonal_sigma_emu64(q):
+    """Block-tridiagonal scattering self-energies in the emulated-FP64 mode (b=128, N_B=8): current
+    and density within 1e-6 of the FP64 oracle, G blocks within 1e-7."""
+    dev = W.random_device(128, 8, n_energies=4, seed=33, offdiag_sigma=True)
+    ref = O.solve(dev)
+    res = q.solve_device(dev, "emu64", refine_max_iter=2)
+    assert np.all(res["status"] == 0)
+    e = _obs_errs(res, ref)
+    assert e["current"] < 1e-6 and e["density"] < 1e-6, e
+    _check(res, ref, 1e-7, 1e-6, keys=("GR_diag", "GR_upper", "GR_lower", "GL_diag", "GL_upper"))
+
+
 @pytest.mark.parametrize("b,nb", [(80, 3), (130, 2), (200, 3)])
 def test_recursive_inverse_without_contacts_fp64(q, b, nb):
     """b > 64 (recursive block inverse + one Newton step), no contacts: every block <= 1e-10."""

@@ -58,3 +58,18 @@ def test_footprint_and_validation(libpath):
     s = q.load().qtx_rgf_plan_create(ctypes.byref(bad), ctypes.byref(h))
     assert s == 1 and not h.value
     assert b"n_blocks" in q.load().qtx_rgf_last_error(None)
+
+
+def test_block_tridiagonal_sigma_descriptor(libpath):
+    """offdiag_sigma needs has_scattering; it adds two b x b work blocks per energy, and per-energy
+    U, V blocks when the off-diagonal self-energies depend on the energy."""
+    import paper_2606_25595_gb300 as q
+    h = ctypes.c_void_p()
+    bad = q.make_desc(8, 32, "fp64", 4, has_scattering=False, offdiag_sigma=True)
+    assert q.load().qtx_rgf_plan_create(ctypes.byref(bad), ctypes.byref(h)) == 1 and not h.value
+    assert b"offdiag_sigma" in q.load().qtx_rgf_last_error(None)
+    base = q.footprint(q.make_desc(8, 32, "fp64", 4))
+    bt = q.footprint(q.make_desc(8, 32, "fp64", 4, offdiag_sigma=True))
+    assert bt - base >= 2 * 4 * 32 * 32 * 16
+    bt_e = q.footprint(q.make_desc(8, 32, "fp64", 4, offdiag_sigma=True, energy_dependent_sigma=True))
+    assert bt_e - bt >= 2 * 7 * 3 * 32 * 32 * 16
