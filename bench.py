@@ -55,6 +55,8 @@ def parse():
                          "uneven: 8 devices x 128 energies in one CUDA graph; ozaki: b=1024 N_B=32 "
                          "emulated FP64 (subset of the 256 energies); serving: Poisson request stream")
     ap.add_argument("--requests", type=int, default=40)
+    ap.add_argument("--storage-bits", type=int, default=0,
+                    help="mixed workloads: keep the left-connected blocks in FPX of this many bits (0 = off)")
     return ap.parse_args()
 
 
@@ -426,7 +428,7 @@ def main():
     din = q.upload(dev)
     outs = ["GR_diag", "GL_diag", "current", "density", "integrals"]
     desc = q.make_desc(nb, b, args.precision, min(args.chunk, ne), refine_max_iter=2,
-                       has_scattering=True, outputs=outs, offdiag_sigma=bt)
+                       has_scattering=True, outputs=outs, offdiag_sigma=bt, storage_bits=args.storage_bits)
     plan = q.Plan(desc)
     cd = torch.device("cuda")
     GR = torch.empty((ne, nb, b, b), dtype=torch.complex128, device=cd)
@@ -588,6 +590,8 @@ def main():
                                        + " scattering self-energies (seed 0)",
                            "global_batch": ne * ws, "precision": args.precision,
                            "energies_in_flight": min(args.chunk, ne),
+                           "storage_bits": args.storage_bits,
+                           "plan_bytes_per_energy_in_flight": q.footprint(desc) // min(args.chunk, ne),
                            "l2": "inputs and working set (>= 16 GB) larger than L2; no flush"},
                 "status_ok": status_ok,
                 "gpu_launches": int(launches),

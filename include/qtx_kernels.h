@@ -51,6 +51,21 @@ qtx_status qtx_lead_self_energy(int n, const void *H00, const void *H01, const d
                                 int n_energies, double eta, double tol, int max_iter, void *SigR,
                                 int *status, void *stream);
 
+/* FPX storage codec (Sec. V): byte-aligned floating-point formats of X = bits in {56, 48, 40, 32,
+ * 24, 16} bits -- a sign bit, the 8-bit exponent and bias of FP32, and X - 9 significand bits
+ * (FP32 itself for X = 32, bfloat16 for X = 16) -- used to store the simulation's blocks in less
+ * memory.  Compression rounds each FP64 value to nearest (ties to even); values beyond the largest
+ * finite one become +-inf, values below 2^-126 FP32-style subnormals, NaN the quiet-NaN code, and
+ * magnitudes below `cutoff` (Sec. III's value cutoff; 0 = none) +0.  The stream of n values is the
+ * concatenation of their X/8-byte little-endian codes, padded with zero codes to a multiple of 8
+ * values: qtx_fpx_bytes(bits, n) = ceil(n / 8) * bits bytes.  Decompression is exact (every FPX
+ * value is an FP64 value).  x, in and out are device pointers, 8-byte aligned; complex arrays are
+ * passed as 2n reals.  Asynchronous on `stream`.  Errors: QTX_ERR_INVALID_ARG (bits not one of the
+ * six widths, n < 0, cutoff < 0 or NaN, NULL or misaligned pointers with n > 0), QTX_ERR_CUDA. */
+size_t qtx_fpx_bytes(int bits, long n);
+qtx_status qtx_fpx_compress(int bits, const double *x, long n, double cutoff, void *out, void *stream);
+qtx_status qtx_fpx_decompress(int bits, const void *in, long n, double *x, void *stream);
+
 /* Size in bytes of the fixed device array behind qtx_zgemm_emu64_noalloc (48 MiB per GPU). */
 #define QTX_NOALLOC_SCRATCH_BYTES ((size_t)48 << 20)
 

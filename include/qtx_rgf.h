@@ -99,6 +99,11 @@ typedef struct {
                                   off-diagonal blocks enter M_{i,i+1}, M_{i+1,i}; Sigma^<'s add the
                                   cross terms of the lesser recursions (forward: -V g L + (V g L)^H in
                                   the bracket of g^<_i; backward: Q = V g^< + (g L)^H) */
+  int storage_bits;            /* 0: the left-connected blocks g_i, g^<_i of the forward sweep are kept
+                                  in the sweep's own type until the backward sweep reads them; X in
+                                  {56, 48, 40, 32, 24, 16}: they are kept in the FPX format of X bits
+                                  (qtx_kernels.h, Sec. V), with two working blocks per kind in the
+                                  sweep's type, which shrinks the footprint per energy in flight */
 } qtx_rgf_desc;
 
 /* Device inputs (caller-owned, complex128 unless noted). */

@@ -31,7 +31,8 @@ BLOCK_OUTPUTS = ("GR_diag", "GR_upper", "GR_lower", "GL_diag", "GL_upper", "GG_d
 EXPORTED = ("qtx_rgf_plan_create", "qtx_rgf_solve", "qtx_rgf_status", "qtx_rgf_destroy",
             "qtx_rgf_last_error", "qtx_rgf_footprint", "qtx_rgf_version", "qtx_zgemm_batched",
             "qtx_zinv_batched", "qtx_lead_self_energy", "qtx_rgf_set_profiling",
-            "qtx_rgf_gemm_profile", "qtx_kernel_launches", "qtx_zgemm_emu64_noalloc")
+            "qtx_rgf_gemm_profile", "qtx_kernel_launches", "qtx_zgemm_emu64_noalloc",
+            "qtx_fpx_bytes", "qtx_fpx_compress", "qtx_fpx_decompress")
 
 
 class QtxError(RuntimeError):
@@ -47,7 +48,7 @@ class Desc(ctypes.Structure):
                 ("has_scattering", ctypes.c_int), ("energy_dependent_sigma", ctypes.c_int),
                 ("leads", ctypes.c_int), ("decim_tol", ctypes.c_double),
                 ("decim_max_iter", ctypes.c_int), ("outputs", ctypes.c_uint),
-                ("offdiag_sigma", ctypes.c_int)]
+                ("offdiag_sigma", ctypes.c_int), ("storage_bits", ctypes.c_int)]
 
 
 class Inputs(ctypes.Structure):
@@ -113,6 +114,12 @@ def load() -> ctypes.CDLL:
     L.qtx_kernel_launches.restype = ctypes.c_longlong
     L.qtx_zgemm_emu64_noalloc.argtypes = [i, i, i, i, vp, l, l, i, vp, l, l, d, d, vp, l, l, vp, l, l, i, vp]
     L.qtx_zgemm_emu64_noalloc.restype = i
+    L.qtx_fpx_bytes.argtypes = [i, l]
+    L.qtx_fpx_bytes.restype = ctypes.c_size_t
+    L.qtx_fpx_compress.argtypes = [i, vp, l, d, vp, vp]
+    L.qtx_fpx_compress.restype = i
+    L.qtx_fpx_decompress.argtypes = [i, vp, l, vp, vp]
+    L.qtx_fpx_decompress.restype = i
     _lib = L
     return L
 
@@ -124,7 +131,7 @@ def lib() -> ctypes.CDLL:
 def make_desc(n_blocks, block_size, precision="fp64", max_energies_in_flight=64,
               refine_max_iter=2, has_S=False, has_scattering=True, energy_dependent_sigma=False,
               leads=False, decim_tol=1e-13, decim_max_iter=100, outputs=None,
-              offdiag_sigma=False) -> Desc:
+              offdiag_sigma=False, storage_bits=0) -> Desc:
     if outputs is None:
         outputs = (1 << 12) - 1
     elif not isinstance(outputs, int):
@@ -136,7 +143,7 @@ def make_desc(n_blocks, block_size, precision="fp64", max_energies_in_flight=64,
                 PRECISION[precision] if isinstance(precision, str) else int(precision),
                 int(refine_max_iter), int(bool(has_S)), int(bool(has_scattering)),
                 int(bool(energy_dependent_sigma)), int(bool(leads)), float(decim_tol),
-                int(decim_max_iter), int(outputs), int(bool(offdiag_sigma)))
+                int(decim_max_iter), int(outputs), int(bool(offdiag_sigma)), int(storage_bits))
 
 
 def kernel_launches() -> int:
@@ -202,7 +209,7 @@ def has_offdiag_sigma(dev: dict) -> bool:
 
 def solve_device(dev: dict, precision: str = "fp64", outputs=None, max_energies_in_flight=64,
                  refine_max_iter=2, weights=None, energies=None, stream=None, plan=None,
-                 device_inputs=None, keep_on_device=False):
+                 device_inputs=None, keep_on_device=False, storage_bits=0):
     """Solve a ``workloads``-style device dict on the GPU and return numpy arrays (or tensors).
 
     Marshalling only: inputs are copied to torch CUDA tensors (complex128), the C ABI is called on
@@ -221,7 +228,8 @@ def solve_device(dev: dict, precision: str = "fp64", outputs=None, max_energies_
     desc = make_desc(nb, b, precision, min(max_energies_in_flight, ne), refine_max_iter,
                      has_S=dev.get("S_diag") is not None, has_scattering=dev.get("SigR") is not None,
                      energy_dependent_sigma=dev.get("SigR") is not None and dev["SigR"].shape[0] > 1,
-                     leads=bool(dev.get("leads")), outputs=want, offdiag_sigma=has_offdiag_sigma(dev))
+                     leads=bool(dev.get("leads")), outputs=want, offdiag_sigma=has_offdiag_sigma(dev),
+                     storage_bits=storage_bits)
     P = plan if plan is not None else Plan(desc)
     cdev = torch.device("cuda")
     res = {}
@@ -323,6 +331,32 @@ def zgemm_batched(A, B, precision="emu64", opA="N", opB="N", alpha=1.0, beta=0.0
     if s != 0:
         raise QtxError(s, "qtx_zgemm_batched")
     return C
+
+
+def fpx_compress(x, bits, cutoff=0.0, stream=None):
+    """FPX codes (uint8 CUDA tensor of qtx_fpx_bytes(bits, n) bytes) of a float64 or complex128 CUDA
+    tensor's n real values.  Marshalling only; the rounding runs in the library's kernel."""
+    import torch
+    xr = torch.view_as_real(x) if x.is_complex() else x
+    xr = xr.contiguous()
+    n = xr.numel()
+    out = torch.empty(max(int(load().qtx_fpx_bytes(int(bits), n)), 8), dtype=torch.uint8, device=x.device)
+    s = load().qtx_fpx_compress(int(bits), xr.data_ptr(), n, float(cutoff), out.data_ptr(),
+                                ctypes.c_void_p(_stream(stream)))
+    if s != 0:
+        raise QtxError(s, "qtx_fpx_compress")
+    return out
+
+
+def fpx_decompress(codes, bits, n, complex_out=False, stream=None):
+    """n FP64 values (n/2 complex128 values if ``complex_out``) decoded from FPX codes."""
+    import torch
+    x = torch.empty(n, dtype=torch.float64, device=codes.device)
+    s = load().qtx_fpx_decompress(int(bits), codes.data_ptr(), int(n), x.data_ptr(),
+                                  ctypes.c_void_p(_stream(stream)))
+    if s != 0:
+        raise QtxError(s, "qtx_fpx_decompress")
+    return torch.view_as_complex(x.view(-1, 2)) if complex_out else x
 
 
 def zinv_batched(A, precision="fp64", refine_iter=2, stream=None):

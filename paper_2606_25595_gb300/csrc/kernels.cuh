@@ -111,4 +111,12 @@ inline int tc_pairs(int digits) { return digits * (digits + 1) / 2; }
 size_t gemm_tc_scratch_bytes(int M, int N, int K, int batch, int digits);
 bool tc_available();
 
+// ---- FPX storage codec (fpx.cu): n_complex T-typed complex values <-> their FPX codes
+bool fpx_width_ok(int bits);
+size_t fpx_bytes(int bits, long n_reals);
+template <typename T>
+cudaError_t fpx_store(int bits, const cx<T>* x, long n_complex, void* out, cudaStream_t st);
+template <typename T>
+cudaError_t fpx_load(int bits, const void* in, long n_complex, cx<T>* x, cudaStream_t st);
+
 }  // namespace qtx

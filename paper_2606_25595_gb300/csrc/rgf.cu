@@ -42,7 +42,8 @@ struct Arena {
 inline bool uv_per_energy(const qtx_rgf_desc& d) { return d.has_S || (d.offdiag_sigma && d.energy_dependent_sigma); }
 
 struct Layout {
-  size_t g, gl, tmp, inv_tmp, U, V, ident, ident_df, ref, f32a, f32tmp, dec, lead, obs, flags, tc_scratch, total;
+  size_t g, gl, gfx, glfx, fx_slot, tmp, inv_tmp, U, V, ident, ident_df, ref, f32a, f32tmp, dec, lead, obs, flags,
+      tc_scratch, total;
   int n_tmp, n_dec;
   size_t tc_bytes;
 };
@@ -91,8 +92,18 @@ Layout make_layout(const qtx_rgf_desc& d) {
   const size_t es = d.precision == QTX_FP32 ? sizeof(cx<float>) : sizeof(cx<double>);
   Arena a;
   L.n_tmp = d.offdiag_sigma ? 14 : 12;  // 12, 13: Sigma^<_{i,i+1} in the sweep's type and g_i Sigma^<_{i,i+1}
-  L.g = a.take(nb * Ec * bb * es);
-  L.gl = a.take(nb * Ec * bb * es);
+  if (d.storage_bits) {
+    // two working blocks per kind in the sweep's type (slices i and i-1 / i+1), every slice's
+    // left-connected blocks in FPX: a slot of fx_slot bytes per slice and kind
+    L.g = a.take(2 * Ec * bb * es);
+    L.gl = a.take(2 * Ec * bb * es);
+    L.fx_slot = fpx_bytes(d.storage_bits, 2 * Ec * bb);
+    L.gfx = a.take(nb * L.fx_slot);
+    L.glfx = a.take(nb * L.fx_slot);
+  } else {
+    L.g = a.take(nb * Ec * bb * es);
+    L.gl = a.take(nb * Ec * bb * es);
+  }
   L.tmp = a.take((size_t)L.n_tmp * Ec * bb * es);
   L.inv_tmp = a.take(Ec * bb * es + 4096);
   const size_t ou = uv_per_energy(d) ? (size_t)(nb > 1 ? nb - 1 : 0) * Ec * bb * es : (size_t)(nb > 1 ? nb - 1 : 0) * bb * es;
@@ -143,8 +154,11 @@ struct Ctx {
     return reinterpret_cast<cx<T>*>(P->ws + base) + (size_t)i * P->Ec * bb;
   }
   cx<T>* tmp(int k) const { return blk(P->L.tmp, k); }
-  cx<T>* g(int i) const { return blk(P->L.g, i); }
-  cx<T>* gl(int i) const { return blk(P->L.gl, i); }
+  // left-connected / full blocks of slice i: slot i, or with FPX storage working block i % 2
+  cx<T>* g(int i) const { return blk(P->L.g, P->d.storage_bits ? i % 2 : i); }
+  cx<T>* gl(int i) const { return blk(P->L.gl, P->d.storage_bits ? i % 2 : i); }
+  void* gfx(int i) const { return P->ws + P->L.gfx + (size_t)i * P->L.fx_slot; }
+  void* glfx(int i) const { return P->ws + P->L.glfx + (size_t)i * P->L.fx_slot; }
 };
 
 template <typename T>
@@ -540,6 +554,12 @@ qtx_status solve_chunk(qtx_rgf_plan_s* P, const qtx_rgf_inputs* in, const qtx_rg
     cx<T>* Y = c.tmp(0);
     if ((s = gemm<T>(P, gargs<T>(b, b, b, gi, b, bb, OP_N, SLi, b, bb, OP_N, nullptr, 0, 0, Y, b, bb, 1.0, 0.0, ne, nullptr), st))) return s;
     if ((s = gemm<T>(P, gargs<T>(b, b, b, Y, b, bb, OP_N, gi, b, bb, OP_C, nullptr, 0, 0, c.gl(i), b, bb, 1.0, 0.0, ne, nullptr), st))) return s;
+    // FPX storage: slices the backward sweep reads back from memory (the last two stay in the
+    // working blocks) are kept compressed
+    if (d.storage_bits && i < nb - 2) {
+      QTX_CK(fpx_store<T>(d.storage_bits, gi, (long)ne * bb, c.gfx(i), st));
+      QTX_CK(fpx_store<T>(d.storage_bits, c.gl(i), (long)ne * bb, c.glfx(i), st));
+    }
   }
 
   // ---- 3. backward sweep.  With P = g_i U_i, Z = V_i g_i, Q = V_i g^<_i:
@@ -584,6 +604,10 @@ qtx_status solve_chunk(qtx_rgf_plan_s* P, const qtx_rgf_inputs* in, const qtx_rg
     cx<T>* GLu = c.tmp(10);
     cx<T>* gi = c.g(i);
     cx<T>* gli = c.gl(i);
+    if (d.storage_bits && i < nb - 2) {  // g_i, g^<_i back from FPX into the working blocks
+      QTX_CK(fpx_load<T>(d.storage_bits, c.gfx(i), (long)ne * bb, gi, st));
+      QTX_CK(fpx_load<T>(d.storage_bits, c.glfx(i), (long)ne * bb, gli, st));
+    }
     auto MM = [&](const cx<T>* A, long sA_, int opA, const cx<T>* B, long sB_, int opB, const cx<T>* C0, cx<T>* C, double al, double be) {
       return gemm<T>(P, gargs<T>(b, b, b, A, b, sA_, opA, B, b, sB_, opB, C0, b, bb, C, b, bb, al, be, ne, nullptr), st);
     };
@@ -706,6 +730,7 @@ qtx_status validate(const qtx_rgf_desc* d, std::string& err) {
   if (d->leads && (d->decim_max_iter < 1 || !(d->decim_tol > 0))) { err = "leads need decim_max_iter >= 1 and decim_tol > 0"; return QTX_ERR_INVALID_ARG; }
   if (d->refine_max_iter < 0) { err = "refine_max_iter must be >= 0"; return QTX_ERR_INVALID_ARG; }
   if (d->offdiag_sigma && !d->has_scattering) { err = "offdiag_sigma needs has_scattering"; return QTX_ERR_INVALID_ARG; }
+  if (d->storage_bits && !fpx_width_ok(d->storage_bits)) { err = "storage_bits must be 0, 56, 48, 40, 32, 24 or 16"; return QTX_ERR_INVALID_ARG; }
   if ((d->precision == QTX_EMU64 || d->precision == QTX_BF16X3) && !tc_available()) {
     err = "tensor-core engine not available in this build";
     return QTX_ERR_UNSUPPORTED;

@@ -201,6 +201,36 @@ def test_block_tridiagonal_sigma_emu64(q):
     _check(res, ref, 1e-7, 1e-6, keys=("GR_diag", "GR_upper", "GR_lower", "GL_diag", "GL_upper"))
 
 
+@pytest.mark.parametrize("nb", [1, 2, 3, 7])
+def test_fpx_storage_fp64(q, nb):
+    """Left-connected blocks kept in FP56 between the sweeps (47-bit significands, relative
+    rounding 2^-48): FP64 parity bar 1e-10 still holds; with FP24 (2^-16) the result moves by more
+    than 1e-9 -- the stored copies are really the ones read back -- and stays within 1e-3."""
+    dev = W.random_device(48, nb, n_energies=3, seed=40 + nb, offdiag_sigma=nb > 1)
+    ref = O.solve(dev)
+    res = q.solve_device(dev, "fp64", storage_bits=56, max_energies_in_flight=2)
+    assert np.all(res["status"] == 0)
+    _check(res, ref, 1e-10, 1e-10)
+    if nb > 3:
+        r24 = q.solve_device(dev, "fp64", storage_bits=24)
+        e = _blk_err(r24["GL_diag"], None, "GL_diag", ref)
+        assert 1e-9 < e < 1e-3, e
+
+
+@pytest.mark.parametrize("bits,tol", [(40, 1e-6), (32, 3e-5)])
+def test_fpx_storage_emu64(q, bits, tol):
+    """Emulated FP64 with the left-connected blocks in FP40 (31-bit significands): current and
+    density within the 1e-6 bar.  FP32 storage (23 bits, relative rounding 6e-8) misses that bar on
+    the current, whose sum over a block row cancels: measured 1.2e-5 (about 200 x the rounding),
+    bound 3e-5; density stays below 1e-6."""
+    dev = W.random_device(128, 8, n_energies=4, seed=3)
+    ref = O.solve(dev)
+    res = q.solve_device(dev, "emu64", refine_max_iter=2, storage_bits=bits)
+    assert np.all(res["status"] == 0)
+    e = _obs_errs(res, ref)
+    assert e["current"] < tol and e["density"] < tol, e
+
+
 @pytest.mark.parametrize("b,nb", [(80, 3), (130, 2), (200, 3)])
 def test_recursive_inverse_without_contacts_fp64(q, b, nb):
     """b > 64 (recursive block inverse + one Newton step), no contacts: every block <= 1e-10."""

@@ -73,3 +73,20 @@ def test_block_tridiagonal_sigma_descriptor(libpath):
     assert bt - base >= 2 * 4 * 32 * 32 * 16
     bt_e = q.footprint(q.make_desc(8, 32, "fp64", 4, offdiag_sigma=True, energy_dependent_sigma=True))
     assert bt_e - bt >= 2 * 7 * 3 * 32 * 32 * 16
+
+
+def test_fpx_storage_descriptor(libpath):
+    """storage_bits must be one of the FPX widths; it replaces the N_B left-connected blocks per kind
+    in the sweep's type by two working blocks plus N_B compressed slots."""
+    import paper_2606_25595_gb300 as q
+    h = ctypes.c_void_p()
+    bad = q.make_desc(8, 32, "fp64", 4, storage_bits=33)
+    assert q.load().qtx_rgf_plan_create(ctypes.byref(bad), ctypes.byref(h)) == 1 and not h.value
+    assert b"storage_bits" in q.load().qtx_rgf_last_error(None)
+    nb, b, ec = 64, 256, 16
+    base = q.footprint(q.make_desc(nb, b, "emu64", ec))
+    for bits in (48, 40, 24):
+        fx = q.footprint(q.make_desc(nb, b, "emu64", ec, storage_bits=bits))
+        saved = 2 * (nb - 2) * ec * b * b * 16 - 2 * nb * ec * (2 * b * b) * bits // 8
+        assert abs((base - fx) - saved) < 1 << 20, (bits, base - fx, saved)
+    assert q.load().qtx_fpx_bytes(40, 10) == 80
