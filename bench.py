@@ -49,11 +49,12 @@ def parse():
     ap.add_argument("--fp64-energies", type=int, default=16, help="energies for the FP64 comparison (0 = skip)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU oracle sample")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="mixed", choices=["mixed", "mixed_bt", "strip", "uneven", "ozaki", "serving"],
+    ap.add_argument("--workload", default="mixed", choices=["mixed", "mixed_bt", "strip", "uneven", "ozaki", "serving", "nrl"],
                     help="mixed: b=256 N_B=64 N_E=512 (default); mixed_bt: the same with block-tridiagonal "
                          "scattering self-energies; strip: W=16 strip FP64 with contacts; "
                          "uneven: 8 devices x 128 energies in one CUDA graph; ozaki: b=1024 N_B=32 "
-                         "emulated FP64 (subset of the 256 energies); serving: Poisson request stream")
+                         "emulated FP64 (subset of the 256 energies); serving: Poisson request stream; "
+                         "nrl: b=3408 N_B=10 (the paper's NR-L shape), per-energy self-energies streamed from host")
     ap.add_argument("--requests", type=int, default=40)
     ap.add_argument("--storage-bits", type=int, default=0,
                     help="mixed workloads: keep the left-connected blocks in FPX of this many bits (0 = off)")
@@ -314,6 +315,47 @@ def run_ozaki(args, q, W):
                                         "frac": ach / peaks.get("bf16_tflops_sustained") if ach else None}})
 
 
+def run_nrl(args, q, W):
+    """b=3408, N_B=10 (the paper's NR-L block shape), emulated FP64, energy-dependent self-energies
+    held in pinned host memory and streamed slice by slice (sigma_stream); one chunk of all energies
+    per step, H2D copies of the self-energies inside the timed region."""
+    import torch
+    cfg = W.NRL_CFG
+    ne = cfg["n_energies"]
+    dev = W.nrl_device(cfg["b"], cfg["n_blocks"], ne, cfg["e_lo"], cfg["e_hi"])
+    nb, b = cfg["n_blocks"], cfg["b"]
+    din = q.upload(dev, sigma_host=True)
+    outs = ["current", "density", "integrals"]
+    desc = q.make_desc(nb, b, args.precision, ne, 2, has_scattering=True, energy_dependent_sigma=True,
+                       outputs=outs, sigma_stream=True, storage_bits=args.storage_bits)
+    plan = q.Plan(desc)
+    o = q.Outputs()
+    cur = torch.empty((ne, nb - 1), dtype=torch.float64, device="cuda")
+    den = torch.empty((ne, nb), dtype=torch.float64, device="cuda")
+    cint = torch.zeros(nb - 1, dtype=torch.float64, device="cuda")
+    dint = torch.zeros(nb, dtype=torch.float64, device="cuda")
+    stat = torch.zeros(ne, dtype=torch.int32, device="cuda")
+    o.current, o.density = cur.data_ptr(), den.data_ptr()
+    o.current_int, o.density_int = cint.data_ptr(), dint.data_ptr()
+    o.status_per_energy = stat.data_ptr()
+    st = torch.cuda.current_stream()
+    plan.set_profiling(True)
+    ms = _timed(lambda: plan.solve(din["_inputs"], o, st.cuda_stream), args.steps, args.warmup)
+    prof = plan.gemm_profile()
+    value = ne * args.steps / (ms / 1e3)
+    peaks, _ = measured_peaks()
+    ach = prof["pipe_flops"] / (prof["ms"] / 1e3) / 1e12 if prof["ms"] else None
+    useful = 136.0 * b ** 3 * nb * ne * args.steps / (ms / 1e3) / 1e12
+    _line(args, value, ms / args.steps, f"NR-L-shaped device b={b} N_B={nb}, {ne} energies per step, "
+          "per-energy scattering self-energies streamed from pinned host memory", args.precision,
+          {"status_ok": bool(torch.all(stat == 0).item()),
+           "plan_bytes": q.footprint(desc), "host_sigma_bytes_per_step": 2 * ne * nb * b * b * 16,
+           "useful_fp64_equiv_tflops": useful,
+           "roofline": {"bound": "tensor", "achieved": ach, "unit": "TFLOP/s",
+                        "peak": peaks.get("bf16_tflops_sustained"),
+                        "frac": ach / peaks.get("bf16_tflops_sustained") if ach else None}})
+
+
 def run_uneven(args, q, W):
     """8 devices (N_B in 16..128, b in 128..512), 128 energies each, all solves captured in one CUDA
     graph (one stream per device), energies in flight per device from the autotuner."""
@@ -411,7 +453,8 @@ def main():
         qbuild.build()
         import paper_2606_25595_gb300 as q
         import workloads as W
-        {"strip": run_strip, "uneven": run_uneven, "ozaki": run_ozaki, "serving": run_serving}[args.workload](args, q, W)
+        {"strip": run_strip, "uneven": run_uneven, "ozaki": run_ozaki, "serving": run_serving,
+         "nrl": run_nrl}[args.workload](args, q, W)
         return
     import numpy as np
     import torch

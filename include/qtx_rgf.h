@@ -82,7 +82,7 @@ enum {
 /* Shapes and numerics, fixed for the life of a plan. */
 typedef struct {
   int n_blocks;                /* N_B >= 1 */
-  int block_size;              /* b, 1 <= b <= 1024 */
+  int block_size;              /* b, 1 <= b <= 4096 */
   int max_energies_in_flight;  /* energies solved concurrently; workspace scales with it (>= 1) */
   qtx_precision precision;
   int refine_max_iter;         /* Newton sweeps X += X (I - A X) per block inverse (QTX_EMU64,
@@ -104,6 +104,13 @@ typedef struct {
                                   {56, 48, 40, 32, 24, 16}: they are kept in the FPX format of X bits
                                   (qtx_kernels.h, Sec. V), with two working blocks per kind in the
                                   sweep's type, which shrinks the footprint per energy in flight */
+  int sigma_stream;            /* 1 (needs has_scattering and energy_dependent_sigma, not offdiag_sigma):
+                                  SigR_diag and SigL_diag are HOST arrays [N_E][N_B][b][b] (pinned, or
+                                  the copies are synchronous); each slice's blocks for the energies of
+                                  a chunk are copied to a device staging area (2 blocks per energy in
+                                  flight) on the solve's stream just before the forward sweep uses
+                                  them, so per-energy self-energies of any number of energies need no
+                                  device memory of their own */
 } qtx_rgf_desc;
 
 /* Device inputs (caller-owned, complex128 unless noted). */

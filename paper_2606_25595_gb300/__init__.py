@@ -48,7 +48,8 @@ class Desc(ctypes.Structure):
                 ("has_scattering", ctypes.c_int), ("energy_dependent_sigma", ctypes.c_int),
                 ("leads", ctypes.c_int), ("decim_tol", ctypes.c_double),
                 ("decim_max_iter", ctypes.c_int), ("outputs", ctypes.c_uint),
-                ("offdiag_sigma", ctypes.c_int), ("storage_bits", ctypes.c_int)]
+                ("offdiag_sigma", ctypes.c_int), ("storage_bits", ctypes.c_int),
+                ("sigma_stream", ctypes.c_int)]
 
 
 class Inputs(ctypes.Structure):
@@ -131,7 +132,7 @@ def lib() -> ctypes.CDLL:
 def make_desc(n_blocks, block_size, precision="fp64", max_energies_in_flight=64,
               refine_max_iter=2, has_S=False, has_scattering=True, energy_dependent_sigma=False,
               leads=False, decim_tol=1e-13, decim_max_iter=100, outputs=None,
-              offdiag_sigma=False, storage_bits=0) -> Desc:
+              offdiag_sigma=False, storage_bits=0, sigma_stream=False) -> Desc:
     if outputs is None:
         outputs = (1 << 12) - 1
     elif not isinstance(outputs, int):
@@ -143,7 +144,8 @@ def make_desc(n_blocks, block_size, precision="fp64", max_energies_in_flight=64,
                 PRECISION[precision] if isinstance(precision, str) else int(precision),
                 int(refine_max_iter), int(bool(has_S)), int(bool(has_scattering)),
                 int(bool(energy_dependent_sigma)), int(bool(leads)), float(decim_tol),
-                int(decim_max_iter), int(outputs), int(bool(offdiag_sigma)), int(storage_bits))
+                int(decim_max_iter), int(outputs), int(bool(offdiag_sigma)), int(storage_bits),
+                int(bool(sigma_stream)))
 
 
 def kernel_launches() -> int:
@@ -209,7 +211,7 @@ def has_offdiag_sigma(dev: dict) -> bool:
 
 def solve_device(dev: dict, precision: str = "fp64", outputs=None, max_energies_in_flight=64,
                  refine_max_iter=2, weights=None, energies=None, stream=None, plan=None,
-                 device_inputs=None, keep_on_device=False, storage_bits=0):
+                 device_inputs=None, keep_on_device=False, storage_bits=0, sigma_stream=False):
     """Solve a ``workloads``-style device dict on the GPU and return numpy arrays (or tensors).
 
     Marshalling only: inputs are copied to torch CUDA tensors (complex128), the C ABI is called on
@@ -221,7 +223,7 @@ def solve_device(dev: dict, precision: str = "fp64", outputs=None, max_energies_
     nb, b = dev["n_blocks"], dev["block_size"]
     E = np.asarray(dev["energies"] if energies is None else energies, dtype=np.float64)
     ne = E.size
-    din = device_inputs if device_inputs is not None else upload(dev, E, weights)
+    din = device_inputs if device_inputs is not None else upload(dev, E, weights, sigma_host=sigma_stream)
     want = list(outputs) if outputs is not None else list(OUT)
     if not dev.get("leads"):
         want = [w for w in want if w not in ("contact", "transmission")]
@@ -229,7 +231,7 @@ def solve_device(dev: dict, precision: str = "fp64", outputs=None, max_energies_
                      has_S=dev.get("S_diag") is not None, has_scattering=dev.get("SigR") is not None,
                      energy_dependent_sigma=dev.get("SigR") is not None and dev["SigR"].shape[0] > 1,
                      leads=bool(dev.get("leads")), outputs=want, offdiag_sigma=has_offdiag_sigma(dev),
-                     storage_bits=storage_bits)
+                     storage_bits=storage_bits, sigma_stream=sigma_stream)
     P = plan if plan is not None else Plan(desc)
     cdev = torch.device("cuda")
     res = {}
@@ -262,14 +264,20 @@ def solve_device(dev: dict, precision: str = "fp64", outputs=None, max_energies_
     return {k: v.cpu().numpy() for k, v in res.items()}
 
 
-def upload(dev: dict, energies=None, weights=None) -> dict:
-    """Copy a device dict's blocks to torch CUDA tensors and build the ``Inputs`` struct."""
+def upload(dev: dict, energies=None, weights=None, sigma_host=False) -> dict:
+    """Copy a device dict's blocks to torch CUDA tensors and build the ``Inputs`` struct.
+
+    ``sigma_host``: keep the (energy-dependent) scattering self-energies in pinned host memory for a
+    plan with ``sigma_stream``."""
     import torch
 
     cdev = torch.device("cuda")
 
     def T(x, dt=torch.complex128):
         return None if x is None else torch.as_tensor(np.ascontiguousarray(x), dtype=dt).to(cdev)
+
+    def Th(x):
+        return None if x is None else torch.as_tensor(np.ascontiguousarray(x), dtype=torch.complex128).pin_memory()
 
     E = np.asarray(dev["energies"] if energies is None else energies, dtype=np.float64)
     d = {"H_diag": T(dev["H_diag"]), "H_upper": T(dev["H_upper"]) if dev["n_blocks"] > 1 else None,
@@ -278,8 +286,9 @@ def upload(dev: dict, energies=None, weights=None) -> dict:
          "weights": T(weights, torch.float64) if weights is not None else None}
     if dev.get("SigR") is not None:
         SR, SL = dev["SigR"], dev["SigL"]
-        d["SigR_diag"] = T(SR[0] if SR.shape[0] == 1 else SR)
-        d["SigL_diag"] = T(SL[0] if SL.shape[0] == 1 else SL)
+        put = Th if sigma_host else T
+        d["SigR_diag"] = put(SR[0] if SR.shape[0] == 1 else SR)
+        d["SigL_diag"] = put(SL[0] if SL.shape[0] == 1 else SL)
     for k in ("SigR_upper", "SigR_lower", "SigL_upper"):
         X = dev.get(k)
         d[k] = None if X is None or X.size == 0 else T(X[0] if X.shape[0] == 1 else X)

@@ -42,7 +42,7 @@ struct Arena {
 inline bool uv_per_energy(const qtx_rgf_desc& d) { return d.has_S || (d.offdiag_sigma && d.energy_dependent_sigma); }
 
 struct Layout {
-  size_t g, gl, gfx, glfx, fx_slot, tmp, inv_tmp, U, V, ident, ident_df, ref, f32a, f32tmp, dec, lead, obs, flags,
+  size_t g, gl, gfx, glfx, fx_slot, sig_stage, tmp, inv_tmp, U, V, ident, ident_df, ref, f32a, f32tmp, dec, lead, obs, flags,
       tc_scratch, total;
   int n_tmp, n_dec;
   size_t tc_bytes;
@@ -105,6 +105,7 @@ Layout make_layout(const qtx_rgf_desc& d) {
     L.gl = a.take(nb * Ec * bb * es);
   }
   L.tmp = a.take((size_t)L.n_tmp * Ec * bb * es);
+  L.sig_stage = a.take(d.sigma_stream ? 2 * Ec * bb * sizeof(cx<double>) : 0);  // Sigma^R_ii, Sigma^<_ii
   L.inv_tmp = a.take(Ec * bb * es + 4096);
   const size_t ou = uv_per_energy(d) ? (size_t)(nb > 1 ? nb - 1 : 0) * Ec * bb * es : (size_t)(nb > 1 ? nb - 1 : 0) * bb * es;
   L.U = a.take(ou);
@@ -504,7 +505,28 @@ qtx_status solve_chunk(qtx_rgf_plan_s* P, const qtx_rgf_inputs* in, const qtx_rg
     const cx<double>* lead = nullptr;
     if (d.leads && i == 0) lead = SR_L;
     else if (d.leads && i == nb - 1) lead = SR_R;
-    QTX_CK(assemble_diag<T>(gi, Hd + (long)i * bb, Sd ? Sd + (long)i * bb : nullptr, sigR(i), sSig, lead, bb, c.E, eta, b, ne, st));
+    // streamed self-energies: this slice's blocks of the chunk's energies, host -> staging area
+    const cx<double>* sRi = sigR(i);
+    const cx<double>* sLi = sigL(i);
+    long sS = sSig;
+    if (d.sigma_stream) {
+      cx<double>* stR = reinterpret_cast<cx<double>*>(P->ws + P->L.sig_stage);
+      cx<double>* stL = stR + (size_t)P->Ec * bb;
+      const size_t row = (size_t)bb * sizeof(cx<double>), pitch = (size_t)nb * row;
+      if (pitch < ((size_t)1 << 31)) {  // one strided copy per kind
+        QTX_CK(cudaMemcpy2DAsync(stR, row, sRi, pitch, row, ne, cudaMemcpyHostToDevice, st));
+        QTX_CK(cudaMemcpy2DAsync(stL, row, sLi, pitch, row, ne, cudaMemcpyHostToDevice, st));
+      } else {                          // pitches beyond the 2D copy's range: one copy per energy
+        for (int e = 0; e < ne; ++e) {
+          QTX_CK(cudaMemcpyAsync(stR + (size_t)e * bb, sRi + (size_t)e * nb * bb, row, cudaMemcpyHostToDevice, st));
+          QTX_CK(cudaMemcpyAsync(stL + (size_t)e * bb, sLi + (size_t)e * nb * bb, row, cudaMemcpyHostToDevice, st));
+        }
+      }
+      sRi = stR;
+      sLi = stL;
+      sS = bb;
+    }
+    QTX_CK(assemble_diag<T>(gi, Hd + (long)i * bb, Sd ? Sd + (long)i * bb : nullptr, sRi, sS, lead, bb, c.E, eta, b, ne, st));
     if (d.leads && nb == 1) {  // one slice touches both contacts
       Term<T> tg; tg.p = gi; tg.s = bb; tg.alpha = 1.0;
       QTX_CK((combine<T, T>(c.tmp(0), bb, tg, none, none, b, ne, nullptr, 0, 0, nullptr, st)));
@@ -521,11 +543,11 @@ qtx_status solve_chunk(qtx_rgf_plan_s* P, const qtx_rgf_inputs* in, const qtx_rg
     if ((s = block_inverse<T>(P, gi, b, ne, nullptr, status, st))) return s;
     // Sigma^<_ii (+ contacts), then the left-connected lesser function
     cx<T>* SLi = c.tmp(1);
-    const cx<double>* sl = sigL(i);
+    const cx<double>* sl = sLi;
     const cx<double>* lsl = nullptr;
     if (d.leads && i == 0) lsl = SL_L;
     else if (d.leads && i == nb - 1) lsl = SL_R;
-    if (sl) QTX_CK(axpby_from64<T>(SLi, bb, sl, sSig, 1.0, lsl, bb, 1.0, b, ne, st));
+    if (sl) QTX_CK(axpby_from64<T>(SLi, bb, sl, sS, 1.0, lsl, bb, 1.0, b, ne, st));
     else if (lsl) QTX_CK(axpby_from64<T>(SLi, bb, lsl, bb, 1.0, nullptr, 0, 0.0, b, ne, st));
     else QTX_CK(cudaMemsetAsync(SLi, 0, (size_t)ne * bb * sizeof(cx<T>), st));
     if (d.leads && nb == 1) {
@@ -724,13 +746,14 @@ qtx_status solve_all(qtx_rgf_plan_s* P, const qtx_rgf_inputs* in, const qtx_rgf_
 qtx_status validate(const qtx_rgf_desc* d, std::string& err) {
   if (!d) { err = "desc is NULL"; return QTX_ERR_INVALID_ARG; }
   if (d->n_blocks < 1) { err = "n_blocks must be >= 1"; return QTX_ERR_INVALID_ARG; }
-  if (d->block_size < 1 || d->block_size > 1024) { err = "block_size must be in [1, 1024]"; return QTX_ERR_INVALID_ARG; }
+  if (d->block_size < 1 || d->block_size > 4096) { err = "block_size must be in [1, 4096]"; return QTX_ERR_INVALID_ARG; }
   if (d->max_energies_in_flight < 1) { err = "max_energies_in_flight must be >= 1"; return QTX_ERR_INVALID_ARG; }
   if (d->precision < QTX_FP64 || d->precision > QTX_EMU64) { err = "unknown precision"; return QTX_ERR_INVALID_ARG; }
   if (d->leads && (d->decim_max_iter < 1 || !(d->decim_tol > 0))) { err = "leads need decim_max_iter >= 1 and decim_tol > 0"; return QTX_ERR_INVALID_ARG; }
   if (d->refine_max_iter < 0) { err = "refine_max_iter must be >= 0"; return QTX_ERR_INVALID_ARG; }
   if (d->offdiag_sigma && !d->has_scattering) { err = "offdiag_sigma needs has_scattering"; return QTX_ERR_INVALID_ARG; }
   if (d->storage_bits && !fpx_width_ok(d->storage_bits)) { err = "storage_bits must be 0, 56, 48, 40, 32, 24 or 16"; return QTX_ERR_INVALID_ARG; }
+  if (d->sigma_stream && (!d->has_scattering || !d->energy_dependent_sigma || d->offdiag_sigma)) { err = "sigma_stream needs has_scattering and energy_dependent_sigma, without offdiag_sigma"; return QTX_ERR_INVALID_ARG; }
   if ((d->precision == QTX_EMU64 || d->precision == QTX_BF16X3) && !tc_available()) {
     err = "tensor-core engine not available in this build";
     return QTX_ERR_UNSUPPORTED;
@@ -1013,7 +1036,7 @@ qtx_status qtx_zgemm_batched(int precision, int M, int N, int K, int opA, const 
 }
 
 qtx_status qtx_zinv_batched(int precision, int n, void* A, long sA, int batch, int refine_iter, int* status, void* stream) {
-  if (n < 1 || n > 1024 || batch < 1 || !A || refine_iter < 0) return QTX_ERR_INVALID_ARG;
+  if (n < 1 || n > 4096 || batch < 1 || !A || refine_iter < 0) return QTX_ERR_INVALID_ARG;
   qtx_rgf_desc d{};
   d.n_blocks = 1;
   d.block_size = n;
@@ -1038,7 +1061,7 @@ qtx_status qtx_zinv_batched(int precision, int n, void* A, long sA, int batch, i
 
 qtx_status qtx_lead_self_energy(int n, const void* H00, const void* H01, const double* energies, int n_energies,
                                 double eta, double tol, int max_iter, void* SigR, int* status, void* stream) {
-  if (n < 1 || n > 1024 || n_energies < 1 || !H00 || !H01 || !energies || !SigR || max_iter < 1 || !(tol > 0))
+  if (n < 1 || n > 4096 || n_energies < 1 || !H00 || !H01 || !energies || !SigR || max_iter < 1 || !(tol > 0))
     return QTX_ERR_INVALID_ARG;
   qtx_rgf_desc d{};
   d.n_blocks = 1;

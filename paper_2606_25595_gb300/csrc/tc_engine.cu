@@ -797,15 +797,46 @@ bool tc_available() {
 // leading digit has shrunk to l1 = 5 bits (dims_of) and six digits would carry only 40 bits.
 static int effective_digits(int digits, int K) { return (digits == 6 && K > 512) ? 7 : digits; }
 
+// Contractions longer than kMaxKChunk run as consecutive K-chunks of at most that length, each
+// added to the previous partial result in the epilogue (C0 = C, beta = 1, df32 addition): the
+// exactness bound of the digit accumulators (the leading digit's l1 bits) only covers K <= 1024.
+constexpr int kMaxKChunk = 1024;
+static int k_chunks(int K) { return K <= kMaxKChunk ? 1 : (K + kMaxKChunk - 1) / kMaxKChunk; }
+
 size_t gemm_tc_scratch_bytes(int M, int N, int K, int batch, int digits) {
-  const int S = effective_digits(digits, K);
-  const tc::Dims d = tc::dims_of(M, N, K, S);
+  const int Kc = (K + k_chunks(K) - 1) / k_chunks(K);
+  const int S = effective_digits(digits, Kc);
+  const tc::Dims d = tc::dims_of(M, N, Kc, S);
   return tc::carve(nullptr, d, batch, S).bytes + 4096;
 }
 
 cudaError_t gemm_tc(const TcArgs& a, int digits, void* scratch, size_t scratch_bytes, int* err_flag,
                     cudaStream_t st, cudaEvent_t* ev) {
   if (a.M <= 0 || a.N <= 0 || a.batch <= 0) return cudaSuccess;
+  const int nc = k_chunks(a.K);
+  if (nc > 1) {
+    // split K: chunk c covers k in [k0, k1); op N operands advance along their columns (A) or rows
+    // (B), op C ones the other way round
+    const int Kc = (a.K + nc - 1) / nc;
+    if (ev) cudaEventRecord(ev[0], st);
+    for (int c = 0; c < nc; ++c) {
+      const int k0 = c * Kc, k1 = a.K < k0 + Kc ? a.K : k0 + Kc;
+      TcArgs t = a;
+      t.K = k1 - k0;
+      t.A = a.A + (a.opA == OP_N ? (long)k0 : (long)k0 * a.lda);
+      t.B = a.B + (a.opB == OP_N ? (long)k0 * a.ldb : (long)k0);
+      if (c > 0) {
+        t.C0 = a.C;
+        t.ldc0 = a.ldc;
+        t.sC0 = a.sC;
+        t.beta = 1.f;
+      }
+      const cudaError_t e = gemm_tc(t, digits, scratch, scratch_bytes, err_flag, st, nullptr);
+      if (e != cudaSuccess) return e;
+    }
+    if (ev) cudaEventRecord(ev[1], st);
+    return cudaSuccess;
+  }
   digits = effective_digits(digits, a.K);
   if (digits == 7) return tc::launch<7, 4>(a, scratch, scratch_bytes, err_flag, st, ev);
   if (digits == 6) return tc::launch<6, 5>(a, scratch, scratch_bytes, err_flag, st, ev);

@@ -94,6 +94,27 @@ def test_emu64_random_error_bound_long_k(q, K, bits):
     assert ratio <= 2.0 ** -bits, np.log2(ratio)
 
 
+@pytest.mark.parametrize("K", [1536, 3408])
+def test_emu64_split_k_error_bound(q, K):
+    """Contractions beyond 1024 run as K-chunks of at most 1024 (each exact in its digit
+    accumulators, 7 digits) added in df32: the 2^-36 (|A| |B|) bound holds at 1536 and at the
+    paper's NR-L block size 3408."""
+    rng = np.random.default_rng(K)
+    M, N, batch = 160, 96, 2
+    A = (rng.standard_normal((batch, M, K)) + 1j * rng.standard_normal((batch, M, K))) * \
+        np.exp(rng.uniform(-3, 3, (batch, M, 1)))
+    B = rng.standard_normal((batch, K, N)) + 1j * rng.standard_normal((batch, K, N))
+    got = q.zgemm_batched(_t(A), _t(B), "emu64").cpu().numpy()
+    ref = A @ B
+    bound = (np.abs(A.real) + np.abs(A.imag)) @ (np.abs(B.real) + np.abs(B.imag))
+    ratio = np.max(np.abs(got - ref) / bound)
+    assert ratio <= 2.0 ** -36, np.log2(ratio)
+    # conjugate-transposed operands take the other chunk strides
+    gotc = q.zgemm_batched(_t(np.conj(np.swapaxes(A, 1, 2))), _t(np.conj(np.swapaxes(B, 1, 2))), "emu64",
+                           opA="C", opB="C").cpu().numpy()
+    assert np.max(np.abs(gotc - ref) / bound) <= 2.0 ** -36
+
+
 def test_bf16x3_error_bound(q):
     """Two digit planes (~13-bit products): |C - C_ref| <= 2^-11 * (|A| |B|)."""
     rng = np.random.default_rng(11)

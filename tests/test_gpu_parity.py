@@ -343,6 +343,37 @@ def test_emu64_rgf_b1024_sampled(q):
     _check(res, ref, 1e-7, 1e-6, keys=("GR_diag", "GR_upper", "GL_diag", "GL_upper"))
 
 
+def test_large_blocks_b2048(q):
+    """b = 2048 blocks (split-K products, six levels of recursive inverse) on a two-slice device at
+    one energy: emulated FP64 current and density within 1e-6 of the oracle, FP64 blocks within
+    1e-10."""
+    dev = W.random_device(2048, 2, n_energies=1, seed=9, energies=np.array([0.31]))
+    ref = O.solve(dev)
+    res = q.solve_device(dev, "emu64", outputs=["GR_diag", "GL_diag", "current", "density"])
+    assert np.all(res["status"] == 0)
+    e = _obs_errs(res, ref)
+    assert e["current"] < 1e-6 and e["density"] < 1e-6, e
+    r64 = q.solve_device(dev, "fp64", outputs=["GR_diag", "GL_diag", "current", "density"])
+    _check(r64, ref, 1e-10, 1e-10, keys=("GR_diag", "GL_diag"))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "emu64"])
+def test_sigma_streamed_from_host(q, precision):
+    """Per-energy self-energies streamed from pinned host memory, slice by slice, into the plan's
+    staging area: bit-identical to the same solve with the self-energies resident on the device,
+    and within the FP64 bar of the oracle."""
+    dev = W.random_device(64, 6, n_energies=5, seed=12)
+    dev["SigR"] = np.concatenate([dev["SigR"] * (1 + 0.2 * k) for k in range(5)])
+    dev["SigL"] = np.concatenate([dev["SigL"] * (1 + 0.3 * k) for k in range(5)])
+    outs = ["GR_diag", "GR_upper", "GL_diag", "GL_upper", "current", "density"]
+    a = q.solve_device(dev, precision, outputs=outs, max_energies_in_flight=2)
+    b = q.solve_device(dev, precision, outputs=outs, max_energies_in_flight=2, sigma_stream=True)
+    for k in outs:
+        assert np.array_equal(a[k], b[k]), k
+    if precision == "fp64":
+        _check(b, O.solve(dev), 1e-10, 1e-10, keys=("GR_diag", "GR_upper", "GL_diag", "GL_upper"))
+
+
 def test_bf16x3_rgf_error_within_stated_bound(q):
     """Two digit planes (~13-bit products, 3 bf16 digit products per real product): the error
     follows kappa * 2^-13 and is large -- G blocks within 0.5, density within 0.2 on this

@@ -33,7 +33,7 @@ from __future__ import annotations
 import numpy as np
 
 __all__ = ["strip", "random_device", "uneven_batch", "serving_requests", "trapezoid_weights",
-           "STRIP_CFG", "MIXED_CFG", "UNEVEN_NB", "UNEVEN_B", "OZAKI_CFG"]
+           "nrl_device", "STRIP_CFG", "MIXED_CFG", "UNEVEN_NB", "UNEVEN_B", "OZAKI_CFG", "NRL_CFG"]
 
 # The five synthetic workloads (sizes only; the generators below draw the values).
 STRIP_CFG = dict(W=16, n_blocks=32, t=-1.0, disorder=0.25, eta=1e-6, mu_L=0.1, mu_R=-0.1,
@@ -42,6 +42,8 @@ MIXED_CFG = dict(b=256, n_blocks=64, n_energies=512, e_lo=-2.0, e_hi=2.0)
 UNEVEN_NB = (16, 24, 32, 48, 64, 96, 112, 128)
 UNEVEN_B = (128, 192, 256, 384, 512)
 OZAKI_CFG = dict(b=1024, n_blocks=32, n_energies=256, e_lo=-2.0, e_hi=2.0)
+# the paper's large nanoribbon device shape (b = 3408, N_B = 10), energies streamed in small chunks
+NRL_CFG = dict(b=3408, n_blocks=10, n_energies=4, e_lo=-1.0, e_hi=1.0)
 
 
 def _chain(W: int, t: float) -> np.ndarray:
@@ -141,6 +143,38 @@ def random_device(b: int, n_blocks: int, n_energies: int = 8, e_lo: float = -2.0
                kT=0.025)
     dev.update(extra)
     return dev
+
+
+def nrl_device(b: int = 3408, n_blocks: int = 10, n_energies: int = 4, e_lo: float = -1.0,
+               e_hi: float = 1.0, seed: int = 0, rank: int = 32, sigma_scale: float = 1e-2,
+               eta: float = 1e-6) -> dict:
+    """Device with the block shape of the paper's large nanoribbon (b = 3408, N_B = 10): H as in
+    ``random_device``; per-energy scattering self-energies Sigma^< = i s (A A^H + I/b), Sigma^> =
+    -i s (B B^H + I/b) with A, B of rank ``rank`` (complex Gaussian, variance 1/rank) and a smooth
+    energy dependence (1 + 0.1 k / N_E at energy k), Sigma^R = (Sigma^> - Sigma^<) / 2.  Arrays are
+    [N_E][N_B][b][b] (complex128, about 2 N_E N_B b^2 16 bytes for the two self-energies)."""
+    rng = np.random.default_rng(seed)
+    H_diag = np.empty((n_blocks, b, b), dtype=np.complex128)
+    for i in range(n_blocks):
+        X = _cgauss(rng, (b, b), 1.0 / b)
+        H_diag[i] = (X + X.conj().T) / np.sqrt(2.0) + np.diag(rng.uniform(-1.0, 1.0, size=b))
+    H_upper = np.stack([_cgauss(rng, (b, b), 0.3 / b) for _ in range(n_blocks - 1)]) if n_blocks > 1 \
+        else np.zeros((0, b, b), np.complex128)
+    SigL = np.empty((n_energies, n_blocks, b, b), dtype=np.complex128)
+    SigR = np.empty((n_energies, n_blocks, b, b), dtype=np.complex128)
+    eye = np.eye(b) / b
+    for i in range(n_blocks):
+        A = _cgauss(rng, (b, rank), 1.0 / rank)
+        B = _cgauss(rng, (b, rank), 1.0 / rank)
+        sl = 1j * sigma_scale * (A @ A.conj().T + eye)
+        sg = -1j * sigma_scale * (B @ B.conj().T + eye)
+        for k in range(n_energies):
+            f = 1.0 + 0.1 * k / max(n_energies, 1)
+            SigL[k, i] = f * sl
+            SigR[k, i] = f * (sg - sl) / 2.0
+    return dict(n_blocks=n_blocks, block_size=b, H_diag=H_diag, H_upper=H_upper, S_diag=None,
+                S_upper=None, SigR=SigR, SigL=SigL, leads=None,
+                energies=np.linspace(e_lo, e_hi, n_energies), eta=eta, mu_L=0.0, mu_R=0.0, kT=0.025)
 
 
 def uneven_batch(n_energies: int = 128, seed: int = 0, nb_list=UNEVEN_NB, b_list=UNEVEN_B,
