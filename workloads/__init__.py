@@ -33,7 +33,8 @@ from __future__ import annotations
 import numpy as np
 
 __all__ = ["strip", "random_device", "uneven_batch", "serving_requests", "trapezoid_weights",
-           "nrl_device", "STRIP_CFG", "MIXED_CFG", "UNEVEN_NB", "UNEVEN_B", "OZAKI_CFG", "NRL_CFG"]
+           "nrl_device", "w_system", "STRIP_CFG", "MIXED_CFG", "UNEVEN_NB", "UNEVEN_B", "OZAKI_CFG",
+           "NRL_CFG", "WSYS_CFG"]
 
 # The five synthetic workloads (sizes only; the generators below draw the values).
 STRIP_CFG = dict(W=16, n_blocks=32, t=-1.0, disorder=0.25, eta=1e-6, mu_L=0.1, mu_R=-0.1,
@@ -44,6 +45,8 @@ UNEVEN_B = (128, 192, 256, 384, 512)
 OZAKI_CFG = dict(b=1024, n_blocks=32, n_energies=256, e_lo=-2.0, e_hi=2.0)
 # the paper's large nanoribbon device shape (b = 3408, N_B = 10), energies streamed in small chunks
 NRL_CFG = dict(b=3408, n_blocks=10, n_energies=4, e_lo=-1.0, e_hi=1.0)
+# screened-Coulomb (W) system: per-energy polarisation blocks
+WSYS_CFG = dict(b=256, n_blocks=32, n_energies=64)
 
 
 def _chain(W: int, t: float) -> np.ndarray:
@@ -175,6 +178,41 @@ def nrl_device(b: int = 3408, n_blocks: int = 10, n_energies: int = 4, e_lo: flo
     return dict(n_blocks=n_blocks, block_size=b, H_diag=H_diag, H_upper=H_upper, S_diag=None,
                 S_upper=None, SigR=SigR, SigL=SigL, leads=None,
                 energies=np.linspace(e_lo, e_hi, n_energies), eta=eta, mu_L=0.0, mu_R=0.0, kT=0.025)
+
+
+def w_system(b: int, n_blocks: int, n_energies: int = 4, seed: int = 0, v_scale: float = 1.0,
+             p_scale: float = 4.0) -> dict:
+    """Screened-Coulomb system inputs (Table I, W row): a Hermitian BT Coulomb matrix V and per-energy
+    BT polarisations.  V_ii = I + v (X + X^H) / (2 sqrt(b)), V_{i,i+1} = v Y / (2 sqrt(b)) (complex
+    Gaussian X, Y of unit variance); P^< = i p F F^H and P^> = -i p G G^H with F, G block-lower-
+    bidiagonal (complex Gaussian blocks of variance 1/b), scaled by (1 + 0.5 k / N_E) at energy k;
+    P^R = (P^> - P^<) / 2 on every block.  With the default scales kappa(M) is 1e2 - 1e3, the range
+    the paper reports for W systems (Sec. IV).  Arrays: V_diag [N_B][b][b], V_upper [N_B-1][b][b];
+    PR_diag [N_E][N_B][b][b], PR_upper / PR_lower / PL_upper / PG_upper [N_E][N_B-1][b][b],
+    PL_diag / PG_diag [N_E][N_B][b][b]."""
+    rng = np.random.default_rng(seed)
+    nu = max(n_blocks - 1, 0)
+    V_diag = np.empty((n_blocks, b, b), np.complex128)
+    for i in range(n_blocks):
+        X = _cgauss(rng, (b, b), 1.0)
+        V_diag[i] = np.eye(b) + v_scale * (X + X.conj().T) / (2.0 * np.sqrt(b))
+    V_upper = np.stack([v_scale * _cgauss(rng, (b, b), 1.0) / (2.0 * np.sqrt(b)) for _ in range(nu)]) \
+        if nu else np.zeros((0, b, b), np.complex128)
+    out = {}
+    for key, sgn in (("PL", 1j), ("PG", -1j)):
+        D = [_cgauss(rng, (b, b), 1.0 / b) for _ in range(n_blocks)]
+        Lo = [_cgauss(rng, (b, b), 1.0 / b) for _ in range(nu)]
+        d0 = np.stack([D[i] @ D[i].conj().T + (Lo[i - 1] @ Lo[i - 1].conj().T if i > 0 else 0)
+                       for i in range(n_blocks)])
+        u0 = np.stack([D[i] @ Lo[i].conj().T for i in range(nu)]) if nu else np.zeros((0, b, b), np.complex128)
+        f = (1.0 + 0.5 * np.arange(n_energies) / max(n_energies, 1))[:, None, None, None]
+        out[key + "_diag"] = sgn * p_scale * f * d0[None]
+        out[key + "_upper"] = sgn * p_scale * f * u0[None]
+    out["PR_diag"] = (out["PG_diag"] - out["PL_diag"]) / 2.0
+    out["PR_upper"] = (out["PG_upper"] - out["PL_upper"]) / 2.0
+    out["PR_lower"] = -np.conj(np.swapaxes(out["PR_upper"], -1, -2))
+    out.update(n_blocks=n_blocks, block_size=b, n_energies=n_energies, V_diag=V_diag, V_upper=V_upper)
+    return out
 
 
 def uneven_batch(n_energies: int = 128, seed: int = 0, nb_list=UNEVEN_NB, b_list=UNEVEN_B,
