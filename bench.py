@@ -49,12 +49,13 @@ def parse():
     ap.add_argument("--fp64-energies", type=int, default=16, help="energies for the FP64 comparison (0 = skip)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU oracle sample")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="mixed", choices=["mixed", "mixed_bt", "strip", "uneven", "ozaki", "serving", "nrl"],
+    ap.add_argument("--workload", default="mixed", choices=["mixed", "mixed_bt", "strip", "uneven", "ozaki", "serving", "nrl", "wsolve"],
                     help="mixed: b=256 N_B=64 N_E=512 (default); mixed_bt: the same with block-tridiagonal "
                          "scattering self-energies; strip: W=16 strip FP64 with contacts; "
                          "uneven: 8 devices x 128 energies in one CUDA graph; ozaki: b=1024 N_B=32 "
                          "emulated FP64 (subset of the 256 energies); serving: Poisson request stream; "
-                         "nrl: b=3408 N_B=10 (the paper's NR-L shape), per-energy self-energies streamed from host")
+                         "nrl: b=3408 N_B=10 (the paper's NR-L shape), per-energy self-energies streamed from host; "
+                         "wsolve: screened-Coulomb system b=256 N_B=32, 64 energies (assembly + two selected solves)")
     ap.add_argument("--requests", type=int, default=40)
     ap.add_argument("--storage-bits", type=int, default=0,
                     help="mixed workloads: keep the left-connected blocks in FPX of this many bits (0 = off)")
@@ -356,6 +357,61 @@ def run_nrl(args, q, W):
                         "frac": ach / peaks.get("bf16_tflops_sustained") if ach else None}})
 
 
+def run_wsolve(args, q, W):
+    """Screened-Coulomb system (Table I, W row): per step, assemble M = I - V P^R and B^<> = V P^<>
+    V^H for all energies and solve M X M^H = B^< and B^> (two selected solves sharing M).  Error
+    against the oracle on a small system of the same generator (b=64, N_B=6, 2 energies)."""
+    import time
+    import numpy as np
+    import torch
+    from oracle import wsys
+    cfg = W.WSYS_CFG
+    b, nb, ne = cfg["b"], cfg["n_blocks"], cfg["n_energies"]
+    w = W.w_system(b, nb, n_energies=ne, seed=0)
+    st = torch.cuda.current_stream()
+    ws = q.WSystem(w, args.precision, max_energies_in_flight=min(args.chunk, ne))
+    step = lambda: ws.run(st.cuda_stream)
+    for _ in range(args.warmup):
+        step()
+    launches0 = q.kernel_launches()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    e0.record(st)
+    ws.plan.set_profiling(True)
+    for _ in range(args.steps):
+        step()
+    e1.record(st)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    launches = q.kernel_launches() - launches0
+    prof = ws.plan.gemm_profile()
+    status_ok = bool(torch.all(ws.res["status"] == 0).item())
+    ms = e0.elapsed_time(e1)
+    small = W.w_system(64, 6, n_energies=2, seed=1)
+    got = q.solve_w(small, args.precision)
+    err = 0.0
+    for k in range(2):
+        PR = (small["PR_diag"][k], small["PR_upper"][k], small["PR_lower"][k])
+        M = wsys.assemble(small["V_diag"], small["V_upper"], PR, (small["PL_diag"][k], small["PL_upper"][k]),
+                          (small["PG_diag"][k], small["PG_upper"][k]))
+        ref = wsys.solve(M, (M["BL_diag"], M["BL_upper"]), (M["BG_diag"], M["BG_upper"]))
+        for key in ("XL_diag", "XG_diag", "XR_diag"):
+            err = max(err, float(np.linalg.norm(got[key][k] - ref[key]) / np.linalg.norm(ref[key])))
+    value = ne * args.steps / (ms / 1e3)
+    peaks, _ = measured_peaks()
+    ach = prof["pipe_flops"] / (prof["ms"] / 1e3) / 1e12 if prof["ms"] else None
+    _line(args, value, ms / args.steps, f"screened-Coulomb system b={b} N_B={nb}, {ne} energies per step "
+          "(assembly of M = I - V P^R, B^<> = V P^<> V^H and two selected solves; inputs resident)",
+          args.precision,
+          {"status_ok": status_ok, "wall_s_per_step": wall / args.steps, "gpu_launches": int(launches),
+           "product_kernel_share": prof["ms"] / ms if ms else None,
+           "roofline": {"bound": "tensor", "achieved": ach, "unit": "TFLOP/s",
+                        "peak": peaks.get("bf16_tflops_sustained"),
+                        "frac": ach / peaks.get("bf16_tflops_sustained") if ach else None},
+           "error_vs_oracle": {"system": "b=64 N_B=6, 2 energies, same generator", "max_rel_frobenius": err}})
+
+
 def run_uneven(args, q, W):
     """8 devices (N_B in 16..128, b in 128..512), 128 energies each, all solves captured in one CUDA
     graph (one stream per device), energies in flight per device from the autotuner."""
@@ -454,7 +510,7 @@ def main():
         import paper_2606_25595_gb300 as q
         import workloads as W
         {"strip": run_strip, "uneven": run_uneven, "ozaki": run_ozaki, "serving": run_serving,
-         "nrl": run_nrl}[args.workload](args, q, W)
+         "nrl": run_nrl, "wsolve": run_wsolve}[args.workload](args, q, W)
         return
     import numpy as np
     import torch

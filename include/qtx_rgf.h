@@ -111,6 +111,15 @@ typedef struct {
                                   flight) on the solve's stream just before the forward sweep uses
                                   them, so per-energy self-energies of any number of energies need no
                                   device memory of their own */
+  int system_input;            /* 1: solve M X M^H = B (Eq. 2) for a caller-given block-tridiagonal M --
+                                  e.g. the screened-Coulomb system M = I - V P^R, B = V P^<> V^H of
+                                  Table I (see qtx_w_assemble) -- instead of M = z S - H - Sigma^R:
+                                  A_i = M_ii, U_i = M_{i,i+1}, V_i = M_{i+1,i} from inputs M_*; B's
+                                  blocks come in SigL_diag (and SigL_upper with offdiag_sigma), H, S,
+                                  Sigma^R, eta and the energies' values are not used.  Needs has_S = 0,
+                                  leads = 0, sigma_stream = 0; GR_* outputs are the BT blocks of M^-1,
+                                  GL_* those of X; GG_*, current, contact, transmission and integrals
+                                  are not produced (their bits must be clear); density = Im Tr X_ii */
 } qtx_rgf_desc;
 
 /* Device inputs (caller-owned, complex128 unless noted). */
@@ -135,6 +144,9 @@ typedef struct {
   const void *SigR_lower;  /* offdiag_sigma: Sigma^R_{i+1,i}, same layout */
   const void *SigL_upper;  /* offdiag_sigma: Sigma^<_{i,i+1}, same layout; Sigma^<_{i+1,i} =
                               -(Sigma^<_{i,i+1})^H (Sigma^< is anti-Hermitian) */
+  const void *M_diag;      /* system_input: M_ii [N_E][N_B][b][b] */
+  const void *M_upper;     /* system_input: M_{i,i+1} [N_E][N_B-1][b][b] */
+  const void *M_lower;     /* system_input: M_{i+1,i} [N_E][N_B-1][b][b] */
 } qtx_rgf_inputs;
 
 /* Device outputs (caller-owned; NULL = not produced).  Layouts as in QTX_OUT_*. */
@@ -168,6 +180,32 @@ const char *qtx_rgf_last_error(qtx_rgf_plan plan);
 
 /* Device workspace bytes a plan with this desc allocates (for admission by HBM footprint). */
 size_t qtx_rgf_footprint(const qtx_rgf_desc *desc);
+
+/* Screened-Coulomb system assembly (Table I, W row): per energy, the block-tridiagonal blocks of
+ *     M = I - V P^R,     B^< = V P^< V^H,     B^> = V P^> V^H
+ * from the exact products of the BT factors (all contributing blocks; blocks beyond the first
+ * off-diagonal are not formed), ready for a system_input solve.  V is Hermitian (V_{i+1,i} =
+ * V_{i,i+1}^H) and shared by all energies; P^R is general; P^< and P^> are anti-Hermitian (their
+ * lower blocks are -(upper)^H).  The block products run in the plan's precision (tcgen05 digit
+ * products for QTX_EMU64) batched over the plan's energies in flight; complex128 in and out. */
+typedef struct {
+  const void *V_diag, *V_upper;              /* [N_B][b][b], [N_B-1][b][b] */
+  const void *PR_diag, *PR_upper, *PR_lower; /* [N_E][N_B][b][b], [N_E][N_B-1][b][b], [N_E][N_B-1][b][b] */
+  const void *PL_diag, *PL_upper;            /* P^<: [N_E][N_B][b][b], [N_E][N_B-1][b][b] */
+  const void *PG_diag, *PG_upper;            /* P^>: same; both NULL = no B^> */
+  int n_energies;                            /* N_E >= 1 */
+  int n_blocks;                              /* 0 = the plan's n_blocks, else 1..plan's n_blocks */
+} qtx_w_inputs;
+typedef struct {
+  void *M_diag, *M_upper, *M_lower;          /* [N_E][N_B][b][b], [N_E][N_B-1][b][b] x 2 */
+  void *BL_diag, *BL_upper;                  /* B^<: [N_E][N_B][b][b], [N_E][N_B-1][b][b] */
+  void *BG_diag, *BG_upper;                  /* B^> (NULL when PG_* are NULL) */
+} qtx_w_outputs;
+/* Uses the plan's workspace (any plan with this b, enough slices, and the wanted precision; a
+ * system_input plan can then solve for X^R and X^< from M and B^<, and again with B^> for X^>).
+ * Asynchronous on `stream`.  Errors: QTX_ERR_INVALID_ARG (NULL required pointers, n_blocks beyond
+ * the plan's), QTX_ERR_CUDA. */
+qtx_status qtx_w_assemble(qtx_rgf_plan plan, const qtx_w_inputs *in, const qtx_w_outputs *out, void *stream);
 
 /* Library version string. */
 const char *qtx_rgf_version(void);

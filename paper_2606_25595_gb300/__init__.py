@@ -14,7 +14,7 @@ import os
 import numpy as np
 
 __all__ = ["lib", "load", "Desc", "Inputs", "Outputs", "Plan", "QtxError", "PRECISION",
-           "OUT", "solve_device", "footprint", "EXPORTED"]
+           "OUT", "solve_device", "solve_w", "WSystem", "footprint", "EXPORTED"]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libqtx_rgf.so")
@@ -32,7 +32,7 @@ EXPORTED = ("qtx_rgf_plan_create", "qtx_rgf_solve", "qtx_rgf_status", "qtx_rgf_d
             "qtx_rgf_last_error", "qtx_rgf_footprint", "qtx_rgf_version", "qtx_zgemm_batched",
             "qtx_zinv_batched", "qtx_lead_self_energy", "qtx_rgf_set_profiling",
             "qtx_rgf_gemm_profile", "qtx_kernel_launches", "qtx_zgemm_emu64_noalloc",
-            "qtx_fpx_bytes", "qtx_fpx_compress", "qtx_fpx_decompress")
+            "qtx_fpx_bytes", "qtx_fpx_compress", "qtx_fpx_decompress", "qtx_w_assemble")
 
 
 class QtxError(RuntimeError):
@@ -49,7 +49,7 @@ class Desc(ctypes.Structure):
                 ("leads", ctypes.c_int), ("decim_tol", ctypes.c_double),
                 ("decim_max_iter", ctypes.c_int), ("outputs", ctypes.c_uint),
                 ("offdiag_sigma", ctypes.c_int), ("storage_bits", ctypes.c_int),
-                ("sigma_stream", ctypes.c_int)]
+                ("sigma_stream", ctypes.c_int), ("system_input", ctypes.c_int)]
 
 
 class Inputs(ctypes.Structure):
@@ -62,7 +62,19 @@ class Inputs(ctypes.Structure):
                 ("kT", ctypes.c_double), ("energies", ctypes.c_void_p),
                 ("weights", ctypes.c_void_p), ("n_energies", ctypes.c_int),
                 ("n_blocks", ctypes.c_int), ("SigR_upper", ctypes.c_void_p),
-                ("SigR_lower", ctypes.c_void_p), ("SigL_upper", ctypes.c_void_p)]
+                ("SigR_lower", ctypes.c_void_p), ("SigL_upper", ctypes.c_void_p),
+                ("M_diag", ctypes.c_void_p), ("M_upper", ctypes.c_void_p), ("M_lower", ctypes.c_void_p)]
+
+
+class WInputs(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_void_p) for n in ("V_diag", "V_upper", "PR_diag", "PR_upper", "PR_lower",
+                                               "PL_diag", "PL_upper", "PG_diag", "PG_upper")] + \
+               [("n_energies", ctypes.c_int), ("n_blocks", ctypes.c_int)]
+
+
+class WOutputs(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_void_p) for n in ("M_diag", "M_upper", "M_lower", "BL_diag", "BL_upper",
+                                               "BG_diag", "BG_upper")]
 
 
 class Outputs(ctypes.Structure):
@@ -115,6 +127,8 @@ def load() -> ctypes.CDLL:
     L.qtx_kernel_launches.restype = ctypes.c_longlong
     L.qtx_zgemm_emu64_noalloc.argtypes = [i, i, i, i, vp, l, l, i, vp, l, l, d, d, vp, l, l, vp, l, l, i, vp]
     L.qtx_zgemm_emu64_noalloc.restype = i
+    L.qtx_w_assemble.argtypes = [ctypes.c_void_p, ctypes.POINTER(WInputs), ctypes.POINTER(WOutputs), vp]
+    L.qtx_w_assemble.restype = i
     L.qtx_fpx_bytes.argtypes = [i, l]
     L.qtx_fpx_bytes.restype = ctypes.c_size_t
     L.qtx_fpx_compress.argtypes = [i, vp, l, d, vp, vp]
@@ -132,7 +146,7 @@ def lib() -> ctypes.CDLL:
 def make_desc(n_blocks, block_size, precision="fp64", max_energies_in_flight=64,
               refine_max_iter=2, has_S=False, has_scattering=True, energy_dependent_sigma=False,
               leads=False, decim_tol=1e-13, decim_max_iter=100, outputs=None,
-              offdiag_sigma=False, storage_bits=0, sigma_stream=False) -> Desc:
+              offdiag_sigma=False, storage_bits=0, sigma_stream=False, system_input=False) -> Desc:
     if outputs is None:
         outputs = (1 << 12) - 1
     elif not isinstance(outputs, int):
@@ -145,7 +159,7 @@ def make_desc(n_blocks, block_size, precision="fp64", max_energies_in_flight=64,
                 int(refine_max_iter), int(bool(has_S)), int(bool(has_scattering)),
                 int(bool(energy_dependent_sigma)), int(bool(leads)), float(decim_tol),
                 int(decim_max_iter), int(outputs), int(bool(offdiag_sigma)), int(storage_bits),
-                int(bool(sigma_stream)))
+                int(bool(sigma_stream)), int(bool(system_input)))
 
 
 def kernel_launches() -> int:
@@ -176,6 +190,10 @@ class Plan:
         self._check(load().qtx_rgf_solve(self._h, ctypes.byref(inputs), ctypes.byref(outputs),
                                          ctypes.c_void_p(stream)))
 
+    def w_assemble(self, inputs: "WInputs", outputs: "WOutputs", stream: int = 0) -> None:
+        self._check(load().qtx_w_assemble(self._h, ctypes.byref(inputs), ctypes.byref(outputs),
+                                          ctypes.c_void_p(stream)))
+
     def status(self) -> int:
         return int(load().qtx_rgf_status(self._h))
 
@@ -202,6 +220,89 @@ class Plan:
 
 def _ptr(t):
     return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+class WSystem:
+    """Screened-Coulomb system (Table I, W row) resident on the GPU: the inputs of a
+    ``workloads.w_system`` dict uploaded once, a system_input plan, and the assembled and solved
+    blocks.  ``run()`` assembles M = I - V P^R and B^<> = V P^<> V^H (BT blocks, ``qtx_w_assemble``)
+    and solves M X M^H = B twice -- with B^< (X^R = BT blocks of M^-1, X^<) and with B^> (X^>).
+    Marshalling only."""
+
+    def __init__(self, w: dict, precision: str = "emu64", max_energies_in_flight=64, greater=True):
+        import torch
+        cd = torch.device("cuda")
+        nb, b, ne = w["n_blocks"], w["block_size"], w["n_energies"]
+        self.nb, self.b, self.ne, self.greater = nb, b, ne, greater
+        nu = max(nb - 1, 0)
+
+        def T(x):
+            return torch.as_tensor(np.ascontiguousarray(x), dtype=torch.complex128).to(cd)
+
+        def E(*shape):
+            return torch.empty(shape, dtype=torch.complex128, device=cd)
+
+        self.win, self.wout, self._keep = WInputs(), WOutputs(), {}
+        for k in ("V_diag", "V_upper", "PR_diag", "PR_upper", "PR_lower", "PL_diag", "PL_upper") + \
+                (("PG_diag", "PG_upper") if greater else ()):
+            self._keep[k] = T(w[k])
+            setattr(self.win, k, self._keep[k].data_ptr() if self._keep[k].numel() else None)
+        self.win.n_energies, self.win.n_blocks = ne, nb
+        self.res = {"M_diag": E(ne, nb, b, b), "M_upper": E(ne, nu, b, b), "M_lower": E(ne, nu, b, b),
+                    "BL_diag": E(ne, nb, b, b), "BL_upper": E(ne, nu, b, b)}
+        if greater:
+            self.res.update(BG_diag=E(ne, nb, b, b), BG_upper=E(ne, nu, b, b))
+        for k, v in self.res.items():
+            setattr(self.wout, k, v.data_ptr() if v.numel() else None)
+        outs = ["GR_diag", "GR_upper", "GR_lower", "GL_diag", "GL_upper"]
+        self.plan = Plan(make_desc(nb, b, precision, min(max_energies_in_flight, ne), 2, has_scattering=True,
+                                   energy_dependent_sigma=True, offdiag_sigma=nb > 1, system_input=True,
+                                   outputs=outs))
+        self.energies = torch.zeros(ne, dtype=torch.float64, device=cd)
+        self.res["status"] = torch.zeros(ne, dtype=torch.int32, device=cd)
+        self._solves = []
+        pairs = [("BL", [("GR_diag", "XR_diag"), ("GR_upper", "XR_upper"), ("GR_lower", "XR_lower"),
+                         ("GL_diag", "XL_diag"), ("GL_upper", "XL_upper")])]
+        if greater:
+            pairs.append(("BG", [("GL_diag", "XG_diag"), ("GL_upper", "XG_upper")]))
+        for rhs, keys in pairs:
+            inp = Inputs()
+            inp.M_diag = self.res["M_diag"].data_ptr()
+            inp.M_upper = self.res["M_upper"].data_ptr() if nu else None
+            inp.M_lower = self.res["M_lower"].data_ptr() if nu else None
+            inp.SigL_diag = self.res[rhs + "_diag"].data_ptr()
+            inp.SigL_upper = self.res[rhs + "_upper"].data_ptr() if nu else None
+            inp.energies, inp.n_energies, inp.n_blocks = self.energies.data_ptr(), ne, nb
+            o = Outputs()
+            for name, key in keys:
+                self.res[key] = E(ne, nb if "diag" in name else nu, b, b)
+                setattr(o, name, self.res[key].data_ptr() if self.res[key].numel() else None)
+            o.status_per_energy = self.res["status"].data_ptr()
+            self._solves.append((inp, o))
+
+    def run(self, stream=None):
+        st = _stream(stream)
+        self.plan.w_assemble(self.win, self.wout, st)
+        for inp, o in self._solves:
+            self.plan.solve(inp, o, st)
+
+    def results(self) -> dict:
+        import torch
+        torch.cuda.synchronize()
+        return {k: v.cpu().numpy() for k, v in self.res.items()}
+
+    def close(self):
+        self.plan.close()
+
+
+def solve_w(w: dict, precision: str = "emu64", max_energies_in_flight=64, greater=True, stream=None):
+    """One-shot ``WSystem``: upload, assemble, solve, return numpy arrays (M_*, BL_*, BG_*, XR_*,
+    XL_*, XG_*, status)."""
+    ws = WSystem(w, precision, max_energies_in_flight, greater)
+    ws.run(stream)
+    out = ws.results()
+    ws.close()
+    return out
 
 
 def has_offdiag_sigma(dev: dict) -> bool:

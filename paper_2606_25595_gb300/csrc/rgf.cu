@@ -39,7 +39,9 @@ struct Arena {
 };
 
 // U_i, V_i differ per energy when z multiplies an overlap block or Sigma^R_{i,i+1} depends on E.
-inline bool uv_per_energy(const qtx_rgf_desc& d) { return d.has_S || (d.offdiag_sigma && d.energy_dependent_sigma); }
+inline bool uv_per_energy(const qtx_rgf_desc& d) {
+  return d.has_S || d.system_input || (d.offdiag_sigma && d.energy_dependent_sigma);
+}
 
 struct Layout {
   size_t g, gl, gfx, glfx, fx_slot, sig_stage, tmp, inv_tmp, U, V, ident, ident_df, ref, f32a, f32tmp, dec, lead, obs, flags,
@@ -459,8 +461,8 @@ qtx_status solve_chunk(qtx_rgf_plan_s* P, const qtx_rgf_inputs* in, const qtx_rg
   const bool odg = d.offdiag_sigma && nb > 1;
   const long sSigU = d.energy_dependent_sigma ? (long)(nb - 1) * bb : 0;
   const long sigUE0 = d.energy_dependent_sigma ? (long)e0 * (nb - 1) * bb : 0;
-  const cx<double>* SRu = odg ? reinterpret_cast<const cx<double>*>(in->SigR_upper) + sigUE0 : nullptr;
-  const cx<double>* SRl = odg ? reinterpret_cast<const cx<double>*>(in->SigR_lower) + sigUE0 : nullptr;
+  const cx<double>* SRu = odg && !d.system_input ? reinterpret_cast<const cx<double>*>(in->SigR_upper) + sigUE0 : nullptr;
+  const cx<double>* SRl = odg && !d.system_input ? reinterpret_cast<const cx<double>*>(in->SigR_lower) + sigUE0 : nullptr;
   const cx<double>* SLu = odg ? reinterpret_cast<const cx<double>*>(in->SigL_upper) + sigUE0 : nullptr;
   // Sigma^<_{i,i+1} in the sweep's type (tmp 12): one block shared by the chunk, or one per energy
   const int nLt = d.energy_dependent_sigma ? ne : 1;
@@ -492,7 +494,16 @@ qtx_status solve_chunk(qtx_rgf_plan_s* P, const qtx_rgf_inputs* in, const qtx_rg
   const long sUV = uvE ? bb : 0;
   auto U = [&](int i) { return Ub + (size_t)i * (uvE ? P->Ec * bb : bb); };
   auto V = [&](int i) { return Vb + (size_t)i * (uvE ? P->Ec * bb : bb); };
+  // system input (M given): per-energy blocks [N_E][N_B(-1)][b][b]
+  const cx<double>* Md = d.system_input ? reinterpret_cast<const cx<double>*>(in->M_diag) + (long)e0 * nb * bb : nullptr;
+  const cx<double>* Mu = d.system_input && nb > 1 ? reinterpret_cast<const cx<double>*>(in->M_upper) + (long)e0 * (nb - 1) * bb : nullptr;
+  const cx<double>* Ml = d.system_input && nb > 1 ? reinterpret_cast<const cx<double>*>(in->M_lower) + (long)e0 * (nb - 1) * bb : nullptr;
   for (int i = 0; i + 1 < nb; ++i) {
+    if (d.system_input) {
+      QTX_CK(axpby_from64<T>(U(i), bb, Mu + (long)i * bb, (long)(nb - 1) * bb, 1.0, nullptr, 0, 0.0, b, ne, st));
+      QTX_CK(axpby_from64<T>(V(i), bb, Ml + (long)i * bb, (long)(nb - 1) * bb, 1.0, nullptr, 0, 0.0, b, ne, st));
+      continue;
+    }
     const cx<double>* sru = SRu ? SRu + (long)i * bb : nullptr;
     const cx<double>* srl = SRl ? SRl + (long)i * bb : nullptr;
     if (uvE) QTX_CK(assemble_offdiag<T>(U(i), V(i), Hu + (long)i * bb, Su ? Su + (long)i * bb : nullptr, c.E, eta, b, ne, st, sru, srl, sSigU));
@@ -526,7 +537,8 @@ qtx_status solve_chunk(qtx_rgf_plan_s* P, const qtx_rgf_inputs* in, const qtx_rg
       sLi = stL;
       sS = bb;
     }
-    QTX_CK(assemble_diag<T>(gi, Hd + (long)i * bb, Sd ? Sd + (long)i * bb : nullptr, sRi, sS, lead, bb, c.E, eta, b, ne, st));
+    if (d.system_input) QTX_CK(axpby_from64<T>(gi, bb, Md + (long)i * bb, (long)nb * bb, 1.0, nullptr, 0, 0.0, b, ne, st));
+    else QTX_CK(assemble_diag<T>(gi, Hd + (long)i * bb, Sd ? Sd + (long)i * bb : nullptr, sRi, sS, lead, bb, c.E, eta, b, ne, st));
     if (d.leads && nb == 1) {  // one slice touches both contacts
       Term<T> tg; tg.p = gi; tg.s = bb; tg.alpha = 1.0;
       QTX_CK((combine<T, T>(c.tmp(0), bb, tg, none, none, b, ne, nullptr, 0, 0, nullptr, st)));
@@ -670,7 +682,8 @@ qtx_status solve_chunk(qtx_rgf_plan_s* P, const qtx_rgf_inputs* in, const qtx_rg
     if (want(QTX_OUT_GL_UPPER, out->GL_upper) && (s = emit<T>(P, out->GL_upper, nb - 1, i, e0, GLu, b, ne, st))) return s;
     if (want(QTX_OUT_GG_DIAG, out->GG_diag) && (s = emit<T>(P, out->GG_diag, nb, i, e0, gli, b, ne, st, gi, gi))) return s;
     if (want(QTX_OUT_GG_UPPER, out->GG_upper) && (s = emit<T>(P, out->GG_upper, nb - 1, i, e0, GLu, b, ne, st, GRu, GRl))) return s;
-    QTX_CK(obs_current<T>(cur + i, ncur, Hu + (long)i * bb, Su ? Su + (long)i * bb : nullptr, GLu, bb, c.E, b, ne, st));
+    if (!d.system_input)
+      QTX_CK(obs_current<T>(cur + i, ncur, Hu + (long)i * bb, Su ? Su + (long)i * bb : nullptr, GLu, bb, c.E, b, ne, st));
     QTX_CK(obs_density<T>(den + i, nb, gli, bb, b, ne, st));
   }
   if (d.leads) {  // left contact current and transmission on slice 0
@@ -754,6 +767,11 @@ qtx_status validate(const qtx_rgf_desc* d, std::string& err) {
   if (d->offdiag_sigma && !d->has_scattering) { err = "offdiag_sigma needs has_scattering"; return QTX_ERR_INVALID_ARG; }
   if (d->storage_bits && !fpx_width_ok(d->storage_bits)) { err = "storage_bits must be 0, 56, 48, 40, 32, 24 or 16"; return QTX_ERR_INVALID_ARG; }
   if (d->sigma_stream && (!d->has_scattering || !d->energy_dependent_sigma || d->offdiag_sigma)) { err = "sigma_stream needs has_scattering and energy_dependent_sigma, without offdiag_sigma"; return QTX_ERR_INVALID_ARG; }
+  if (d->system_input) {
+    const unsigned bad = QTX_OUT_GG_DIAG | QTX_OUT_GG_UPPER | QTX_OUT_CURRENT | QTX_OUT_CONTACT | QTX_OUT_TRANSMISSION | QTX_OUT_INTEGRALS;
+    if (d->has_S || d->leads || d->sigma_stream) { err = "system_input needs has_S = 0, leads = 0, sigma_stream = 0"; return QTX_ERR_INVALID_ARG; }
+    if (d->outputs & bad) { err = "system_input produces no G^>, current, contact, transmission or integrals outputs"; return QTX_ERR_INVALID_ARG; }
+  }
   if ((d->precision == QTX_EMU64 || d->precision == QTX_BF16X3) && !tc_available()) {
     err = "tensor-core engine not available in this build";
     return QTX_ERR_UNSUPPORTED;
@@ -762,6 +780,116 @@ qtx_status validate(const qtx_rgf_desc* d, std::string& err) {
 }
 
 }  // namespace
+
+// ----------------------------------------------------------------------------- W-system assembly
+// Table I, W row: per energy the BT blocks of M = I - V P^R and B^<> = V P^<> V^H from the exact
+// block products of the BT factors.  Row i of V P is (V P)_ij = sum_k V_ik P_kj over k = i-1..i+1
+// with |k - j| <= 1 (j = i-1..i+1 for M; i-2..i+2 for B, whose blocks B_ij = sum_l (V P)_il
+// (V_jl)^H need l up to j+1).  Each block product is one batched launch over the chunk's energies,
+// V shared (batch stride 0).  Temporaries: 0-4 V blocks, 5 one P block, 6-10 row i of V P, 11 B.
+template <typename T>
+qtx_status w_assemble_chunk(qtx_rgf_plan_s* P, const qtx_w_inputs* in, const qtx_w_outputs* out, int nb,
+                            int e0, int ne, cudaStream_t st) {
+  const int b = P->b;
+  const long bb = P->bb, nu = nb - 1;
+  Ctx<T> c{P, st, ne, nullptr, nullptr, bb, b};
+  const cx<double>* Vd = reinterpret_cast<const cx<double>*>(in->V_diag);
+  const cx<double>* Vu = reinterpret_cast<const cx<double>*>(in->V_upper);
+  // block j of a per-energy array [N_E][n][b][b], first energy of the chunk
+  auto pe = [&](const void* X, long n, long j) {
+    return reinterpret_cast<const cx<double>*>(X) + ((long)e0 * n + j) * bb;
+  };
+  // V slots: 0 V_ii, 1 V_{i+1,i+1}, 2 V_{i-1,i}, 3 V_{i,i+1}, 4 V_{i+1,i+2}
+  cx<T>* Vt[5] = {c.tmp(0), c.tmp(1), c.tmp(2), c.tmp(3), c.tmp(4)};
+  cx<T>* Pt = c.tmp(5);
+  cx<T>* acc[5] = {c.tmp(6), c.tmp(7), c.tmp(8), c.tmp(9), c.tmp(10)};  // (V P)_{i,i-2} .. (V P)_{i,i+2}
+  cx<T>* Bt = c.tmp(11);
+  auto toT = [&](cx<T>* dst, const cx<double>* src, long sSrc, int batch) {
+    return axpby_from64<T>(dst, bb, src, sSrc, 1.0, nullptr, 0, 0.0, b, batch, st);
+  };
+  auto mm = [&](const cx<T>* A, long sA, int opA, const cx<T>* B, long sB, int opB, cx<T>* C, double al,
+                bool first) {
+    return gemm<T>(P, gargs<T>(b, b, b, A, b, sA, opA, B, b, sB, opB, first ? nullptr : C, b, bb, C, b, bb, al,
+                               first ? 0.0 : 1.0, ne, nullptr), st);
+  };
+  // out[e][j] = alpha X (+ I), complex128, n blocks per energy
+  auto emit64 = [&](void* dst, long n, long j, const cx<T>* X, double alpha, bool ident) -> qtx_status {
+    cx<double>* o = reinterpret_cast<cx<double>*>(dst) + ((long)e0 * n + j) * bb;
+    Term<T> t0; t0.p = X; t0.s = bb; t0.alpha = alpha;
+    Term<T> none;
+    QTX_CK((combine<T, double>(o, n * bb, t0, none, none, b, ne, nullptr, 0.0, 0.0, nullptr, st)));
+    if (ident) QTX_CK(add_identity<double>(o, n * bb, b, ne, nullptr, st));
+    return QTX_OK;
+  };
+  qtx_status s;
+  for (int i = 0; i < nb; ++i) {
+    QTX_CK(toT(Vt[0], Vd + (long)i * bb, 0, 1));
+    if (i + 1 < nb) QTX_CK(toT(Vt[1], Vd + (long)(i + 1) * bb, 0, 1));
+    if (i >= 1) QTX_CK(toT(Vt[2], Vu + (long)(i - 1) * bb, 0, 1));
+    if (i + 1 < nb) QTX_CK(toT(Vt[3], Vu + (long)i * bb, 0, 1));
+    if (i + 2 < nb) QTX_CK(toT(Vt[4], Vu + (long)(i + 1) * bb, 0, 1));
+    // row i of V P for j = i-W .. i+W.  V_ik: k = i-1 -> V_{i-1,i}^H, k = i -> V_ii, k = i+1 -> V_{i,i+1}.
+    // P_kj: diagonal, upper (j = k+1), lower (j = k-1): given, or -(P_{j,j+1})^H for anti-Hermitian P.
+    auto row = [&](const void* Pd, const void* Pu, const void* Pl, int W) -> qtx_status {
+      for (int dj = -W; dj <= W; ++dj) {
+        const int j = i + dj;
+        if (j < 0 || j >= nb) continue;
+        bool first = true;
+        for (int k = i - 1; k <= i + 1; ++k) {
+          if (k < 0 || k >= nb || k - j > 1 || j - k > 1) continue;
+          const cx<T>* Vk = k == i ? Vt[0] : (k == i + 1 ? Vt[3] : Vt[2]);
+          const int opV = k == i - 1 ? OP_C : OP_N;
+          int opP = OP_N;
+          double al = 1.0;
+          if (k == j) QTX_CK(toT(Pt, pe(Pd, nb, k), (long)nb * bb, ne));
+          else if (j == k + 1) QTX_CK(toT(Pt, pe(Pu, nu, k), nu * bb, ne));
+          else if (Pl) QTX_CK(toT(Pt, pe(Pl, nu, j), nu * bb, ne));
+          else {
+            QTX_CK(toT(Pt, pe(Pu, nu, j), nu * bb, ne));
+            opP = OP_C;
+            al = -1.0;
+          }
+          if ((s = mm(Vk, 0, opV, Pt, bb, opP, acc[dj + 2], al, first))) return s;
+          first = false;
+        }
+      }
+      return QTX_OK;
+    };
+    // M_ii = I - (V P^R)_ii, M_{i,i+1} = -(V P^R)_{i,i+1}, M_{i,i-1} = -(V P^R)_{i,i-1}
+    if ((s = row(in->PR_diag, in->PR_upper, in->PR_lower, 1))) return s;
+    if ((s = emit64(out->M_diag, nb, i, acc[2], -1.0, true))) return s;
+    if (i + 1 < nb && (s = emit64(out->M_upper, nu, i, acc[3], -1.0, false))) return s;
+    if (i >= 1 && (s = emit64(out->M_lower, nu, i - 1, acc[1], -1.0, false))) return s;
+    for (int kind = 0; kind < 2; ++kind) {
+      const void* Pd = kind ? in->PG_diag : in->PL_diag;
+      const void* Pu = kind ? in->PG_upper : in->PL_upper;
+      void* Od = kind ? out->BG_diag : out->BL_diag;
+      void* Ou = kind ? out->BG_upper : out->BL_upper;
+      if (!Pd) continue;
+      if ((s = row(Pd, Pu, nullptr, 2))) return s;
+      // B_ii = sum_l (V P)_il (V_il)^H, l = i-1..i+1:  (V_{i,i-1})^H = V_{i-1,i}, V_ii^H, V_{i,i+1}^H
+      bool first = true;
+      for (int l = i - 1; l <= i + 1; ++l) {
+        if (l < 0 || l >= nb) continue;
+        const cx<T>* Vl = l == i ? Vt[0] : (l == i + 1 ? Vt[3] : Vt[2]);
+        if ((s = mm(acc[l - i + 2], bb, OP_N, Vl, 0, l == i - 1 ? OP_N : OP_C, Bt, 1.0, first))) return s;
+        first = false;
+      }
+      if ((s = emit64(Od, nb, i, Bt, 1.0, false))) return s;
+      if (i + 1 < nb) {
+        // B_{i,i+1} = sum_l (V P)_il (V_{i+1,l})^H, l = i..i+2:  V_{i,i+1}, V_{i+1,i+1}^H, V_{i+1,i+2}^H
+        first = true;
+        for (int l = i; l <= i + 2 && l < nb; ++l) {
+          const cx<T>* Vl = l == i ? Vt[3] : (l == i + 1 ? Vt[1] : Vt[4]);
+          if ((s = mm(acc[l - i + 2], bb, OP_N, Vl, 0, l == i ? OP_N : OP_C, Bt, 1.0, first))) return s;
+          first = false;
+        }
+        if ((s = emit64(Ou, nu, i, Bt, 1.0, false))) return s;
+      }
+    }
+  }
+  return QTX_OK;
+}
 
 extern "C" {
 
@@ -816,11 +944,14 @@ qtx_status qtx_rgf_solve(qtx_rgf_plan P, const qtx_rgf_inputs* in, const qtx_rgf
   if (!P) return QTX_ERR_INVALID_ARG;
   if (!in || !out) { P->err = "inputs/outputs NULL"; return QTX_ERR_INVALID_ARG; }
   if (in->n_energies < 1 || !in->energies) { P->err = "need n_energies >= 1 and an energies array"; return QTX_ERR_INVALID_ARG; }
-  if (!in->H_diag || (P->nb > 1 && !in->H_upper)) { P->err = "H_diag / H_upper missing"; return QTX_ERR_INVALID_ARG; }
+  const int nbs = in->n_blocks ? in->n_blocks : P->d.n_blocks;
+  if (P->d.system_input) {
+    if (!in->M_diag || (nbs > 1 && (!in->M_upper || !in->M_lower))) { P->err = "system_input set but M blocks missing"; return QTX_ERR_INVALID_ARG; }
+  } else if (!in->H_diag || (nbs > 1 && !in->H_upper)) { P->err = "H_diag / H_upper missing"; return QTX_ERR_INVALID_ARG; }
   if (P->d.has_S && (!in->S_diag || (P->nb > 1 && !in->S_upper))) { P->err = "has_S set but S pointers missing"; return QTX_ERR_INVALID_ARG; }
-  if (P->d.has_scattering && (!in->SigR_diag || !in->SigL_diag)) { P->err = "has_scattering set but Sigma pointers missing"; return QTX_ERR_INVALID_ARG; }
+  if (P->d.has_scattering && (!in->SigL_diag || (!P->d.system_input && !in->SigR_diag))) { P->err = "has_scattering set but Sigma pointers missing"; return QTX_ERR_INVALID_ARG; }
   if (P->d.offdiag_sigma && (in->n_blocks ? in->n_blocks : P->d.n_blocks) > 1 &&
-      (!in->SigR_upper || !in->SigR_lower || !in->SigL_upper)) { P->err = "offdiag_sigma set but off-diagonal Sigma pointers missing"; return QTX_ERR_INVALID_ARG; }
+      (!in->SigL_upper || (!P->d.system_input && (!in->SigR_upper || !in->SigR_lower)))) { P->err = "offdiag_sigma set but off-diagonal Sigma pointers missing"; return QTX_ERR_INVALID_ARG; }
   if (P->d.leads && (!in->lead_H00_L || !in->lead_H01_L || !in->lead_H00_R || !in->lead_H01_R)) { P->err = "leads set but lead blocks missing"; return QTX_ERR_INVALID_ARG; }
   if (P->d.leads && !(in->kT > 0)) { P->err = "leads need kT > 0"; return QTX_ERR_INVALID_ARG; }
   if (in->n_blocks < 0 || in->n_blocks > P->d.n_blocks) { P->err = "inputs->n_blocks exceeds the plan's n_blocks"; return QTX_ERR_INVALID_ARG; }
@@ -841,6 +972,36 @@ qtx_status qtx_rgf_solve(qtx_rgf_plan P, const qtx_rgf_inputs* in, const qtx_rgf
   P->out_status = out->status_per_energy;
   P->out_status_n = in->n_energies;
   return s;
+}
+
+qtx_status qtx_w_assemble(qtx_rgf_plan P, const qtx_w_inputs* in, const qtx_w_outputs* out, void* stream) {
+  if (!P) return QTX_ERR_INVALID_ARG;
+  if (!in || !out) { P->err = "inputs/outputs NULL"; return QTX_ERR_INVALID_ARG; }
+  const int nb = in->n_blocks ? in->n_blocks : P->d.n_blocks;
+  if (in->n_blocks < 0 || nb > P->d.n_blocks || in->n_energies < 1) { P->err = "n_blocks / n_energies out of range"; return QTX_ERR_INVALID_ARG; }
+  if (!in->V_diag || !in->PR_diag || !in->PL_diag || !out->M_diag || !out->BL_diag) { P->err = "W assembly: diagonal blocks missing"; return QTX_ERR_INVALID_ARG; }
+  if (nb > 1 && (!in->V_upper || !in->PR_upper || !in->PR_lower || !in->PL_upper || !out->M_upper || !out->M_lower || !out->BL_upper)) {
+    P->err = "W assembly: off-diagonal blocks missing";
+    return QTX_ERR_INVALID_ARG;
+  }
+  const bool pg = in->PG_diag != nullptr;
+  if ((!pg && in->PG_upper) || (pg && ((nb > 1 && !in->PG_upper) || !out->BG_diag || (nb > 1 && !out->BG_upper)))) {
+    P->err = "W assembly: P^> (diagonal and upper) and B^> must come together";
+    return QTX_ERR_INVALID_ARG;
+  }
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  P->last = st;
+  for (int e0 = 0; e0 < in->n_energies; e0 += P->Ec) {
+    const int ne = std::min(P->Ec, in->n_energies - e0);
+    qtx_status s;
+    if (P->d.precision == QTX_FP32) s = w_assemble_chunk<float>(P, in, out, nb, e0, ne, st);
+    else if (P->d.precision == QTX_FP64) s = w_assemble_chunk<double>(P, in, out, nb, e0, ne, st);
+    else s = w_assemble_chunk<df>(P, in, out, nb, e0, ne, st);
+    if (s) return s;
+  }
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) { P->err = cudaGetErrorString(e); return QTX_ERR_CUDA; }
+  return QTX_OK;
 }
 
 qtx_status qtx_rgf_status(qtx_rgf_plan P) {
