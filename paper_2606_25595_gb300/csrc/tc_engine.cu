@@ -341,6 +341,186 @@ __global__ void __launch_bounds__(320, 1) k_tc_gemm(TcParams p) {
   }
 }
 
+// Persistent variant: one CTA per SM walks the tiles t = blockIdx.x, blockIdx.x + gridDim.x, ...
+// (column tile fastest, then row tile, then batch entry).  The stage ring and its barriers run on
+// across tiles, and TMEM changes hands through two more barriers: accf (the MMA thread's commit:
+// a tile's accumulators are complete) and acce (the epilogue's arrival: it has read them into
+// registers and the staging area).  So the producer's loads and the MMAs of tile j+1 overlap the
+// epilogue's global stores of tile j, and the prologue (TMEM allocation, barrier set-up, first
+// loads) is paid once per SM rather than once per tile.  The staging area is separate from the
+// stage ring (NST = 3 stages fit beside it for 6 digit planes).
+constexpr int OUT_BYTES = BM * OUT_LD * (int)sizeof(cx<df>);
+
+template <int S, int NST>
+__global__ void __launch_bounds__(320, 1) k_tc_gemm_persist(TcParams p, int n_tiles, int NBt, int MBt) {
+  constexpr int STAGE = S * (TILE_A + TILE_B);
+  constexpr int NACC = n_acc(S);
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  cx<df>* out = reinterpret_cast<cx<df>*>(base + NST * STAGE);  // [BM][OUT_LD] staging
+  uint64_t* full = reinterpret_cast<uint64_t*>(base + NST * STAGE + OUT_BYTES);
+  uint64_t* empty = full + NST;
+  uint64_t* accf = empty + NST;
+  uint64_t* acce = accf + 1;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(acce + 1);
+  __shared__ int s_got;
+  __shared__ int s_eB[BNC];
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int per_e = NBt * MBt;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NST; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accf, 1);
+    mbar_init(acce, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)), "r"(512) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tslot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      long g = 0;  // stage counter across tiles
+      bool ok = true;
+      for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+        const int e = t / per_e, mblk = (t / NBt) % MBt, nblk = t % NBt;
+        if (p.active && !p.active[e]) continue;
+        const long MB = p.M_pad / BM, NB = 2L * p.N_pad / BNR;
+        const long ea = p.a_batched ? e : 0, eb = p.b_batched ? e : 0;
+        for (int ks = 0; ks < p.nks; ++ks, ++g) {
+          const int s = (int)(g % NST);
+          const uint32_t ph = (uint32_t)(g / NST) & 1u;
+          if (!mbar_wait(&empty[s], ph ^ 1u, p.err)) { ok = false; break; }
+          mbar_expect_tx(&full[s], STAGE);
+          unsigned char* st = base + s * STAGE;
+          for (int d = 0; d < S; ++d) {
+            bulk_load(st + d * TILE_A, p.pa + (((ea * S + d) * MB + mblk) * p.nks + ks) * (long)TILE_A, TILE_A, &full[s]);
+            bulk_load(st + S * TILE_A + d * TILE_B, p.pb + (((eb * S + d) * NB + nblk) * p.nks + ks) * (long)TILE_B,
+                      TILE_B, &full[s]);
+          }
+        }
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      long g = 0;
+      int j = 0;  // tiles processed by this CTA
+      bool ok = true;
+      for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+        const int e = t / per_e;
+        if (p.active && !p.active[e]) continue;
+        // TMEM is free once the epilogue has read the previous tile's accumulators
+        if (!mbar_wait(acce, ((uint32_t)j & 1u) ^ 1u, p.err)) break;
+        fence_after();
+        uint32_t started = 0;
+        for (int ks = 0; ks < p.nks; ++ks, ++g) {
+          const int s = (int)(g % NST);
+          const uint32_t ph = (uint32_t)(g / NST) & 1u;
+          if (!mbar_wait(&full[s], ph, p.err)) { ok = false; break; }
+          fence_after();
+          const uint32_t sa = su32(base + s * STAGE);
+#pragma unroll
+          for (int i = 1; i <= S; ++i) {
+#pragma unroll
+            for (int jj = 1; jj <= S + 1 - i; ++jj) {
+              const int gacc = acc_of(i, jj);
+              const uint64_t ad = sdesc(sa + (i - 1) * TILE_A);
+              const uint64_t bd = sdesc(sa + S * TILE_A + (jj - 1) * TILE_B);
+              mma(tmem + gacc * ACC_COLS, ad, bd, (started >> gacc) & 1u);
+              started |= 1u << gacc;
+            }
+          }
+          mma_commit(&empty[s]);
+        }
+        if (!ok) break;
+        mma_commit(accf);
+        ++j;
+      }
+    }
+    __syncwarp();
+  } else {
+    // epilogue: warps 2..9; TMEM lane quarter = warp % 4, column half = (warp - 2) / 4
+    const int q = warp & 3, h = (warp - 2) >> 2;
+    const int r = q * 32 + lane;
+    const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16);
+    int j = 0;
+    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+      const int e = t / per_e, mblk = (t / NBt) % MBt, nblk = t % NBt;
+      if (p.active && !p.active[e]) continue;
+      const int m = mblk * BM + r;
+      const int eAm = p.eA[(long)(p.a_batched ? e : 0) * p.M_pad + m];
+      // every epilogue thread is done with the previous tile's staging area and exponents
+      __syncwarp();
+      asm volatile("bar.sync 1, 256;" ::: "memory");
+      if (threadIdx.x >= 64 && threadIdx.x < 64 + BNC)
+        s_eB[threadIdx.x - 64] = p.eB[(long)(p.b_batched ? e : 0) * p.N_pad + nblk * BNC + threadIdx.x - 64];
+      if (threadIdx.x == 64) s_got = mbar_wait(accf, (uint32_t)j & 1u, p.err) ? 1 : 0;
+      __syncwarp();
+      asm volatile("bar.sync 2, 256;" ::: "memory");
+      if (!s_got) break;
+      fence_after();
+#pragma unroll 1
+      for (int c0 = h * (BNC / 2); c0 < (h + 1) * (BNC / 2); c0 += 8) {
+        uint32_t vr[NACC][8], vi[NACC][8];
+#pragma unroll
+        for (int gq = 0; gq < NACC; ++gq) {
+          tmem_ld8(trow + gq * ACC_COLS + c0, vr[gq]);
+          tmem_ld8(trow + gq * ACC_COLS + BNC + c0, vi[gq]);
+        }
+        tmem_wait_ld();
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          int Es = eAm + s_eB[c0 + c] - p.escale;
+          Es = Es < -250 ? -250 : (Es > 250 ? 250 : Es);
+          const float f1 = __int_as_float((Es / 2 + 127) << 23), f2 = __int_as_float((Es - Es / 2 + 127) << 23);
+          const df sr = sum_acc<NACC>(vr, c), si = sum_acc<NACC>(vi, c);
+          cx<df> o;
+          o.re = mkdf(sr.hi * f1 * f2 * p.alpha, sr.lo * f1 * f2 * p.alpha);
+          o.im = mkdf(si.hi * f1 * f2 * p.alpha, si.lo * f1 * f2 * p.alpha);
+          out[r * OUT_LD + c0 + c] = o;
+        }
+      }
+      // accumulators read (tcgen05.wait::ld above): hand TMEM back to the MMA thread
+      fence_before();
+      __syncwarp();
+      asm volatile("bar.sync 1, 256;" ::: "memory");
+      if (threadIdx.x == 64) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(acce)) : "memory");
+      const cx<df>* C0e = p.C0 ? p.C0 + (long)e * p.sC0 : nullptr;
+      cx<df>* Ce = p.C + (long)e * p.sC;
+      for (int idx = threadIdx.x - 64; idx < BM * BNC; idx += 256) {
+        const int rr = idx / BNC, cc = idx % BNC;
+        const int mm = mblk * BM + rr, nn = nblk * BNC + cc;
+        if (mm < p.M && nn < p.N) {
+          cx<df> v = out[rr * OUT_LD + cc];
+          if (C0e && p.beta != 0.f) {
+            const cx<df> c0v = C0e[(long)mm * p.ldc0 + nn];
+            v.re = df_add(v.re, df_mulf(c0v.re, p.beta));
+            v.im = df_add(v.im, df_mulf(c0v.im, p.beta));
+          }
+          Ce[(long)mm * p.ldc + nn] = v;
+        }
+      }
+      ++j;
+    }
+  }
+  __syncwarp();
+  fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+  }
+}
+
 // ------------------------------------------------------------------------------ digitizer
 // Per-row exponent of the logical operand L (R x K): L(r, k) = X[r][k] (direct) or X[k][r]
 // (transposed).  e[r] = max over k of the exponent of max(|Re|, |Im|) (hi parts).  One CTA per 32
@@ -736,7 +916,8 @@ cudaError_t digitize(const cx<df>* X, long ldx, long sX, int opX, int side, int 
   return cudaGetLastError();
 }
 
-template <int S, int NST>
+// PERSIST: the persistent kernel (one CTA per SM over all tiles) instead of one CTA per tile.
+template <int S, int NST, bool PERSIST = false>
 cudaError_t launch(const TcArgs& a, void* scratch, size_t scratch_bytes, int* err_flag, cudaStream_t st,
                    cudaEvent_t* ev) {
   const Dims d = dims_of(a.M, a.N, a.K, S);
@@ -769,15 +950,34 @@ cudaError_t launch(const TcArgs& a, void* scratch, size_t scratch_bytes, int* er
   p.b_batched = bb_;
   p.active = a.active;
   p.err = err_flag;
-  const size_t smem = (size_t)NST * S * (TILE_A + TILE_B) + 1024 + 256;
-  static bool attr = false;
-  if (!attr) {
-    if ((e = cudaFuncSetAttribute(k_tc_gemm<S, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
-    attr = true;
+  if constexpr (PERSIST) {
+    const size_t smem = (size_t)NST * S * (TILE_A + TILE_B) + OUT_BYTES + 1024 + 256;
+    static bool attr = false;
+    static int sms = 0;
+    if (!attr) {
+      if ((e = cudaFuncSetAttribute(k_tc_gemm_persist<S, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
+      int dev = 0;
+      if ((e = cudaGetDevice(&dev))) return e;
+      if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))) return e;
+      attr = true;
+    }
+    const int NBt = d.N_pad / BNC, MBt = d.M_pad / BM;
+    const long tiles = (long)NBt * MBt * a.batch;
+    if (tiles > 0x7fffffffL) return cudaErrorInvalidValue;
+    const int grid = (int)(tiles < sms ? tiles : sms);
+    if (ev) cudaEventRecord(ev[0], st);
+    k_tc_gemm_persist<S, NST><<<grid, 320, smem, st>>>(p, (int)tiles, NBt, MBt);
+  } else {
+    const size_t smem = (size_t)NST * S * (TILE_A + TILE_B) + 1024 + 256;
+    static bool attr = false;
+    if (!attr) {
+      if ((e = cudaFuncSetAttribute(k_tc_gemm<S, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
+      attr = true;
+    }
+    dim3 grid(d.N_pad / BNC, d.M_pad / BM, a.batch);
+    if (ev) cudaEventRecord(ev[0], st);
+    k_tc_gemm<S, NST><<<grid, 320, smem, st>>>(p);
   }
-  dim3 grid(d.N_pad / BNC, d.M_pad / BM, a.batch);
-  if (ev) cudaEventRecord(ev[0], st);
-  k_tc_gemm<S, NST><<<grid, 320, smem, st>>>(p);
   count_launch();
   if (ev) cudaEventRecord(ev[1], st);
   return cudaGetLastError();
@@ -839,7 +1039,7 @@ cudaError_t gemm_tc(const TcArgs& a, int digits, void* scratch, size_t scratch_b
   }
   digits = effective_digits(digits, a.K);
   if (digits == 7) return tc::launch<7, 4>(a, scratch, scratch_bytes, err_flag, st, ev);
-  if (digits == 6) return tc::launch<6, 5>(a, scratch, scratch_bytes, err_flag, st, ev);
+  if (digits == 6) return tc::launch<6, 3, true>(a, scratch, scratch_bytes, err_flag, st, ev);
   if (digits == 2) return tc::launch<2, 8>(a, scratch, scratch_bytes, err_flag, st, ev);
   return cudaErrorInvalidValue;
 }
