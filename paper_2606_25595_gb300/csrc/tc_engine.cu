@@ -1038,9 +1038,9 @@ cudaError_t gemm_tc(const TcArgs& a, int digits, void* scratch, size_t scratch_b
     return cudaSuccess;
   }
   digits = effective_digits(digits, a.K);
-  if (digits == 7) return tc::launch<7, 4>(a, scratch, scratch_bytes, err_flag, st, ev);
+  if (digits == 7) return tc::launch<7, 2, true>(a, scratch, scratch_bytes, err_flag, st, ev);
   if (digits == 6) return tc::launch<6, 3, true>(a, scratch, scratch_bytes, err_flag, st, ev);
-  if (digits == 2) return tc::launch<2, 8>(a, scratch, scratch_bytes, err_flag, st, ev);
+  if (digits == 2) return tc::launch<2, 8, true>(a, scratch, scratch_bytes, err_flag, st, ev);
   return cudaErrorInvalidValue;
 }
 
