@@ -26,15 +26,18 @@
 // digit planes are stored transposed (N x K, K-major) with rows permuted so that the 48 "re" rows
 // and the 48 "im" rows of each CTA tile are contiguous.
 //
-// Kernel structure (one CTA per 128 x 48 complex output tile, 10 warps):
+// Kernel structure (persistent: one CTA per SM walking 128 x 48 complex output tiles, 10 warps):
 //   warp 0   producer: one bulk asynchronous copy (cp.async.bulk, mbarrier complete-tx) per plane
 //            tile of one K-stage (16 K-elements; the digitiser stores every tile contiguously, already
-//            in the 32-byte-swizzled K-major layout the MMA descriptors expect), 4-8 stages deep;
-//   warp 1   allocates 512 TMEM columns; one thread issues the tcgen05.mma's (2 K16 steps x pairs)
-//            and tcgen05.commit's the stage back to the producer;
+//            in the 32-byte-swizzled K-major layout the MMA descriptors expect), a ring of 2-8 stages
+//            that runs on across tiles;
+//   warp 1   allocates 512 TMEM columns once; one thread issues the tcgen05.mma's (2 K16 steps x
+//            pairs), tcgen05.commit's each stage back to the producer and each finished tile to the
+//            epilogue, and waits for the epilogue to release TMEM before the next tile;
 //   warps 2-9 epilogue (two warps per TMEM lane quarter, one per column half): tcgen05.ld of the
-//            accumulators, TwoSum recombination into df32, row/column scaling, staging through the
-//            (then idle) pipeline shared memory, and coalesced stores with the beta * C0 term.
+//            accumulators, TwoSum recombination into df32, row/column scaling into a staging area,
+//            release of TMEM, then coalesced stores with the beta * C0 term -- overlapping the next
+//            tile's mainloop.
 // Every mbarrier wait is bounded (2 s of %globaltimer); on expiry the kernel sets *err and unwinds.
 #include <cuda_bf16.h>
 
@@ -190,158 +193,7 @@ __device__ __forceinline__ df sum_acc(const uint32_t (&v)[NACC][8], int c) {
   return mkdf(h, e - (h - s));
 }
 
-template <int S, int NST>
-__global__ void __launch_bounds__(320, 1) k_tc_gemm(TcParams p) {
-  constexpr int STAGE = S * (TILE_A + TILE_B);
-  constexpr int NACC = n_acc(S);
-  extern __shared__ unsigned char smem_raw[];
-  const int e = blockIdx.z;
-  if (p.active && !p.active[e]) return;
-  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* full = reinterpret_cast<uint64_t*>(base + NST * STAGE);
-  uint64_t* empty = full + NST;
-  uint64_t* accb = empty + NST;
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(accb + 1);
-  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int nblk = blockIdx.x, mblk = blockIdx.y;
-
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < NST; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
-    }
-    mbar_init(accb, 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)), "r"(512) : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
-  fence_before();
-  __syncthreads();
-  fence_after();
-  const uint32_t tmem = *tslot;
-
-  if (warp == 0) {
-    if (lane == 0) {
-      for (int ks = 0; ks < p.nks; ++ks) {
-        const int s = ks % NST;
-        const uint32_t ph = (uint32_t)(ks / NST) & 1u;
-        if (!mbar_wait(&empty[s], ph ^ 1u, p.err)) break;
-        mbar_expect_tx(&full[s], STAGE);
-        unsigned char* st = base + s * STAGE;
-        const long MB = p.M_pad / BM, NB = 2L * p.N_pad / BNR;
-        const long ea = p.a_batched ? e : 0, eb = p.b_batched ? e : 0;
-        for (int d = 0; d < S; ++d) {
-          bulk_load(st + d * TILE_A, p.pa + (((ea * S + d) * MB + mblk) * p.nks + ks) * (long)TILE_A, TILE_A, &full[s]);
-          bulk_load(st + S * TILE_A + d * TILE_B, p.pb + (((eb * S + d) * NB + nblk) * p.nks + ks) * (long)TILE_B,
-                    TILE_B, &full[s]);
-        }
-      }
-    }
-    __syncwarp();  // reconverge before the CTA barrier (bar.sync counts whole warps)
-  } else if (warp == 1) {
-    if (lane == 0) {
-      uint32_t started = 0;  // bit g set once accumulator g has been written
-      bool ok = true;
-      for (int ks = 0; ks < p.nks && ok; ++ks) {
-        const int s = ks % NST;
-        const uint32_t ph = (uint32_t)(ks / NST) & 1u;
-        if (!mbar_wait(&full[s], ph, p.err)) { ok = false; break; }
-        fence_after();
-        const uint32_t sa = su32(base + s * STAGE);
-#pragma unroll
-        for (int i = 1; i <= S; ++i) {
-#pragma unroll
-          for (int j = 1; j <= S + 1 - i; ++j) {
-            const int g = acc_of(i, j);
-            const uint64_t ad = sdesc(sa + (i - 1) * TILE_A);
-            const uint64_t bd = sdesc(sa + S * TILE_A + (j - 1) * TILE_B);
-            mma(tmem + g * ACC_COLS, ad, bd, (started >> g) & 1u);
-            started |= 1u << g;
-          }
-        }
-        mma_commit(&empty[s]);
-      }
-      mma_commit(accb);
-    }
-    __syncwarp();
-  } else {
-    // epilogue: warps 2..9; TMEM lane quarter = warp % 4, column half = (warp - 2) / 4
-    const int q = warp & 3, h = (warp - 2) >> 2;
-    const int r = q * 32 + lane;
-    const int m = mblk * BM + r;
-    // one thread waits for the accumulators; the other epilogue threads sleep in a named barrier
-    // instead of polling shared memory while the tensor core reads its operands from it
-    // The scale exponents are fetched while the mainloop runs: this row's into a register, the
-    // tile's 48 column exponents into shared memory (global loads in the epilogue's inner loop would
-    // put an L2 round trip on its critical path).
-    __shared__ int s_got;
-    __shared__ int s_eB[BNC];
-    const int eAm = p.eA[(long)(p.a_batched ? e : 0) * p.M_pad + m];
-    if (threadIdx.x >= 64 && threadIdx.x < 64 + BNC)
-      s_eB[threadIdx.x - 64] = p.eB[(long)(p.b_batched ? e : 0) * p.N_pad + nblk * BNC + threadIdx.x - 64];
-    if (threadIdx.x == 64) s_got = mbar_wait(accb, 0, p.err) ? 1 : 0;
-    __syncwarp();
-    asm volatile("bar.sync 2, 256;" ::: "memory");
-    const bool got = s_got != 0;
-    fence_after();
-    cx<df>* out = reinterpret_cast<cx<df>*>(base);  // [BM][OUT_LD] staging (pipeline smem is idle now)
-    if (got) {
-      const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16);
-#pragma unroll 1
-      for (int c0 = h * (BNC / 2); c0 < (h + 1) * (BNC / 2); c0 += 8) {
-        uint32_t vr[NACC][8], vi[NACC][8];
-#pragma unroll
-        for (int g = 0; g < NACC; ++g) {
-          tmem_ld8(trow + g * ACC_COLS + c0, vr[g]);
-          tmem_ld8(trow + g * ACC_COLS + BNC + c0, vi[g]);
-        }
-        tmem_wait_ld();
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          // 2^Es as two factors (as scale2), shared by the four parts of the output value
-          int Es = eAm + s_eB[c0 + c] - p.escale;
-          Es = Es < -250 ? -250 : (Es > 250 ? 250 : Es);
-          const float f1 = __int_as_float((Es / 2 + 127) << 23), f2 = __int_as_float((Es - Es / 2 + 127) << 23);
-          const df sr = sum_acc<NACC>(vr, c), si = sum_acc<NACC>(vi, c);
-          cx<df> o;
-          o.re = mkdf(sr.hi * f1 * f2 * p.alpha, sr.lo * f1 * f2 * p.alpha);
-          o.im = mkdf(si.hi * f1 * f2 * p.alpha, si.lo * f1 * f2 * p.alpha);
-          out[r * OUT_LD + c0 + c] = o;
-        }
-      }
-    }
-    __syncwarp();
-    asm volatile("bar.sync 1, 256;" ::: "memory");  // the eight epilogue warps
-    if (got) {
-      const cx<df>* C0e = p.C0 ? p.C0 + (long)e * p.sC0 : nullptr;
-      cx<df>* Ce = p.C + (long)e * p.sC;
-      for (int idx = threadIdx.x - 64; idx < BM * BNC; idx += 256) {
-        const int rr = idx / BNC, cc = idx % BNC;
-        const int mm = mblk * BM + rr, nn = nblk * BNC + cc;
-        if (mm < p.M && nn < p.N) {
-          cx<df> v = out[rr * OUT_LD + cc];
-          if (C0e && p.beta != 0.f) {
-            const cx<df> c0v = C0e[(long)mm * p.ldc0 + nn];
-            v.re = df_add(v.re, df_mulf(c0v.re, p.beta));
-            v.im = df_add(v.im, df_mulf(c0v.im, p.beta));
-          }
-          Ce[(long)mm * p.ldc + nn] = v;
-        }
-      }
-    }
-  }
-  __syncwarp();
-  fence_before();
-  __syncthreads();
-  if (warp == 1) {
-    fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
-  }
-}
-
-// Persistent variant: one CTA per SM walks the tiles t = blockIdx.x, blockIdx.x + gridDim.x, ...
+// The product kernel is persistent: one CTA per SM walks the tiles t = blockIdx.x, blockIdx.x + gridDim.x, ...
 // (column tile fastest, then row tile, then batch entry).  The stage ring and its barriers run on
 // across tiles, and TMEM changes hands through two more barriers: accf (the MMA thread's commit:
 // a tile's accumulators are complete) and acce (the epilogue's arrival: it has read them into
@@ -352,7 +204,7 @@ __global__ void __launch_bounds__(320, 1) k_tc_gemm(TcParams p) {
 constexpr int OUT_BYTES = BM * OUT_LD * (int)sizeof(cx<df>);
 
 template <int S, int NST>
-__global__ void __launch_bounds__(320, 1) k_tc_gemm_persist(TcParams p, int n_tiles, int NBt, int MBt) {
+__global__ void __launch_bounds__(320, 1) k_tc_gemm(TcParams p, int n_tiles, int NBt, int MBt) {
   constexpr int STAGE = S * (TILE_A + TILE_B);
   constexpr int NACC = n_acc(S);
   extern __shared__ unsigned char smem_raw[];
@@ -916,8 +768,7 @@ cudaError_t digitize(const cx<df>* X, long ldx, long sX, int opX, int side, int 
   return cudaGetLastError();
 }
 
-// PERSIST: the persistent kernel (one CTA per SM over all tiles) instead of one CTA per tile.
-template <int S, int NST, bool PERSIST = false>
+template <int S, int NST>
 cudaError_t launch(const TcArgs& a, void* scratch, size_t scratch_bytes, int* err_flag, cudaStream_t st,
                    cudaEvent_t* ev) {
   const Dims d = dims_of(a.M, a.N, a.K, S);
@@ -950,34 +801,22 @@ cudaError_t launch(const TcArgs& a, void* scratch, size_t scratch_bytes, int* er
   p.b_batched = bb_;
   p.active = a.active;
   p.err = err_flag;
-  if constexpr (PERSIST) {
-    const size_t smem = (size_t)NST * S * (TILE_A + TILE_B) + OUT_BYTES + 1024 + 256;
-    static bool attr = false;
-    static int sms = 0;
-    if (!attr) {
-      if ((e = cudaFuncSetAttribute(k_tc_gemm_persist<S, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
-      int dev = 0;
-      if ((e = cudaGetDevice(&dev))) return e;
-      if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))) return e;
-      attr = true;
-    }
-    const int NBt = d.N_pad / BNC, MBt = d.M_pad / BM;
-    const long tiles = (long)NBt * MBt * a.batch;
-    if (tiles > 0x7fffffffL) return cudaErrorInvalidValue;
-    const int grid = (int)(tiles < sms ? tiles : sms);
-    if (ev) cudaEventRecord(ev[0], st);
-    k_tc_gemm_persist<S, NST><<<grid, 320, smem, st>>>(p, (int)tiles, NBt, MBt);
-  } else {
-    const size_t smem = (size_t)NST * S * (TILE_A + TILE_B) + 1024 + 256;
-    static bool attr = false;
-    if (!attr) {
-      if ((e = cudaFuncSetAttribute(k_tc_gemm<S, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
-      attr = true;
-    }
-    dim3 grid(d.N_pad / BNC, d.M_pad / BM, a.batch);
-    if (ev) cudaEventRecord(ev[0], st);
-    k_tc_gemm<S, NST><<<grid, 320, smem, st>>>(p);
+  const size_t smem = (size_t)NST * S * (TILE_A + TILE_B) + OUT_BYTES + 1024 + 256;
+  static bool attr = false;
+  static int sms = 0;
+  if (!attr) {
+    if ((e = cudaFuncSetAttribute(k_tc_gemm<S, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev))) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))) return e;
+    attr = true;
   }
+  const int NBt = d.N_pad / BNC, MBt = d.M_pad / BM;
+  const long tiles = (long)NBt * MBt * a.batch;
+  if (tiles > 0x7fffffffL) return cudaErrorInvalidValue;
+  const int grid = (int)(tiles < sms ? tiles : sms);  // one CTA per SM (the kernel holds 230 KB of smem)
+  if (ev) cudaEventRecord(ev[0], st);
+  k_tc_gemm<S, NST><<<grid, 320, smem, st>>>(p, (int)tiles, NBt, MBt);
   count_launch();
   if (ev) cudaEventRecord(ev[1], st);
   return cudaGetLastError();
@@ -1038,9 +877,9 @@ cudaError_t gemm_tc(const TcArgs& a, int digits, void* scratch, size_t scratch_b
     return cudaSuccess;
   }
   digits = effective_digits(digits, a.K);
-  if (digits == 7) return tc::launch<7, 2, true>(a, scratch, scratch_bytes, err_flag, st, ev);
-  if (digits == 6) return tc::launch<6, 3, true>(a, scratch, scratch_bytes, err_flag, st, ev);
-  if (digits == 2) return tc::launch<2, 8, true>(a, scratch, scratch_bytes, err_flag, st, ev);
+  if (digits == 7) return tc::launch<7, 2>(a, scratch, scratch_bytes, err_flag, st, ev);
+  if (digits == 6) return tc::launch<6, 3>(a, scratch, scratch_bytes, err_flag, st, ev);
+  if (digits == 2) return tc::launch<2, 8>(a, scratch, scratch_bytes, err_flag, st, ev);
   return cudaErrorInvalidValue;
 }
 
