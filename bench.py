@@ -63,31 +63,18 @@ def parse():
 
 
 def dist_init():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    if ws <= 1:
-        return 0, 1, 0
-    import torch
-    import torch.distributed as dist
-    lr = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(lr)
-    dist.init_process_group("nccl")
-    return dist.get_rank(), ws, lr
+    from paper_2606_25595_gb300 import dist as D
+    return D.init()
 
 
 def barrier(ws):
-    if ws > 1:
-        import torch.distributed as dist
-        dist.barrier()
+    from paper_2606_25595_gb300 import dist as D
+    D.barrier(ws)
 
 
 def max_over_ranks(x, ws):
-    if ws <= 1:
-        return x
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    from paper_2606_25595_gb300 import dist as D
+    return D.max_over_ranks(x, ws)
 
 
 def captured_traffic(energies_per_launch):
