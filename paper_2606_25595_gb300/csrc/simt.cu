@@ -11,16 +11,22 @@ namespace qtx {
 std::atomic<long long> g_launches{0};
 
 // ============================================================================ batched GEMM
-// Tile BM x BN of C per CTA, K staged through shared memory BK at a time; each thread owns a
-// TM x TN sub-grid interleaved with stride (BM/TM, BN/TN) so smem reads of a warp are contiguous.
+// Tile BM x BN of C per CTA, K staged through shared memory BK at a time (two buffers: the next
+// stage's global loads are issued into registers before the current stage's FMAs and stored to
+// the other buffer after them, one barrier per stage); each thread owns a TM x TN sub-grid
+// interleaved with stride (BM/TM, BN/TN) so smem reads of a warp are contiguous.
 template <typename T, int BM, int BN, int BK, int TM, int TN>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN))
     k_gemm(GemmArgs<T> g) {
+  // FP32: two stage buffers (load latency hidden behind the FMAs); FP64 is bound by the FP64 pipe,
+  // where one buffer with twice the K per stage (half the barriers) is faster
+  constexpr int NBUF = sizeof(T) == 4 ? 2 : 1;
   constexpr int TX = BN / TN, TY = BM / TM, NT = TX * TY;
+  constexpr int LA = (BM * BK + NT - 1) / NT, LB = (BK * BN + NT - 1) / NT;  // loads per thread
   const int e = blockIdx.z;
   if (g.active && !g.active[e]) return;
-  __shared__ cx<T> As[BK][BM + 1];
-  __shared__ cx<T> Bs[BK][BN + 1];
+  __shared__ cx<T> As[NBUF][BK][BM + 1];
+  __shared__ cx<T> Bs[NBUF][BK][BN + 1];
   const int tid = threadIdx.x;
   const int tx = tid % TX, ty = tid / TX;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
@@ -32,39 +38,84 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
 #pragma unroll
     for (int j = 0; j < TN; ++j) acc[i][j] = mk<T>(0, 0);
 
-  for (int k0 = 0; k0 < g.K; k0 += BK) {
-    for (int idx = tid; idx < BM * BK; idx += NT) {
+  cx<T> ra[LA], rb[LB];
+  auto load = [&](int k0) {
+#pragma unroll
+    for (int l = 0; l < LA; ++l) {
+      const int idx = tid + l * NT;
       int mm, kk;
       if (g.opA == OP_N) { kk = idx % BK; mm = idx / BK; }
       else { mm = idx % BM; kk = idx / BM; }
       const int m = m0 + mm, k = k0 + kk;
       cx<T> v = mk<T>(0, 0);
-      if (m < g.M && k < g.K) v = (g.opA == OP_N) ? A[(long)m * g.lda + k] : conj(A[(long)k * g.lda + m]);
-      As[kk][mm] = v;
+      if (idx < BM * BK && m < g.M && k < g.K) v = (g.opA == OP_N) ? A[(long)m * g.lda + k] : conj(A[(long)k * g.lda + m]);
+      ra[l] = v;
     }
-    for (int idx = tid; idx < BK * BN; idx += NT) {
+#pragma unroll
+    for (int l = 0; l < LB; ++l) {
+      const int idx = tid + l * NT;
       int kk, nn;
       if (g.opB == OP_N) { nn = idx % BN; kk = idx / BN; }
       else { kk = idx % BK; nn = idx / BK; }
       const int k = k0 + kk, n = n0 + nn;
       cx<T> v = mk<T>(0, 0);
-      if (k < g.K && n < g.N) v = (g.opB == OP_N) ? B[(long)k * g.ldb + n] : conj(B[(long)n * g.ldb + k]);
-      Bs[kk][nn] = v;
+      if (idx < BK * BN && k < g.K && n < g.N) v = (g.opB == OP_N) ? B[(long)k * g.ldb + n] : conj(B[(long)n * g.ldb + k]);
+      rb[l] = v;
     }
-    __syncthreads();
+  };
+  auto store = [&](int buf) {
+#pragma unroll
+    for (int l = 0; l < LA; ++l) {
+      const int idx = tid + l * NT;
+      if (idx < BM * BK) {
+        if (g.opA == OP_N) As[buf][idx % BK][idx / BK] = ra[l];
+        else As[buf][idx / BM][idx % BM] = ra[l];
+      }
+    }
+#pragma unroll
+    for (int l = 0; l < LB; ++l) {
+      const int idx = tid + l * NT;
+      if (idx < BK * BN) {
+        if (g.opB == OP_N) Bs[buf][idx / BN][idx % BN] = rb[l];
+        else Bs[buf][idx % BK][idx / BK] = rb[l];
+      }
+    }
+  };
+  auto fma_stage = [&](int buf) {
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
       cx<T> a[TM], bb[TN];
 #pragma unroll
-      for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + i * TY];
+      for (int i = 0; i < TM; ++i) a[i] = As[buf][kk][ty + i * TY];
 #pragma unroll
-      for (int j = 0; j < TN; ++j) bb[j] = Bs[kk][tx + j * TX];
+      for (int j = 0; j < TN; ++j) bb[j] = Bs[buf][kk][tx + j * TX];
 #pragma unroll
       for (int i = 0; i < TM; ++i)
 #pragma unroll
         for (int j = 0; j < TN; ++j) cfma(acc[i][j], a[i], bb[j]);
     }
+  };
+  if constexpr (NBUF == 2) {
+    load(0);
+    store(0);
     __syncthreads();
+    int buf = 0;
+    for (int k0 = 0; k0 < g.K; k0 += BK) {
+      const bool more = k0 + BK < g.K;
+      if (more) load(k0 + BK);
+      fma_stage(buf);
+      if (more) store(buf ^ 1);
+      __syncthreads();
+      buf ^= 1;
+    }
+  } else {
+    for (int k0 = 0; k0 < g.K; k0 += BK) {
+      load(k0);
+      store(0);
+      __syncthreads();
+      fma_stage(0);
+      __syncthreads();
+    }
   }
   cx<T>* C = g.C + (long)e * g.sC;
   const cx<T>* C0 = g.C0 ? g.C0 + (long)e * g.sC0 : nullptr;
@@ -95,7 +146,9 @@ template <typename T>
 cudaError_t gemm_simt(const GemmArgs<T>& g, cudaStream_t st) {
   if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return cudaSuccess;
   if (g.M <= 32 && g.N <= 32) return launch_gemm<T, 32, 32, 16, 2, 2>(g, st);
-  if (sizeof(T) == 4 && g.M >= 128 && g.N >= 128) return launch_gemm<T, 128, 128, 8, 8, 8>(g, st);
+  if constexpr (sizeof(T) == 4) {
+    if (g.M >= 128 && g.N >= 128) return launch_gemm<T, 128, 128, 8, 8, 8>(g, st);
+  }
   return launch_gemm<T, 64, 64, 16, 4, 4>(g, st);
 }
 template cudaError_t gemm_simt<double>(const GemmArgs<double>&, cudaStream_t);
