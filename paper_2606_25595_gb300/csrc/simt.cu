@@ -2,6 +2,7 @@
 // Gauss-Jordan elimination with partial pivoting, elementwise block combinations, assembly of
 // the block rows of M, and the FP64 observable reductions of Sec. II-B.
 #include <cmath>
+#include <type_traits>
 
 #include "df32.cuh"
 #include "kernels.cuh"
@@ -344,8 +345,8 @@ struct AccSel<float, double> {
   using type = double;
 };
 template <>
-struct AccSel<df, double> {
-  using type = double;
+struct AccSel<df, double> {  // df32 sums, converted to FP64 once (no FP64 arithmetic)
+  using type = df;
 };
 template <>
 struct AccSel<df, df> {
@@ -391,6 +392,8 @@ template <>
 __device__ __forceinline__ df acc_out<df>(df a) { return a; }
 template <>
 __device__ __forceinline__ float acc_out<float>(df a) { return a.hi + a.lo; }
+template <>
+__device__ __forceinline__ double acc_out<double>(df a) { return to_d(a); }
 
 // 32 x 32 output tiles; conjugate-transposed terms are staged through shared memory so that both
 // the read and the write stay coalesced.
@@ -491,6 +494,29 @@ __global__ void k_assemble_diag(cx<T>* out, const cx<double>* H, const cx<double
   const double Er = E[e];
   for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < bb; idx += (long)gridDim.x * blockDim.x) {
     const int r = (int)(idx / b), c = (int)(idx % b);
+    if constexpr (std::is_same<T, df>::value) {
+      if (!S) {  // df32 arithmetic on the exactly split inputs: no FP64 operations
+        df vr = r == c ? from_d<df>(Er) : mkdf(0.f, 0.f), vi = r == c ? from_d<df>(eta) : mkdf(0.f, 0.f);
+        const cx<double> h = H[idx];
+        vr = df_sub(vr, from_d<df>(h.re));
+        vi = df_sub(vi, from_d<df>(h.im));
+        if (SigR) {
+          const cx<double> x = SigR[(long)e * sSig + idx];
+          vr = df_sub(vr, from_d<df>(x.re));
+          vi = df_sub(vi, from_d<df>(x.im));
+        }
+        if (lead) {
+          const cx<double> x = lead[(long)e * sLead + idx];
+          vr = df_sub(vr, from_d<df>(x.re));
+          vi = df_sub(vi, from_d<df>(x.im));
+        }
+        cx<df> o;
+        o.re = vr;
+        o.im = vi;
+        out[(long)e * bb + idx] = o;
+        continue;
+      }
+    }
     cx<double> s = S ? S[idx] : mk<double>(r == c ? 1.0 : 0.0, 0.0);
     cx<double> v = mk<double>(Er * s.re - eta * s.im, Er * s.im + eta * s.re) - H[idx];
     if (SigR) v = v - SigR[(long)e * sSig + idx];
@@ -518,9 +544,27 @@ __global__ void k_axpby_from64(cx<T>* out, long sOut, const cx<double>* X, long 
   const int e = blockIdx.y;
   const long bb = (long)b * b;
   for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < bb; idx += (long)gridDim.x * blockDim.x) {
-    cx<double> v = c1 * X[(long)e * sX + idx];
-    if (Y) v = v + c2 * Y[(long)e * sY + idx];
-    out[(long)e * sOut + idx] = cvt<T>(v);
+    if constexpr (std::is_same<T, df>::value) {  // df32 arithmetic: no FP64 operations
+      auto scaled = [](double c, double x) {
+        const df v = from_d<df>(x);
+        return c == 1.0 ? v : (c == -1.0 ? df_neg(v) : df_mul(v, from_d<df>(c)));
+      };
+      const cx<double> x = X[(long)e * sX + idx];
+      df vr = scaled(c1, x.re), vi = scaled(c1, x.im);
+      if (Y) {
+        const cx<double> y = Y[(long)e * sY + idx];
+        vr = df_add(vr, scaled(c2, y.re));
+        vi = df_add(vi, scaled(c2, y.im));
+      }
+      cx<df> o;
+      o.re = vr;
+      o.im = vi;
+      out[(long)e * sOut + idx] = o;
+    } else {
+      cx<double> v = c1 * X[(long)e * sX + idx];
+      if (Y) v = v + c2 * Y[(long)e * sY + idx];
+      out[(long)e * sOut + idx] = cvt<T>(v);
+    }
   }
 }
 template <typename T>
