@@ -186,6 +186,15 @@ struct GemmArgs {
   const int* active;
 };
 
+// A digitised operand kept across products (digit planes and scale exponents in caller-owned
+// memory of gemm_tc_operand_bytes): mode 1 digitises the operand into it, mode 2 uses the planes
+// already there (the operand, its op and shape unchanged since the mode-1 product).
+struct TcOperand {
+  unsigned char* planes = nullptr;
+  int* expo = nullptr;
+  int mode = 0;
+};
+
 // Arguments of the tensor-core engine (complex df32 operands and result).
 struct TcArgs {
   int M, N, K;
@@ -196,6 +205,8 @@ struct TcArgs {
   float alpha, beta;
   int batch;
   const int* active;
+  TcOperand* opndA = nullptr;  // optional kept / reused digit planes of op(A), op(B)
+  TcOperand* opndB = nullptr;
 };
 
 }  // namespace qtx

@@ -109,6 +109,10 @@ cudaError_t gemm_tc(const TcArgs& a, int digits, void* scratch, size_t scratch_b
 // digit products (pairs i + j <= digits + 1) the engine issues per real product
 inline int tc_pairs(int digits) { return digits * (digits + 1) / 2; }
 size_t gemm_tc_scratch_bytes(int M, int N, int K, int batch, int digits);
+// Bytes of a TcOperand for op(A) (side 0, R = M rows) or op(B) (side 1, R = N columns) of K; 0 when
+// the product would be split along K (operands cannot be kept then).  tc_operand_at carves one.
+size_t gemm_tc_operand_bytes(int side, int R, int K, int batch, int digits);
+TcOperand tc_operand_at(void* base, int side, int R, int K, int batch, int digits);
 bool tc_available();
 
 // ---- FPX storage codec (fpx.cu): n_complex T-typed complex values <-> their FPX codes

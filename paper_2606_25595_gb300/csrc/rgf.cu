@@ -44,7 +44,7 @@ inline bool uv_per_energy(const qtx_rgf_desc& d) {
 }
 
 struct Layout {
-  size_t g, gl, gfx, glfx, fx_slot, sig_stage, tmp, inv_tmp, U, V, ident, ident_df, ref, f32a, f32tmp, dec, lead, obs, flags,
+  size_t g, gl, gfx, glfx, fx_slot, sig_stage, opnd[3], opnd_bytes[3], tmp, inv_tmp, U, V, ident, ident_df, ref, f32a, f32tmp, dec, lead, obs, flags,
       tc_scratch, total;
   int n_tmp, n_dec;
   size_t tc_bytes;
@@ -127,6 +127,12 @@ Layout make_layout(const qtx_rgf_desc& d) {
   L.tc_bytes = 0;
   if (mixed) L.tc_bytes = gemm_tc_scratch_bytes((int)b, (int)b, (int)b, (int)Ec, d.precision == QTX_EMU64 ? 6 : 2);
   L.tc_scratch = a.take(L.tc_bytes);
+  // kept digitised operands (emulated modes): two left operands and one right operand, b x b, E_c
+  // energies (none when the products are split along K)
+  for (int k = 0; k < 3; ++k) {
+    L.opnd_bytes[k] = mixed ? gemm_tc_operand_bytes(k < 2 ? 0 : 1, (int)b, (int)b, (int)Ec, d.precision == QTX_EMU64 ? 6 : 2) : 0;
+    L.opnd[k] = a.take(L.opnd_bytes[k]);
+  }
   L.total = a.off;
   return L;
 }
@@ -179,8 +185,20 @@ GemmArgs<T> gargs(int M, int N, int K, const cx<T>* A, long lda, long sA, int op
 }
 
 // GEMM dispatch by the plan's precision (FP32 and FP64: SIMT; EMU64 / BF16X3: tensor-core engine).
+// Which kept digitised operands (tensor-core modes) a product uses: slot 0, 1 (left operands) or
+// 2 (right operand), mode KEEP (digitise into the slot) or REUSE (take the slot's planes: the operand,
+// its op and its shape are unchanged since the KEEP product).  Ignored by the SIMT modes.
+enum { DG_NONE = 0, DG_KEEP = 1, DG_REUSE = 2 };
+struct DigitHint {
+  int a_slot = -1, a_mode = DG_NONE, b_slot = -1, b_mode = DG_NONE;
+};
+inline DigitHint keepA(int slot) { DigitHint h; h.a_slot = slot; h.a_mode = DG_KEEP; return h; }
+inline DigitHint reuseA(int slot) { DigitHint h; h.a_slot = slot; h.a_mode = DG_REUSE; return h; }
+inline DigitHint keepB(int slot) { DigitHint h; h.b_slot = slot; h.b_mode = DG_KEEP; return h; }
+
 template <typename T>
-qtx_status gemm(qtx_rgf_plan_s* P, const GemmArgs<T>& g, cudaStream_t st, bool force_simt = false);
+qtx_status gemm(qtx_rgf_plan_s* P, const GemmArgs<T>& g, cudaStream_t st, bool force_simt = false,
+                DigitHint hint = DigitHint{});
 
 // The profiled product kernel is the plan's own: the SIMT GEMM in the FP64 / FP32 modes, the
 // tensor-core GEMM in the emulated modes (whose FP32 starting-guess inverse also calls SIMT GEMMs,
@@ -200,17 +218,30 @@ qtx_status gemm_simt_prof(qtx_rgf_plan_s* P, const GemmArgs<T>& g, cudaStream_t 
   return QTX_OK;
 }
 template <>
-qtx_status gemm<float>(qtx_rgf_plan_s* P, const GemmArgs<float>& g, cudaStream_t st, bool) {
+qtx_status gemm<float>(qtx_rgf_plan_s* P, const GemmArgs<float>& g, cudaStream_t st, bool, DigitHint) {
   return gemm_simt_prof<float>(P, g, st);
 }
 template <>
-qtx_status gemm<double>(qtx_rgf_plan_s* P, const GemmArgs<double>& g, cudaStream_t st, bool) {
+qtx_status gemm<double>(qtx_rgf_plan_s* P, const GemmArgs<double>& g, cudaStream_t st, bool, DigitHint) {
   return gemm_simt_prof<double>(P, g, st);
 }
 inline int tc_digits(const qtx_rgf_desc& d) { return d.precision == QTX_EMU64 ? 6 : 2; }
 template <>
-qtx_status gemm<df>(qtx_rgf_plan_s* P, const GemmArgs<df>& g, cudaStream_t st, bool) {
+qtx_status gemm<df>(qtx_rgf_plan_s* P, const GemmArgs<df>& g, cudaStream_t st, bool, DigitHint hint) {
   TcArgs a;
+  // kept operands: only for the plan's b x b x b products, when slots exist
+  TcOperand oa, ob;
+  const bool square = g.M == P->b && g.N == P->b && g.K == P->b && g.batch <= P->Ec;
+  if (square && hint.a_mode != DG_NONE && P->L.opnd_bytes[hint.a_slot]) {
+    oa = tc_operand_at(P->ws + P->L.opnd[hint.a_slot], 0, P->b, P->b, P->Ec, tc_digits(P->d));
+    oa.mode = hint.a_mode;
+    a.opndA = &oa;
+  }
+  if (square && hint.b_mode != DG_NONE && P->L.opnd_bytes[hint.b_slot]) {
+    ob = tc_operand_at(P->ws + P->L.opnd[hint.b_slot], 1, P->b, P->b, P->Ec, tc_digits(P->d));
+    ob.mode = hint.b_mode;
+    a.opndB = &ob;
+  }
   a.M = g.M; a.N = g.N; a.K = g.K;
   a.A = g.A; a.lda = g.lda; a.sA = g.sA; a.opA = g.opA;
   a.B = g.B; a.ldb = g.ldb; a.sB = g.sB; a.opB = g.opB;
@@ -339,7 +370,9 @@ qtx_status block_inverse<df>(qtx_rgf_plan_s* P, cx<df>* A, int n, int batch, con
   Term<float> none32;
   QTX_CK((combine<float, df>(A, nn, tX, none32, none32, n, batch, nullptr, 0.0, 0.0, active, st)));
   for (int it = 0; it < P->d.refine_max_iter; ++it) {
-    if ((s = gemm<df>(P, gargs<df>(n, n, n, Acopy, n, nn, OP_N, A, n, nn, OP_N, I, n, 0, R, n, nn, -1.0, 1.0, batch, active), st))) return s;
+    // Acopy's digit planes serve every sweep
+    if ((s = gemm<df>(P, gargs<df>(n, n, n, Acopy, n, nn, OP_N, A, n, nn, OP_N, I, n, 0, R, n, nn, -1.0, 1.0, batch, active), st,
+                      false, it == 0 ? keepA(0) : reuseA(0)))) return s;
     if ((s = gemm<df>(P, gargs<df>(n, n, n, A, n, nn, OP_N, R, n, nn, OP_N, A, n, nn, Xn, n, nn, 1.0, 1.0, batch, active), st))) return s;
     Term<df> tXn; tXn.p = Xn; tXn.s = nn; tXn.alpha = 1.0;
     QTX_CK((combine<df, df>(A, nn, tXn, none, none, n, batch, nullptr, 0.0, 0.0, active, st)));
@@ -642,9 +675,14 @@ qtx_status solve_chunk(qtx_rgf_plan_s* P, const qtx_rgf_inputs* in, const qtx_rg
       QTX_CK(fpx_load<T>(d.storage_bits, c.gfx(i), (long)ne * bb, gi, st));
       QTX_CK(fpx_load<T>(d.storage_bits, c.glfx(i), (long)ne * bb, gli, st));
     }
-    auto MM = [&](const cx<T>* A, long sA_, int opA, const cx<T>* B, long sB_, int opB, const cx<T>* C0, cx<T>* C, double al, double be) {
-      return gemm<T>(P, gargs<T>(b, b, b, A, b, sA_, opA, B, b, sB_, opB, C0, b, bb, C, b, bb, al, be, ne, nullptr), st);
+    auto MM = [&](const cx<T>* A, long sA_, int opA, const cx<T>* B, long sB_, int opB, const cx<T>* C0, cx<T>* C, double al, double be,
+                  DigitHint h = DigitHint{}) {
+      return gemm<T>(P, gargs<T>(b, b, b, A, b, sA_, opA, B, b, sB_, opB, C0, b, bb, C, b, bb, al, be, ne, nullptr), st, false, h);
     };
+    // kept digit planes (tensor-core modes): slot 0 = P (left operand of three products), slot 1 =
+    // G_{i+1,i+1} (left operand of two), slot 2 = Q (right operand of two)
+    DigitHint x2;
+    x2.a_slot = 1; x2.a_mode = DG_REUSE; x2.b_slot = 2; x2.b_mode = DG_REUSE;
     if ((s = MM(gi, bb, OP_N, U(i), sUV, OP_N, nullptr, Pm, 1.0, 0.0))) return s;
     if ((s = MM(V(i), sUV, OP_N, gi, bb, OP_N, nullptr, Z, 1.0, 0.0))) return s;
     cx<T>* Rl = odg ? c.tmp(13) : nullptr;  // block-tridiagonal Sigma^<: g_i Sigma^<_{i,i+1} (g_i still left-connected)
@@ -653,19 +691,19 @@ qtx_status solve_chunk(qtx_rgf_plan_s* P, const qtx_rgf_inputs* in, const qtx_rg
       if (!Lt) return QTX_ERR_CUDA;
       if ((s = MM(gi, bb, OP_N, Lt, sLt, OP_N, nullptr, Rl, 1.0, 0.0))) return s;
     }
-    if ((s = MM(GRn, bb, OP_N, Z, bb, OP_N, nullptr, GRl, -1.0, 0.0))) return s;
-    if ((s = MM(Pm, bb, OP_N, GRn, bb, OP_N, nullptr, GRu, -1.0, 0.0))) return s;
-    if ((s = MM(Pm, bb, OP_N, GRl, bb, OP_N, gi, gi, -1.0, 1.0))) return s;   // g_i <- G_ii
+    if ((s = MM(GRn, bb, OP_N, Z, bb, OP_N, nullptr, GRl, -1.0, 0.0, keepA(1)))) return s;
+    if ((s = MM(Pm, bb, OP_N, GRn, bb, OP_N, nullptr, GRu, -1.0, 0.0, keepA(0)))) return s;
+    if ((s = MM(Pm, bb, OP_N, GRl, bb, OP_N, gi, gi, -1.0, 1.0, reuseA(0)))) return s;   // g_i <- G_ii
     if ((s = MM(V(i), sUV, OP_N, gli, bb, OP_N, nullptr, Q, 1.0, 0.0))) return s;
     if (odg) {  // Q = V_i g^<_i + (g_i Sigma^<_{i,i+1})^H
       Term<T> t0; t0.p = Q; t0.s = bb; t0.alpha = 1.0;
       Term<T> t1; t1.p = Rl; t1.s = bb; t1.alpha = 1.0; t1.op = OP_C;
       QTX_CK((combine<T, T>(Q, bb, t0, t1, none, b, ne, nullptr, 0, 0, nullptr, st)));
     }
-    if ((s = MM(GRu, bb, OP_N, Q, bb, OP_N, nullptr, K, -1.0, 0.0))) return s;
-    if ((s = MM(Pm, bb, OP_N, GLn, bb, OP_N, nullptr, PGL, 1.0, 0.0))) return s;
+    if ((s = MM(GRu, bb, OP_N, Q, bb, OP_N, nullptr, K, -1.0, 0.0, keepB(2)))) return s;
+    if ((s = MM(Pm, bb, OP_N, GLn, bb, OP_N, nullptr, PGL, 1.0, 0.0, reuseA(0)))) return s;
     if ((s = MM(PGL, bb, OP_N, Pm, bb, OP_C, gli, gli, 1.0, 1.0))) return s;   // g^<_i + PGL P^H
-    if ((s = MM(GRn, bb, OP_N, Q, bb, OP_N, nullptr, X2, 1.0, 0.0))) return s;
+    if ((s = MM(GRn, bb, OP_N, Q, bb, OP_N, nullptr, X2, 1.0, 0.0, x2))) return s;
     {
       Term<T> t0; t0.p = gli; t0.s = bb; t0.alpha = 1.0;
       Term<T> t1; t1.p = K; t1.s = bb; t1.alpha = 1.0;

@@ -776,13 +776,21 @@ cudaError_t launch(const TcArgs& a, void* scratch, size_t scratch_bytes, int* er
   if (s.bytes > scratch_bytes) return cudaErrorInvalidValue;
   cudaError_t e;
   const int ab = a.sA != 0, bb_ = a.sB != 0;
-  if ((e = digitize<S>(a.A, a.lda, a.sA, a.opA, 0, a.M, a.K, d, s.ea, s.pa, ab ? a.batch : 1, ab ? a.active : nullptr, st))) return e;
-  if ((e = digitize<S>(a.B, a.ldb, a.sB, a.opB, 1, a.N, a.K, d, s.eb, s.pb, bb_ ? a.batch : 1, bb_ ? a.active : nullptr, st))) return e;
+  // digit planes and exponents of each operand: in the scratch, or in a kept operand (digitised
+  // there now, or reused as they are)
+  unsigned char* pa = a.opndA ? a.opndA->planes : s.pa;
+  unsigned char* pb = a.opndB ? a.opndB->planes : s.pb;
+  int* ea = a.opndA ? a.opndA->expo : s.ea;
+  int* eb = a.opndB ? a.opndB->expo : s.eb;
+  if (!(a.opndA && a.opndA->mode == 2))
+    if ((e = digitize<S>(a.A, a.lda, a.sA, a.opA, 0, a.M, a.K, d, ea, pa, ab ? a.batch : 1, ab ? a.active : nullptr, st))) return e;
+  if (!(a.opndB && a.opndB->mode == 2))
+    if ((e = digitize<S>(a.B, a.ldb, a.sB, a.opB, 1, a.N, a.K, d, eb, pb, bb_ ? a.batch : 1, bb_ ? a.active : nullptr, st))) return e;
   TcParams p;
-  p.pa = s.pa;
-  p.pb = s.pb;
-  p.eA = s.ea;
-  p.eB = s.eb;
+  p.pa = pa;
+  p.pb = pb;
+  p.eA = ea;
+  p.eB = eb;
   p.M_pad = d.M_pad;
   p.N_pad = d.N_pad;
   p.nks = 2 * d.K_pad / BKS;
@@ -849,6 +857,27 @@ size_t gemm_tc_scratch_bytes(int M, int N, int K, int batch, int digits) {
   return tc::carve(nullptr, d, batch, S).bytes + 4096;
 }
 
+static size_t al1k(size_t x) { return (x + 1023) & ~size_t(1023); }
+
+size_t gemm_tc_operand_bytes(int side, int R, int K, int batch, int digits) {
+  if (k_chunks(K) > 1) return 0;
+  const int S = effective_digits(digits, K);
+  const tc::Dims d = side == 0 ? tc::dims_of(R, 1, K, S) : tc::dims_of(1, R, K, S);
+  const size_t rows = side == 0 ? (size_t)d.M_pad : 2 * (size_t)d.N_pad;
+  const size_t pad = side == 0 ? (size_t)d.M_pad : (size_t)d.N_pad;
+  return al1k((size_t)batch * S * rows * 2 * d.K_pad * 2) + al1k((size_t)batch * pad * sizeof(int));
+}
+
+TcOperand tc_operand_at(void* base, int side, int R, int K, int batch, int digits) {
+  const int S = effective_digits(digits, K);
+  const tc::Dims d = side == 0 ? tc::dims_of(R, 1, K, S) : tc::dims_of(1, R, K, S);
+  const size_t rows = side == 0 ? (size_t)d.M_pad : 2 * (size_t)d.N_pad;
+  TcOperand o;
+  o.planes = reinterpret_cast<unsigned char*>(base);
+  o.expo = reinterpret_cast<int*>(o.planes + al1k((size_t)batch * S * rows * 2 * d.K_pad * 2));
+  return o;
+}
+
 cudaError_t gemm_tc(const TcArgs& a, int digits, void* scratch, size_t scratch_bytes, int* err_flag,
                     cudaStream_t st, cudaEvent_t* ev) {
   if (a.M <= 0 || a.N <= 0 || a.batch <= 0) return cudaSuccess;
@@ -861,6 +890,7 @@ cudaError_t gemm_tc(const TcArgs& a, int digits, void* scratch, size_t scratch_b
     for (int c = 0; c < nc; ++c) {
       const int k0 = c * Kc, k1 = a.K < k0 + Kc ? a.K : k0 + Kc;
       TcArgs t = a;
+      t.opndA = t.opndB = nullptr;  // kept operands cover whole contractions only
       t.K = k1 - k0;
       t.A = a.A + (a.opA == OP_N ? (long)k0 : (long)k0 * a.lda);
       t.B = a.B + (a.opB == OP_N ? (long)k0 * a.ldb : (long)k0);
