@@ -84,7 +84,7 @@ qtx_status qtx_fpx_decompress(int bits, const void *in, long n, double *x, void 
  *     streams, other host threads) race on it; serialise them.
  *   - The call synchronises `stream` before returning (it reads the wait flag).
  * Errors: QTX_ERR_OOM when the call needs more scratch than QTX_NOALLOC_SCRATCH_BYTES -- about
- * 16 B x (M K + K N + 2 M N) + the digit planes (12 B x 6 planes x (M_pad K_pad + 2 N_pad K_pad) with
+ * 16 B x (M K + K N + 2 M N) + the digit planes (6 planes x (4 M_pad K_pad + 6 N_pad K_pad) bytes with
  * M_pad = 128-multiple, N_pad = 48-multiple, K_pad = 32-multiple) per batch entry, e.g. at most 5
  * entries of 256 x 256 x 256 -- nothing is enqueued then; QTX_ERR_INVALID_ARG, QTX_ERR_UNSUPPORTED,
  * QTX_ERR_CUDA, QTX_ERR_TIMEOUT as for qtx_zgemm_batched. */

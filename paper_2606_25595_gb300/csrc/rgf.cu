@@ -582,7 +582,9 @@ qtx_status solve_chunk(qtx_rgf_plan_s* P, const qtx_rgf_inputs* in, const qtx_rg
     }
     if (i > 0) {
       cx<T>* Tm = c.tmp(0);
-      if ((s = gemm<T>(P, gargs<T>(b, b, b, c.g(i - 1), b, bb, OP_N, U(i - 1), b, sUV, OP_N, nullptr, 0, 0, Tm, b, bb, 1.0, 0.0, ne, nullptr), st))) return s;
+      // g_{i-1} was the left operand of the previous slice's g_{i-1} Sigma^<: its digit planes are kept
+      if ((s = gemm<T>(P, gargs<T>(b, b, b, c.g(i - 1), b, bb, OP_N, U(i - 1), b, sUV, OP_N, nullptr, 0, 0, Tm, b, bb, 1.0, 0.0, ne, nullptr), st,
+                       false, reuseA(1)))) return s;
       if ((s = gemm<T>(P, gargs<T>(b, b, b, V(i - 1), b, sUV, OP_N, Tm, b, bb, OP_N, gi, b, bb, gi, b, bb, -1.0, 1.0, ne, nullptr), st))) return s;
     }
     if ((s = block_inverse<T>(P, gi, b, ne, nullptr, status, st))) return s;
@@ -619,7 +621,8 @@ qtx_status solve_chunk(qtx_rgf_plan_s* P, const qtx_rgf_inputs* in, const qtx_rg
       }
     }
     cx<T>* Y = c.tmp(0);
-    if ((s = gemm<T>(P, gargs<T>(b, b, b, gi, b, bb, OP_N, SLi, b, bb, OP_N, nullptr, 0, 0, Y, b, bb, 1.0, 0.0, ne, nullptr), st))) return s;
+    if ((s = gemm<T>(P, gargs<T>(b, b, b, gi, b, bb, OP_N, SLi, b, bb, OP_N, nullptr, 0, 0, Y, b, bb, 1.0, 0.0, ne, nullptr), st,
+                     false, keepA(1)))) return s;
     if ((s = gemm<T>(P, gargs<T>(b, b, b, Y, b, bb, OP_N, gi, b, bb, OP_C, nullptr, 0, 0, c.gl(i), b, bb, 1.0, 0.0, ne, nullptr), st))) return s;
     // FPX storage: slices the backward sweep reads back from memory (the last two stay in the
     // working blocks) are kept compressed

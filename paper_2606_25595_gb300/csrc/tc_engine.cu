@@ -23,8 +23,9 @@
 // Complex arithmetic uses the real embedding (4M form):
 //     [D_re | D_im] = [A_re | A_im] * [[B_re, B_im], [-B_im, B_re]]
 // so one MMA chain with N = 96 real columns produces 48 complex columns.  The right operand's
-// digit planes are stored transposed (N x K, K-major) with rows permuted so that the 48 "re" rows
-// and the 48 "im" rows of each CTA tile are contiguous.
+// digit planes are stored transposed (N x K, K-major) as three 48-row sub-tiles per block of 48
+// columns and 16 complex k -- Re B, Im B and -Im B -- which the producer pairs into the 96 rows the
+// MMA reads: (Re, Im) against A's real parts, (-Im, Re) against its imaginary parts.
 //
 // Kernel structure (persistent: one CTA per SM walking 128 x 48 complex output tiles, 10 warps):
 //   warp 0   producer: one bulk asynchronous copy (cp.async.bulk, mbarrier complete-tx) per plane
@@ -56,7 +57,8 @@ constexpr int BNC = 48;        // complex output columns per CTA
 constexpr int BNR = 2 * BNC;   // real (embedded) columns per CTA = MMA N
 constexpr int BKS = 16;        // bf16 K elements per stage (32-byte rows, 32B swizzle) = one MMA K
 constexpr int TILE_A = BM * BKS * 2;   // bytes of one A-plane tile (128 rows x 32 B)
-constexpr int TILE_B = BNR * BKS * 2;  // bytes of one B-plane tile (96 rows x 32 B)
+constexpr int TILE_B = BNR * BKS * 2;  // bytes of one B-plane tile in shared memory (96 rows x 32 B)
+constexpr int SUB_B = BNC * BKS * 2;   // bytes of one 48-row sub-tile of the right operand's planes
 constexpr int ACC_COLS = BNR;  // TMEM columns per accumulator
 constexpr int OUT_LD = BNC + 1;  // row stride (complex elements) of the epilogue's smem staging
 constexpr int DW = 7;          // bits per digit below the leading one
@@ -163,7 +165,7 @@ __host__ __device__ constexpr int n_acc(int S) { return S + 1 >= 6 ? 5 : S; }
 // ------------------------------------------------------------------------------ GEMM kernel
 struct TcParams {
   const unsigned char* pa;  // A plane tiles [batch'][S][M_pad/128][nks][TILE_A]
-  const unsigned char* pb;  // B plane tiles [batch'][S][2 N_pad/96][nks][TILE_B]
+  const unsigned char* pb;  // B plane sub-tiles [batch'][S][N_pad/48][K_pad/16][3][SUB_B]: Re, Im, -Im
   const int* eA;   // [batch][M_pad] row exponents of op(A)
   const int* eB;   // [batch][N_pad] column exponents of op(B)
   int M_pad, N_pad, nks;  // nks: K-stages of 32 over the embedded K (2 * K_pad)
@@ -245,7 +247,7 @@ __global__ void __launch_bounds__(320, 1) k_tc_gemm(TcParams p, int n_tiles, int
       for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
         const int e = t / per_e, mblk = (t / NBt) % MBt, nblk = t % NBt;
         if (p.active && !p.active[e]) continue;
-        const long MB = p.M_pad / BM, NB = 2L * p.N_pad / BNR;
+        const long MB = p.M_pad / BM, NB = p.N_pad / BNC, nkb = p.nks / 2;
         const long ea = p.a_batched ? e : 0, eb = p.b_batched ? e : 0;
         for (int ks = 0; ks < p.nks; ++ks, ++g) {
           const int s = (int)(g % NST);
@@ -253,10 +255,16 @@ __global__ void __launch_bounds__(320, 1) k_tc_gemm(TcParams p, int n_tiles, int
           if (!mbar_wait(&empty[s], ph ^ 1u, p.err)) { ok = false; break; }
           mbar_expect_tx(&full[s], STAGE);
           unsigned char* st = base + s * STAGE;
+          // K-stages [0, nkb) meet A's real parts: B rows (Re, Im); stages [nkb, 2 nkb) meet A's
+          // imaginary parts: B rows (-Im, Re)
+          const int part = ks >= nkb, kb = (int)(ks - part * nkb);
+          const int s0 = part ? 2 : 0, s1 = part ? 0 : 1;
           for (int d = 0; d < S; ++d) {
             bulk_load(st + d * TILE_A, p.pa + (((ea * S + d) * MB + mblk) * p.nks + ks) * (long)TILE_A, TILE_A, &full[s]);
-            bulk_load(st + S * TILE_A + d * TILE_B, p.pb + (((eb * S + d) * NB + nblk) * p.nks + ks) * (long)TILE_B,
-                      TILE_B, &full[s]);
+            const unsigned char* sb = p.pb + (((eb * S + d) * NB + nblk) * nkb + kb) * 3L * SUB_B;
+            unsigned char* db = st + S * TILE_A + d * TILE_B;
+            bulk_load(db, sb + s0 * SUB_B, SUB_B, &full[s]);
+            bulk_load(db + SUB_B, sb + s1 * SUB_B, SUB_B, &full[s]);
           }
         }
       }
@@ -374,132 +382,6 @@ __global__ void __launch_bounds__(320, 1) k_tc_gemm(TcParams p, int n_tiles, int
 }
 
 // ------------------------------------------------------------------------------ digitizer
-// Per-row exponent of the logical operand L (R x K): L(r, k) = X[r][k] (direct) or X[k][r]
-// (transposed).  e[r] = max over k of the exponent of max(|Re|, |Im|) (hi parts).  One CTA per 32
-// logical rows: 8 warps stride over k, lanes over rows (transposed, coalesced along r) or over k
-// (direct, coalesced along k); partial maxima meet in shared memory.
-__global__ void __launch_bounds__(256) k_row_expo(const cx<df>* X, long ldx, long sX, int R, int K, int R_pad,
-                                                  int transposed, int* eout, const int* active) {
-  const int e = blockIdx.y;
-  if (active && !active[e]) return;
-  __shared__ int part[8][33];
-  const cx<df>* Xe = X + (long)e * sX;
-  const int r0 = blockIdx.x * 32, w = threadIdx.x / 32, lane = threadIdx.x % 32;
-  if (transposed) {
-    const int r = r0 + lane;
-    int mx = -1000;
-    if (r < R)
-      for (int k = w; k < K; k += 8) {
-        const cx<df> v = Xe[(long)k * ldx + r];
-        mx = max(mx, max(df_expo(v.re.hi), df_expo(v.im.hi)));
-      }
-    part[w][lane] = mx;
-  } else {
-    for (int q = 0; q < 4; ++q) {
-      const int rr = w + 8 * q, r = r0 + rr;
-      int mx = -1000;
-      if (r < R)
-        for (int k = lane; k < K; k += 32) {
-          const cx<df> v = Xe[(long)r * ldx + k];
-          mx = max(mx, max(df_expo(v.re.hi), df_expo(v.im.hi)));
-        }
-      for (int off = 16; off > 0; off >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-      if (lane == 0) part[q][w] = mx;  // row rr = w + 8 q
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    const int rr = threadIdx.x, r = r0 + rr;
-    int mx = -1000;
-    if (transposed) {
-      for (int ww = 0; ww < 8; ++ww) mx = max(mx, part[ww][rr]);
-    } else {
-      mx = part[rr / 8][rr % 8];
-    }
-    if (r < R_pad) eout[(long)e * R_pad + r] = mx;
-  }
-}
-
-// v = round((hi + lo) * 2^sh), then S balanced base-128 digits (d_1 most significant).
-template <int S>
-__device__ __forceinline__ void digits_of(df x, int sh, int (&d)[S]) {
-  long long t = f2fix(x.hi, sh) + f2fix(x.lo, sh);
-#pragma unroll
-  for (int i = S - 1; i >= 1; --i) {
-    const int di = (int)((t + 64) & 127) - 64;
-    d[i] = di;
-    t = (t - di) >> DW;
-  }
-  d[0] = (int)t;
-}
-
-// Digit planes of one operand.  side 0 (left, A = op(X), M x K): plane[e][i][r][k] = digit_i(Re L),
-// plane[e][i][r][K_pad + k] = digit_i(Im L).  side 1 (right, B = op(X), K x N, logical row r = column
-// n of B): rows re = (n/48)*96 + n%48 and im = re + 48 of the embedded, transposed operand:
-//   [re row] = [ Re B(:,n) | -Im B(:,n) ],   [im row] = [ Im B(:,n) | Re B(:,n) ].
-template <int S>
-__global__ void __launch_bounds__(256) k_digitize(const cx<df>* X, long ldx, long sX, int R, int K,
-                                                  int R_pad, int K_pad, int transposed, int conj_,
-                                                  int side, const int* eR, int P, unsigned char* planes,
-                                                  long rows_plane, const int* active) {
-  const int e = blockIdx.z;
-  if (active && !active[e]) return;
-  __shared__ cx<df> tile[32][33];
-  const int k0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
-  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
-  const cx<df>* Xe = X + (long)e * sX;
-  const cx<df> zero = {mkdf(0.f, 0.f), mkdf(0.f, 0.f)};
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int a = ty + 8 * q;
-    if (!transposed) {  // tile[a][tx] = L(r0 + a, k0 + tx) = X[r0 + a][k0 + tx]
-      const int r = r0 + a, k = k0 + tx;
-      tile[a][tx] = (r < R && k < K) ? Xe[(long)r * ldx + k] : zero;
-    } else {            // tile[tx][a] = L(r0 + tx, k0 + a) = X[k0 + a][r0 + tx]
-      const int r = r0 + tx, k = k0 + a;
-      tile[tx][a] = (r < R && k < K) ? Xe[(long)k * ldx + r] : zero;
-    }
-  }
-  __syncthreads();
-  // plane tiles: [e][i][row_block][k_stage][tile], rows per block 128 (A) or 96 (B), 16 k per stage
-  const int rows_blk = side == 0 ? BM : BNR;
-  const long tile_bytes = (long)rows_blk * BKS * 2;
-  const long nks = 2L * K_pad / BKS;
-  const long plane_bytes = (rows_plane / rows_blk) * nks * tile_bytes;
-  auto put = [&](unsigned char* pl, long row, int kcol, float val) {
-    const long blk = row / rows_blk, rr = row % rows_blk, ks = kcol / BKS, kk = kcol % BKS;
-    *reinterpret_cast<__nv_bfloat16*>(pl + (blk * nks + ks) * tile_bytes + sw32_offset((uint32_t)rr, (uint32_t)kk)) =
-        __float2bfloat16_rn(val);
-  };
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int rr = ty + 8 * q, r = r0 + rr, k = k0 + tx;
-    if (r >= R_pad) continue;
-    cx<df> v = tile[rr][tx];
-    if (conj_) v.im = df_neg(v.im);
-    const int sh = P - eR[(long)e * R_pad + r];
-    int dr[S], di[S];
-    digits_of<S>(v.re, sh, dr);
-    digits_of<S>(v.im, sh, di);
-    unsigned char* pe = planes + (long)e * S * plane_bytes;
-#pragma unroll
-    for (int i = 0; i < S; ++i) {
-      const float sc = __int_as_float((127 - DW * i) << 23);  // 2^(-7 i)
-      unsigned char* pl = pe + (long)i * plane_bytes;
-      if (side == 0) {
-        put(pl, r, k, (float)dr[i] * sc);
-        put(pl, r, K_pad + k, (float)di[i] * sc);
-      } else {
-        const long rre = (long)(r / BNC) * BNR + (r % BNC), rim = rre + BNC;
-        put(pl, rre, k, (float)dr[i] * sc);
-        put(pl, rre, K_pad + k, -(float)di[i] * sc);
-        put(pl, rim, k, (float)di[i] * sc);
-        put(pl, rim, K_pad + k, (float)dr[i] * sc);
-      }
-    }
-  }
-}
-
 // Digits of one df32 value in floating point (used by the fused pass).  With the row scaled so the
 // leading digit's unit is 1 (x' = x 2^(l1 - 1 - e_row), |x'| < 2^(l1-1)), digit i (0-based) is a
 // multiple of U_i = 2^(-7 i) -- exactly the pre-scaled plane value d_i 2^(-7 i).  Each digit is the
@@ -617,16 +499,22 @@ __global__ void __launch_bounds__(32 * RPC) k_digitize_rows(const cx<df>* X, lon
   __syncthreads();
   if (t < RPC && r0 + t < R_pad) eout[(long)e * R_pad + r0 + t] = s_ex[t];
   // ---- digits: item = (row rr, complex k = 8 kc .. 8 kc + 7)
-  const int rows_blk = side == 0 ? BM : BNR;
-  const long tile_bytes = (long)rows_blk * BKS * 2;
-  const long nks = 2L * K_pad / BKS;
-  const long plane_bytes = (rows_plane / rows_blk) * nks * tile_bytes;
+  // left operand: [row_block of 128][k_stage of 16 embedded k][128 x 32 B] tiles, embedded k' = k for
+  // Re, K_pad + k for Im.  right operand: [col_block of 48][k_block of 16 complex k][3][48 x 32 B]
+  // sub-tiles holding Re, Im and -Im (the producer pairs them into the (Re, Im) and (-Im, Re) rows).
+  const long nks = 2L * K_pad / BKS, nkb = K_pad / BKS;
+  const long plane_bytes = side == 0 ? (rows_plane / BM) * nks * (long)TILE_A : (long)(R_pad / BNC) * nkb * 3 * SUB_B;
   unsigned char* pe = planes + (long)e * S * plane_bytes;
   const int nkc = K_pad / 8;
-  // byte offset of the 16-byte chunk holding embedded k' .. k' + 7 (k' a multiple of 8) of plane row
+  // byte offset of the 16-byte chunk holding embedded k' .. k' + 7 (k' a multiple of 8) of row r (left)
   auto chunk_off = [&](long row, int kp) -> long {
-    const long blk = row / rows_blk, rr_ = row % rows_blk, ks = kp / BKS, kk = kp % BKS;
-    return (blk * nks + ks) * tile_bytes + sw32_offset((uint32_t)rr_, (uint32_t)kk);
+    const long blk = row / BM, rr_ = row % BM, ks = kp / BKS, kk = kp % BKS;
+    return (blk * nks + ks) * TILE_A + sw32_offset((uint32_t)rr_, (uint32_t)kk);
+  };
+  // ... of complex k .. k + 7 of column r (right), in sub-tile `sub`
+  auto sub_off = [&](long col, int k, int sub) -> long {
+    const long cb = col / BNC, rr_ = col % BNC, kb = k / BKS, kk = k % BKS;
+    return ((cb * nkb + kb) * 3 + sub) * (long)SUB_B + sw32_offset((uint32_t)rr_, (uint32_t)kk);
   };
 #pragma unroll 1
   for (int item = t; item < RPC * nkc; item += NT) {
@@ -666,18 +554,15 @@ __global__ void __launch_bounds__(32 * RPC) k_digitize_rows(const cx<df>* X, lon
         *reinterpret_cast<uint4*>(pl + o_im) = make_uint4(wim[i][0], wim[i][1], wim[i][2], wim[i][3]);
       }
     } else {
-      const long rre = (long)(r / BNC) * BNR + (r % BNC), rim = rre + BNC;
-      const long o1 = chunk_off(rre, k8), o2 = chunk_off(rre, K_pad + k8);
-      const long o3 = chunk_off(rim, k8), o4 = chunk_off(rim, K_pad + k8);
+      const long o0 = sub_off(r, k8, 0), o1 = sub_off(r, k8, 1), o2 = sub_off(r, k8, 2);
       const uint32_t SGN = 0x80008000u;  // bf16 sign bits of both halves
 #pragma unroll
       for (int i = 0; i < S; ++i) {
         unsigned char* pl = pe + (long)i * plane_bytes;
-        *reinterpret_cast<uint4*>(pl + o1) = make_uint4(wre[i][0], wre[i][1], wre[i][2], wre[i][3]);
+        *reinterpret_cast<uint4*>(pl + o0) = make_uint4(wre[i][0], wre[i][1], wre[i][2], wre[i][3]);
+        *reinterpret_cast<uint4*>(pl + o1) = make_uint4(wim[i][0], wim[i][1], wim[i][2], wim[i][3]);
         *reinterpret_cast<uint4*>(pl + o2) =
             make_uint4(wim[i][0] ^ SGN, wim[i][1] ^ SGN, wim[i][2] ^ SGN, wim[i][3] ^ SGN);
-        *reinterpret_cast<uint4*>(pl + o3) = make_uint4(wim[i][0], wim[i][1], wim[i][2], wim[i][3]);
-        *reinterpret_cast<uint4*>(pl + o4) = make_uint4(wre[i][0], wre[i][1], wre[i][2], wre[i][3]);
       }
     }
   }
@@ -711,7 +596,7 @@ inline Scratch carve(void* base, const Dims& d, int batch, int S) {
   Scratch s;
   unsigned char* p = reinterpret_cast<unsigned char*>(base);
   const size_t a = al((size_t)batch * S * d.M_pad * 2 * d.K_pad * sizeof(__nv_bfloat16));
-  const size_t b = al((size_t)batch * S * 2 * d.N_pad * 2 * d.K_pad * sizeof(__nv_bfloat16));  // 2 N_pad rows
+  const size_t b = al((size_t)batch * S * (d.N_pad / BNC) * (d.K_pad / BKS) * 3 * SUB_B);  // Re, Im, -Im sub-tiles
   const size_t ea = al((size_t)batch * d.M_pad * sizeof(int));
   const size_t eb = al((size_t)batch * d.N_pad * sizeof(int));
   s.pa = p;
@@ -737,7 +622,8 @@ cudaError_t digitize(const cx<df>* X, long ldx, long sX, int opX, int side, int 
   // different CTAs overlap), else a single row up to the 200 KB the kernel is allowed
   const size_t row_bytes = (size_t)(strip_skew(d.K_pad) + 1) * sizeof(cx<df>);
   const int rpc = 2 * row_bytes <= 48 * 1024 ? 2 : 1;
-  if (rpc * row_bytes <= 200 * 1024) {
+  if (rpc * row_bytes > 200 * 1024) return cudaErrorInvalidValue;  // K-chunks of <= 1024 always fit
+  {
     static bool attr = false;
     if (!attr) {
       cudaError_t ea = cudaFuncSetAttribute(k_digitize_rows<S, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -754,18 +640,6 @@ cudaError_t digitize(const cx<df>* X, long ldx, long sX, int opX, int side, int 
     count_launch();
     return cudaGetLastError();
   }
-  {
-    dim3 g((R_pad + 31) / 32, batch);
-    k_row_expo<<<g, 256, 0, st>>>(X, ldx, sX, R, K, R_pad, transposed, eout, active);
-    count_launch();
-  }
-  cudaError_t err = cudaGetLastError();
-  if (err != cudaSuccess) return err;
-  dim3 g(d.K_pad / 32, (R_pad + 31) / 32, batch);
-  k_digitize<S><<<g, 256, 0, st>>>(X, ldx, sX, R, K, R_pad, d.K_pad, transposed, cj, side, eout, d.P, planes,
-                                   rows_plane, active);
-  count_launch();
-  return cudaGetLastError();
 }
 
 template <int S, int NST>
@@ -858,23 +732,25 @@ size_t gemm_tc_scratch_bytes(int M, int N, int K, int batch, int digits) {
 }
 
 static size_t al1k(size_t x) { return (x + 1023) & ~size_t(1023); }
+// digit-plane bytes of one operand (as carve lays them out)
+static size_t plane_bytes_of(int side, const tc::Dims& d, int batch, int S) {
+  return side == 0 ? (size_t)batch * S * d.M_pad * 2 * d.K_pad * 2
+                   : (size_t)batch * S * (d.N_pad / tc::BNC) * (d.K_pad / tc::BKS) * 3 * tc::SUB_B;
+}
 
 size_t gemm_tc_operand_bytes(int side, int R, int K, int batch, int digits) {
   if (k_chunks(K) > 1) return 0;
   const int S = effective_digits(digits, K);
   const tc::Dims d = side == 0 ? tc::dims_of(R, 1, K, S) : tc::dims_of(1, R, K, S);
-  const size_t rows = side == 0 ? (size_t)d.M_pad : 2 * (size_t)d.N_pad;
-  const size_t pad = side == 0 ? (size_t)d.M_pad : (size_t)d.N_pad;
-  return al1k((size_t)batch * S * rows * 2 * d.K_pad * 2) + al1k((size_t)batch * pad * sizeof(int));
+  return al1k(plane_bytes_of(side, d, batch, S)) + al1k((size_t)batch * (side == 0 ? d.M_pad : d.N_pad) * sizeof(int));
 }
 
 TcOperand tc_operand_at(void* base, int side, int R, int K, int batch, int digits) {
   const int S = effective_digits(digits, K);
   const tc::Dims d = side == 0 ? tc::dims_of(R, 1, K, S) : tc::dims_of(1, R, K, S);
-  const size_t rows = side == 0 ? (size_t)d.M_pad : 2 * (size_t)d.N_pad;
   TcOperand o;
   o.planes = reinterpret_cast<unsigned char*>(base);
-  o.expo = reinterpret_cast<int*>(o.planes + al1k((size_t)batch * S * rows * 2 * d.K_pad * 2));
+  o.expo = reinterpret_cast<int*>(o.planes + al1k(plane_bytes_of(side, d, batch, S)));
   return o;
 }
 
