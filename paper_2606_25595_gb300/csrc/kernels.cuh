@@ -31,6 +31,10 @@ struct Term {
   long s = 0;     // batch stride (complex elements); 0 shares one block
   int op = OP_N;
   double alpha = 0.0;
+  // set by combine() on the host from alpha: +1 / -1 / general (with alpha rounded to FP32), so the
+  // df32 and FP32 accumulations make no per-element FP64 comparisons (GB300's FP64 pipe is 1/64 rate)
+  int kind = 0;
+  float alpha_f = 0.f;
 };
 template <typename Tin, typename Tout>
 cudaError_t combine(cx<Tout>* out, long sOut, Term<Tin> t0, Term<Tin> t1, Term<Tin> t2, int b,

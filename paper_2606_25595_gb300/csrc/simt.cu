@@ -377,6 +377,19 @@ __device__ __forceinline__ void acc_axpy(df& a, double alpha, X x) {
   const df v = as_df(x);
   a = df_add(a, alpha == 1.0 ? v : (alpha == -1.0 ? df_neg(v) : df_mulf(v, (float)alpha)));
 }
+// the same with the coefficient classified on the host (kind +1 / -1 / 0 = general, alpha in FP32)
+template <typename X>
+__device__ __forceinline__ void acc_axpy_k(df& a, int kind, float alpha_f, double, X x) {
+  const df v = as_df(x);
+  a = df_add(a, kind == 1 ? v : (kind == -1 ? df_neg(v) : df_mulf(v, alpha_f)));
+}
+template <typename X>
+__device__ __forceinline__ void acc_axpy_k(float& a, int, float alpha_f, double, X x) {
+  a = fmaf(alpha_f, (float)to_d(x), a);
+}
+__device__ __forceinline__ void acc_axpy_k(float& a, int, float alpha_f, double, float x) { a = fmaf(alpha_f, x, a); }
+template <typename X>
+__device__ __forceinline__ void acc_axpy_k(double& a, int, float, double alpha, X x) { a += alpha * to_d(x); }
 __device__ __forceinline__ void acc_add_d(double& a, double z) { a += z; }
 __device__ __forceinline__ void acc_add_d(float& a, double z) { a += (float)z; }
 __device__ __forceinline__ void acc_add_d(df& a, double z) { a = df_add(a, from_d<df>(z)); }
@@ -400,7 +413,7 @@ __device__ __forceinline__ double acc_out<double>(df a) { return to_d(a); }
 template <typename Tin, typename Tout>
 __global__ void __launch_bounds__(256) k_combine(cx<Tout>* out, long sOut, Term<Tin> t0, Term<Tin> t1,
                                                  Term<Tin> t2, int b, const double* E, double eta,
-                                                 double diag_coef, const int* active) {
+                                                 double diag_coef, int has_diag, const int* active) {
   using Acc = typename AccSel<Tin, Tout>::type;
   const int e = blockIdx.z;
   if (active && !active[e]) return;
@@ -425,8 +438,8 @@ __global__ void __launch_bounds__(256) k_combine(cx<Tout>* out, long sOut, Term<
         const int r = r0 + ty + 8 * q, c = c0 + tx;
         if (r < b && c < b) {
           const cx<Tin> v = X[(long)r * b + c];
-          acc_axpy(accr[q], T_.alpha, v.re);
-          acc_axpy(acci[q], T_.alpha, v.im);
+          acc_axpy_k(accr[q], T_.kind, T_.alpha_f, T_.alpha, v.re);
+          acc_axpy_k(acci[q], T_.kind, T_.alpha_f, T_.alpha, v.im);
         }
       }
     } else {
@@ -443,8 +456,8 @@ __global__ void __launch_bounds__(256) k_combine(cx<Tout>* out, long sOut, Term<
         const int r = r0 + ty + 8 * q, c = c0 + tx;
         if (r < b && c < b) {
           const cx<Tin> v = tile[tx][ty + 8 * q];
-          acc_axpy(accr[q], T_.alpha, v.re);
-          acc_axpy(acci[q], -T_.alpha, v.im);
+          acc_axpy_k(accr[q], T_.kind, T_.alpha_f, T_.alpha, v.re);
+          acc_axpy_k(acci[q], -T_.kind, -T_.alpha_f, -T_.alpha, v.im);
         }
       }
     }
@@ -454,7 +467,7 @@ __global__ void __launch_bounds__(256) k_combine(cx<Tout>* out, long sOut, Term<
   for (int q = 0; q < 4; ++q) {
     const int r = r0 + ty + 8 * q, c = c0 + tx;
     if (r < b && c < b) {
-      if (r == c && diag_coef != 0.0) {
+      if (r == c && has_diag) {
         acc_add_d(accr[q], E ? diag_coef * E[e] : 0.0);
         acc_add_d(acci[q], diag_coef * eta);
       }
@@ -470,8 +483,15 @@ template <typename Tin, typename Tout>
 cudaError_t combine(cx<Tout>* out, long sOut, Term<Tin> t0, Term<Tin> t1, Term<Tin> t2, int b,
                     int batch, const double* E, double eta, double diag_coef, const int* active,
                     cudaStream_t st) {
+  auto classify = [](Term<Tin>& t) {
+    t.kind = t.alpha == 1.0 ? 1 : (t.alpha == -1.0 ? -1 : 0);
+    t.alpha_f = (float)t.alpha;
+  };
+  classify(t0);
+  classify(t1);
+  classify(t2);
   dim3 grid((b + 31) / 32, (b + 31) / 32, batch);
-  k_combine<Tin, Tout><<<grid, 256, 0, st>>>(out, sOut, t0, t1, t2, b, E, eta, diag_coef, active);
+  k_combine<Tin, Tout><<<grid, 256, 0, st>>>(out, sOut, t0, t1, t2, b, E, eta, diag_coef, diag_coef != 0.0, active);
   count_launch();
   return cudaGetLastError();
 }
@@ -540,21 +560,22 @@ template cudaError_t assemble_diag<df>(cx<df>*, const cx<double>*, const cx<doub
 
 template <typename T>
 __global__ void k_axpby_from64(cx<T>* out, long sOut, const cx<double>* X, long sX, double c1,
-                               const cx<double>* Y, long sY, double c2, int b) {
+                               const cx<double>* Y, long sY, double c2, int b, int k1, int k2) {
   const int e = blockIdx.y;
   const long bb = (long)b * b;
   for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < bb; idx += (long)gridDim.x * blockDim.x) {
     if constexpr (std::is_same<T, df>::value) {  // df32 arithmetic: no FP64 operations
-      auto scaled = [](double c, double x) {
+      // k = +1 / -1 / 0 (general coefficient, split to df32 once per element)
+      auto scaled = [](int k, double c, double x) {
         const df v = from_d<df>(x);
-        return c == 1.0 ? v : (c == -1.0 ? df_neg(v) : df_mul(v, from_d<df>(c)));
+        return k == 1 ? v : (k == -1 ? df_neg(v) : df_mul(v, from_d<df>(c)));
       };
       const cx<double> x = X[(long)e * sX + idx];
-      df vr = scaled(c1, x.re), vi = scaled(c1, x.im);
+      df vr = scaled(k1, c1, x.re), vi = scaled(k1, c1, x.im);
       if (Y) {
         const cx<double> y = Y[(long)e * sY + idx];
-        vr = df_add(vr, scaled(c2, y.re));
-        vi = df_add(vi, scaled(c2, y.im));
+        vr = df_add(vr, scaled(k2, c2, y.re));
+        vi = df_add(vi, scaled(k2, c2, y.im));
       }
       cx<df> o;
       o.re = vr;
@@ -572,7 +593,8 @@ cudaError_t axpby_from64(cx<T>* out, long sOut, const cx<double>* X, long sX, do
                          const cx<double>* Y, long sY, double c2, int b, int batch, cudaStream_t st) {
   const long bb = (long)b * b;
   dim3 grid((unsigned)((bb + 255) / 256 < 1024 ? (bb + 255) / 256 : 1024), batch);
-  k_axpby_from64<T><<<grid, 256, 0, st>>>(out, sOut, X, sX, c1, Y, sY, c2, b);
+  const int k1 = c1 == 1.0 ? 1 : (c1 == -1.0 ? -1 : 0), k2 = c2 == 1.0 ? 1 : (c2 == -1.0 ? -1 : 0);
+  k_axpby_from64<T><<<grid, 256, 0, st>>>(out, sOut, X, sX, c1, Y, sY, c2, b, k1, k2);
   count_launch();
   return cudaGetLastError();
 }
@@ -701,6 +723,26 @@ __global__ void __launch_bounds__(256) k_obs_current(double* cur, long ldcur, co
   const double Er = E[e];
   const cx<T>* G = GLu + (long)e * sG;
   double s = 0.0;
+  if constexpr (std::is_same<T, df>::value) {
+    if (!Sup) {  // df32 products and sums: no FP64 arithmetic per element
+      df a = mkdf(0.f, 0.f);
+      for (long idx = threadIdx.x; idx < bb; idx += blockDim.x) {
+        const cx<double> x = Hup[idx];
+        const cx<df> g = G[idx];
+        a = df_add(a, df_add(df_mul(from_d<df>(x.re), g.re), df_mul(from_d<df>(x.im), g.im)));
+      }
+      __shared__ df red[8];
+      for (int off = 16; off > 0; off >>= 1)
+        a = df_add(a, mkdf(__shfl_down_sync(0xffffffffu, a.hi, off), __shfl_down_sync(0xffffffffu, a.lo, off)));
+      if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = a;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        for (int i = 1; i < (int)blockDim.x / 32; ++i) a = df_add(a, red[i]);
+        cur[(long)e * ldcur] = -2.0 * to_d(a);
+      }
+      return;
+    }
+  }
   for (long idx = threadIdx.x; idx < bb; idx += blockDim.x) {
     cx<double> x = Hup[idx];
     if (Sup) x = x - Er * Sup[idx];
