@@ -57,6 +57,10 @@ def parse():
                          "nrl: b=3408 N_B=10 (the paper's NR-L shape), per-energy self-energies streamed from host; "
                          "wsolve: screened-Coulomb system b=256 N_B=32, 64 energies (assembly + two selected solves)")
     ap.add_argument("--requests", type=int, default=40)
+    ap.add_argument("--refine-tol", type=float, default=2.0 ** -13,
+                    help="mixed workloads: an energy stops its Newton sweeps once ||I - A X||_F <= this "
+                         "(the next residual is then <= its square, 2^-26); the FP32 starting inverses of the "
+                         "b=256 device have residuals of 3e-5 - 7e-5, so one sweep; 0 = always 2 sweeps")
     ap.add_argument("--storage-bits", type=int, default=0,
                     help="mixed workloads: keep the left-connected blocks in FPX of this many bits (0 = off)")
     return ap.parse_args()
@@ -514,7 +518,8 @@ def main():
     din = q.upload(dev)
     outs = ["GR_diag", "GL_diag", "current", "density", "integrals"]
     desc = q.make_desc(nb, b, args.precision, min(args.chunk, ne), refine_max_iter=2,
-                       has_scattering=True, outputs=outs, offdiag_sigma=bt, storage_bits=args.storage_bits)
+                       has_scattering=True, outputs=outs, offdiag_sigma=bt, storage_bits=args.storage_bits,
+                       refine_tol=args.refine_tol)
     plan = q.Plan(desc)
     cd = torch.device("cuda")
     GR = torch.empty((ne, nb, b, b), dtype=torch.complex128, device=cd)
@@ -677,6 +682,7 @@ def main():
                            "global_batch": ne * ws, "precision": args.precision,
                            "energies_in_flight": min(args.chunk, ne),
                            "storage_bits": args.storage_bits,
+                           "refine_max_iter": 2, "refine_tol": args.refine_tol,
                            "plan_bytes_per_energy_in_flight": q.footprint(desc) // min(args.chunk, ne),
                            "l2": "inputs and working set (>= 16 GB) larger than L2; no flush"},
                 "status_ok": status_ok,

@@ -120,6 +120,10 @@ typedef struct {
                                   leads = 0, sigma_stream = 0; GR_* outputs are the BT blocks of M^-1,
                                   GL_* those of X; GG_*, current, contact, transmission and integrals
                                   are not produced (their bits must be clear); density = Im Tr X_ii */
+  double refine_tol;           /* QTX_EMU64 / QTX_BF16X3: an energy stops its Newton sweeps once the
+                                  Frobenius norm of its residual I - A X is at most refine_tol (the
+                                  next iterate's residual is then at most refine_tol^2); 0 = always
+                                  refine_max_iter sweeps */
 } qtx_rgf_desc;
 
 /* Device inputs (caller-owned, complex128 unless noted). */

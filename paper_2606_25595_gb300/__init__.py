@@ -49,7 +49,8 @@ class Desc(ctypes.Structure):
                 ("leads", ctypes.c_int), ("decim_tol", ctypes.c_double),
                 ("decim_max_iter", ctypes.c_int), ("outputs", ctypes.c_uint),
                 ("offdiag_sigma", ctypes.c_int), ("storage_bits", ctypes.c_int),
-                ("sigma_stream", ctypes.c_int), ("system_input", ctypes.c_int)]
+                ("sigma_stream", ctypes.c_int), ("system_input", ctypes.c_int),
+                ("refine_tol", ctypes.c_double)]
 
 
 class Inputs(ctypes.Structure):
@@ -146,7 +147,8 @@ def lib() -> ctypes.CDLL:
 def make_desc(n_blocks, block_size, precision="fp64", max_energies_in_flight=64,
               refine_max_iter=2, has_S=False, has_scattering=True, energy_dependent_sigma=False,
               leads=False, decim_tol=1e-13, decim_max_iter=100, outputs=None,
-              offdiag_sigma=False, storage_bits=0, sigma_stream=False, system_input=False) -> Desc:
+              offdiag_sigma=False, storage_bits=0, sigma_stream=False, system_input=False,
+              refine_tol=0.0) -> Desc:
     if outputs is None:
         outputs = (1 << 12) - 1
     elif not isinstance(outputs, int):
@@ -159,7 +161,7 @@ def make_desc(n_blocks, block_size, precision="fp64", max_energies_in_flight=64,
                 int(refine_max_iter), int(bool(has_S)), int(bool(has_scattering)),
                 int(bool(energy_dependent_sigma)), int(bool(leads)), float(decim_tol),
                 int(decim_max_iter), int(outputs), int(bool(offdiag_sigma)), int(storage_bits),
-                int(bool(sigma_stream)), int(bool(system_input)))
+                int(bool(sigma_stream)), int(bool(system_input)), float(refine_tol))
 
 
 def kernel_launches() -> int:

@@ -44,7 +44,7 @@ inline bool uv_per_energy(const qtx_rgf_desc& d) {
 }
 
 struct Layout {
-  size_t g, gl, gfx, glfx, fx_slot, sig_stage, opnd[3], opnd_bytes[3], tmp, inv_tmp, U, V, ident, ident_df, ref, f32a, f32tmp, dec, lead, obs, flags,
+  size_t g, gl, gfx, glfx, fx_slot, sig_stage, opnd[3], opnd_bytes[3], refine_act, tmp, inv_tmp, U, V, ident, ident_df, ref, f32a, f32tmp, dec, lead, obs, flags,
       tc_scratch, total;
   int n_tmp, n_dec;
   size_t tc_bytes;
@@ -124,6 +124,7 @@ Layout make_layout(const qtx_rgf_desc& d) {
   // per-energy observables: current, density, contact(2), transmission, scratch(2)
   L.obs = a.take((size_t)Ec * (2 * nb + 8) * sizeof(double));
   L.flags = a.take((size_t)Ec * 3 * sizeof(int) + 64);
+  L.refine_act = a.take((size_t)Ec * 2 * sizeof(int) + 64);  // per-energy sweep masks (ping-pong)
   L.tc_bytes = 0;
   if (mixed) L.tc_bytes = gemm_tc_scratch_bytes((int)b, (int)b, (int)b, (int)Ec, d.precision == QTX_EMU64 ? 6 : 2);
   L.tc_scratch = a.take(L.tc_bytes);
@@ -369,13 +370,23 @@ qtx_status block_inverse<df>(qtx_rgf_plan_s* P, cx<df>* A, int n, int batch, con
   Term<float> tX; tX.p = A32; tX.s = nn; tX.alpha = 1.0;
   Term<float> none32;
   QTX_CK((combine<float, df>(A, nn, tX, none32, none32, n, batch, nullptr, 0.0, 0.0, active, st)));
+  // With refine_tol > 0 an energy leaves the sweeps once ||I - A X||_F <= refine_tol: the masks
+  // (ping-pong in refine_act) make every later product, digitisation and combination skip it.
+  int* masks = reinterpret_cast<int*>(P->ws + P->L.refine_act);
+  const int* act = active;
   for (int it = 0; it < P->d.refine_max_iter; ++it) {
     // Acopy's digit planes serve every sweep
-    if ((s = gemm<df>(P, gargs<df>(n, n, n, Acopy, n, nn, OP_N, A, n, nn, OP_N, I, n, 0, R, n, nn, -1.0, 1.0, batch, active), st,
+    if ((s = gemm<df>(P, gargs<df>(n, n, n, Acopy, n, nn, OP_N, A, n, nn, OP_N, I, n, 0, R, n, nn, -1.0, 1.0, batch, act), st,
                       false, it == 0 ? keepA(0) : reuseA(0)))) return s;
-    if ((s = gemm<df>(P, gargs<df>(n, n, n, A, n, nn, OP_N, R, n, nn, OP_N, A, n, nn, Xn, n, nn, 1.0, 1.0, batch, active), st))) return s;
+    int* next = nullptr;
+    if (P->d.refine_tol > 0.0 && it + 1 < P->d.refine_max_iter) {
+      next = masks + (it & 1) * P->Ec;
+      QTX_CK(residual_mask(R, nn, n, batch, P->d.refine_tol, act, next, st));
+    }
+    if ((s = gemm<df>(P, gargs<df>(n, n, n, A, n, nn, OP_N, R, n, nn, OP_N, A, n, nn, Xn, n, nn, 1.0, 1.0, batch, act), st))) return s;
     Term<df> tXn; tXn.p = Xn; tXn.s = nn; tXn.alpha = 1.0;
-    QTX_CK((combine<df, df>(A, nn, tXn, none, none, n, batch, nullptr, 0.0, 0.0, active, st)));
+    QTX_CK((combine<df, df>(A, nn, tXn, none, none, n, batch, nullptr, 0.0, 0.0, act, st)));
+    if (next) act = next;
   }
   return QTX_OK;
 }
@@ -805,6 +816,7 @@ qtx_status validate(const qtx_rgf_desc* d, std::string& err) {
   if (d->precision < QTX_FP64 || d->precision > QTX_EMU64) { err = "unknown precision"; return QTX_ERR_INVALID_ARG; }
   if (d->leads && (d->decim_max_iter < 1 || !(d->decim_tol > 0))) { err = "leads need decim_max_iter >= 1 and decim_tol > 0"; return QTX_ERR_INVALID_ARG; }
   if (d->refine_max_iter < 0) { err = "refine_max_iter must be >= 0"; return QTX_ERR_INVALID_ARG; }
+  if (!(d->refine_tol >= 0.0)) { err = "refine_tol must be >= 0"; return QTX_ERR_INVALID_ARG; }
   if (d->offdiag_sigma && !d->has_scattering) { err = "offdiag_sigma needs has_scattering"; return QTX_ERR_INVALID_ARG; }
   if (d->storage_bits && !fpx_width_ok(d->storage_bits)) { err = "storage_bits must be 0, 56, 48, 40, 32, 24 or 16"; return QTX_ERR_INVALID_ARG; }
   if (d->sigma_stream && (!d->has_scattering || !d->energy_dependent_sigma || d->offdiag_sigma)) { err = "sigma_stream needs has_scattering and energy_dependent_sigma, without offdiag_sigma"; return QTX_ERR_INVALID_ARG; }

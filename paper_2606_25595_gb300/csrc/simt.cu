@@ -659,6 +659,32 @@ template cudaError_t assemble_offdiag<double>(cx<double>*, cx<double>*, const cx
 template cudaError_t assemble_offdiag<float>(cx<float>*, cx<float>*, const cx<double>*, const cx<double>*, const double*, double, int, int, cudaStream_t, const cx<double>*, const cx<double>*, long);
 template cudaError_t assemble_offdiag<df>(cx<df>*, cx<df>*, const cx<double>*, const cx<double>*, const double*, double, int, int, cudaStream_t, const cx<double>*, const cx<double>*, long);
 
+__global__ void __launch_bounds__(256) k_residual_mask(const cx<df>* R, long sR, long nn, float tol2,
+                                                       const int* active, int* next) {
+  const int e = blockIdx.x;
+  if (active && !active[e]) {
+    if (threadIdx.x == 0) next[e] = 0;
+    return;
+  }
+  const cx<df>* X = R + (long)e * sR;
+  float s = 0.f;
+  for (long i = threadIdx.x; i < nn; i += blockDim.x) s = fmaf(X[i].re.hi, X[i].re.hi, fmaf(X[i].im.hi, X[i].im.hi, s));
+  __shared__ float red[8];
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+  if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < 8; ++w) s += red[w];
+    next[e] = s > tol2 ? 1 : 0;
+  }
+}
+cudaError_t residual_mask(const cx<df>* R, long sR, int n, int batch, double tol, const int* active, int* next,
+                          cudaStream_t st) {
+  k_residual_mask<<<batch, 256, 0, st>>>(R, sR, (long)n * n, (float)(tol * tol), active, next);
+  count_launch();
+  return cudaGetLastError();
+}
+
 template <typename T>
 __global__ void k_add_identity(cx<T>* X, long sX, int n, const int* active) {
   const int e = blockIdx.y;

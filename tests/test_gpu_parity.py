@@ -315,6 +315,24 @@ def test_emu64_rgf_meets_1e6_small(q):
     _check(res, ref, 1e-7, 1e-6, keys=("GR_diag", "GR_upper", "GR_lower", "GL_diag", "GL_upper"))
 
 
+def test_emu64_adaptive_refinement(q):
+    """Per-energy Newton sweeps stop once ||I - A X||_F <= refine_tol.  With a tolerance every
+    residual meets after one sweep the result is bit-identical to refine_max_iter = 1; with
+    2^-16 (the next residual is then at most 2^-32) current and density stay within 1e-6."""
+    dev = W.random_device(128, 8, n_energies=4, seed=3)
+    outs = ["GR_diag", "GL_diag", "current", "density"]
+    one = q.solve_device(dev, "emu64", refine_max_iter=1, outputs=outs)
+    d = q.make_desc(8, 128, "emu64", 4, 3, has_scattering=True, outputs=outs, refine_tol=1.0)
+    loose = q.solve_device(dev, "emu64", refine_max_iter=3, outputs=outs, plan=q.Plan(d))
+    for k in outs:
+        assert np.array_equal(one[k], loose[k]), k
+    d = q.make_desc(8, 128, "emu64", 4, 3, has_scattering=True, outputs=outs, refine_tol=2.0 ** -16)
+    res = q.solve_device(dev, "emu64", refine_max_iter=3, outputs=outs, plan=q.Plan(d))
+    ref = O.solve(dev)
+    e = _obs_errs(res, ref)
+    assert e["current"] < 1e-6 and e["density"] < 1e-6, e
+
+
 def test_emu64_rgf_mixed_workload_sampled(q):
     """b=256, N_B=64 (the mixed-precision workload) at sampled energies: current and density
     within 1e-6 of the FP64 oracle."""

@@ -90,3 +90,11 @@ def test_fpx_storage_descriptor(libpath):
         saved = 2 * (nb - 2) * ec * b * b * 16 - 2 * nb * ec * (2 * b * b) * bits // 8
         assert abs((base - fx) - saved) < 1 << 20, (bits, base - fx, saved)
     assert q.load().qtx_fpx_bytes(40, 10) == 80
+
+
+def test_refine_tol_validation(libpath):
+    import paper_2606_25595_gb300 as q
+    h = ctypes.c_void_p()
+    bad = q.make_desc(4, 16, "emu64", 2, refine_tol=-1.0)
+    assert q.load().qtx_rgf_plan_create(ctypes.byref(bad), ctypes.byref(h)) == 1
+    assert b"refine_tol" in q.load().qtx_rgf_last_error(None)
