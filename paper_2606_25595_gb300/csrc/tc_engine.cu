@@ -22,7 +22,8 @@
 //
 // Complex arithmetic uses the real embedding (4M form):
 //     [D_re | D_im] = [A_re | A_im] * [[B_re, B_im], [-B_im, B_re]]
-// so one MMA chain with N = 96 real columns produces 48 complex columns.  The right operand's
+// so one MMA chain with N = 96 real columns produces 48 complex columns (the last column tile of a
+// product takes only its N - 48 (tiles - 1) columns rounded up to 8, with a narrower MMA N).  The right operand's
 // digit planes are stored transposed (N x K, K-major) as three 48-row sub-tiles per block of 48
 // columns and 16 complex k -- Re B, Im B and -Im B -- which the producer pairs into the 96 rows the
 // MMA reads: (Re, Im) against A's real parts, (-Im, Re) against its imaginary parts.
@@ -127,15 +128,18 @@ __host__ __device__ __forceinline__ uint32_t sw32_offset(uint32_t rr, uint32_t k
   const uint32_t o = rr * 32u + kk * 2u;
   return o ^ (((o >> 7) & 1u) << 4);
 }
-// Instruction descriptor: kind::f16, D = F32, A = B = BF16, both K-major, M = 128, N = 96.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BNR >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+// Instruction descriptor: kind::f16, D = F32, A = B = BF16, both K-major, M = 128, N = n (a multiple
+// of 16 up to 96 here).
+__host__ __device__ constexpr uint32_t idesc_n(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
 
-__device__ __forceinline__ void mma(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t accumulate) {
+__device__ __forceinline__ void mma(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t accumulate) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-      ::"r"(dtmem), "l"(ad), "l"(bd), "r"(kIdesc), "r"(accumulate)
+      ::"r"(dtmem), "l"(ad), "l"(bd), "r"(idesc), "r"(accumulate)
       : "memory");
 }
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
@@ -170,6 +174,7 @@ struct TcParams {
   const int* eB;   // [batch][N_pad] column exponents of op(B)
   int M_pad, N_pad, nks;  // nks: K-stages of 32 over the embedded K (2 * K_pad)
   int M, N;
+  int bn_last;     // complex columns the last column tile computes: N - 48 (NBt - 1), rounded up to 8
   cx<df>* C; long ldc, sC;
   const cx<df>* C0; long ldc0, sC0;
   float alpha, beta;
@@ -195,8 +200,21 @@ __device__ __forceinline__ df sum_acc(const uint32_t (&v)[NACC][8], int c) {
   return mkdf(h, e - (h - s));
 }
 
-// The product kernel is persistent: one CTA per SM walks the tiles t = blockIdx.x, blockIdx.x + gridDim.x, ...
-// (column tile fastest, then row tile, then batch entry).  The stage ring and its barriers run on
+// Tile of round k for this CTA.  Round k covers tiles [k G, (k + 1) G) (G = gridDim.x; column tile
+// fastest, then row tile, then batch entry), dealt to the CTAs rotated by one per round: the
+// narrower last column tile then falls to every CTA equally often (whenever G - 1 is coprime to the
+// number of column tiles, always for 152 SMs) rather than to a fixed subset of them, while the
+// tiles in flight at any time stay those of a few neighbouring batch entries, which share operands
+// through L2.
+__device__ __forceinline__ long tile_at(int k) {
+  const int G = (int)gridDim.x;
+  int b = (int)blockIdx.x - k % G;
+  if (b < 0) b += G;
+  return (long)k * G + b;
+}
+
+// The product kernel is persistent: one CTA per SM walks the tiles of successive rounds (tile_at).
+// The stage ring and its barriers run on
 // across tiles, and TMEM changes hands through two more barriers: accf (the MMA thread's commit:
 // a tile's accumulators are complete) and acce (the epilogue's arrival: it has read them into
 // registers and the staging area).  So the producer's loads and the MMAs of tile j+1 overlap the
@@ -244,16 +262,21 @@ __global__ void __launch_bounds__(320, 1) k_tc_gemm(TcParams p, int n_tiles, int
     if (lane == 0) {
       long g = 0;  // stage counter across tiles
       bool ok = true;
-      for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
-        const int e = t / per_e, mblk = (t / NBt) % MBt, nblk = t % NBt;
+      for (int k = 0; ok; ++k) {
+        const long t = tile_at(k);
+        if (t >= n_tiles) break;
+        const int e = (int)(t / per_e), mblk = (int)((t / NBt) % MBt), nblk = (int)(t % NBt);
         if (p.active && !p.active[e]) continue;
         const long MB = p.M_pad / BM, NB = p.N_pad / BNC, nkb = p.nks / 2;
         const long ea = p.a_batched ? e : 0, eb = p.b_batched ? e : 0;
+        // rows taken from each 48-row sub-tile: all of them, or the last tile's first bn_last (a
+        // multiple of 8 rows = whole 256-byte swizzle groups, so the pair stays in the MMA layout)
+        const uint32_t sub = (uint32_t)(nblk == NBt - 1 ? p.bn_last : BNC) * BKS * 2;
         for (int ks = 0; ks < p.nks; ++ks, ++g) {
           const int s = (int)(g % NST);
           const uint32_t ph = (uint32_t)(g / NST) & 1u;
           if (!mbar_wait(&empty[s], ph ^ 1u, p.err)) { ok = false; break; }
-          mbar_expect_tx(&full[s], STAGE);
+          mbar_expect_tx(&full[s], S * (TILE_A + 2 * sub));
           unsigned char* st = base + s * STAGE;
           // K-stages [0, nkb) meet A's real parts: B rows (Re, Im); stages [nkb, 2 nkb) meet A's
           // imaginary parts: B rows (-Im, Re)
@@ -263,8 +286,8 @@ __global__ void __launch_bounds__(320, 1) k_tc_gemm(TcParams p, int n_tiles, int
             bulk_load(st + d * TILE_A, p.pa + (((ea * S + d) * MB + mblk) * p.nks + ks) * (long)TILE_A, TILE_A, &full[s]);
             const unsigned char* sb = p.pb + (((eb * S + d) * NB + nblk) * nkb + kb) * 3L * SUB_B;
             unsigned char* db = st + S * TILE_A + d * TILE_B;
-            bulk_load(db, sb + s0 * SUB_B, SUB_B, &full[s]);
-            bulk_load(db + SUB_B, sb + s1 * SUB_B, SUB_B, &full[s]);
+            bulk_load(db, sb + s0 * SUB_B, sub, &full[s]);
+            bulk_load(db + sub, sb + s1 * SUB_B, sub, &full[s]);
           }
         }
       }
@@ -275,9 +298,12 @@ __global__ void __launch_bounds__(320, 1) k_tc_gemm(TcParams p, int n_tiles, int
       long g = 0;
       int j = 0;  // tiles processed by this CTA
       bool ok = true;
-      for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
-        const int e = t / per_e;
+      for (int k = 0; ok; ++k) {
+        const long t = tile_at(k);
+        if (t >= n_tiles) break;
+        const int e = (int)(t / per_e);
         if (p.active && !p.active[e]) continue;
+        const uint32_t idesc = idesc_n(2 * (t % NBt == NBt - 1 ? p.bn_last : BNC));
         // TMEM is free once the epilogue has read the previous tile's accumulators
         if (!mbar_wait(acce, ((uint32_t)j & 1u) ^ 1u, p.err)) break;
         fence_after();
@@ -295,7 +321,7 @@ __global__ void __launch_bounds__(320, 1) k_tc_gemm(TcParams p, int n_tiles, int
               const int gacc = acc_of(i, jj);
               const uint64_t ad = sdesc(sa + (i - 1) * TILE_A);
               const uint64_t bd = sdesc(sa + S * TILE_A + (jj - 1) * TILE_B);
-              mma(tmem + gacc * ACC_COLS, ad, bd, (started >> gacc) & 1u);
+              mma(tmem + gacc * ACC_COLS, ad, bd, idesc, (started >> gacc) & 1u);
               started |= 1u << gacc;
             }
           }
@@ -313,9 +339,13 @@ __global__ void __launch_bounds__(320, 1) k_tc_gemm(TcParams p, int n_tiles, int
     const int r = q * 32 + lane;
     const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16);
     int j = 0;
-    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
-      const int e = t / per_e, mblk = (t / NBt) % MBt, nblk = t % NBt;
+    for (int k = 0;; ++k) {
+      const long t = tile_at(k);
+      if (t >= n_tiles) break;
+      const int e = (int)(t / per_e), mblk = (int)((t / NBt) % MBt), nblk = (int)(t % NBt);
       if (p.active && !p.active[e]) continue;
+      // complex columns of this tile: Re parts in TMEM columns [0, bn), Im parts in [bn, 2 bn)
+      const int bn = nblk == NBt - 1 ? p.bn_last : BNC;
       const int m = mblk * BM + r;
       const int eAm = p.eA[(long)(p.a_batched ? e : 0) * p.M_pad + m];
       // every epilogue thread is done with the previous tile's staging area and exponents
@@ -328,13 +358,14 @@ __global__ void __launch_bounds__(320, 1) k_tc_gemm(TcParams p, int n_tiles, int
       asm volatile("bar.sync 2, 256;" ::: "memory");
       if (!s_got) break;
       fence_after();
+      // the two warps of a lane quarter take alternate chunks of 8 columns
 #pragma unroll 1
-      for (int c0 = h * (BNC / 2); c0 < (h + 1) * (BNC / 2); c0 += 8) {
+      for (int c0 = 8 * h; c0 < bn; c0 += 16) {
         uint32_t vr[NACC][8], vi[NACC][8];
 #pragma unroll
         for (int gq = 0; gq < NACC; ++gq) {
           tmem_ld8(trow + gq * ACC_COLS + c0, vr[gq]);
-          tmem_ld8(trow + gq * ACC_COLS + BNC + c0, vi[gq]);
+          tmem_ld8(trow + gq * ACC_COLS + bn + c0, vi[gq]);
         }
         tmem_wait_ld();
 #pragma unroll
@@ -356,8 +387,8 @@ __global__ void __launch_bounds__(320, 1) k_tc_gemm(TcParams p, int n_tiles, int
       if (threadIdx.x == 64) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(acce)) : "memory");
       const cx<df>* C0e = p.C0 ? p.C0 + (long)e * p.sC0 : nullptr;
       cx<df>* Ce = p.C + (long)e * p.sC;
-      for (int idx = threadIdx.x - 64; idx < BM * BNC; idx += 256) {
-        const int rr = idx / BNC, cc = idx % BNC;
+      for (int idx = threadIdx.x - 64; idx < BM * bn; idx += 256) {
+        const int rr = idx / bn, cc = idx % bn;
         const int mm = mblk * BM + rr, nn = nblk * BNC + cc;
         if (mm < p.M && nn < p.N) {
           cx<df> v = out[rr * OUT_LD + cc];
@@ -506,6 +537,9 @@ __global__ void __launch_bounds__(32 * RPC) k_digitize_rows(const cx<df>* X, lon
   const long plane_bytes = side == 0 ? (rows_plane / BM) * nks * (long)TILE_A : (long)(R_pad / BNC) * nkb * 3 * SUB_B;
   unsigned char* pe = planes + (long)e * S * plane_bytes;
   const int nkc = K_pad / 8;
+  // rows whose planes are written: right-operand columns past N rounded up to 8 are never read (the
+  // last column tile's MMA takes only its first bn_last rows), so they stay unwritten
+  const int R_wr = side == 1 ? min(R_pad, (R + 7) / 8 * 8) : R_pad;
   // byte offset of the 16-byte chunk holding embedded k' .. k' + 7 (k' a multiple of 8) of row r (left)
   auto chunk_off = [&](long row, int kp) -> long {
     const long blk = row / BM, rr_ = row % BM, ks = kp / BKS, kk = kp % BKS;
@@ -519,7 +553,7 @@ __global__ void __launch_bounds__(32 * RPC) k_digitize_rows(const cx<df>* X, lon
 #pragma unroll 1
   for (int item = t; item < RPC * nkc; item += NT) {
     const int rr = item / nkc, kc = item % nkc, r = r0 + rr;
-    if (r >= R_pad) continue;
+    if (r >= R_wr) continue;
     // scale 2^(l1 - 1 - e_row) = 2^(P - 7 (S-1) - e_row), as two factors (e_row may be -1000)
     int Es = P - DW * (S - 1) - s_ex[rr];
     Es = Es < -250 ? -250 : (Es > 250 ? 250 : Es);
@@ -694,6 +728,8 @@ cudaError_t launch(const TcArgs& a, void* scratch, size_t scratch_bytes, int* er
     attr = true;
   }
   const int NBt = d.N_pad / BNC, MBt = d.M_pad / BM;
+  const int tail = a.N - (NBt - 1) * BNC;  // 1..48 complex columns in the last column tile
+  p.bn_last = (tail + 7) / 8 * 8;
   const long tiles = (long)NBt * MBt * a.batch;
   if (tiles > 0x7fffffffL) return cudaErrorInvalidValue;
   const int grid = (int)(tiles < sms ? tiles : sms);  // one CTA per SM (the kernel holds 230 KB of smem)

@@ -31,7 +31,11 @@ def _op(X, op):
     return X if op == "N" else np.conj(np.swapaxes(X, -1, -2))
 
 
-SHAPES = [(128, 64, 32, 1), (130, 70, 50, 3), (16, 16, 16, 4), (256, 256, 256, 2), (33, 200, 300, 2)]
+# N covers every kind of last column tile (48 columns per tile): 16 (64, 16, 256), 22 -> 24 (70),
+# 8 (200), a full 48 (96), 41 -> 48 and a single column; the last shape has 400 tiles, so the
+# persistent CTAs run several rounds and a partial one
+SHAPES = [(128, 64, 32, 1), (130, 70, 50, 3), (16, 16, 16, 4), (256, 256, 256, 2), (33, 200, 300, 2),
+          (64, 96, 48, 2), (40, 41, 24, 3), (17, 1, 16, 2), (256, 200, 64, 40)]
 
 
 @pytest.mark.parametrize("M,N,K,batch", SHAPES)
