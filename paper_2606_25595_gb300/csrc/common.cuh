@@ -72,11 +72,16 @@ __host__ __device__ __forceinline__ df df_split_fp64(double x) {
   return r;
 }
 __host__ __device__ __forceinline__ double df_sum_fp64(df a) { return (double)a.hi + (double)a.lo; }
+// The FP64 formulas for the rare operands the integer paths leave to them, kept out of line: inlined,
+// the compiler may if-convert them, and then every element issues their FP64 instructions (1/64 rate).
+static __device__ __noinline__ df df_split_fp64_rare(double x) { return df_split_fp64(x); }
+static __device__ __noinline__ double df_sum_fp64_rare(df a) { return df_sum_fp64(a); }
 
 __device__ __forceinline__ df df_split_int(double x) {
   const unsigned long long u = (unsigned long long)__double_as_longlong(x);
   const int e = (int)((u >> 52) & 0x7FF) - 1023;  // x = +-M 2^(e-52), M in [2^52, 2^53)
-  if (e < -74 || e > 126) return df_split_fp64(x);
+  if ((u << 1) == 0ull) return df{__uint_as_float((unsigned)(u >> 32)), 0.f};  // +-0: (+-0, +0)
+  if (e < -74 || e > 126) return df_split_fp64_rare(x);
   const unsigned long long M = (u & ((1ull << 52) - 1)) | (1ull << 52);
   unsigned long long q = M >> 29;  // hi's 24-bit significand, rounded to nearest even
   const unsigned long long rem = M & ((1ull << 29) - 1);
@@ -105,13 +110,15 @@ __device__ __forceinline__ df df_split_int(double x) {
 __device__ __forceinline__ double df_sum_int(df a) {
   const unsigned uh = __float_as_uint(a.hi), ul = __float_as_uint(a.lo);
   const int fh = (int)((uh >> 23) & 0xFF), fl = (int)((ul >> 23) & 0xFF);
-  if (fh == 0 || fh == 0xFF || fl == 0xFF || (fl == 0 && (ul & 0x7FFFFFu))) return df_sum_fp64(a);
+  if (((uh | ul) << 1) == 0u)  // both parts +-0: RN(hi + lo) is -0 only if both are
+    return __longlong_as_double((long long)((unsigned long long)(uh & ul & 0x80000000u) << 32));
+  if (fh == 0 || fh == 0xFF || fl == 0xFF || (fl == 0 && (ul & 0x7FFFFFu))) return df_sum_fp64_rare(a);
   const unsigned long long sh = uh >> 31;
   const unsigned long long hi_mant = (unsigned long long)(uh & 0x7FFFFFu) << 29;
   if (fl == 0)  // lo = +-0: hi itself
     return __longlong_as_double((long long)((sh << 63) | ((unsigned long long)(fh - 127 + 1023) << 52) | hi_mant));
   const int d = fh - fl;
-  if (d < 23 || d > 100) return df_sum_fp64(a);
+  if (d < 23 || d > 100) return df_sum_fp64_rare(a);
   const long long Mh = (long long)((uh & 0x7FFFFFu) | 0x800000u);
   const long long Ml = (long long)((ul & 0x7FFFFFu) | 0x800000u);
   const long long sMl = (ul >> 31) == sh ? Ml : -Ml;
