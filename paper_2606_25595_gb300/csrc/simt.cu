@@ -510,10 +510,10 @@ __global__ void k_assemble_diag(cx<T>* out, const cx<double>* H, const cx<double
                                 const cx<double>* SigR, long sSig, const cx<double>* lead,
                                 long sLead, const double* E, double eta, int b) {
   const int e = blockIdx.y;
-  const long bb = (long)b * b;
+  const int bb = b * b;  // b <= 4096: 32-bit indices (no 64-bit division per element)
   const double Er = E[e];
-  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < bb; idx += (long)gridDim.x * blockDim.x) {
-    const int r = (int)(idx / b), c = (int)(idx % b);
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < bb; idx += gridDim.x * blockDim.x) {
+    const int r = idx / b, c = idx - r * b;
     if constexpr (std::is_same<T, df>::value) {
       if (!S) {  // df32 arithmetic on the exactly split inputs: no FP64 operations
         df vr = r == c ? from_d<df>(Er) : mkdf(0.f, 0.f), vi = r == c ? from_d<df>(eta) : mkdf(0.f, 0.f);
