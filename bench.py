@@ -55,7 +55,7 @@ def parse():
                          "uneven: 8 devices x 128 energies in one CUDA graph; ozaki: b=1024 N_B=32 "
                          "emulated FP64 (subset of the 256 energies); serving: Poisson request stream; "
                          "nrl: b=3408 N_B=10 (the paper's NR-L shape), per-energy self-energies streamed from host; "
-                         "wsolve: screened-Coulomb system b=256 N_B=32, 64 energies (assembly + two selected solves)")
+                         "wsolve: screened-Coulomb system b=256 N_B=32, 64 energies (assembly + one selected solve for B^< and B^>)")
     ap.add_argument("--requests", type=int, default=40)
     ap.add_argument("--refine-tol", type=float, default=2.0 ** -13,
                     help="mixed workloads: an energy stops its Newton sweeps once ||I - A X||_F <= this "
@@ -350,8 +350,9 @@ def run_nrl(args, q, W):
 
 def run_wsolve(args, q, W):
     """Screened-Coulomb system (Table I, W row): per step, assemble M = I - V P^R and B^<> = V P^<>
-    V^H for all energies and solve M X M^H = B^< and B^> (two selected solves sharing M).  Error
-    against the oracle on a small system of the same generator (b=64, N_B=6, 2 energies)."""
+    V^H for all energies and solve M X M^H = B^< and B^> (one selected solve with two right-hand
+    sides sharing the retarded sweep).  Error against the oracle on a small system of the same
+    generator (b=64, N_B=6, 2 energies)."""
     import time
     import numpy as np
     import torch
@@ -393,7 +394,7 @@ def run_wsolve(args, q, W):
     peaks, _ = measured_peaks()
     ach = prof["pipe_flops"] / (prof["ms"] / 1e3) / 1e12 if prof["ms"] else None
     _line(args, value, ms / args.steps, f"screened-Coulomb system b={b} N_B={nb}, {ne} energies per step "
-          "(assembly of M = I - V P^R, B^<> = V P^<> V^H and two selected solves; inputs resident)",
+          "(assembly of M = I - V P^R, B^<> = V P^<> V^H and the selected solve for B^< and B^>; inputs resident)",
           args.precision,
           {"status_ok": status_ok, "wall_s_per_step": wall / args.steps, "gpu_launches": int(launches),
            "product_kernel_share": prof["ms"] / ms if ms else None,

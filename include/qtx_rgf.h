@@ -118,12 +118,20 @@ typedef struct {
                                   blocks come in SigL_diag (and SigL_upper with offdiag_sigma), H, S,
                                   Sigma^R, eta and the energies' values are not used.  Needs has_S = 0,
                                   leads = 0, sigma_stream = 0; GR_* outputs are the BT blocks of M^-1,
-                                  GL_* those of X; GG_*, current, contact, transmission and integrals
-                                  are not produced (their bits must be clear); density = Im Tr X_ii */
+                                  GL_* those of X; GG_* (unless second_rhs), current, contact,
+                                  transmission and integrals are not produced (their bits must be
+                                  clear); density = Im Tr X_ii */
   double refine_tol;           /* QTX_EMU64 / QTX_BF16X3: an energy stops its Newton sweeps once the
                                   Frobenius norm of its residual I - A X is at most refine_tol (the
                                   next iterate's residual is then at most refine_tol^2); 0 = always
                                   refine_max_iter sweeps */
+  int second_rhs;              /* 1 (needs system_input, not storage_bits): the solve takes a second
+                                  right-hand side B2 in SigG_diag (and SigG_upper with offdiag_sigma)
+                                  and writes the BT blocks of M^-1 B2 M^-H to GG_diag / GG_upper,
+                                  sharing the retarded sweep (the inverses and the G^R blocks) with
+                                  the first right-hand side -- e.g. X^> of the W system from B^>
+                                  alongside X^< from B^<.  The plan then keeps one more set of
+                                  left-connected blocks (N_B blocks per energy in flight) */
 } qtx_rgf_desc;
 
 /* Device inputs (caller-owned, complex128 unless noted). */
@@ -151,6 +159,9 @@ typedef struct {
   const void *M_diag;      /* system_input: M_ii [N_E][N_B][b][b] */
   const void *M_upper;     /* system_input: M_{i,i+1} [N_E][N_B-1][b][b] */
   const void *M_lower;     /* system_input: M_{i+1,i} [N_E][N_B-1][b][b] */
+  const void *SigG_diag;   /* second_rhs: B2_ii, the layout of SigL_diag */
+  const void *SigG_upper;  /* second_rhs with offdiag_sigma: B2_{i,i+1}, the layout of SigL_upper;
+                              B2_{i+1,i} = -(B2_{i,i+1})^H */
 } qtx_rgf_inputs;
 
 /* Device outputs (caller-owned; NULL = not produced).  Layouts as in QTX_OUT_*. */
@@ -206,7 +217,8 @@ typedef struct {
   void *BG_diag, *BG_upper;                  /* B^> (NULL when PG_* are NULL) */
 } qtx_w_outputs;
 /* Uses the plan's workspace (any plan with this b, enough slices, and the wanted precision; a
- * system_input plan can then solve for X^R and X^< from M and B^<, and again with B^> for X^>).
+ * system_input plan can then solve for X^R and X^< from M and B^<, and with second_rhs for X^> from
+ * B^> in the same solve).
  * Asynchronous on `stream`.  Errors: QTX_ERR_INVALID_ARG (NULL required pointers, n_blocks beyond
  * the plan's), QTX_ERR_CUDA. */
 qtx_status qtx_w_assemble(qtx_rgf_plan plan, const qtx_w_inputs *in, const qtx_w_outputs *out, void *stream);

@@ -50,7 +50,7 @@ class Desc(ctypes.Structure):
                 ("decim_max_iter", ctypes.c_int), ("outputs", ctypes.c_uint),
                 ("offdiag_sigma", ctypes.c_int), ("storage_bits", ctypes.c_int),
                 ("sigma_stream", ctypes.c_int), ("system_input", ctypes.c_int),
-                ("refine_tol", ctypes.c_double)]
+                ("refine_tol", ctypes.c_double), ("second_rhs", ctypes.c_int)]
 
 
 class Inputs(ctypes.Structure):
@@ -64,7 +64,8 @@ class Inputs(ctypes.Structure):
                 ("weights", ctypes.c_void_p), ("n_energies", ctypes.c_int),
                 ("n_blocks", ctypes.c_int), ("SigR_upper", ctypes.c_void_p),
                 ("SigR_lower", ctypes.c_void_p), ("SigL_upper", ctypes.c_void_p),
-                ("M_diag", ctypes.c_void_p), ("M_upper", ctypes.c_void_p), ("M_lower", ctypes.c_void_p)]
+                ("M_diag", ctypes.c_void_p), ("M_upper", ctypes.c_void_p), ("M_lower", ctypes.c_void_p),
+                ("SigG_diag", ctypes.c_void_p), ("SigG_upper", ctypes.c_void_p)]
 
 
 class WInputs(ctypes.Structure):
@@ -148,7 +149,7 @@ def make_desc(n_blocks, block_size, precision="fp64", max_energies_in_flight=64,
               refine_max_iter=2, has_S=False, has_scattering=True, energy_dependent_sigma=False,
               leads=False, decim_tol=1e-13, decim_max_iter=100, outputs=None,
               offdiag_sigma=False, storage_bits=0, sigma_stream=False, system_input=False,
-              refine_tol=0.0) -> Desc:
+              refine_tol=0.0, second_rhs=False) -> Desc:
     if outputs is None:
         outputs = (1 << 12) - 1
     elif not isinstance(outputs, int):
@@ -161,7 +162,8 @@ def make_desc(n_blocks, block_size, precision="fp64", max_energies_in_flight=64,
                 int(refine_max_iter), int(bool(has_S)), int(bool(has_scattering)),
                 int(bool(energy_dependent_sigma)), int(bool(leads)), float(decim_tol),
                 int(decim_max_iter), int(outputs), int(bool(offdiag_sigma)), int(storage_bits),
-                int(bool(sigma_stream)), int(bool(system_input)), float(refine_tol))
+                int(bool(sigma_stream)), int(bool(system_input)), float(refine_tol),
+                int(bool(second_rhs)))
 
 
 def kernel_launches() -> int:
@@ -228,8 +230,8 @@ class WSystem:
     """Screened-Coulomb system (Table I, W row) resident on the GPU: the inputs of a
     ``workloads.w_system`` dict uploaded once, a system_input plan, and the assembled and solved
     blocks.  ``run()`` assembles M = I - V P^R and B^<> = V P^<> V^H (BT blocks, ``qtx_w_assemble``)
-    and solves M X M^H = B twice -- with B^< (X^R = BT blocks of M^-1, X^<) and with B^> (X^>).
-    Marshalling only."""
+    and solves M X M^H = B for X^R (BT blocks of M^-1) and X^< from B^<, and X^> from B^> as the
+    plan's second right-hand side, in one solve that shares the retarded sweep.  Marshalling only."""
 
     def __init__(self, w: dict, precision: str = "emu64", max_energies_in_flight=64, greater=True):
         import torch
@@ -256,37 +258,38 @@ class WSystem:
             self.res.update(BG_diag=E(ne, nb, b, b), BG_upper=E(ne, nu, b, b))
         for k, v in self.res.items():
             setattr(self.wout, k, v.data_ptr() if v.numel() else None)
-        outs = ["GR_diag", "GR_upper", "GR_lower", "GL_diag", "GL_upper"]
+        outs = ["GR_diag", "GR_upper", "GR_lower", "GL_diag", "GL_upper"] + \
+            (["GG_diag", "GG_upper"] if greater else [])
         self.plan = Plan(make_desc(nb, b, precision, min(max_energies_in_flight, ne), 2, has_scattering=True,
                                    energy_dependent_sigma=True, offdiag_sigma=nb > 1, system_input=True,
-                                   outputs=outs))
+                                   outputs=outs, second_rhs=greater))
         self.energies = torch.zeros(ne, dtype=torch.float64, device=cd)
         self.res["status"] = torch.zeros(ne, dtype=torch.int32, device=cd)
-        self._solves = []
-        pairs = [("BL", [("GR_diag", "XR_diag"), ("GR_upper", "XR_upper"), ("GR_lower", "XR_lower"),
-                         ("GL_diag", "XL_diag"), ("GL_upper", "XL_upper")])]
+        keys = [("GR_diag", "XR_diag"), ("GR_upper", "XR_upper"), ("GR_lower", "XR_lower"),
+                ("GL_diag", "XL_diag"), ("GL_upper", "XL_upper")]
         if greater:
-            pairs.append(("BG", [("GL_diag", "XG_diag"), ("GL_upper", "XG_upper")]))
-        for rhs, keys in pairs:
-            inp = Inputs()
-            inp.M_diag = self.res["M_diag"].data_ptr()
-            inp.M_upper = self.res["M_upper"].data_ptr() if nu else None
-            inp.M_lower = self.res["M_lower"].data_ptr() if nu else None
-            inp.SigL_diag = self.res[rhs + "_diag"].data_ptr()
-            inp.SigL_upper = self.res[rhs + "_upper"].data_ptr() if nu else None
-            inp.energies, inp.n_energies, inp.n_blocks = self.energies.data_ptr(), ne, nb
-            o = Outputs()
-            for name, key in keys:
-                self.res[key] = E(ne, nb if "diag" in name else nu, b, b)
-                setattr(o, name, self.res[key].data_ptr() if self.res[key].numel() else None)
-            o.status_per_energy = self.res["status"].data_ptr()
-            self._solves.append((inp, o))
+            keys += [("GG_diag", "XG_diag"), ("GG_upper", "XG_upper")]
+        inp = Inputs()
+        inp.M_diag = self.res["M_diag"].data_ptr()
+        inp.M_upper = self.res["M_upper"].data_ptr() if nu else None
+        inp.M_lower = self.res["M_lower"].data_ptr() if nu else None
+        inp.SigL_diag = self.res["BL_diag"].data_ptr()
+        inp.SigL_upper = self.res["BL_upper"].data_ptr() if nu else None
+        if greater:
+            inp.SigG_diag = self.res["BG_diag"].data_ptr()
+            inp.SigG_upper = self.res["BG_upper"].data_ptr() if nu else None
+        inp.energies, inp.n_energies, inp.n_blocks = self.energies.data_ptr(), ne, nb
+        o = Outputs()
+        for name, key in keys:
+            self.res[key] = E(ne, nb if "diag" in name else nu, b, b)
+            setattr(o, name, self.res[key].data_ptr() if self.res[key].numel() else None)
+        o.status_per_energy = self.res["status"].data_ptr()
+        self._solve = (inp, o)
 
     def run(self, stream=None):
         st = _stream(stream)
         self.plan.w_assemble(self.win, self.wout, st)
-        for inp, o in self._solves:
-            self.plan.solve(inp, o, st)
+        self.plan.solve(*self._solve, st)
 
     def results(self) -> dict:
         import torch

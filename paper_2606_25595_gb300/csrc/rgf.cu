@@ -44,7 +44,7 @@ inline bool uv_per_energy(const qtx_rgf_desc& d) {
 }
 
 struct Layout {
-  size_t g, gl, gfx, glfx, fx_slot, sig_stage, opnd[3], opnd_bytes[3], refine_act, tmp, inv_tmp, U, V, ident, ident_df, ref, f32a, f32tmp, dec, lead, obs, flags,
+  size_t g, gl, gl2, gfx, glfx, fx_slot, sig_stage, opnd[3], opnd_bytes[3], refine_act, tmp, inv_tmp, U, V, ident, ident_df, ref, f32a, f32tmp, dec, lead, obs, flags,
       tc_scratch, total;
   int n_tmp, n_dec;
   size_t tc_bytes;
@@ -93,7 +93,8 @@ Layout make_layout(const qtx_rgf_desc& d) {
   const size_t bb = (size_t)b * b;
   const size_t es = d.precision == QTX_FP32 ? sizeof(cx<float>) : sizeof(cx<double>);
   Arena a;
-  L.n_tmp = d.offdiag_sigma ? 14 : 12;  // 12, 13: Sigma^<_{i,i+1} in the sweep's type and g_i Sigma^<_{i,i+1}
+  // 12, 13: Sigma^<_{i,i+1} in the sweep's type and g_i Sigma^<_{i,i+1}; 14: g_i B2_{i,i+1} (second_rhs)
+  L.n_tmp = d.offdiag_sigma ? (d.second_rhs ? 15 : 14) : 12;
   if (d.storage_bits) {
     // two working blocks per kind in the sweep's type (slices i and i-1 / i+1), every slice's
     // left-connected blocks in FPX: a slot of fx_slot bytes per slice and kind
@@ -106,6 +107,7 @@ Layout make_layout(const qtx_rgf_desc& d) {
     L.g = a.take(nb * Ec * bb * es);
     L.gl = a.take(nb * Ec * bb * es);
   }
+  L.gl2 = a.take(d.second_rhs ? nb * Ec * bb * es : 0);  // left-connected blocks of the second right-hand side
   L.tmp = a.take((size_t)L.n_tmp * Ec * bb * es);
   L.sig_stage = a.take(d.sigma_stream ? 2 * Ec * bb * sizeof(cx<double>) : 0);  // Sigma^R_ii, Sigma^<_ii
   L.inv_tmp = a.take(Ec * bb * es + 4096);
@@ -167,6 +169,8 @@ struct Ctx {
   // left-connected / full blocks of slice i: slot i, or with FPX storage working block i % 2
   cx<T>* g(int i) const { return blk(P->L.g, P->d.storage_bits ? i % 2 : i); }
   cx<T>* gl(int i) const { return blk(P->L.gl, P->d.storage_bits ? i % 2 : i); }
+  // lesser-type blocks of right-hand side k (k = 1: second_rhs, never FPX-stored)
+  cx<T>* glk(int k, int i) const { return k ? blk(P->L.gl2, i) : gl(i); }
   void* gfx(int i) const { return P->ws + P->L.gfx + (size_t)i * P->L.fx_slot; }
   void* glfx(int i) const { return P->ws + P->L.glfx + (size_t)i * P->L.fx_slot; }
 };
@@ -501,6 +505,10 @@ qtx_status solve_chunk(qtx_rgf_plan_s* P, const qtx_rgf_inputs* in, const qtx_rg
   const long sigE0 = d.energy_dependent_sigma ? (long)e0 * nb * bb : 0;
   auto sigR = [&](int i) { return SRd ? SRd + sigE0 + (long)i * bb : nullptr; };
   auto sigL = [&](int i) { return SLd ? SLd + sigE0 + (long)i * bb : nullptr; };
+  // second right-hand side (second_rhs): B2 in the layout of Sigma^<
+  const int nrhs = d.second_rhs ? 2 : 1;
+  const cx<double>* SGd = d.second_rhs ? reinterpret_cast<const cx<double>*>(in->SigG_diag) : nullptr;
+  auto sigG = [&](int i) { return SGd ? SGd + sigE0 + (long)i * bb : nullptr; };
   // off-diagonal scattering blocks [N_E or 1][N_B-1][b][b]
   const bool odg = d.offdiag_sigma && nb > 1;
   const long sSigU = d.energy_dependent_sigma ? (long)(nb - 1) * bb : 0;
@@ -508,12 +516,14 @@ qtx_status solve_chunk(qtx_rgf_plan_s* P, const qtx_rgf_inputs* in, const qtx_rg
   const cx<double>* SRu = odg && !d.system_input ? reinterpret_cast<const cx<double>*>(in->SigR_upper) + sigUE0 : nullptr;
   const cx<double>* SRl = odg && !d.system_input ? reinterpret_cast<const cx<double>*>(in->SigR_lower) + sigUE0 : nullptr;
   const cx<double>* SLu = odg ? reinterpret_cast<const cx<double>*>(in->SigL_upper) + sigUE0 : nullptr;
+  const cx<double>* SGu = odg && d.second_rhs ? reinterpret_cast<const cx<double>*>(in->SigG_upper) + sigUE0 : nullptr;
   // Sigma^<_{i,i+1} in the sweep's type (tmp 12): one block shared by the chunk, or one per energy
   const int nLt = d.energy_dependent_sigma ? ne : 1;
   const long sLt = d.energy_dependent_sigma ? bb : 0;
-  auto load_L = [&](int i) -> cx<T>* {
+  // right-hand side k's upper block of slice i (k = 1: B2_{i,i+1})
+  auto load_L = [&](int k, int i) -> cx<T>* {
     cx<T>* Lt = c.tmp(12);
-    if (axpby_from64<T>(Lt, bb, SLu + (long)i * bb, sSigU, 1.0, nullptr, 0, 0.0, b, nLt, st) != cudaSuccess) return nullptr;
+    if (axpby_from64<T>(Lt, bb, (k ? SGu : SLu) + (long)i * bb, sSigU, 1.0, nullptr, 0, 0.0, b, nLt, st) != cudaSuccess) return nullptr;
     return Lt;
   };
   qtx_status s;
@@ -599,42 +609,47 @@ qtx_status solve_chunk(qtx_rgf_plan_s* P, const qtx_rgf_inputs* in, const qtx_rg
       if ((s = gemm<T>(P, gargs<T>(b, b, b, V(i - 1), b, sUV, OP_N, Tm, b, bb, OP_N, gi, b, bb, gi, b, bb, -1.0, 1.0, ne, nullptr), st))) return s;
     }
     if ((s = block_inverse<T>(P, gi, b, ne, nullptr, status, st))) return s;
-    // Sigma^<_ii (+ contacts), then the left-connected lesser function
-    cx<T>* SLi = c.tmp(1);
-    const cx<double>* sl = sLi;
-    const cx<double>* lsl = nullptr;
-    if (d.leads && i == 0) lsl = SL_L;
-    else if (d.leads && i == nb - 1) lsl = SL_R;
-    if (sl) QTX_CK(axpby_from64<T>(SLi, bb, sl, sS, 1.0, lsl, bb, 1.0, b, ne, st));
-    else if (lsl) QTX_CK(axpby_from64<T>(SLi, bb, lsl, bb, 1.0, nullptr, 0, 0.0, b, ne, st));
-    else QTX_CK(cudaMemsetAsync(SLi, 0, (size_t)ne * bb * sizeof(cx<T>), st));
-    if (d.leads && nb == 1) {
-      QTX_CK(axpby_from64<T>(c.tmp(2), bb, SL_R, bb, 1.0, nullptr, 0, 0.0, b, ne, st));
-      Term<T> t0; t0.p = SLi; t0.s = bb; t0.alpha = 1.0;
-      Term<T> t1; t1.p = c.tmp(2); t1.s = bb; t1.alpha = 1.0;
-      QTX_CK((combine<T, T>(SLi, bb, t0, t1, none, b, ne, nullptr, 0, 0, nullptr, st)));
-    }
-    if (i > 0) {
-      cx<T>* X = c.tmp(0);
-      if ((s = gemm<T>(P, gargs<T>(b, b, b, V(i - 1), b, sUV, OP_N, c.gl(i - 1), b, bb, OP_N, nullptr, 0, 0, X, b, bb, 1.0, 0.0, ne, nullptr), st))) return s;
-      if ((s = gemm<T>(P, gargs<T>(b, b, b, X, b, bb, OP_N, V(i - 1), b, sUV, OP_C, SLi, b, bb, SLi, b, bb, 1.0, 1.0, ne, nullptr), st))) return s;
-      if (odg) {  // block-tridiagonal Sigma^<: bracket += -Y + Y^H, Y = V_{i-1} g_{i-1} Sigma^<_{i-1,i}
-        cx<T>* Zf = c.tmp(2);
-        cx<T>* Yf = c.tmp(3);
-        cx<T>* Lt = load_L(i - 1);
-        if (!Lt) return QTX_ERR_CUDA;
-        if ((s = gemm<T>(P, gargs<T>(b, b, b, V(i - 1), b, sUV, OP_N, c.g(i - 1), b, bb, OP_N, nullptr, 0, 0, Zf, b, bb, 1.0, 0.0, ne, nullptr), st))) return s;
-        if ((s = gemm<T>(P, gargs<T>(b, b, b, Zf, b, bb, OP_N, Lt, b, sLt, OP_N, nullptr, 0, 0, Yf, b, bb, 1.0, 0.0, ne, nullptr), st))) return s;
+    // block-tridiagonal right-hand sides: V_{i-1} g_{i-1} of the cross term, shared by both
+    cx<T>* Zf = c.tmp(2);
+    if (i > 0 && odg &&
+        (s = gemm<T>(P, gargs<T>(b, b, b, V(i - 1), b, sUV, OP_N, c.g(i - 1), b, bb, OP_N, nullptr, 0, 0, Zf, b, bb, 1.0, 0.0, ne, nullptr), st)))
+      return s;
+    for (int k = 0; k < nrhs; ++k) {
+      // Sigma^<_ii (+ contacts; or B2_ii), then the left-connected lesser function of right-hand side k
+      cx<T>* SLi = c.tmp(1);
+      const cx<double>* sl = k ? sigG(i) : sLi;
+      const cx<double>* lsl = nullptr;
+      if (k == 0 && d.leads && i == 0) lsl = SL_L;
+      else if (k == 0 && d.leads && i == nb - 1) lsl = SL_R;
+      if (sl) QTX_CK(axpby_from64<T>(SLi, bb, sl, sS, 1.0, lsl, bb, 1.0, b, ne, st));
+      else if (lsl) QTX_CK(axpby_from64<T>(SLi, bb, lsl, bb, 1.0, nullptr, 0, 0.0, b, ne, st));
+      else QTX_CK(cudaMemsetAsync(SLi, 0, (size_t)ne * bb * sizeof(cx<T>), st));
+      if (k == 0 && d.leads && nb == 1) {
+        QTX_CK(axpby_from64<T>(c.tmp(2), bb, SL_R, bb, 1.0, nullptr, 0, 0.0, b, ne, st));
         Term<T> t0; t0.p = SLi; t0.s = bb; t0.alpha = 1.0;
-        Term<T> t1; t1.p = Yf; t1.s = bb; t1.alpha = -1.0;
-        Term<T> t2; t2.p = Yf; t2.s = bb; t2.alpha = 1.0; t2.op = OP_C;
-        QTX_CK((combine<T, T>(SLi, bb, t0, t1, t2, b, ne, nullptr, 0, 0, nullptr, st)));
+        Term<T> t1; t1.p = c.tmp(2); t1.s = bb; t1.alpha = 1.0;
+        QTX_CK((combine<T, T>(SLi, bb, t0, t1, none, b, ne, nullptr, 0, 0, nullptr, st)));
       }
-    }
-    cx<T>* Y = c.tmp(0);
-    if ((s = gemm<T>(P, gargs<T>(b, b, b, gi, b, bb, OP_N, SLi, b, bb, OP_N, nullptr, 0, 0, Y, b, bb, 1.0, 0.0, ne, nullptr), st,
-                     false, keepA(1)))) return s;
-    if ((s = gemm<T>(P, gargs<T>(b, b, b, Y, b, bb, OP_N, gi, b, bb, OP_C, nullptr, 0, 0, c.gl(i), b, bb, 1.0, 0.0, ne, nullptr), st))) return s;
+      if (i > 0) {
+        cx<T>* X = c.tmp(0);
+        if ((s = gemm<T>(P, gargs<T>(b, b, b, V(i - 1), b, sUV, OP_N, c.glk(k, i - 1), b, bb, OP_N, nullptr, 0, 0, X, b, bb, 1.0, 0.0, ne, nullptr), st))) return s;
+        if ((s = gemm<T>(P, gargs<T>(b, b, b, X, b, bb, OP_N, V(i - 1), b, sUV, OP_C, SLi, b, bb, SLi, b, bb, 1.0, 1.0, ne, nullptr), st))) return s;
+        if (odg) {  // block-tridiagonal Sigma^<: bracket += -Y + Y^H, Y = V_{i-1} g_{i-1} Sigma^<_{i-1,i}
+          cx<T>* Yf = c.tmp(3);
+          cx<T>* Lt = load_L(k, i - 1);
+          if (!Lt) return QTX_ERR_CUDA;
+          if ((s = gemm<T>(P, gargs<T>(b, b, b, Zf, b, bb, OP_N, Lt, b, sLt, OP_N, nullptr, 0, 0, Yf, b, bb, 1.0, 0.0, ne, nullptr), st))) return s;
+          Term<T> t0; t0.p = SLi; t0.s = bb; t0.alpha = 1.0;
+          Term<T> t1; t1.p = Yf; t1.s = bb; t1.alpha = -1.0;
+          Term<T> t2; t2.p = Yf; t2.s = bb; t2.alpha = 1.0; t2.op = OP_C;
+          QTX_CK((combine<T, T>(SLi, bb, t0, t1, t2, b, ne, nullptr, 0, 0, nullptr, st)));
+        }
+      }
+      cx<T>* Y = c.tmp(0);
+      if ((s = gemm<T>(P, gargs<T>(b, b, b, gi, b, bb, OP_N, SLi, b, bb, OP_N, nullptr, 0, 0, Y, b, bb, 1.0, 0.0, ne, nullptr), st,
+                       false, k ? reuseA(1) : keepA(1)))) return s;
+      if ((s = gemm<T>(P, gargs<T>(b, b, b, Y, b, bb, OP_N, gi, b, bb, OP_C, nullptr, 0, 0, c.glk(k, i), b, bb, 1.0, 0.0, ne, nullptr), st))) return s;
+    }  // right-hand sides
     // FPX storage: slices the backward sweep reads back from memory (the last two stay in the
     // working blocks) are kept compressed
     if (d.storage_bits && i < nb - 2) {
@@ -660,7 +675,10 @@ qtx_status solve_chunk(qtx_rgf_plan_s* P, const qtx_rgf_inputs* in, const qtx_rg
     const int i = nb - 1;
     if (want(QTX_OUT_GR_DIAG, out->GR_diag) && (s = emit<T>(P, out->GR_diag, nb, i, e0, c.g(i), b, ne, st))) return s;
     if (want(QTX_OUT_GL_DIAG, out->GL_diag) && (s = emit<T>(P, out->GL_diag, nb, i, e0, c.gl(i), b, ne, st))) return s;
-    if (want(QTX_OUT_GG_DIAG, out->GG_diag) && (s = emit<T>(P, out->GG_diag, nb, i, e0, c.gl(i), b, ne, st, c.g(i), c.g(i)))) return s;
+    if (want(QTX_OUT_GG_DIAG, out->GG_diag) &&
+        (s = d.second_rhs ? emit<T>(P, out->GG_diag, nb, i, e0, c.glk(1, i), b, ne, st)
+                          : emit<T>(P, out->GG_diag, nb, i, e0, c.gl(i), b, ne, st, c.g(i), c.g(i))))
+      return s;
     QTX_CK(obs_density<T>(den + i, nb, c.gl(i), bb, b, ne, st));
     if (d.leads) {  // right contact current on slice N_B-1:  G^> = G^< + G^R - G^A
       cx<T>* GG = c.tmp(0);
@@ -673,7 +691,6 @@ qtx_status solve_chunk(qtx_rgf_plan_s* P, const qtx_rgf_inputs* in, const qtx_rg
   }
   for (int i = nb - 2; i >= 0; --i) {
     cx<T>* GRn = c.g(i + 1);
-    cx<T>* GLn = c.gl(i + 1);
     cx<T>* Pm = c.tmp(2);
     cx<T>* Z = c.tmp(3);
     cx<T>* GRl = c.tmp(4);
@@ -684,10 +701,9 @@ qtx_status solve_chunk(qtx_rgf_plan_s* P, const qtx_rgf_inputs* in, const qtx_rg
     cx<T>* X2 = c.tmp(9);
     cx<T>* GLu = c.tmp(10);
     cx<T>* gi = c.g(i);
-    cx<T>* gli = c.gl(i);
     if (d.storage_bits && i < nb - 2) {  // g_i, g^<_i back from FPX into the working blocks
       QTX_CK(fpx_load<T>(d.storage_bits, c.gfx(i), (long)ne * bb, gi, st));
-      QTX_CK(fpx_load<T>(d.storage_bits, c.glfx(i), (long)ne * bb, gli, st));
+      QTX_CK(fpx_load<T>(d.storage_bits, c.glfx(i), (long)ne * bb, c.gl(i), st));
     }
     auto MM = [&](const cx<T>* A, long sA_, int opA, const cx<T>* B, long sB_, int opB, const cx<T>* C0, cx<T>* C, double al, double be,
                   DigitHint h = DigitHint{}) {
@@ -699,44 +715,59 @@ qtx_status solve_chunk(qtx_rgf_plan_s* P, const qtx_rgf_inputs* in, const qtx_rg
     x2.a_slot = 1; x2.a_mode = DG_REUSE; x2.b_slot = 2; x2.b_mode = DG_REUSE;
     if ((s = MM(gi, bb, OP_N, U(i), sUV, OP_N, nullptr, Pm, 1.0, 0.0))) return s;
     if ((s = MM(V(i), sUV, OP_N, gi, bb, OP_N, nullptr, Z, 1.0, 0.0))) return s;
-    cx<T>* Rl = odg ? c.tmp(13) : nullptr;  // block-tridiagonal Sigma^<: g_i Sigma^<_{i,i+1} (g_i still left-connected)
+    // block-tridiagonal right-hand side k: g_i L_k with L_k its upper block (g_i still left-connected)
+    auto Rl = [&](int k) { return odg ? c.tmp(13 + k) : nullptr; };
     if (odg) {
-      cx<T>* Lt = load_L(i);
-      if (!Lt) return QTX_ERR_CUDA;
-      if ((s = MM(gi, bb, OP_N, Lt, sLt, OP_N, nullptr, Rl, 1.0, 0.0))) return s;
+      for (int k = 0; k < nrhs; ++k) {
+        cx<T>* Lt = load_L(k, i);
+        if (!Lt) return QTX_ERR_CUDA;
+        if ((s = MM(gi, bb, OP_N, Lt, sLt, OP_N, nullptr, Rl(k), 1.0, 0.0))) return s;
+      }
     }
     if ((s = MM(GRn, bb, OP_N, Z, bb, OP_N, nullptr, GRl, -1.0, 0.0, keepA(1)))) return s;
     if ((s = MM(Pm, bb, OP_N, GRn, bb, OP_N, nullptr, GRu, -1.0, 0.0, keepA(0)))) return s;
     if ((s = MM(Pm, bb, OP_N, GRl, bb, OP_N, gi, gi, -1.0, 1.0, reuseA(0)))) return s;   // g_i <- G_ii
-    if ((s = MM(V(i), sUV, OP_N, gli, bb, OP_N, nullptr, Q, 1.0, 0.0))) return s;
-    if (odg) {  // Q = V_i g^<_i + (g_i Sigma^<_{i,i+1})^H
-      Term<T> t0; t0.p = Q; t0.s = bb; t0.alpha = 1.0;
-      Term<T> t1; t1.p = Rl; t1.s = bb; t1.alpha = 1.0; t1.op = OP_C;
-      QTX_CK((combine<T, T>(Q, bb, t0, t1, none, b, ne, nullptr, 0, 0, nullptr, st)));
-    }
-    if ((s = MM(GRu, bb, OP_N, Q, bb, OP_N, nullptr, K, -1.0, 0.0, keepB(2)))) return s;
-    if ((s = MM(Pm, bb, OP_N, GLn, bb, OP_N, nullptr, PGL, 1.0, 0.0, reuseA(0)))) return s;
-    if ((s = MM(PGL, bb, OP_N, Pm, bb, OP_C, gli, gli, 1.0, 1.0))) return s;   // g^<_i + PGL P^H
-    if ((s = MM(GRn, bb, OP_N, Q, bb, OP_N, nullptr, X2, 1.0, 0.0, x2))) return s;
-    {
-      Term<T> t0; t0.p = gli; t0.s = bb; t0.alpha = 1.0;
-      Term<T> t1; t1.p = K; t1.s = bb; t1.alpha = 1.0;
-      Term<T> t2; t2.p = K; t2.s = bb; t2.alpha = -1.0; t2.op = OP_C;
-      QTX_CK((combine<T, T>(gli, bb, t0, t1, t2, b, ne, nullptr, 0, 0, nullptr, st)));   // G^<_ii
-      Term<T> u0; u0.p = PGL; u0.s = bb; u0.alpha = -1.0;
-      Term<T> u1; u1.p = X2; u1.s = bb; u1.alpha = 1.0; u1.op = OP_C;
-      QTX_CK((combine<T, T>(GLu, bb, u0, u1, none, b, ne, nullptr, 0, 0, nullptr, st)));  // G^<_{i,i+1}
-    }
     if (want(QTX_OUT_GR_DIAG, out->GR_diag) && (s = emit<T>(P, out->GR_diag, nb, i, e0, gi, b, ne, st))) return s;
     if (want(QTX_OUT_GR_UPPER, out->GR_upper) && (s = emit<T>(P, out->GR_upper, nb - 1, i, e0, GRu, b, ne, st))) return s;
     if (want(QTX_OUT_GR_LOWER, out->GR_lower) && (s = emit<T>(P, out->GR_lower, nb - 1, i, e0, GRl, b, ne, st))) return s;
-    if (want(QTX_OUT_GL_DIAG, out->GL_diag) && (s = emit<T>(P, out->GL_diag, nb, i, e0, gli, b, ne, st))) return s;
-    if (want(QTX_OUT_GL_UPPER, out->GL_upper) && (s = emit<T>(P, out->GL_upper, nb - 1, i, e0, GLu, b, ne, st))) return s;
-    if (want(QTX_OUT_GG_DIAG, out->GG_diag) && (s = emit<T>(P, out->GG_diag, nb, i, e0, gli, b, ne, st, gi, gi))) return s;
-    if (want(QTX_OUT_GG_UPPER, out->GG_upper) && (s = emit<T>(P, out->GG_upper, nb - 1, i, e0, GLu, b, ne, st, GRu, GRl))) return s;
-    if (!d.system_input)
-      QTX_CK(obs_current<T>(cur + i, ncur, Hu + (long)i * bb, Su ? Su + (long)i * bb : nullptr, GLu, bb, c.E, b, ne, st));
-    QTX_CK(obs_density<T>(den + i, nb, gli, bb, b, ne, st));
+    // lesser-type blocks of each right-hand side on the shared retarded ones
+    for (int k = 0; k < nrhs; ++k) {
+      cx<T>* gli = c.glk(k, i);
+      cx<T>* GLn = c.glk(k, i + 1);
+      if ((s = MM(V(i), sUV, OP_N, gli, bb, OP_N, nullptr, Q, 1.0, 0.0))) return s;
+      if (odg) {  // Q = V_i g^<_i + (g_i Sigma^<_{i,i+1})^H
+        Term<T> t0; t0.p = Q; t0.s = bb; t0.alpha = 1.0;
+        Term<T> t1; t1.p = Rl(k); t1.s = bb; t1.alpha = 1.0; t1.op = OP_C;
+        QTX_CK((combine<T, T>(Q, bb, t0, t1, none, b, ne, nullptr, 0, 0, nullptr, st)));
+      }
+      if ((s = MM(GRu, bb, OP_N, Q, bb, OP_N, nullptr, K, -1.0, 0.0, keepB(2)))) return s;
+      if ((s = MM(Pm, bb, OP_N, GLn, bb, OP_N, nullptr, PGL, 1.0, 0.0, reuseA(0)))) return s;
+      if ((s = MM(PGL, bb, OP_N, Pm, bb, OP_C, gli, gli, 1.0, 1.0))) return s;   // g^<_i + PGL P^H
+      if ((s = MM(GRn, bb, OP_N, Q, bb, OP_N, nullptr, X2, 1.0, 0.0, x2))) return s;
+      {
+        Term<T> t0; t0.p = gli; t0.s = bb; t0.alpha = 1.0;
+        Term<T> t1; t1.p = K; t1.s = bb; t1.alpha = 1.0;
+        Term<T> t2; t2.p = K; t2.s = bb; t2.alpha = -1.0; t2.op = OP_C;
+        QTX_CK((combine<T, T>(gli, bb, t0, t1, t2, b, ne, nullptr, 0, 0, nullptr, st)));   // G^<_ii
+        Term<T> u0; u0.p = PGL; u0.s = bb; u0.alpha = -1.0;
+        Term<T> u1; u1.p = X2; u1.s = bb; u1.alpha = 1.0; u1.op = OP_C;
+        QTX_CK((combine<T, T>(GLu, bb, u0, u1, none, b, ne, nullptr, 0, 0, nullptr, st)));  // G^<_{i,i+1}
+      }
+      if (k == 1) {  // the second right-hand side's blocks are the GG outputs
+        if (want(QTX_OUT_GG_DIAG, out->GG_diag) && (s = emit<T>(P, out->GG_diag, nb, i, e0, gli, b, ne, st))) return s;
+        if (want(QTX_OUT_GG_UPPER, out->GG_upper) && (s = emit<T>(P, out->GG_upper, nb - 1, i, e0, GLu, b, ne, st))) return s;
+        continue;
+      }
+      if (want(QTX_OUT_GL_DIAG, out->GL_diag) && (s = emit<T>(P, out->GL_diag, nb, i, e0, gli, b, ne, st))) return s;
+      if (want(QTX_OUT_GL_UPPER, out->GL_upper) && (s = emit<T>(P, out->GL_upper, nb - 1, i, e0, GLu, b, ne, st))) return s;
+      if (!d.second_rhs) {
+        if (want(QTX_OUT_GG_DIAG, out->GG_diag) && (s = emit<T>(P, out->GG_diag, nb, i, e0, gli, b, ne, st, gi, gi))) return s;
+        if (want(QTX_OUT_GG_UPPER, out->GG_upper) && (s = emit<T>(P, out->GG_upper, nb - 1, i, e0, GLu, b, ne, st, GRu, GRl))) return s;
+      }
+      if (!d.system_input)
+        QTX_CK(obs_current<T>(cur + i, ncur, Hu + (long)i * bb, Su ? Su + (long)i * bb : nullptr, GLu, bb, c.E, b, ne, st));
+      QTX_CK(obs_density<T>(den + i, nb, gli, bb, b, ne, st));
+    }
   }
   if (d.leads) {  // left contact current and transmission on slice 0
     cx<T>* GG = c.tmp(0);
@@ -820,10 +851,11 @@ qtx_status validate(const qtx_rgf_desc* d, std::string& err) {
   if (d->offdiag_sigma && !d->has_scattering) { err = "offdiag_sigma needs has_scattering"; return QTX_ERR_INVALID_ARG; }
   if (d->storage_bits && !fpx_width_ok(d->storage_bits)) { err = "storage_bits must be 0, 56, 48, 40, 32, 24 or 16"; return QTX_ERR_INVALID_ARG; }
   if (d->sigma_stream && (!d->has_scattering || !d->energy_dependent_sigma || d->offdiag_sigma)) { err = "sigma_stream needs has_scattering and energy_dependent_sigma, without offdiag_sigma"; return QTX_ERR_INVALID_ARG; }
+  if (d->second_rhs && (!d->system_input || d->storage_bits)) { err = "second_rhs needs system_input and storage_bits = 0"; return QTX_ERR_INVALID_ARG; }
   if (d->system_input) {
-    const unsigned bad = QTX_OUT_GG_DIAG | QTX_OUT_GG_UPPER | QTX_OUT_CURRENT | QTX_OUT_CONTACT | QTX_OUT_TRANSMISSION | QTX_OUT_INTEGRALS;
+    const unsigned bad = (d->second_rhs ? 0u : QTX_OUT_GG_DIAG | QTX_OUT_GG_UPPER) | QTX_OUT_CURRENT | QTX_OUT_CONTACT | QTX_OUT_TRANSMISSION | QTX_OUT_INTEGRALS;
     if (d->has_S || d->leads || d->sigma_stream) { err = "system_input needs has_S = 0, leads = 0, sigma_stream = 0"; return QTX_ERR_INVALID_ARG; }
-    if (d->outputs & bad) { err = "system_input produces no G^>, current, contact, transmission or integrals outputs"; return QTX_ERR_INVALID_ARG; }
+    if (d->outputs & bad) { err = "system_input produces no G^> (without second_rhs), current, contact, transmission or integrals outputs"; return QTX_ERR_INVALID_ARG; }
   }
   if ((d->precision == QTX_EMU64 || d->precision == QTX_BF16X3) && !tc_available()) {
     err = "tensor-core engine not available in this build";
@@ -1005,6 +1037,7 @@ qtx_status qtx_rgf_solve(qtx_rgf_plan P, const qtx_rgf_inputs* in, const qtx_rgf
   if (P->d.has_scattering && (!in->SigL_diag || (!P->d.system_input && !in->SigR_diag))) { P->err = "has_scattering set but Sigma pointers missing"; return QTX_ERR_INVALID_ARG; }
   if (P->d.offdiag_sigma && (in->n_blocks ? in->n_blocks : P->d.n_blocks) > 1 &&
       (!in->SigL_upper || (!P->d.system_input && (!in->SigR_upper || !in->SigR_lower)))) { P->err = "offdiag_sigma set but off-diagonal Sigma pointers missing"; return QTX_ERR_INVALID_ARG; }
+  if (P->d.second_rhs && (!in->SigG_diag || (P->d.offdiag_sigma && nbs > 1 && !in->SigG_upper))) { P->err = "second_rhs set but SigG blocks missing"; return QTX_ERR_INVALID_ARG; }
   if (P->d.leads && (!in->lead_H00_L || !in->lead_H01_L || !in->lead_H00_R || !in->lead_H01_R)) { P->err = "leads set but lead blocks missing"; return QTX_ERR_INVALID_ARG; }
   if (P->d.leads && !(in->kT > 0)) { P->err = "leads need kT > 0"; return QTX_ERR_INVALID_ARG; }
   if (in->n_blocks < 0 || in->n_blocks > P->d.n_blocks) { P->err = "inputs->n_blocks exceeds the plan's n_blocks"; return QTX_ERR_INVALID_ARG; }

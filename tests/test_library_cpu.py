@@ -98,3 +98,25 @@ def test_refine_tol_validation(libpath):
     bad = q.make_desc(4, 16, "emu64", 2, refine_tol=-1.0)
     assert q.load().qtx_rgf_plan_create(ctypes.byref(bad), ctypes.byref(h)) == 1
     assert b"refine_tol" in q.load().qtx_rgf_last_error(None)
+
+
+def test_second_rhs_descriptor(libpath):
+    """second_rhs needs system_input and no FPX storage; it keeps one more set of left-connected
+    blocks (N_B per energy in flight) and, with block-tridiagonal right-hand sides, one more work
+    block; GG outputs are then allowed on a system_input plan."""
+    import paper_2606_25595_gb300 as q
+    h = ctypes.c_void_p()
+    lib = q.load()
+    bad = q.make_desc(4, 16, "fp64", 2, second_rhs=True, outputs=["GR_diag"])
+    assert lib.qtx_rgf_plan_create(ctypes.byref(bad), ctypes.byref(h)) == 1 and not h.value
+    assert b"second_rhs" in lib.qtx_rgf_last_error(None)
+    bad = q.make_desc(4, 16, "fp64", 2, system_input=True, second_rhs=True, storage_bits=40,
+                      outputs=["GR_diag"])
+    assert lib.qtx_rgf_plan_create(ctypes.byref(bad), ctypes.byref(h)) == 1
+    assert b"second_rhs" in lib.qtx_rgf_last_error(None)
+    nb, b, ec = 8, 32, 4
+    kw = dict(energy_dependent_sigma=True, offdiag_sigma=True, system_input=True)
+    one = q.footprint(q.make_desc(nb, b, "fp64", ec, outputs=["GR_diag", "GL_diag"], **kw))
+    two = q.footprint(q.make_desc(nb, b, "fp64", ec, outputs=["GR_diag", "GL_diag", "GG_diag"],
+                                  second_rhs=True, **kw))
+    assert two - one == (nb + 1) * ec * b * b * 16
