@@ -214,6 +214,7 @@ struct TcArgs {
   const int* active;
   TcOperand* opndA = nullptr;  // optional kept / reused digit planes of op(A), op(B)
   TcOperand* opndB = nullptr;
+  bool f32 = false;            // A, B, C0, C point to cx<float> arrays (four digit planes only)
 };
 
 }  // namespace qtx

@@ -222,8 +222,28 @@ qtx_status gemm_simt_prof(qtx_rgf_plan_s* P, const GemmArgs<T>& g, cudaStream_t 
   }
   return QTX_OK;
 }
+// The emulated-FP64 mode's FP32 starting inverse: its products of at least kTcF32Min in every
+// dimension run on the tensor cores with four digit planes (~27-bit products, at least FP32's
+// precision; every digit group exact), the smaller ones on the SIMT GEMM.
+constexpr int kTcF32Min = 96;
 template <>
 qtx_status gemm<float>(qtx_rgf_plan_s* P, const GemmArgs<float>& g, cudaStream_t st, bool, DigitHint) {
+  if (P->d.precision == QTX_EMU64 && g.M >= kTcF32Min && g.N >= kTcF32Min && g.K >= kTcF32Min && g.K <= 1024 &&
+      gemm_tc_scratch_bytes(g.M, g.N, g.K, g.batch, 4) <= P->L.tc_bytes) {
+    TcArgs a;
+    a.f32 = true;
+    a.M = g.M; a.N = g.N; a.K = g.K;
+    a.A = reinterpret_cast<const cx<df>*>(g.A); a.lda = g.lda; a.sA = g.sA; a.opA = g.opA;
+    a.B = reinterpret_cast<const cx<df>*>(g.B); a.ldb = g.ldb; a.sB = g.sB; a.opB = g.opB;
+    a.C0 = reinterpret_cast<const cx<df>*>(g.C0); a.ldc0 = g.ldc0; a.sC0 = g.sC0;
+    a.C = reinterpret_cast<cx<df>*>(g.C); a.ldc = g.ldc; a.sC = g.sC;
+    a.alpha = (float)g.alpha; a.beta = (float)g.beta;
+    a.batch = g.batch; a.active = g.active;
+    cudaEvent_t* ev = P->prof ? P->next_events() : nullptr;
+    QTX_CK(gemm_tc(a, 4, P->ws + P->L.tc_scratch, P->L.tc_bytes, P->d_err_flag, st, ev));
+    if (ev) P->pipe_flops += 8.0 * g.M * g.N * g.K * g.batch * tc_pairs(4);  // no FP64-equivalent work
+    return QTX_OK;
+  }
   return gemm_simt_prof<float>(P, g, st);
 }
 template <>

@@ -175,8 +175,8 @@ struct TcParams {
   int M_pad, N_pad, nks;  // nks: K-stages of 32 over the embedded K (2 * K_pad)
   int M, N;
   int bn_last;     // complex columns the last column tile computes: N - 48 (NBt - 1), rounded up to 8
-  cx<df>* C; long ldc, sC;
-  const cx<df>* C0; long ldc0, sC0;
+  void* C; long ldc, sC;         // cx<df>, or cx<float> for the FP32 products (IO = float)
+  const void* C0; long ldc0, sC0;
   float alpha, beta;
   int escale;      // exponent shift of the recombined sum: 2 l1 - 2
   int a_batched, b_batched;  // 0: the operand is shared by the whole batch (digitized once)
@@ -223,7 +223,17 @@ __device__ __forceinline__ long tile_at(int k) {
 // stage ring (NST = 3 stages fit beside it for 6 digit planes).
 constexpr int OUT_BYTES = BM * OUT_LD * (int)sizeof(cx<df>);
 
-template <int S, int NST>
+// IO: element type of C and C0 -- df (the emulated-FP64 products) or float (the products of the
+// FP32 starting inverse, four digit planes: ~27-bit products, all digit groups exact).
+template <typename IO> __device__ __forceinline__ cx<IO> c_from_df(cx<df> v);
+template <> __device__ __forceinline__ cx<df> c_from_df<df>(cx<df> v) { return v; }
+template <> __device__ __forceinline__ cx<float> c_from_df<float>(cx<df> v) {
+  return mk<float>(v.re.hi + v.re.lo, v.im.hi + v.im.lo);
+}
+__device__ __forceinline__ df df_of(df x) { return x; }
+__device__ __forceinline__ df df_of(float x) { return mkdf(x, 0.f); }
+
+template <int S, int NST, typename IO>
 __global__ void __launch_bounds__(320, 1) k_tc_gemm(TcParams p, int n_tiles, int NBt, int MBt) {
   constexpr int STAGE = S * (TILE_A + TILE_B);
   constexpr int NACC = n_acc(S);
@@ -385,19 +395,19 @@ __global__ void __launch_bounds__(320, 1) k_tc_gemm(TcParams p, int n_tiles, int
       __syncwarp();
       asm volatile("bar.sync 1, 256;" ::: "memory");
       if (threadIdx.x == 64) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(acce)) : "memory");
-      const cx<df>* C0e = p.C0 ? p.C0 + (long)e * p.sC0 : nullptr;
-      cx<df>* Ce = p.C + (long)e * p.sC;
+      const cx<IO>* C0e = p.C0 ? reinterpret_cast<const cx<IO>*>(p.C0) + (long)e * p.sC0 : nullptr;
+      cx<IO>* Ce = reinterpret_cast<cx<IO>*>(p.C) + (long)e * p.sC;
       for (int idx = threadIdx.x - 64; idx < BM * bn; idx += 256) {
         const int rr = idx / bn, cc = idx % bn;
         const int mm = mblk * BM + rr, nn = nblk * BNC + cc;
         if (mm < p.M && nn < p.N) {
           cx<df> v = out[rr * OUT_LD + cc];
           if (C0e && p.beta != 0.f) {
-            const cx<df> c0v = C0e[(long)mm * p.ldc0 + nn];
-            v.re = df_add(v.re, df_mulf(c0v.re, p.beta));
-            v.im = df_add(v.im, df_mulf(c0v.im, p.beta));
+            const cx<IO> c0v = C0e[(long)mm * p.ldc0 + nn];
+            v.re = df_add(v.re, df_mulf(df_of(c0v.re), p.beta));
+            v.im = df_add(v.im, df_mulf(df_of(c0v.im), p.beta));
           }
-          Ce[(long)mm * p.ldc + nn] = v;
+          Ce[(long)mm * p.ldc + nn] = c_from_df<IO>(v);
         }
       }
       ++j;
@@ -465,8 +475,8 @@ __device__ __forceinline__ uint32_t bf16x2_bits(float lo_half, float hi_half) {
 // flip, exact).  Rows r >= R and k >= K are written as zero digits, with exponent -1000.
 __host__ __device__ constexpr int strip_skew(int k) { return k + (k >> 3); }
 
-template <int S, int RPC>
-__global__ void __launch_bounds__(32 * RPC) k_digitize_rows(const cx<df>* X, long ldx, long sX, int R, int K, int R_pad,
+template <int S, int RPC, typename TI>
+__global__ void __launch_bounds__(32 * RPC) k_digitize_rows(const cx<TI>* X, long ldx, long sX, int R, int K, int R_pad,
                                                        int K_pad, int transposed, int conj_, int side, int* eout,
                                                        int P, unsigned char* planes, long rows_plane,
                                                        const int* active) {
@@ -477,7 +487,15 @@ __global__ void __launch_bounds__(32 * RPC) k_digitize_rows(const cx<df>* X, lon
   cx<df>* strip = reinterpret_cast<cx<df>*>(dsm);
   __shared__ int s_ex[RPC];
   constexpr int NT = 32 * RPC;  // threads: one warp per strip row
-  const cx<df>* Xe = X + (long)e * sX;
+  const cx<TI>* Xe = X + (long)e * sX;
+  // an element as df32 (FP32 inputs: lo = 0)
+  auto ld = [&](long off) -> cx<df> {
+    const cx<TI> x = Xe[off];
+    cx<df> v;
+    v.re = df_of(x.re);
+    v.im = df_of(x.im);
+    return v;
+  };
   const int r0 = blockIdx.x * RPC, t = threadIdx.x;
   if (t < RPC) s_ex[t] = -1000;
   __syncthreads();
@@ -493,7 +511,7 @@ __global__ void __launch_bounds__(32 * RPC) k_digitize_rows(const cx<df>* X, lon
 #pragma unroll
       for (int rr = 0; rr < RPC; ++rr) {
         const int r = r0 + rr;
-        v[rr] = (r < R && k < K) ? Xe[(long)r * ldx + k] : zero;
+        v[rr] = (r < R && k < K) ? ld((long)r * ldx + k) : zero;
       }
 #pragma unroll
       for (int rr = 0; rr < RPC; ++rr) {
@@ -516,7 +534,7 @@ __global__ void __launch_bounds__(32 * RPC) k_digitize_rows(const cx<df>* X, lon
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int k = k0 + u * KS;
-        v[u] = (r < R && k < K) ? Xe[(long)k * ldx + r] : zero;
+        v[u] = (r < R && k < K) ? ld((long)k * ldx + r) : zero;
       }
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
@@ -641,8 +659,8 @@ inline Scratch carve(void* base, const Dims& d, int batch, int S) {
   return s;
 }
 
-template <int S>
-cudaError_t digitize(const cx<df>* X, long ldx, long sX, int opX, int side, int R, int K, const Dims& d,
+template <int S, typename TI>
+cudaError_t digitize(const cx<TI>* X, long ldx, long sX, int opX, int side, int R, int K, const Dims& d,
                      int* eout, unsigned char* planes, int batch, const int* active, cudaStream_t st) {
   // logical row r of the operand: left A = op(X): row r of op(X); right B = op(X): column r of op(X)
   //   left  N: X[r][k] direct      left  H: conj(X[k][r]) transposed
@@ -660,25 +678,29 @@ cudaError_t digitize(const cx<df>* X, long ldx, long sX, int opX, int side, int 
   {
     static bool attr = false;
     if (!attr) {
-      cudaError_t ea = cudaFuncSetAttribute(k_digitize_rows<S, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      if (ea == cudaSuccess) ea = cudaFuncSetAttribute(k_digitize_rows<S, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      cudaError_t ea = cudaFuncSetAttribute(k_digitize_rows<S, 2, TI>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      if (ea == cudaSuccess) ea = cudaFuncSetAttribute(k_digitize_rows<S, 1, TI>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
       if (ea != cudaSuccess) return ea;
       attr = true;
     }
     const size_t smem = rpc * row_bytes;
     dim3 g(R_pad / rpc, batch);
     if (rpc == 2)
-      k_digitize_rows<S, 2><<<g, 64, smem, st>>>(X, ldx, sX, R, K, R_pad, d.K_pad, transposed, cj, side, eout, d.P, planes, rows_plane, active);
+      k_digitize_rows<S, 2, TI><<<g, 64, smem, st>>>(X, ldx, sX, R, K, R_pad, d.K_pad, transposed, cj, side, eout, d.P, planes, rows_plane, active);
     else
-      k_digitize_rows<S, 1><<<g, 32, smem, st>>>(X, ldx, sX, R, K, R_pad, d.K_pad, transposed, cj, side, eout, d.P, planes, rows_plane, active);
+      k_digitize_rows<S, 1, TI><<<g, 32, smem, st>>>(X, ldx, sX, R, K, R_pad, d.K_pad, transposed, cj, side, eout, d.P, planes, rows_plane, active);
     count_launch();
     return cudaGetLastError();
   }
 }
 
-template <int S, int NST>
+template <int S, int NST, typename IO>
 cudaError_t launch(const TcArgs& a, void* scratch, size_t scratch_bytes, int* err_flag, cudaStream_t st,
                    cudaEvent_t* ev) {
+  // operand and result pointers in the IO type (TcArgs carries the df32 ones; f32 products pass
+  // FP32 arrays through the same fields)
+  const cx<IO>* A = reinterpret_cast<const cx<IO>*>(a.A);
+  const cx<IO>* B = reinterpret_cast<const cx<IO>*>(a.B);
   const Dims d = dims_of(a.M, a.N, a.K, S);
   Scratch s = carve(scratch, d, a.batch, S);
   if (s.bytes > scratch_bytes) return cudaErrorInvalidValue;
@@ -691,9 +713,9 @@ cudaError_t launch(const TcArgs& a, void* scratch, size_t scratch_bytes, int* er
   int* ea = a.opndA ? a.opndA->expo : s.ea;
   int* eb = a.opndB ? a.opndB->expo : s.eb;
   if (!(a.opndA && a.opndA->mode == 2))
-    if ((e = digitize<S>(a.A, a.lda, a.sA, a.opA, 0, a.M, a.K, d, ea, pa, ab ? a.batch : 1, ab ? a.active : nullptr, st))) return e;
+    if ((e = digitize<S, IO>(A, a.lda, a.sA, a.opA, 0, a.M, a.K, d, ea, pa, ab ? a.batch : 1, ab ? a.active : nullptr, st))) return e;
   if (!(a.opndB && a.opndB->mode == 2))
-    if ((e = digitize<S>(a.B, a.ldb, a.sB, a.opB, 1, a.N, a.K, d, eb, pb, bb_ ? a.batch : 1, bb_ ? a.active : nullptr, st))) return e;
+    if ((e = digitize<S, IO>(B, a.ldb, a.sB, a.opB, 1, a.N, a.K, d, eb, pb, bb_ ? a.batch : 1, bb_ ? a.active : nullptr, st))) return e;
   TcParams p;
   p.pa = pa;
   p.pb = pb;
@@ -721,7 +743,7 @@ cudaError_t launch(const TcArgs& a, void* scratch, size_t scratch_bytes, int* er
   static bool attr = false;
   static int sms = 0;
   if (!attr) {
-    if ((e = cudaFuncSetAttribute(k_tc_gemm<S, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
+    if ((e = cudaFuncSetAttribute(k_tc_gemm<S, NST, IO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
     int dev = 0;
     if ((e = cudaGetDevice(&dev))) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))) return e;
@@ -734,7 +756,7 @@ cudaError_t launch(const TcArgs& a, void* scratch, size_t scratch_bytes, int* er
   if (tiles > 0x7fffffffL) return cudaErrorInvalidValue;
   const int grid = (int)(tiles < sms ? tiles : sms);  // one CTA per SM (the kernel holds 230 KB of smem)
   if (ev) cudaEventRecord(ev[0], st);
-  k_tc_gemm<S, NST><<<grid, 320, smem, st>>>(p, (int)tiles, NBt, MBt);
+  k_tc_gemm<S, NST, IO><<<grid, 320, smem, st>>>(p, (int)tiles, NBt, MBt);
   count_launch();
   if (ev) cudaEventRecord(ev[1], st);
   return cudaGetLastError();
@@ -794,6 +816,7 @@ cudaError_t gemm_tc(const TcArgs& a, int digits, void* scratch, size_t scratch_b
                     cudaStream_t st, cudaEvent_t* ev) {
   if (a.M <= 0 || a.N <= 0 || a.batch <= 0) return cudaSuccess;
   const int nc = k_chunks(a.K);
+  if (nc > 1 && a.f32) return cudaErrorInvalidValue;  // the FP32 products are short contractions
   if (nc > 1) {
     // split K: chunk c covers k in [k0, k1); op N operands advance along their columns (A) or rows
     // (B), op C ones the other way round
@@ -819,9 +842,10 @@ cudaError_t gemm_tc(const TcArgs& a, int digits, void* scratch, size_t scratch_b
     return cudaSuccess;
   }
   digits = effective_digits(digits, a.K);
-  if (digits == 7) return tc::launch<7, 2>(a, scratch, scratch_bytes, err_flag, st, ev);
-  if (digits == 6) return tc::launch<6, 3>(a, scratch, scratch_bytes, err_flag, st, ev);
-  if (digits == 2) return tc::launch<2, 8>(a, scratch, scratch_bytes, err_flag, st, ev);
+  if (a.f32) return digits == 4 ? tc::launch<4, 4, float>(a, scratch, scratch_bytes, err_flag, st, ev) : cudaErrorInvalidValue;
+  if (digits == 7) return tc::launch<7, 2, df>(a, scratch, scratch_bytes, err_flag, st, ev);
+  if (digits == 6) return tc::launch<6, 3, df>(a, scratch, scratch_bytes, err_flag, st, ev);
+  if (digits == 2) return tc::launch<2, 8, df>(a, scratch, scratch_bytes, err_flag, st, ev);
   return cudaErrorInvalidValue;
 }
 
