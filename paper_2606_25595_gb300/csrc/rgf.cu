@@ -206,8 +206,8 @@ qtx_status gemm(qtx_rgf_plan_s* P, const GemmArgs<T>& g, cudaStream_t st, bool f
                 DigitHint hint = DigitHint{});
 
 // The profiled product kernel is the plan's own: the SIMT GEMM in the FP64 / FP32 modes, the
-// tensor-core GEMM in the emulated modes (whose FP32 starting-guess inverse also calls SIMT GEMMs,
-// which are not counted).
+// tensor-core GEMM in the emulated modes (whose FP32 starting-guess inverse also calls GEMMs -- SIMT,
+// or the tensor cores' four-plane FP32 instance -- which are not counted).
 template <typename T>
 qtx_status gemm_simt_prof(qtx_rgf_plan_s* P, const GemmArgs<T>& g, cudaStream_t st) {
   const bool mine = P->d.precision == QTX_FP64 || P->d.precision == QTX_FP32;
@@ -239,9 +239,7 @@ qtx_status gemm<float>(qtx_rgf_plan_s* P, const GemmArgs<float>& g, cudaStream_t
     a.C = reinterpret_cast<cx<df>*>(g.C); a.ldc = g.ldc; a.sC = g.sC;
     a.alpha = (float)g.alpha; a.beta = (float)g.beta;
     a.batch = g.batch; a.active = g.active;
-    cudaEvent_t* ev = P->prof ? P->next_events() : nullptr;
-    QTX_CK(gemm_tc(a, 4, P->ws + P->L.tc_scratch, P->L.tc_bytes, P->d_err_flag, st, ev));
-    if (ev) P->pipe_flops += 8.0 * g.M * g.N * g.K * g.batch * tc_pairs(4);  // no FP64-equivalent work
+    QTX_CK(gemm_tc(a, 4, P->ws + P->L.tc_scratch, P->L.tc_bytes, P->d_err_flag, st, nullptr));
     return QTX_OK;
   }
   return gemm_simt_prof<float>(P, g, st);
