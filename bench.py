@@ -189,12 +189,12 @@ def run_reference(args):
         n += len(done)
     value = n / t
     cores = os.cpu_count()
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": f"random BT device b={args.block} N_B={args.slices} "
-                                   f"N_E={args.energies} on [-2,2], scattering self-energies",
+            "config": {"workload": f"random BT device b={args.block} N_B={args.slices} N_E={args.energies} on [-2,2], "
+                                   "block-diagonal scattering self-energies (seed 0)",
                        "global_batch": args.energies, "precision": "fp64-oracle"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{per_step} energies of the {args.energies}-energy grid per step"},
