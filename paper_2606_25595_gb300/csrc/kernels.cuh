@@ -108,8 +108,9 @@ cudaError_t integrate_add(double* acc, const double* val, long ld, int n, const 
                           cudaStream_t st);
 
 // ---- tensor-core engine (tc_engine.cu): emulated-precision batched complex GEMM on sm_103a.
-// `digits` bf16 digit planes per operand (6: ~41-bit products from 21 digit products; 2: ~13-bit
-// products from 3).  `scratch` holds the digit planes and scale exponents.
+// `digits` bf16 digit planes per operand (6: ~41-bit products from 21 digit products, 7 of them
+// taken for K > 512; 2: ~13-bit products from 3; 4 with a.f32: ~27-bit products from 10 for FP32
+// operands and results).  `scratch` holds the digit planes and scale exponents.
 // `ev` (optional, two events) brackets the tensor-core GEMM kernel itself (not the digitiser).
 cudaError_t gemm_tc(const TcArgs& a, int digits, void* scratch, size_t scratch_bytes, int* err_flag,
                     cudaStream_t st, cudaEvent_t* ev = nullptr);
