@@ -72,11 +72,12 @@ cudaError_t assemble_offdiag(cx<T>* U, cx<T>* V, const cx<double>* Hup, const cx
                              const cx<double>* SRu = nullptr, const cx<double>* SRl = nullptr, long sSR = 0);
 
 // ---- observables, FP64 accumulation
-// cur[e * ldcur] = 2 Re Tr[(H_up - E S_up) G^<_{i+1,i}],  G^<_{i+1,i} = -(GLu)^H
+// cur[e * ldcur] = 2 Re Tr[(H_up - E S_up) G^<_{i+1,i}],  G^<_{i+1,i} = -(GLu)^H.  With a device
+// scratch of scratch_doubles doubles, one energy's trace may be split over several CTAs.
 template <typename T>
 cudaError_t obs_current(double* cur, long ldcur, const cx<double>* Hup, const cx<double>* Sup,
                         const cx<T>* GLu, long sG, const double* E, int b, int batch,
-                        cudaStream_t st);
+                        cudaStream_t st, double* scratch = nullptr, long scratch_doubles = 0);
 // den[e * ldden] = Im Tr GL[e]
 template <typename T>
 cudaError_t obs_density(double* den, long ldden, const cx<T>* GL, long sG, int b, int batch,

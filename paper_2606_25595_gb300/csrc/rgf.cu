@@ -783,7 +783,8 @@ qtx_status solve_chunk(qtx_rgf_plan_s* P, const qtx_rgf_inputs* in, const qtx_rg
         if (want(QTX_OUT_GG_UPPER, out->GG_upper) && (s = emit<T>(P, out->GG_upper, nb - 1, i, e0, GLu, b, ne, st, GRu, GRl))) return s;
       }
       if (!d.system_input)
-        QTX_CK(obs_current<T>(cur + i, ncur, Hu + (long)i * bb, Su ? Su + (long)i * bb : nullptr, GLu, bb, c.E, b, ne, st));
+        QTX_CK(obs_current<T>(cur + i, ncur, Hu + (long)i * bb, Su ? Su + (long)i * bb : nullptr, GLu, bb, c.E, b, ne, st,
+                              reinterpret_cast<double*>(c.tmp(0)), (long)ne * bb * (long)sizeof(cx<T>) / (long)sizeof(double)));
       QTX_CK(obs_density<T>(den + i, nb, gli, bb, b, ne, st));
     }
   }

@@ -740,19 +740,24 @@ __device__ __forceinline__ double block_sum(double v) {
   return s;  // valid in thread 0
 }
 
+// One energy's trace is split over `parts` CTAs (blockIdx.x) when the batch alone would leave most
+// SMs idle (few energies of large blocks); each writes its partial sum (df32, or FP64 when FP64
+// arithmetic is used) to `partial`, and k_obs_current_sum adds them in a fixed order.
 template <typename T>
 __global__ void __launch_bounds__(256) k_obs_current(double* cur, long ldcur, const cx<double>* Hup,
                                                      const cx<double>* Sup, const cx<T>* GLu, long sG,
-                                                     const double* E, int b) {
-  const int e = blockIdx.x;
+                                                     const double* E, int b, int parts, double* partial) {
+  const int e = blockIdx.y, part = blockIdx.x;
   const long bb = (long)b * b;
+  const long chunk = (bb + parts - 1) / parts;
+  const long i0 = (long)part * chunk, i1 = i0 + chunk < bb ? i0 + chunk : bb;
   const double Er = E[e];
   const cx<T>* G = GLu + (long)e * sG;
   double s = 0.0;
   if constexpr (std::is_same<T, df>::value) {
     if (!Sup) {  // df32 products and sums: no FP64 arithmetic per element
       df a = mkdf(0.f, 0.f);
-      for (long idx = threadIdx.x; idx < bb; idx += blockDim.x) {
+      for (long idx = i0 + threadIdx.x; idx < i1; idx += blockDim.x) {
         const cx<double> x = Hup[idx];
         const cx<df> g = G[idx];
         a = df_add(a, df_add(df_mul(from_d<df>(x.re), g.re), df_mul(from_d<df>(x.im), g.im)));
@@ -764,12 +769,13 @@ __global__ void __launch_bounds__(256) k_obs_current(double* cur, long ldcur, co
       __syncthreads();
       if (threadIdx.x == 0) {
         for (int i = 1; i < (int)blockDim.x / 32; ++i) a = df_add(a, red[i]);
-        cur[(long)e * ldcur] = -2.0 * to_d(a);
+        if (parts == 1) cur[(long)e * ldcur] = -2.0 * to_d(a);
+        else reinterpret_cast<df*>(partial)[(long)e * parts + part] = a;
       }
       return;
     }
   }
-  for (long idx = threadIdx.x; idx < bb; idx += blockDim.x) {
+  for (long idx = i0 + threadIdx.x; idx < i1; idx += blockDim.x) {
     cx<double> x = Hup[idx];
     if (Sup) x = x - Er * Sup[idx];
     const cx<double> gg = cvt<double>(G[idx]);
@@ -777,18 +783,55 @@ __global__ void __launch_bounds__(256) k_obs_current(double* cur, long ldcur, co
   }
   s = block_sum(s);
   // 2 Re Tr[X (-GLu^H)] = -2 sum_jk Re(X_jk conj(GLu_jk))
-  if (threadIdx.x == 0) cur[(long)e * ldcur] = -2.0 * s;
+  if (threadIdx.x == 0) {
+    if (parts == 1) cur[(long)e * ldcur] = -2.0 * s;
+    else partial[(long)e * parts + part] = s;
+  }
+}
+// the partial sums of one energy, in order (df32 partials: the df32 path of k_obs_current)
+__global__ void k_obs_current_sum(double* cur, long ldcur, const double* partial, int parts, int df_parts) {
+  const int e = blockIdx.x;
+  if (threadIdx.x != 0) return;
+  if (df_parts) {
+    const df* pp = reinterpret_cast<const df*>(partial) + (long)e * parts;
+    df a = pp[0];
+    for (int k = 1; k < parts; ++k) a = df_add(a, pp[k]);
+    cur[(long)e * ldcur] = -2.0 * to_d(a);
+  } else {
+    double a = 0.0;
+    for (int k = 0; k < parts; ++k) a += partial[(long)e * parts + k];
+    cur[(long)e * ldcur] = -2.0 * a;
+  }
 }
 template <typename T>
 cudaError_t obs_current(double* cur, long ldcur, const cx<double>* Hup, const cx<double>* Sup,
-                        const cx<T>* GLu, long sG, const double* E, int b, int batch, cudaStream_t st) {
-  k_obs_current<T><<<batch, 256, 0, st>>>(cur, ldcur, Hup, Sup, GLu, sG, E, b);
+                        const cx<T>* GLu, long sG, const double* E, int b, int batch, cudaStream_t st,
+                        double* scratch, long scratch_doubles) {
+  // about two CTAs per SM in all; at least 64 K elements per CTA
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      sms = 1;
+  }
+  const long bb = (long)b * b;
+  long parts = (2L * sms + batch - 1) / batch;
+  const long by_size = bb / 65536 > 0 ? bb / 65536 : 1;
+  if (parts > by_size) parts = by_size;
+  if (parts > 1024) parts = 1024;
+  if (!scratch || parts * batch > scratch_doubles) parts = 1;
+  dim3 grid((unsigned)parts, batch);
+  k_obs_current<T><<<grid, 256, 0, st>>>(cur, ldcur, Hup, Sup, GLu, sG, E, b, (int)parts, scratch);
   count_launch();
+  if (parts > 1) {
+    k_obs_current_sum<<<batch, 32, 0, st>>>(cur, ldcur, scratch, (int)parts, std::is_same<T, df>::value && !Sup);
+    count_launch();
+  }
   return cudaGetLastError();
 }
-template cudaError_t obs_current<double>(double*, long, const cx<double>*, const cx<double>*, const cx<double>*, long, const double*, int, int, cudaStream_t);
-template cudaError_t obs_current<float>(double*, long, const cx<double>*, const cx<double>*, const cx<float>*, long, const double*, int, int, cudaStream_t);
-template cudaError_t obs_current<df>(double*, long, const cx<double>*, const cx<double>*, const cx<df>*, long, const double*, int, int, cudaStream_t);
+template cudaError_t obs_current<double>(double*, long, const cx<double>*, const cx<double>*, const cx<double>*, long, const double*, int, int, cudaStream_t, double*, long);
+template cudaError_t obs_current<float>(double*, long, const cx<double>*, const cx<double>*, const cx<float>*, long, const double*, int, int, cudaStream_t, double*, long);
+template cudaError_t obs_current<df>(double*, long, const cx<double>*, const cx<double>*, const cx<df>*, long, const double*, int, int, cudaStream_t, double*, long);
 
 template <typename T>
 __global__ void k_obs_density(double* den, long ldden, const cx<T>* GL, long sG, int b) {
