@@ -57,10 +57,10 @@ def parse():
                          "nrl: b=3408 N_B=10 (the paper's NR-L shape), per-energy self-energies streamed from host; "
                          "wsolve: screened-Coulomb system b=256 N_B=32, 64 energies (assembly + one selected solve for B^< and B^>)")
     ap.add_argument("--requests", type=int, default=40)
-    ap.add_argument("--refine-tol", type=float, default=2.0 ** -13,
+    ap.add_argument("--refine-tol", type=float, default=2.0 ** -12,
                     help="mixed workloads: an energy stops its Newton sweeps once ||I - A X||_F <= this "
-                         "(the next residual is then <= its square, 2^-26); the FP32 starting inverses of the "
-                         "b=256 device have residuals of 3e-5 - 7e-5, so one sweep; 0 = always 2 sweeps")
+                         "(the next residual is then <= its square, 2^-24, below the digit products' error); "
+                         "0 = always 2 sweeps")
     ap.add_argument("--storage-bits", type=int, default=0,
                     help="mixed workloads: keep the left-connected blocks in FPX of this many bits (0 = off)")
     return ap.parse_args()
