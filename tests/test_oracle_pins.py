@@ -5,6 +5,8 @@
 * the closed-form self-energy and Green's function of a clean tight-binding strip;
 * a long truncated lead solved densely (orientation of the lead coupling);
 * the clean strip's integer transmission and Landauer current;
+* closed forms of the Fermi function, the trapezoid weights, the integrated current of a clean
+  chain and the integrated density of a broadened level;
 * invariants: anti-Hermitian G^<, PSD spectral function, exact current continuity, and the
   equilibrium (fluctuation-dissipation) case with zero current.
 """
@@ -318,12 +320,74 @@ def test_equilibrium_fluctuation_dissipation():
         assert np.abs(r["current"]).max() < 1e-10
 
 
-def test_integration_weights_and_normalisation():
-    """Integrated current = sum_E w_E I(E); density integral carries 1/(2 pi)."""
-    s = W.strip(n_blocks=4, n_energies=9, e_lo=-0.2, e_hi=0.2, disorder=0.0, eta=1e-10)
-    out = O.solve(s)
-    w = W.trapezoid_weights(s["energies"])
-    assert np.allclose(out["current_int"], w @ out["current"], rtol=0, atol=1e-14)
-    assert np.allclose(out["density_int"], (w @ out["density"]) / (2 * np.pi), rtol=0, atol=1e-14)
-    # Landauer: clean strip, T constant over the window -> I = T * int (f_L - f_R) dE
-    assert np.all(out["current_int"] > 0)
+def test_fermi_values_fixed_by_the_definition():
+    """f(x) = 1 / (1 + exp(x / kT)): f(mu) = 1/2, f(mu + kT ln 3) = 1/4, f(mu - kT ln 3) = 3/4,
+    f(mu + kT ln 9) = 1/10, particle-hole symmetry f(mu + x) + f(mu - x) = 1, and the limits far
+    from mu without overflow.  A wrong temperature scale (x / (2 kT)) or sign fails these."""
+    for mu, kT in ((0.1, 0.025), (-0.3, 0.1), (0.0, 1e-3)):
+        assert O.fermi(mu, mu, kT) == 0.5
+        assert abs(O.fermi(mu + kT * np.log(3.0), mu, kT) - 0.25) < 1e-15
+        assert abs(O.fermi(mu - kT * np.log(3.0), mu, kT) - 0.75) < 1e-15
+        assert abs(O.fermi(mu + kT * np.log(9.0), mu, kT) - 0.1) < 1e-15
+        for x in (0.3 * kT, 2.0 * kT, 17.0 * kT):
+            assert abs(O.fermi(mu + x, mu, kT) + O.fermi(mu - x, mu, kT) - 1.0) < 1e-15
+        assert O.fermi(mu + 2000.0 * kT, mu, kT) == 0.0
+        assert O.fermi(mu - 2000.0 * kT, mu, kT) == 1.0
+
+
+def test_trapezoid_weights_closed_forms():
+    """Uniform grid on [a, b] with spacing h: sum w = b - a, sum w E = (b^2 - a^2)/2 (exact for
+    linear integrands), sum w E^2 = (b^3 - a^3)/3 + (b - a) h^2 / 6 (the rule's exact error on a
+    quadratic); a non-uniform grid integrates linear functions exactly."""
+    a, b, n = -1.3, 2.1, 37
+    E = np.linspace(a, b, n)
+    h = (b - a) / (n - 1)
+    w = W.trapezoid_weights(E)
+    assert abs(w.sum() - (b - a)) < 1e-14
+    assert abs(w @ E - (b * b - a * a) / 2) < 1e-14
+    assert abs(w @ E ** 2 - ((b ** 3 - a ** 3) / 3 + (b - a) * h * h / 6)) < 1e-13
+    Eg = np.sort(np.random.default_rng(3).uniform(a, b, 25))
+    wg = W.trapezoid_weights(Eg)
+    assert abs(wg @ (2.0 * Eg - 0.7) - ((Eg[-1] ** 2 - Eg[0] ** 2) - 0.7 * (Eg[-1] - Eg[0]))) < 1e-13
+    assert W.trapezoid_weights(np.array([0.4])).tolist() == [0.0]
+
+
+def test_integrated_current_of_a_clean_chain_equals_the_bias():
+    """Clean 1D chain (W = 1 strip, |t| = 1): T(E) = 1 for |E| < 2, so the integrated Landauer
+    current over a window that holds both Fermi tails is T (mu_L - mu_R) exactly,
+    int (f_L - f_R) dE = mu_L - mu_R.  Window [-0.7, 0.7] (tails e^-24 at kT = 0.025), 140 points
+    (E = 0, the chain's band centre where decimation at eta = 1e-10 loses its digits in the first
+    sweep, is not on the grid); the trapezoid error of this smooth, decaying integrand is far below
+    the tolerance."""
+    cfg = W.STRIP_CFG
+    s = W.strip(W=1, n_blocks=4, disorder=0.0, eta=1e-10, n_energies=140, e_lo=-0.7, e_hi=0.7,
+                mu_L=cfg["mu_L"], mu_R=cfg["mu_R"], kT=cfg["kT"])
+    out = O.solve(s, keep_blocks=False)
+    assert np.abs(out["transmission"] - 1.0).max() < 1e-8
+    assert np.abs(out["current_int"] - (cfg["mu_L"] - cfg["mu_R"])).max() < 1e-8
+
+
+def test_integrated_density_of_a_broadened_level_closed_form():
+    """One level eps0 with a wide-band self-energy Sigma^R = -i Gamma/2 in equilibrium,
+    Sigma^< = i f(E) Gamma: n(E) = Im G^< = f(E) Gamma / ((E - eps0)^2 + Gamma^2/4), and the
+    density integral sum_E w_E n(E) / (2 pi) over [E_lo, mu + 40 kT] equals the occupation of the
+    Lorentzian level, 1/2 - Im psi(1/2 + (Gamma/2 + i (eps0 - mu)) / (2 pi kT)) / pi (psi: digamma),
+    minus the part of the Lorentzian below E_lo, (arctan(2 (E_lo - eps0) / Gamma) + pi/2) / pi.
+    Pins the 1/(2 pi) of the density integral, the Fermi function's temperature scale inside an
+    integral, and the trapezoid weights (its error here is ~1e-9)."""
+    from scipy.special import psi
+    eps0, gam, mu, kT = 0.0, 0.4, 0.05, 0.02
+    E = np.linspace(-2.0, mu + 40 * kT, 2851)
+    f = np.array([O.fermi(e, mu, kT) for e in E])
+    dev = dict(n_blocks=1, block_size=1, H_diag=np.full((1, 1, 1), eps0, np.complex128),
+               H_upper=np.zeros((0, 1, 1), np.complex128), S_diag=None, S_upper=None,
+               SigR=np.full((1, 1, 1, 1), -0.5j * gam, np.complex128),
+               SigL=(1j * gam * f)[:, None, None, None].astype(np.complex128),
+               leads=None, energies=E, eta=1e-12, mu_L=mu, mu_R=mu, kT=kT)
+    out = O.solve(dev, keep_blocks=False)
+    n_all = 0.5 - np.imag(psi(0.5 + (gam / 2 + 1j * (eps0 - mu)) / (2 * np.pi * kT))) / np.pi
+    below = (np.arctan(2 * (E[0] - eps0) / gam) + np.pi / 2) / np.pi
+    assert abs(out["density_int"][0] - (n_all - below)) < 1e-8
+    # the per-energy density is the Lorentzian times the occupation
+    lor = gam / ((E - eps0) ** 2 + gam ** 2 / 4)
+    assert np.abs(out["density"][:, 0] - f * lor).max() < 1e-10 * lor.max()
