@@ -407,44 +407,30 @@ def run_wsolve(args, q, W):
 def run_uneven(args, q, W):
     """8 devices (N_B in 16..128, b in 128..512), 128 energies each, all solves captured in one CUDA
     graph (one stream per device), energies in flight per device from the autotuner."""
+    import numpy as np
     import torch
     from paper_2606_25595_gb300 import autotune
+    from paper_2606_25595_gb300.batch import UnevenBatch
     prec = args.precision if args.precision != "emu64" else "fp32"
     devs = W.uneven_batch(n_energies=128)
-    setups, chunks = [], []
+    chunks = []
     for dev in devs:
         din = q.upload(dev)
-        ec = autotune.best_chunk(din, dev["block_size"], dev["n_blocks"], prec, 128,
-                                 budget_bytes=24 << 30)
-        chunks.append(ec)
+        chunks.append(autotune.best_chunk(din, dev["block_size"], dev["n_blocks"], prec, 128,
+                                          budget_bytes=24 << 30))
         del din
-        setups.append(_solve_setup(q, dev, prec, ec, ["current", "density", "integrals"]))
-    streams = [torch.cuda.Stream() for _ in devs]
-    cap = torch.cuda.Stream()
-
-    def launch_all():
-        for k, s in enumerate(streams):
-            s.wait_stream(torch.cuda.current_stream())
-            plan, din, o, _ = setups[k]
-            plan.solve(din["_inputs"], o, s.cuda_stream)
-        for s in streams:
-            torch.cuda.current_stream().wait_stream(s)
-
-    launch_all()
-    torch.cuda.synchronize()
-    graph = torch.cuda.CUDAGraph()
+    ub = UnevenBatch(devs, prec, chunks)
     captured = True
     try:
-        with torch.cuda.graph(graph, stream=cap):
-            launch_all()
+        ub.capture()
     except Exception as ex:  # capture refused: fall back to direct launches, say so
         captured = False
         sys.stderr.write(f"graph capture failed: {ex}\n")
     torch.cuda.synchronize()
-    step = graph.replay if captured else launch_all
+    step = ub.replay if captured else ub.launch
     ms = _timed(step, args.steps, args.warmup)
-    ne_total = 128 * len(devs)
-    ok = all(bool(torch.all(s[3]["status"] == 0).item()) for s in setups)
+    ne_total = ub.n_energies
+    ok = all(bool(np.all(r["status"] == 0)) for r in ub.results())
     _line(args, ne_total * args.steps / (ms / 1e3), ms / args.steps,
           "8 random BT devices (N_B, b) = " + ", ".join(f"({d['n_blocks']},{d['block_size']})" for d in devs)
           + ", 128 energies each", prec,

@@ -24,7 +24,8 @@ enum { QTX_OP_N = 0, QTX_OP_C = 1 /* conjugate transpose */ };
  * strideA/B/C0/C batch strides in complex elements (0 shares one matrix across the batch).
  * precision: QTX_FP64 / QTX_FP32 on the CUDA cores; QTX_EMU64 / QTX_BF16X3 on the tcgen05 tensor cores
  * with 6 (7 when K > 512) / 2 bf16 digit planes per operand (Ozaki-style slicing, Sec. II-C), inputs
- * and outputs rounded to df32 (hi + lo FP32 pairs) on the way in and out.  C0 may be NULL when beta == 0; C may
+ * and outputs rounded to df32 (hi + lo FP32 pairs) on the way in and out; alpha and beta are applied as
+ * df32 pairs as well (~48 bits: a scalar such as 0.1 adds no FP32-sized error).  C0 may be NULL when beta == 0; C may
  * alias C0 (same layout).  Errors: QTX_ERR_INVALID_ARG (sizes < 0, NULL operands),
  * QTX_ERR_UNSUPPORTED (tensor-core modes on a GPU other than sm_103), QTX_ERR_CUDA, QTX_ERR_TIMEOUT
  * (a bounded wait inside the tensor-core kernel expired; the context stays usable). */
@@ -46,7 +47,8 @@ qtx_status qtx_zinv_batched(int precision, int n, void *A, long strideA, int bat
  * decimation in FP64, batched over energies: H00, H01 are n x n (H01 couples a lead cell to the next
  * one away from the device), energies[n_energies] a device array, z = E + i eta.  Output
  * SigR[n_energies][n][n]; status[e] = QTX_ERR_NOT_CONVERGED when max|alpha|,|beta| did not fall below
- * tol * max|H01| within max_iter sweeps.  Synchronises `stream` every few sweeps to test convergence. */
+ * tol * max|H01| within max_iter sweeps (convergence is tested on the device).  Synchronises `stream`
+ * once before returning (the call's temporary plan is freed). */
 qtx_status qtx_lead_self_energy(int n, const void *H00, const void *H01, const double *energies,
                                 int n_energies, double eta, double tol, int max_iter, void *SigR,
                                 int *status, void *stream);
@@ -78,7 +80,10 @@ qtx_status qtx_fpx_decompress(int bits, const void *in, long n, double *x, void 
  * library image; every GPU that loads the library holds it until the process exits.  No cudaMalloc,
  * cudaFree or allocating library routine is called.
  *   - The first call on each device (with that device current) resolves the array's device address
- *     once with cudaGetSymbolAddress; make that first call outside any stream capture.
+ *     with cudaGetSymbolAddress and caches it for that device's context; a call that finds another
+ *     context current (after cudaDeviceReset) resolves it again.  Make the first call on a device,
+ *     and the first after a reset, outside any stream capture.
+ *   - On QTX_ERR_CUDA the runtime's last error has been cleared (cudaGetLastError).
  *   - Calls share the array and it keeps the last call's contents: the wait flag is cleared at the
  *     start of every call and everything else is rewritten.  Calls that overlap on the GPU (other
  *     streams, other host threads) race on it; serialise them.

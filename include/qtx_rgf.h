@@ -52,7 +52,10 @@ typedef enum {
  * in FP64 and the lead decimation always runs in FP64. */
 typedef enum {
   QTX_FP64 = 0,   /* complex128 throughout (SIMT DFMA) -- the plain FP64 path */
-  QTX_FP32 = 1,   /* complex64 products and inverses (SIMT FFMA) */
+  QTX_FP32 = 1,   /* complex64 storage; products with all dimensions >= 96 (and K <= 1024) on the
+                     tcgen05 tensor cores from 4 bf16 digit planes per operand (10 digit products,
+                     ~27-bit products, every digit group exact), smaller products and the leaf
+                     inverses on the CUDA cores (FFMA) */
   QTX_BF16X3 = 2, /* products from 2 bf16 digit planes per operand (3 digit products, ~13-bit
                      products) on the tcgen05 tensor cores; df32 storage; refined inverses */
   QTX_EMU64 = 3   /* emulated FP64: products from 6 bf16 digit planes per operand (21 digit products
@@ -178,8 +181,11 @@ typedef struct qtx_rgf_plan_s *qtx_rgf_plan;
 qtx_status qtx_rgf_plan_create(const qtx_rgf_desc *desc, qtx_rgf_plan *out);
 
 /* Enqueue the solve of all n_energies on `stream` (a cudaStream_t; NULL = legacy default stream).
- * Energies are processed in chunks of max_energies_in_flight.  Returns after enqueueing, except
- * that lead decimation synchronises the stream once per few sweeps to test convergence. */
+ * Energies are processed in chunks of max_energies_in_flight.  Returns after enqueueing: the lead
+ * decimation tests convergence on the device (lead blocks of at most 32: the whole iteration of an
+ * energy in one CTA; larger: decim_max_iter masked sweeps), so with status_per_energy given the
+ * solve makes no host synchronisation and can be captured in a CUDA graph.  Without
+ * status_per_energy the library synchronises once per chunk to keep the worst status. */
 qtx_status qtx_rgf_solve(qtx_rgf_plan plan, const qtx_rgf_inputs *in, const qtx_rgf_outputs *out,
                          void *stream);
 

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libqtx_rgf.so")
-SOURCES = ["simt.cu", "rgf.cu", "tc_engine.cu", "noalloc.cu", "fpx.cu"]
+SOURCES = ["simt.cu", "rgf.cu", "tc_engine.cu", "noalloc.cu", "fpx.cu", "decim.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xptxas", "-warn-spills"]

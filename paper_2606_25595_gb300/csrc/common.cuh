@@ -209,7 +209,7 @@ struct TcArgs {
   const cx<df>* B; long ldb, sB; int opB;
   const cx<df>* C0; long ldc0, sC0;
   cx<df>* C; long ldc, sC;
-  float alpha, beta;
+  double alpha, beta;          // applied in df32 (split into hi + lo FP32 parts by the launcher)
   int batch;
   const int* active;
   TcOperand* opndA = nullptr;  // optional kept / reused digit planes of op(A), op(B)

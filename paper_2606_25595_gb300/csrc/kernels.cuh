@@ -96,9 +96,21 @@ cudaError_t obs_frob_dot(double* out, long ld, const cx<double>* X, long sX, con
 // ---- lead post-processing: from Sigma^R (complex128) build Gamma, Sigma^<, Sigma^>
 cudaError_t lead_sigmas(const cx<double>* SR, cx<double>* Gam, cx<double>* SL, cx<double>* SG,
                         const double* E, double mu, double kT, int b, int batch, cudaStream_t st);
-// per batch entry: if the largest modulus over X and Y is < tol, clear active[e]; count sweeps
-cudaError_t decim_converged(const cx<double>* X, const cx<double>* Y, int b, double tol,
-                            int* active, int* sweeps, int batch, cudaStream_t st);
+// per batch entry: if the largest modulus over X and Y is < tol_rel * max(*scale, or 1 if 0), clear
+// active[e]; count sweeps (scale is a device scalar, e.g. from max_modulus)
+cudaError_t decim_converged(const cx<double>* X, const cx<double>* Y, int b, double tol_rel,
+                            const double* scale, int* active, int* sweeps, int batch, cudaStream_t st);
+// out[0] = largest modulus of the n complex values X[0..n) (device scalar)
+cudaError_t max_modulus(const cx<double>* X, long n, double* out, cudaStream_t st);
+// p[0..n) = v
+cudaError_t fill_int(int* p, int v, int n, cudaStream_t st);
+// The whole decimation of a lead block of size n <= kDecimSmallMax per energy in one CTA (decim.cu):
+// SR[e] = H01 g_s(E[e] + i eta) H01^H; status[e] = QTX_ERR_NOT_CONVERGED / QTX_ERR_SINGULAR (only
+// raised from 0).  No host synchronisation.
+constexpr int kDecimSmallMax = 32;
+cudaError_t decimate_small(const cx<double>* H00, const cx<double>* H01, const double* E, double eta,
+                           double tol_rel, int max_iter, int n, int batch, cx<double>* SR, int* status,
+                           cudaStream_t st);
 // set status[e] = code for entries still active (decimation not converged)
 cudaError_t flag_active(const int* active, int* status, int code, int batch, cudaStream_t st);
 

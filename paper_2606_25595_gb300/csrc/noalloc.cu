@@ -10,13 +10,17 @@
 //
 // Set-up: a __device__ array's name in host code is only a host-side stand-in, not a device address.
 // The first call on each device, with that device current, resolves the real address with
-// cudaGetSymbolAddress (checked) and caches it per device; later calls reuse it.  Make the first call
-// on a device outside any stream capture.
+// cudaGetSymbolAddress (checked) and caches it per device together with the id of the context it
+// belongs to; later calls reuse it while the device's current context is the same one (after
+// cudaDeviceReset the runtime makes a new context, and the next call resolves the address again).
+// Make the first call on a device, and the first after a reset, outside any stream capture.
 //
 // Sharing: all calls share the one array and it keeps the last call's contents.  The wait flag is
 // cleared (cudaMemsetAsync) at the start of each call; everything else is fully rewritten.  Calls that
 // overlap on the GPU (different streams, or different host threads without ordering) race on the
 // array and must be serialised by the caller.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "../../include/qtx_kernels.h"
@@ -32,6 +36,37 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_addr[kMaxDevices] = {};
+unsigned long long g_ctx[kMaxDevices] = {};  // id of the context g_addr[dev] was resolved in
+
+// Id of the current context (0 if none is current or the driver cannot say).  The two driver
+// functions are looked up through the runtime, so the library has no link-time dependency on the
+// driver library (it still loads on a machine without a GPU driver).
+unsigned long long current_ctx_id() {
+  typedef CUresult (*get_current_t)(CUcontext*);
+  typedef CUresult (*get_id_t)(CUcontext, unsigned long long*);
+  static get_current_t get_current = nullptr;
+  static get_id_t get_id = nullptr;
+  static bool looked_up = false;
+  if (!looked_up) {
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    cudaDriverEntryPointQueryResult r1, r2;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 4000, cudaEnableDefault, &r1) == cudaSuccess &&
+        r1 == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<get_current_t>(f1);
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &r2) == cudaSuccess &&
+        r2 == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<get_id_t>(f2);
+    cudaGetLastError();
+    looked_up = true;
+  }
+  if (!get_current || !get_id) return 0;
+  CUcontext c = nullptr;
+  unsigned long long id = 0;
+  if (get_current(&c) != CUDA_SUCCESS || !c) return 0;
+  if (get_id(c, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
 
 size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -76,11 +111,17 @@ qtx_status qtx_zgemm_emu64_noalloc(int M, int N, int K, int opA, const void* A, 
   unsigned char* base = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_addr[dev]) {
+    const unsigned long long ctx = current_ctx_id();
+    if (!g_addr[dev] || ctx == 0 || ctx != g_ctx[dev]) {
       void* p = nullptr;
-      const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-      if (e != cudaSuccess || !p) return QTX_ERR_CUDA;
+      const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);  // makes the context current
+      if (e != cudaSuccess || !p) {
+        cudaGetLastError();
+        g_addr[dev] = nullptr;
+        return QTX_ERR_CUDA;
+      }
       g_addr[dev] = p;
+      g_ctx[dev] = current_ctx_id();
     }
     base = reinterpret_cast<unsigned char*>(g_addr[dev]);
   }
@@ -104,7 +145,7 @@ qtx_status qtx_zgemm_emu64_noalloc(int M, int N, int K, int opA, const void* A, 
     t.B = b; t.ldb = cB; t.sB = nB > 1 ? (long)rB * cB : 0; t.opB = opB;
     t.C0 = nC0 ? c0 : nullptr; t.ldc0 = N; t.sC0 = nC0 > 1 ? (long)M * N : 0;
     t.C = c; t.ldc = N; t.sC = (long)M * N;
-    t.alpha = (float)alpha; t.beta = nC0 ? (float)beta : 0.f;
+    t.alpha = alpha; t.beta = nC0 ? beta : 0.0;
     t.batch = batch; t.active = nullptr;
     e = gemm_tc(t, 6, base + cv.tc, kNoAllocBytes - cv.tc, flag, st);
   }
@@ -113,7 +154,10 @@ qtx_status qtx_zgemm_emu64_noalloc(int M, int N, int K, int opA, const void* A, 
   int hflag = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) return QTX_ERR_CUDA;
+  if (e != cudaSuccess) {
+    cudaGetLastError();  // leave no error pending in the runtime for the caller's next call
+    return QTX_ERR_CUDA;
+  }
   if (hflag) return QTX_ERR_TIMEOUT;
   return QTX_OK;
 }

@@ -44,7 +44,7 @@ inline bool uv_per_energy(const qtx_rgf_desc& d) {
 }
 
 struct Layout {
-  size_t g, gl, gl2, gfx, glfx, fx_slot, sig_stage, opnd[3], opnd_bytes[3], refine_act, tmp, inv_tmp, U, V, ident, ident_df, ref, f32a, f32tmp, dec, lead, obs, flags,
+  size_t g, gl, gl2, gfx, glfx, fx_slot, sig_stage, opnd[3], opnd_bytes[3], refine_act, tmp, inv_tmp, U, V, ident, ident_df, ref, f32a, f32tmp, dec, lead, obs, flags, dscale,
       tc_scratch, total;
   int n_tmp, n_dec;
   size_t tc_bytes;
@@ -126,9 +126,12 @@ Layout make_layout(const qtx_rgf_desc& d) {
   // per-energy observables: current, density, contact(2), transmission, scratch(2)
   L.obs = a.take((size_t)Ec * (2 * nb + 8) * sizeof(double));
   L.flags = a.take((size_t)Ec * 3 * sizeof(int) + 64);
+  L.dscale = a.take(64);  // device scalars (the decimation's tolerance scale)
   L.refine_act = a.take((size_t)Ec * 2 * sizeof(int) + 64);  // per-energy sweep masks (ping-pong)
   L.tc_bytes = 0;
   if (mixed) L.tc_bytes = gemm_tc_scratch_bytes((int)b, (int)b, (int)b, (int)Ec, d.precision == QTX_EMU64 ? 6 : 2);
+  // the FP32 mode's products of 96 and more (four digit planes; the recursive inverse's halves too)
+  if (d.precision == QTX_FP32 && b >= 96 && b <= 1024) L.tc_bytes = gemm_tc_scratch_bytes((int)b, (int)b, (int)b, (int)Ec, 4);
   L.tc_scratch = a.take(L.tc_bytes);
   // kept digitised operands (emulated modes): two left operands and one right operand, b x b, E_c
   // energies (none when the products are split along K)
@@ -222,13 +225,14 @@ qtx_status gemm_simt_prof(qtx_rgf_plan_s* P, const GemmArgs<T>& g, cudaStream_t 
   }
   return QTX_OK;
 }
-// The emulated-FP64 mode's FP32 starting inverse: its products of at least kTcF32Min in every
-// dimension run on the tensor cores with four digit planes (~27-bit products, at least FP32's
-// precision; every digit group exact), the smaller ones on the SIMT GEMM.
+// complex64 products (the FP32 mode, and the emulated-FP64 mode's FP32 starting inverse): those of
+// at least kTcF32Min in every dimension run on the tensor cores with four digit planes (~27-bit
+// products, at least FP32's precision; every digit group exact), the smaller ones on the SIMT GEMM.
 constexpr int kTcF32Min = 96;
+inline bool f32_on_tc(const qtx_rgf_desc& d) { return d.precision == QTX_EMU64 || d.precision == QTX_FP32; }
 template <>
 qtx_status gemm<float>(qtx_rgf_plan_s* P, const GemmArgs<float>& g, cudaStream_t st, bool, DigitHint) {
-  if (P->d.precision == QTX_EMU64 && g.M >= kTcF32Min && g.N >= kTcF32Min && g.K >= kTcF32Min && g.K <= 1024 &&
+  if (f32_on_tc(P->d) && g.M >= kTcF32Min && g.N >= kTcF32Min && g.K >= kTcF32Min && g.K <= 1024 &&
       gemm_tc_scratch_bytes(g.M, g.N, g.K, g.batch, 4) <= P->L.tc_bytes) {
     TcArgs a;
     a.f32 = true;
@@ -237,9 +241,17 @@ qtx_status gemm<float>(qtx_rgf_plan_s* P, const GemmArgs<float>& g, cudaStream_t
     a.B = reinterpret_cast<const cx<df>*>(g.B); a.ldb = g.ldb; a.sB = g.sB; a.opB = g.opB;
     a.C0 = reinterpret_cast<const cx<df>*>(g.C0); a.ldc0 = g.ldc0; a.sC0 = g.sC0;
     a.C = reinterpret_cast<cx<df>*>(g.C); a.ldc = g.ldc; a.sC = g.sC;
-    a.alpha = (float)g.alpha; a.beta = (float)g.beta;
+    a.alpha = g.alpha; a.beta = g.beta;
     a.batch = g.batch; a.active = g.active;
-    QTX_CK(gemm_tc(a, 4, P->ws + P->L.tc_scratch, P->L.tc_bytes, P->d_err_flag, st, nullptr));
+    // in the FP32 mode these are the plan's own products (profiled); in the emulated mode they
+    // belong to the starting inverse (not counted)
+    cudaEvent_t* ev = (P->prof && P->d.precision == QTX_FP32) ? P->next_events() : nullptr;
+    QTX_CK(gemm_tc(a, 4, P->ws + P->L.tc_scratch, P->L.tc_bytes, P->d_err_flag, st, ev));
+    if (ev) {
+      const double f = 8.0 * g.M * g.N * g.K * g.batch;
+      P->pipe_flops += f * tc_pairs(4);
+      P->useful_flops += f;
+    }
     return QTX_OK;
   }
   return gemm_simt_prof<float>(P, g, st);
@@ -270,7 +282,7 @@ qtx_status gemm<df>(qtx_rgf_plan_s* P, const GemmArgs<df>& g, cudaStream_t st, b
   a.B = g.B; a.ldb = g.ldb; a.sB = g.sB; a.opB = g.opB;
   a.C0 = g.C0; a.ldc0 = g.ldc0; a.sC0 = g.sC0;
   a.C = g.C; a.ldc = g.ldc; a.sC = g.sC;
-  a.alpha = (float)g.alpha; a.beta = (float)g.beta;
+  a.alpha = g.alpha; a.beta = g.beta;
   a.batch = g.batch; a.active = g.active;
   cudaEvent_t* ev = P->prof ? P->next_events() : nullptr;
   QTX_CK(gemm_tc(a, tc_digits(P->d), P->ws + P->L.tc_scratch, P->L.tc_bytes, P->d_err_flag, st, ev));
@@ -415,6 +427,11 @@ qtx_status block_inverse<df>(qtx_rgf_plan_s* P, cx<df>* A, int n, int batch, con
 
 // ----------------------------------------------------------------------------- contacts
 // Batched Sancho-Rubio decimation for one contact (FP64); result Sigma^R = H01 g_s H01^H in SR.
+// Nothing here reads back to the host: for lead blocks of at most kDecimSmallMax the whole iteration
+// of an energy runs in one CTA (decimate_small); larger blocks run decim_max_iter sweeps of batched
+// launches in which converged energies are masked off on the device (their launches return at once),
+// with the tolerance scale max|H01| computed on the device too.  A solve with contacts therefore
+// makes no host synchronisation and can be captured in a CUDA graph.
 template <typename T>
 qtx_status contact(const Ctx<T>& c, const cx<double>* H00, const cx<double>* H01, double eta,
                    cx<double>* SR) {
@@ -422,6 +439,10 @@ qtx_status contact(const Ctx<T>& c, const cx<double>* H00, const cx<double>* H01
   const int b = c.b, ne = c.ne;
   const long bb = c.bb;
   cudaStream_t st = c.st;
+  if (b <= kDecimSmallMax) {
+    QTX_CK(decimate_small(H00, H01, c.E, eta, P->d.decim_tol, P->d.decim_max_iter, b, ne, SR, c.status, st));
+    return QTX_OK;
+  }
   cx<double>* D = reinterpret_cast<cx<double>*>(P->ws + P->L.dec);
   auto buf = [&](int k) { return D + (size_t)k * P->Ec * bb; };
   cx<double>*alpha = buf(0), *beta = buf(1), *eps = buf(2), *eps_s = buf(3), *g = buf(4), *ag = buf(5),
@@ -429,12 +450,8 @@ qtx_status contact(const Ctx<T>& c, const cx<double>* H00, const cx<double>* H01
   int* flags = reinterpret_cast<int*>(P->ws + P->L.flags);
   int* active = flags;
   int* sweeps = flags + P->Ec;
-  std::vector<cx<double>> h(bb);
-  QTX_CK(cudaMemcpyAsync(h.data(), H01, bb * sizeof(cx<double>), cudaMemcpyDeviceToHost, st));
-  QTX_CK(cudaStreamSynchronize(st));
-  double scale = 0.0;
-  for (auto& v : h) scale = std::max(scale, std::hypot(v.re, v.im));
-  const double tol = P->d.decim_tol * (scale > 0 ? scale : 1.0);
+  double* scale = reinterpret_cast<double*>(P->ws + P->L.dscale);
+  QTX_CK(max_modulus(H01, bb, scale, st));
 
   Term<double> none;
   Term<double> t01; t01.p = H01; t01.s = 0; t01.alpha = 1.0;
@@ -444,10 +461,8 @@ qtx_status contact(const Ctx<T>& c, const cx<double>* H00, const cx<double>* H01
   QTX_CK((combine<double, double>(beta, bb, t01h, none, none, b, ne, nullptr, 0, 0, nullptr, st)));
   QTX_CK((combine<double, double>(eps, bb, t00, none, none, b, ne, nullptr, 0, 0, nullptr, st)));
   QTX_CK((combine<double, double>(eps_s, bb, t00, none, none, b, ne, nullptr, 0, 0, nullptr, st)));
-  std::vector<int> ones(ne, 1);
-  QTX_CK(cudaMemcpyAsync(active, ones.data(), ne * sizeof(int), cudaMemcpyHostToDevice, st));
+  QTX_CK(fill_int(active, 1, ne, st));
   QTX_CK(cudaMemsetAsync(sweeps, 0, ne * sizeof(int), st));
-  std::vector<int> act(ne);
   qtx_status s;
   auto G = [&](const cx<double>* A, const cx<double>* B, cx<double>* C) {
     return gemm<double>(P, gargs<double>(b, b, b, A, b, bb, OP_N, B, b, bb, OP_N, nullptr, 0, 0, C, b, bb, 1.0, 0.0, ne, active), st, true);
@@ -472,14 +487,7 @@ qtx_status contact(const Ctx<T>& c, const cx<double>* H00, const cx<double>* H01
     Term<double> tt2; tt2.p = t2; tt2.s = bb; tt2.alpha = 1.0;
     QTX_CK((combine<double, double>(alpha, bb, tt1, none, none, b, ne, nullptr, 0, 0, active, st)));
     QTX_CK((combine<double, double>(beta, bb, tt2, none, none, b, ne, nullptr, 0, 0, active, st)));
-    QTX_CK(decim_converged(alpha, beta, b, tol, active, sweeps, ne, st));
-    if (it % 4 == 0 || it == P->d.decim_max_iter) {
-      QTX_CK(cudaMemcpyAsync(act.data(), active, ne * sizeof(int), cudaMemcpyDeviceToHost, st));
-      QTX_CK(cudaStreamSynchronize(st));
-      bool any = false;
-      for (int v : act) any |= (v != 0);
-      if (!any) break;
-    }
+    QTX_CK(decim_converged(alpha, beta, b, P->d.decim_tol, scale, active, sweeps, ne, st));
   }
   QTX_CK(flag_active(active, c.status, (int)QTX_ERR_NOT_CONVERGED, ne, st));
   Term<double> tes; tes.p = eps_s; tes.s = bb; tes.alpha = -1.0;
@@ -1219,7 +1227,7 @@ qtx_status zgemm_via(int precision, int M, int N, int K, int opA, const void* A,
       t.B = (const cx<df>*)b; t.ldb = cB; t.sB = nB > 1 ? (long)rB * cB : 0; t.opB = opB;
       t.C0 = nC0 ? (const cx<df>*)c0 : nullptr; t.ldc0 = N; t.sC0 = nC0 > 1 ? (long)M * N : 0;
       t.C = (cx<df>*)c; t.ldc = N; t.sC = (long)M * N;
-      t.alpha = (float)alpha; t.beta = nC0 ? (float)beta : 0.f;
+      t.alpha = alpha; t.beta = nC0 ? beta : 0.0;
       t.batch = batch; t.active = nullptr;
       CK(gemm_tc(t, digits, scr, scr_bytes, flag, st));
     } else {

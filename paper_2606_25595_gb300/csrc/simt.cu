@@ -675,7 +675,8 @@ __global__ void __launch_bounds__(256) k_residual_mask(const cx<df>* R, long sR,
   __syncthreads();
   if (threadIdx.x == 0) {
     for (int w = 1; w < 8; ++w) s += red[w];
-    next[e] = s > tol2 ? 1 : 0;
+    // a NaN or infinite norm compares false against tol2: such an energy keeps refining
+    next[e] = (s <= tol2) ? 0 : 1;
   }
 }
 cudaError_t residual_mask(const cx<df>* R, long sR, int n, int batch, double tol, const int* active, int* next,
@@ -941,10 +942,42 @@ cudaError_t lead_sigmas(const cx<double>* SR, cx<double>* Gam, cx<double>* SL, c
   return cudaGetLastError();
 }
 
+// out[0] = max |X_jk| over one b x b block (the decimation's tolerance scale, kept on the device)
+__global__ void __launch_bounds__(256) k_max_modulus(const cx<double>* X, long n, double* out) {
+  double m = 0.0;
+  for (long idx = threadIdx.x; idx < n; idx += blockDim.x) m = fmax(m, hypot(X[idx].re, X[idx].im));
+  for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, off));
+  __shared__ double red[8];
+  if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 1; i < 8; ++i) m = fmax(m, red[i]);
+    out[0] = m;
+  }
+}
+cudaError_t max_modulus(const cx<double>* X, long n, double* out, cudaStream_t st) {
+  k_max_modulus<<<1, 256, 0, st>>>(X, n, out);
+  count_launch();
+  return cudaGetLastError();
+}
+
+__global__ void k_fill_int(int* p, int v, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = v;
+}
+cudaError_t fill_int(int* p, int v, int n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_fill_int<<<(n + 255) / 256, 256, 0, st>>>(p, v, n);
+  count_launch();
+  return cudaGetLastError();
+}
+
 __global__ void __launch_bounds__(256) k_decim_converged(const cx<double>* X, const cx<double>* Y, int b,
-                                                         double tol, int* active, int* sweeps) {
+                                                         double tol_rel, const double* scale, int* active,
+                                                         int* sweeps) {
   const int e = blockIdx.x;
   if (!active[e]) return;
+  const double tol = tol_rel * (*scale > 0.0 ? *scale : 1.0);
   const long bb = (long)b * b;
   double m = 0.0;
   for (long idx = threadIdx.x; idx < bb; idx += blockDim.x) {
@@ -962,9 +995,9 @@ __global__ void __launch_bounds__(256) k_decim_converged(const cx<double>* X, co
     if (m < tol) active[e] = 0;
   }
 }
-cudaError_t decim_converged(const cx<double>* X, const cx<double>* Y, int b, double tol, int* active,
-                            int* sweeps, int batch, cudaStream_t st) {
-  k_decim_converged<<<batch, 256, 0, st>>>(X, Y, b, tol, active, sweeps);
+cudaError_t decim_converged(const cx<double>* X, const cx<double>* Y, int b, double tol_rel, const double* scale,
+                            int* active, int* sweeps, int batch, cudaStream_t st) {
+  k_decim_converged<<<batch, 256, 0, st>>>(X, Y, b, tol_rel, scale, active, sweeps);
   count_launch();
   return cudaGetLastError();
 }

@@ -177,7 +177,9 @@ struct TcParams {
   int bn_last;     // complex columns the last column tile computes: N - 48 (NBt - 1), rounded up to 8
   void* C; long ldc, sC;         // cx<df>, or cx<float> for the FP32 products (IO = float)
   const void* C0; long ldc0, sC0;
-  float alpha, beta;
+  df alpha, beta;  // as df32 pairs; the kinds say how they enter the epilogue:
+  int akind;       //   alpha: 0 = +1, 1 = -1, 2 = general (df32 product)
+  int bkind;       //   beta:  0 = +1, 1 = -1, 2 = general, 3 = no beta * C0 term
   int escale;      // exponent shift of the recombined sum: 2 l1 - 2
   int a_batched, b_batched;  // 0: the operand is shared by the whole batch (digitized once)
   const int* active;
@@ -384,9 +386,17 @@ __global__ void __launch_bounds__(320, 1) k_tc_gemm(TcParams p, int n_tiles, int
           Es = Es < -250 ? -250 : (Es > 250 ? 250 : Es);
           const float f1 = __int_as_float((Es / 2 + 127) << 23), f2 = __int_as_float((Es - Es / 2 + 127) << 23);
           const df sr = sum_acc<NACC>(vr, c), si = sum_acc<NACC>(vi, c);
+          // the scales are powers of two: exact (barring over/underflow)
           cx<df> o;
-          o.re = mkdf(sr.hi * f1 * f2 * p.alpha, sr.lo * f1 * f2 * p.alpha);
-          o.im = mkdf(si.hi * f1 * f2 * p.alpha, si.lo * f1 * f2 * p.alpha);
+          o.re = mkdf(sr.hi * f1 * f2, sr.lo * f1 * f2);
+          o.im = mkdf(si.hi * f1 * f2, si.lo * f1 * f2);
+          if (p.akind == 1) {
+            o.re = df_neg(o.re);
+            o.im = df_neg(o.im);
+          } else if (p.akind == 2) {
+            o.re = df_mul(o.re, p.alpha);
+            o.im = df_mul(o.im, p.alpha);
+          }
           out[r * OUT_LD + c0 + c] = o;
         }
       }
@@ -402,10 +412,18 @@ __global__ void __launch_bounds__(320, 1) k_tc_gemm(TcParams p, int n_tiles, int
         const int mm = mblk * BM + rr, nn = nblk * BNC + cc;
         if (mm < p.M && nn < p.N) {
           cx<df> v = out[rr * OUT_LD + cc];
-          if (C0e && p.beta != 0.f) {
+          if (C0e && p.bkind != 3) {
             const cx<IO> c0v = C0e[(long)mm * p.ldc0 + nn];
-            v.re = df_add(v.re, df_mulf(df_of(c0v.re), p.beta));
-            v.im = df_add(v.im, df_mulf(df_of(c0v.im), p.beta));
+            df c0r = df_of(c0v.re), c0i = df_of(c0v.im);
+            if (p.bkind == 1) {
+              c0r = df_neg(c0r);
+              c0i = df_neg(c0i);
+            } else if (p.bkind == 2) {
+              c0r = df_mul(c0r, p.beta);
+              c0i = df_mul(c0i, p.beta);
+            }
+            v.re = df_add(v.re, c0r);
+            v.im = df_add(v.im, c0i);
           }
           Ce[(long)mm * p.ldc + nn] = c_from_df<IO>(v);
         }
@@ -732,8 +750,14 @@ cudaError_t launch(const TcArgs& a, void* scratch, size_t scratch_bytes, int* er
   p.C0 = a.C0;
   p.ldc0 = a.ldc0;
   p.sC0 = a.sC0;
-  p.alpha = a.alpha;
-  p.beta = a.beta;
+  // alpha, beta as df32 pairs (an FP64 scalar such as 0.1 keeps ~48 bits) and their kinds
+  auto kind_of = [](double x, df& v) {
+    v = df_split_fp64(x);
+    return x == 1.0 ? 0 : (x == -1.0 ? 1 : 2);
+  };
+  p.akind = kind_of(a.alpha, p.alpha);
+  p.bkind = (a.C0 && a.beta != 0.0) ? kind_of(a.beta, p.beta) : 3;
+  if (p.bkind == 3) p.beta = df_split_fp64(0.0);
   p.escale = 2 * d.l1 - 2;
   p.a_batched = ab;
   p.b_batched = bb_;
@@ -833,7 +857,7 @@ cudaError_t gemm_tc(const TcArgs& a, int digits, void* scratch, size_t scratch_b
         t.C0 = a.C;
         t.ldc0 = a.ldc;
         t.sC0 = a.sC;
-        t.beta = 1.f;
+        t.beta = 1.0;
       }
       const cudaError_t e = gemm_tc(t, digits, scratch, scratch_bytes, err_flag, st, nullptr);
       if (e != cudaSuccess) return e;

@@ -80,6 +80,25 @@ def test_emu64_random_error_bound(q, M, N, K, batch):
     assert np.all(np.abs(got - ref) <= 2.0 ** -36 * bound)
 
 
+@pytest.mark.parametrize("M,N,K,batch,alpha,beta", [(256, 256, 256, 2, 0.1, 1.0 / 3.0),
+                                                    (130, 70, 50, 3, -1.0 / 3.0, 0.1),
+                                                    (64, 96, 1536, 2, 0.1, -1.0 / 7.0)])
+def test_emu64_general_alpha_beta(q, M, N, K, batch, alpha, beta):
+    """Scalars that FP32 cannot hold (0.1, 1/3, 1/7) enter in df32 (~48 bits): the result stays within
+    the products' 2^-36 |alpha| (|A| |B|) plus 2^-40 |beta C0|; an FP32-rounded alpha or beta would
+    add ~2^-24 of every element.  The last case runs split along K (C0 enters the first chunk)."""
+    rng = np.random.default_rng(M + 3 * K)
+    A = (rng.standard_normal((batch, M, K)) + 1j * rng.standard_normal((batch, M, K))) * \
+        np.exp(rng.uniform(-3, 3, (batch, M, 1)))
+    B = rng.standard_normal((batch, K, N)) + 1j * rng.standard_normal((batch, K, N))
+    C0 = rng.standard_normal((batch, M, N)) + 1j * rng.standard_normal((batch, M, N))
+    got = q.zgemm_batched(_t(A), _t(B), "emu64", alpha=alpha, beta=beta, C0=_t(C0)).cpu().numpy()
+    ref = alpha * (A @ B) + beta * C0
+    bound = (np.abs(A.real) + np.abs(A.imag)) @ (np.abs(B.real) + np.abs(B.imag))
+    tol = 2.0 ** -36 * abs(alpha) * bound + 2.0 ** -40 * abs(beta) * (np.abs(C0.real) + np.abs(C0.imag))
+    assert np.all(np.abs(got - ref) <= tol), np.log2(np.max(np.abs(got - ref) / tol))
+
+
 @pytest.mark.parametrize("K,bits", [(512, 35), (1024, 36)])
 def test_emu64_random_error_bound_long_k(q, K, bits):
     """Long contractions (b = 512, 1024 blocks): the leading digit shrinks to keep the exact
