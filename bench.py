@@ -61,6 +61,10 @@ def parse():
                     help="mixed workloads: an energy stops its Newton sweeps once ||I - A X||_F <= this "
                          "(the next residual is then <= its square, 2^-24, below the digit products' error); "
                          "0 = always 2 sweeps")
+    ap.add_argument("--modes", default="fp32,bf16x3",
+                    help="mixed workloads: other precision modes timed on the same workload after the headline "
+                         "(one solve each, all energies), with their error against the oracle sample")
+    ap.add_argument("--no-modes", action="store_true")
     ap.add_argument("--storage-bits", type=int, default=0,
                     help="mixed workloads: keep the left-connected blocks in FPX of this many bits (0 = off)")
     return ap.parse_args()
@@ -638,6 +642,37 @@ def main():
                     "density": float(np.abs(d_h - d64n).max() / np.abs(d64n).max())}}
         del p64
 
+    # ---------------------------------------------------------------- the other modes on the same workload
+    # (all energies, same chunk and refinement; per-energy current and density kept for the errors)
+    modes = {}
+    if args.modes and args.precision == "emu64" and not args.no_modes:
+        c_main, d_main = cur.cpu().numpy(), den.cpu().numpy()
+        del plan, GR, GL
+        torch.cuda.empty_cache()
+        for m in args.modes.split(","):
+            pm = q.Plan(q.make_desc(nb, b, m, min(args.chunk, ne), refine_max_iter=2, has_scattering=True,
+                                    outputs=["current", "density"], offdiag_sigma=bt, refine_tol=args.refine_tol))
+            cm = torch.empty_like(cur)
+            dm = torch.empty_like(den)
+            sm = torch.zeros_like(stat)
+            om = q.Outputs()
+            om.current, om.density, om.status_per_energy = cm.data_ptr(), dm.data_ptr(), sm.data_ptr()
+            pm.solve(din["_inputs"], om, stream.cuda_stream)  # warm-up
+            torch.cuda.synchronize()
+            h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            h0.record(stream)
+            pm.solve(din["_inputs"], om, stream.cuda_stream)
+            h1.record(stream)
+            torch.cuda.synchronize()
+            modes[m] = {"value": ws * ne / (h0.elapsed_time(h1) / 1e3), "unit": UNIT,
+                        "status_ok": bool(torch.all(sm == 0).item()),
+                        "_cur": cm.cpu().numpy(), "_den": dm.cpu().numpy()}
+            pm.close()
+            del pm
+        cur_host, den_host = c_main, d_main
+    else:
+        cur_host, den_host = cur.cpu().numpy(), den.cpu().numpy()
+
     # ---------------------------------------------------------------- CPU oracle sample + error
     cpu = None
     err = None
@@ -649,12 +684,19 @@ def main():
         cpu = {"value": len(done) / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                "sample": f"{len(done)} of the {ne} energies (numpy complex128, LAPACK inv, "
                          f"{dt:.1f} s)"}
-        c_g, d_g = cur.cpu().numpy(), den.cpu().numpy()
+        c_g, d_g = cur_host, den_host
         cr = np.stack([res[k][0] for k in done])
         dr = np.stack([res[k][1] for k in done])
         err = {"energies": len(done),
                "current": float(np.abs(c_g[done] - cr).max() / np.abs(cr).max()),
                "density": float(np.abs(d_g[done] - dr).max() / np.abs(dr).max())}
+        for m, v in modes.items():
+            v["error_vs_oracle"] = {"energies": len(done),
+                                    "current": float(np.abs(v["_cur"][done] - cr).max() / np.abs(cr).max()),
+                                    "density": float(np.abs(v["_den"][done] - dr).max() / np.abs(dr).max())}
+    for v in modes.values():
+        v.pop("_cur", None)
+        v.pop("_den", None)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -674,7 +716,7 @@ def main():
                            "l2": "inputs and working set (>= 16 GB) larger than L2; no flush"},
                 "status_ok": status_ok,
                 "gpu_launches": int(launches),
-                "clocks": clocks, "roofline": roofline, "e2e": e2e, "fp64_path": fp64,
+                "clocks": clocks, "roofline": roofline, "e2e": e2e, "fp64_path": fp64, "other_modes": modes,
                 "cpu_baseline": cpu, "error_vs_oracle": err}
         print(json.dumps(line), flush=True)
     if ws > 1:

@@ -73,8 +73,9 @@ def lead_self_energy(E, eta, H00, H01, tol=1e-13, max_iter=100):
 
 def rgf_energy(E, dev):
     """Selected blocks and observables at one energy for a ballistic device with contacts (S = I, no
-    scattering self-energies): GR_diag, GL_diag and current, density, contact currents, transmission,
-    as in ``oracle.rgf`` (formulas in its module docstring)."""
+    scattering self-energies): every block kind (G^R diagonal, upper, lower; G^< diagonal, upper; G^>
+    = G^< + G^R - G^A diagonal and upper) and current, density, contact currents, transmission, as in
+    ``oracle.rgf`` (formulas in its module docstring)."""
     assert dev.get("leads") and dev.get("SigR") is None and dev.get("S_diag") is None
     nb, b = dev["n_blocks"], dev["block_size"]
     eta, kT = dev["eta"], dev["kT"]
@@ -102,13 +103,13 @@ def rgf_energy(E, dev):
         br = SL[i] if i == 0 else SL[i] + V[i - 1] @ gl[i - 1] @ _H(V[i - 1])
         gl[i] = g[i] @ br @ _H(g[i])
     G, GL = [None] * nb, [None] * nb
-    GLu = [None] * (nb - 1)
+    GLu, GRu, GRl = [None] * (nb - 1), [None] * (nb - 1), [None] * (nb - 1)
     G[nb - 1], GL[nb - 1] = g[nb - 1], gl[nb - 1]
     for i in range(nb - 2, -1, -1):
         P = g[i] @ U[i]
-        Gl = -G[i + 1] @ V[i] @ g[i]
-        Gu = -P @ G[i + 1]
-        G[i] = g[i] - P @ Gl
+        GRl[i] = -G[i + 1] @ V[i] @ g[i]
+        GRu[i] = -P @ G[i + 1]
+        G[i] = g[i] - P @ GRl[i]
         Q = V[i] @ gl[i]
         K = P @ G[i + 1] @ Q
         GL[i] = gl[i] + P @ GL[i + 1] @ _H(P) + K - _H(K)
@@ -122,5 +123,9 @@ def rgf_energy(E, dev):
     gam = con["L"]["Gamma"]
     A00 = 1j * (G[0] - _H(G[0]))
     T = np.real(np.trace(gam @ A00) - np.trace(gam @ G[0] @ gam @ _H(G[0])))
-    return dict(GR_diag=np.stack(G), GL_diag=np.stack(GL), current=cur, density=den,
-                contact=np.array(contact), transmission=T)
+    GG = [GL[i] + G[i] - _H(G[i]) for i in range(nb)]
+    GGu = [GLu[i] + GRu[i] - _H(GRl[i]) for i in range(nb - 1)]
+    stk = lambda lst: np.stack(lst) if lst else np.zeros((0, b, b), LD)  # noqa: E731
+    return dict(GR_diag=stk(G), GR_upper=stk(GRu), GR_lower=stk(GRl), GL_diag=stk(GL), GL_upper=stk(GLu),
+                GG_diag=stk(GG), GG_upper=stk(GGu), current=cur, density=den, contact=np.array(contact),
+                transmission=T)

@@ -75,14 +75,15 @@ def _check(res, ref, tol_blk, tol_obs, keys=BLOCKS, obs=("current", "density")):
 
 # Eq. 6 of the paper: error ~ kappa * eps_m.  With contacts the kappa that matters is that of the
 # decimation's inverted blocks (z - eps), which reaches ~3e4 at eta = 1e-6.  There even the FP64
-# oracle (LAPACK inverses) is up to 3.5e-10 -- 141 kappa_dec eps_64 -- from the exact G blocks
-# (tests/test_oracle_hiprec.py, against an extended-precision evaluation), so a flat 1e-10 bar on
-# blocks cannot hold at those energies for any FP64 evaluation.  Blocks are therefore held to
-# max(1e-10, KAPPA_X kappa_dec(E) eps_64) of the extended-precision values (and the FP64 oracle to
-# twice that, as the two errors add), observables and energy integrals to a flat 1e-10.
-KAPPA_X = 256
-# random contacts (kappa_dec up to ~1e6) have no extended reference: blocks against the oracle with
-# the sum of both bars
+# oracle (LAPACK inverses) is up to 3.5e-10 -- 141 kappa_dec eps_64 -- from the exact G blocks, and
+# how far depends on the platform's LAPACK (on the Arm host of the GPU ~3.5e-10 at E = -3.278 where
+# the x86 one is 2.4e-12).  So on the strip every block and observable is judged against an
+# extended-precision evaluation (oracle.hiprec, pinned in tests/test_oracle_hiprec.py): observables
+# and energy integrals to a flat 1e-10, blocks to max(1e-10, KAPPA_X kappa_dec(E) eps_64) (this path:
+# at most 237 kappa_dec eps_64 measured, the FP64 oracle 141).
+KAPPA_X = 512
+# random contacts (kappa_dec up to ~1e6; no extended reference): blocks against the FP64 oracle,
+# whose own error adds to the path's
 KAPPA_C = 2 * KAPPA_X
 
 
@@ -110,57 +111,43 @@ def _check_obs_kappa(res, ref, keys=("current", "density", "contact", "transmiss
         assert np.all(err < tol_e), (k, err.max())
 
 
-def _strip_fixture():
-    import os
-    rows = np.loadtxt(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "strip_extended.txt"))
-    nb = W.STRIP_CFG["n_blocks"]
-    return dict(energies=rows[:, 0], transmission=rows[:, 1], contact=rows[:, 2:4],
-                current=rows[:, 4:4 + nb - 1], density=rows[:, 4 + nb - 1:4 + 2 * nb - 1])
+def _strip_against_extended(q, dev):
+    """GPU FP64 solve of a strip against oracle.hiprec at every energy: observables and both energy
+    integrals within 1e-10 (relative to the largest magnitude over the grid), every block kind within
+    max(1e-10, KAPPA_X kappa_dec(E) eps_64) (relative Frobenius per energy; G^> against the norm of its
+    summands, as _scale says)."""
+    from oracle import hiprec
+    res = q.solve_device(dev, "fp64")
+    assert np.all(res["status"] == 0)
+    kap = O.solve(dev, track_cond=True, keep_blocks=False)["decim_cond"]
+    ne = len(dev["energies"])
+    xs = [hiprec.rgf_energy(float(E), dev) for E in dev["energies"]]
+    ext = {k: np.stack([np.asarray(x[k], dtype=np.complex128 if k in BLOCKS else np.float64) for x in xs])
+           for k in BLOCKS + ("current", "density", "contact", "transmission")}
+    for k in ("current", "density", "contact", "transmission"):
+        x = ext[k].reshape(ne, -1)
+        g = np.asarray(res[k]).reshape(ne, -1)
+        assert np.abs(g - x).max() < 1e-10 * np.abs(x).max(), (k, np.abs(g - x).max() / np.abs(x).max())
+    w = W.trapezoid_weights(dev["energies"])
+    assert _obs_err(res["current_int"], w @ ext["current"]) < 1e-10
+    assert _obs_err(res["density_int"], (w @ ext["density"]) / (2 * np.pi)) < 1e-10
+    tol = np.maximum(1e-10, KAPPA_X * kap * 2.0 ** -53)
+    for k in BLOCKS:
+        errs = _errs(res, ext, k)
+        assert np.all(errs < tol), (k, errs.max(), dev["energies"][np.argmax(errs / tol)])
 
 
 def test_strip_fp64_full_config(q):
-    """W=16 strip, b=16, N_B=32, 64 energies, Sancho-Rubio contacts at eta = 1e-6, FP64, judged
-    against the extended-precision values (oracle.hiprec; the observables in
-    tests/golden/strip_extended.txt): current, density, contact currents and transmission within
-    1e-10 of their largest magnitude over the grid, both energy integrals within 1e-10; G^R and G^<
-    diagonal blocks at the four worst-conditioned energies within max(1e-10, KAPPA_X kappa_dec eps_64)
-    of the extended-precision blocks; every block kind at every energy within 1e-10 of the FP64 oracle
-    at the median energy and within max(1e-10, 2 KAPPA_X kappa_dec eps_64) everywhere."""
-    from oracle import hiprec
-    dev = W.strip(**{k: v for k, v in W.STRIP_CFG.items()})
-    ref = O.solve(dev, track_cond=True)
-    res = q.solve_device(dev, "fp64")
-    assert np.all(res["status"] == 0)
-    fx = _strip_fixture()
-    assert np.array_equal(fx["energies"], dev["energies"])
-    for k in ("current", "density", "contact", "transmission"):
-        x = np.asarray(fx[k]).reshape(64, -1)
-        g = np.asarray(res[k]).reshape(64, -1)
-        assert np.abs(g - x).max() < 1e-10 * np.abs(x).max(), (k, np.abs(g - x).max() / np.abs(x).max())
-    w = W.trapezoid_weights(fx["energies"])
-    ci, di = w @ fx["current"], (w @ fx["density"]) / (2 * np.pi)
-    assert _obs_err(res["current_int"], ci) < 1e-10
-    assert _obs_err(res["density_int"], di) < 1e-10
-    worst = np.argsort(ref["decim_cond"])[::-1][:4]
-    for e in worst:
-        x = hiprec.rgf_energy(float(dev["energies"][e]), dev)
-        tol = max(1e-10, KAPPA_X * ref["decim_cond"][e] * 2.0 ** -53)
-        for k in ("GR_diag", "GL_diag"):
-            xb = x[k].astype(np.complex128)
-            err = np.linalg.norm(res[k][e] - xb) / np.linalg.norm(xb)
-            assert err < tol, (k, dev["energies"][e], err, tol)
-    _check_blocks_kappa(res, ref)
+    """W=16 strip, b=16, N_B=32, 64 energies, Sancho-Rubio contacts at eta = 1e-6, FP64, against the
+    extended-precision evaluation (_strip_against_extended)."""
+    _strip_against_extended(q, W.strip(**{k: v for k, v in W.STRIP_CFG.items()}))
 
 
 def test_strip_fp64_eta_1e3(q):
     """Same strip with eta = 1e-3: same bars."""
     cfg = dict(W.STRIP_CFG)
     cfg["eta"] = 1e-3
-    dev = W.strip(**cfg)
-    ref = O.solve(dev, track_cond=True)
-    res = q.solve_device(dev, "fp64")
-    _check_blocks_kappa(res, ref)
-    _check_obs_kappa(res, ref)
+    _strip_against_extended(q, W.strip(**cfg))
 
 
 @pytest.mark.parametrize("b,nb,ne,chunk", [(5, 3, 3, 2), (37, 4, 3, 3), (80, 3, 2, 1),
