@@ -229,6 +229,32 @@ typedef struct {
  * the plan's), QTX_ERR_CUDA. */
 qtx_status qtx_w_assemble(qtx_rgf_plan plan, const qtx_w_inputs *in, const qtx_w_outputs *out, void *stream);
 
+/* Groups: several plans -- devices of different N_B and b, each with its own energies, inputs and
+ * outputs -- solved together (the uneven batches of Sec. II-A's energy-parallel solve: every energy of
+ * every device is independent).  qtx_rgf_group_solve runs each member's qtx_rgf_solve on its own
+ * stream (forked from and joined back to `stream`) and pools the members' small tensor-core products:
+ * a product that fills two waves of the GPU alone is launched at once on its member's stream; smaller
+ * ones are posted and launched together -- ONE persistent kernel over the union of their tiles, up to
+ * 8 products of one kernel variant per launch -- once they fill two waves, once every member still
+ * solving has posted one, or after a short host wait.  Every member's results equal its plan's solo
+ * solve bit for bit.  Every member needs status_per_energy (a solo solve without it
+ * synchronises the host).  The call returns after enqueueing everything; it makes no host
+ * synchronisation, so it can be captured in a CUDA graph.  The plans stay owned by the caller and
+ * must outlive the group; a plan belongs to at most one solving group at a time and must not be
+ * solved on its own meanwhile.
+ * Errors: QTX_ERR_INVALID_ARG (NULL arguments, a member without status_per_energy), the first failing
+ * member's status (message in qtx_rgf_group_last_error), QTX_ERR_CUDA. */
+typedef struct qtx_rgf_group_s *qtx_rgf_group;
+qtx_status qtx_rgf_group_create(int n_plans, const qtx_rgf_plan *plans, qtx_rgf_group *out);
+qtx_status qtx_rgf_group_solve(qtx_rgf_group group, const qtx_rgf_inputs *const *inputs,
+                               const qtx_rgf_outputs *const *outputs, void *stream);
+qtx_status qtx_rgf_group_destroy(qtx_rgf_group group);
+const char *qtx_rgf_group_last_error(qtx_rgf_group group);
+/* Pooled product-kernel launches this group has issued, and the products they covered (monotonic;
+ * for tests and profiling). */
+long long qtx_rgf_group_launches(qtx_rgf_group group);
+long long qtx_rgf_group_pooled_products(qtx_rgf_group group);
+
 /* Library version string. */
 const char *qtx_rgf_version(void);
 

@@ -13,7 +13,7 @@ import os
 
 import numpy as np
 
-__all__ = ["lib", "load", "Desc", "Inputs", "Outputs", "Plan", "QtxError", "PRECISION",
+__all__ = ["lib", "load", "Desc", "Inputs", "Outputs", "Plan", "Group", "QtxError", "PRECISION",
            "OUT", "solve_device", "solve_w", "WSystem", "footprint", "EXPORTED"]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -32,7 +32,9 @@ EXPORTED = ("qtx_rgf_plan_create", "qtx_rgf_solve", "qtx_rgf_status", "qtx_rgf_d
             "qtx_rgf_last_error", "qtx_rgf_footprint", "qtx_rgf_version", "qtx_zgemm_batched",
             "qtx_zinv_batched", "qtx_lead_self_energy", "qtx_rgf_set_profiling",
             "qtx_rgf_gemm_profile", "qtx_kernel_launches", "qtx_zgemm_emu64_noalloc",
-            "qtx_fpx_bytes", "qtx_fpx_compress", "qtx_fpx_decompress", "qtx_w_assemble")
+            "qtx_fpx_bytes", "qtx_fpx_compress", "qtx_fpx_decompress", "qtx_w_assemble",
+            "qtx_rgf_group_create", "qtx_rgf_group_solve", "qtx_rgf_group_destroy",
+            "qtx_rgf_group_last_error", "qtx_rgf_group_launches", "qtx_rgf_group_pooled_products")
 
 
 class QtxError(RuntimeError):
@@ -131,6 +133,18 @@ def load() -> ctypes.CDLL:
     L.qtx_zgemm_emu64_noalloc.restype = i
     L.qtx_w_assemble.argtypes = [ctypes.c_void_p, ctypes.POINTER(WInputs), ctypes.POINTER(WOutputs), vp]
     L.qtx_w_assemble.restype = i
+    L.qtx_rgf_group_create.argtypes = [i, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p)]
+    L.qtx_rgf_group_create.restype = i
+    L.qtx_rgf_group_solve.argtypes = [vp, ctypes.POINTER(ctypes.POINTER(Inputs)), ctypes.POINTER(ctypes.POINTER(Outputs)), vp]
+    L.qtx_rgf_group_solve.restype = i
+    L.qtx_rgf_group_destroy.argtypes = [vp]
+    L.qtx_rgf_group_destroy.restype = i
+    L.qtx_rgf_group_last_error.argtypes = [vp]
+    L.qtx_rgf_group_last_error.restype = ctypes.c_char_p
+    L.qtx_rgf_group_launches.argtypes = [vp]
+    L.qtx_rgf_group_launches.restype = ctypes.c_longlong
+    L.qtx_rgf_group_pooled_products.argtypes = [vp]
+    L.qtx_rgf_group_pooled_products.restype = ctypes.c_longlong
     L.qtx_fpx_bytes.argtypes = [i, l]
     L.qtx_fpx_bytes.restype = ctypes.c_size_t
     L.qtx_fpx_compress.argtypes = [i, vp, l, d, vp, vp]
@@ -213,6 +227,46 @@ class Plan:
     def close(self):
         if getattr(self, "_h", None):
             load().qtx_rgf_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Group:
+    """Owns a ``qtx_rgf_group``: several plans solved together, their tensor-core products pooled
+    into shared persistent launches (include/qtx_rgf.h).  Marshalling only."""
+
+    def __init__(self, plans: list):
+        L = load()
+        self.plans = list(plans)
+        arr = (ctypes.c_void_p * len(plans))(*[p._h for p in plans])
+        h = ctypes.c_void_p()
+        s = L.qtx_rgf_group_create(len(plans), arr, ctypes.byref(h))
+        if s != 0:
+            raise QtxError(s, L.qtx_rgf_group_last_error(None).decode())
+        self._h = h
+
+    def solve(self, inputs: list, outputs: list, stream: int = 0) -> None:
+        L = load()
+        ia = (ctypes.POINTER(Inputs) * len(inputs))(*[ctypes.pointer(x) for x in inputs])
+        oa = (ctypes.POINTER(Outputs) * len(outputs))(*[ctypes.pointer(x) for x in outputs])
+        s = L.qtx_rgf_group_solve(self._h, ia, oa, ctypes.c_void_p(stream))
+        if s != 0:
+            raise QtxError(s, L.qtx_rgf_group_last_error(self._h).decode())
+
+    def launches(self) -> int:
+        return int(load().qtx_rgf_group_launches(self._h))
+
+    def pooled_products(self) -> int:
+        return int(load().qtx_rgf_group_pooled_products(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().qtx_rgf_group_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -3,17 +3,19 @@ energy grid, solved together and replayed as one CUDA graph.
 
 Energies are independent (Sec. II-A: Eq. 2 is solved per energy), so devices of different shapes
 share the GPU without any exchange.  Each device gets its own plan (workspace sized for its shape and
-energies in flight) and its own stream; one ``capture()`` records every device's solve, forked from
-and joined back to a capture stream, into a single CUDA graph, and ``replay()`` launches that graph.
-Solves without contacts and with a per-energy status output make no host synchronisation, so they
-capture cleanly.  This module only marshals arguments and orders launches; every step of the solves
-runs in the library's kernels.
+energies in flight).  With ``grouped`` (the default) the plans form a ``qtx_rgf_group``: one call
+solves every device, each on its own stream, and at every step the tensor-core products of all
+devices run as one persistent kernel launch over the union of their tiles.  Otherwise each device's
+solve is launched on its own stream.  ``capture()`` records one launch of the whole batch into a CUDA
+graph and ``replay()`` replays it.  Solves with a per-energy status output make no host
+synchronisation, so they capture cleanly.  This module only marshals arguments and orders launches;
+every step of the solves runs in the library's kernels.
 """
 from __future__ import annotations
 
 import numpy as np
 
-from . import Outputs, Plan, make_desc, upload
+from . import Group, Outputs, Plan, make_desc, upload
 
 
 class UnevenBatch:
@@ -23,9 +25,10 @@ class UnevenBatch:
     ``outputs``: names as in ``make_desc``; per-energy arrays and integrals are kept on the device."""
 
     def __init__(self, devs: list, precision: str = "fp32", chunks=None, refine_max_iter: int = 2,
-                 refine_tol: float = 0.0, outputs=("current", "density", "integrals")):
+                 refine_tol: float = 0.0, outputs=("current", "density", "integrals"), grouped: bool = True):
         import torch
         self.devs = devs
+        self.grouped = grouped
         self.precision = precision
         self.items = []
         for k, dev in enumerate(devs):
@@ -60,6 +63,7 @@ class UnevenBatch:
             o.status_per_energy = bufs["status"].data_ptr()
             self.items.append(dict(plan=plan, din=din, out=o, bufs=bufs, chunk=ec, n_energies=ne))
         self.streams = [torch.cuda.Stream() for _ in devs]
+        self.group = Group([it["plan"] for it in self.items]) if grouped else None
         self.graph = None
 
     @property
@@ -67,10 +71,14 @@ class UnevenBatch:
         return sum(it["n_energies"] for it in self.items)
 
     def launch(self):
-        """Enqueue every device's solve on its own stream, forked from and joined back to the
-        current stream."""
+        """Enqueue every device's solve, forked from and joined back to the current stream: one group
+        solve (pooled product launches), or one solve per device on its own stream."""
         import torch
         cur = torch.cuda.current_stream()
+        if self.group is not None:
+            self.group.solve([it["din"]["_inputs"] for it in self.items], [it["out"] for it in self.items],
+                             cur.cuda_stream)
+            return
         for it, s in zip(self.items, self.streams):
             s.wait_stream(cur)
             it["plan"].solve(it["din"]["_inputs"], it["out"], s.cuda_stream)
@@ -83,7 +91,8 @@ class UnevenBatch:
         self.launch()
         torch.cuda.synchronize()
         g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g, stream=torch.cuda.Stream()):
+        # a group solve enqueues from one host thread per device into the capturing streams
+        with torch.cuda.graph(g, stream=torch.cuda.Stream(), capture_error_mode="thread_local"):
             self.launch()
         torch.cuda.synchronize()
         self.graph = g
@@ -100,5 +109,8 @@ class UnevenBatch:
 
     def close(self):
         self.graph = None
+        if self.group is not None:
+            self.group.close()
+            self.group = None
         for it in self.items:
             it["plan"].close()

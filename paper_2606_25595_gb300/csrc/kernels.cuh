@@ -127,6 +127,42 @@ cudaError_t integrate_add(double* acc, const double* val, long ld, int n, const 
 // `ev` (optional, two events) brackets the tensor-core GEMM kernel itself (not the digitiser).
 cudaError_t gemm_tc(const TcArgs& a, int digits, void* scratch, size_t scratch_bytes, int* err_flag,
                     cudaStream_t st, cudaEvent_t* ev = nullptr);
+// Kernel parameters of one tensor-core product (filled by gemm_tc_prepare).
+struct TcParams {
+  const unsigned char* pa;  // A plane tiles [batch'][S][M_pad/128][nks][128 x 32 B]
+  const unsigned char* pb;  // B plane sub-tiles [batch'][S][N_pad/48][K_pad/16][3][48 x 32 B]: Re, Im, -Im
+  const int* eA;   // [batch][M_pad] row exponents of op(A)
+  const int* eB;   // [batch][N_pad] column exponents of op(B)
+  int M_pad, N_pad, nks;  // nks: K-stages of 16 over the embedded K (2 * K_pad)
+  int M, N;
+  int bn_last;     // complex columns the last column tile computes: N - 48 (NBt - 1), rounded up to 8
+  void* C; long ldc, sC;         // cx<df>, or cx<float> for the FP32 products
+  const void* C0; long ldc0, sC0;
+  df alpha, beta;  // as df32 pairs; the kinds say how they enter the epilogue:
+  int akind;       //   alpha: 0 = +1, 1 = -1, 2 = general (df32 product)
+  int bkind;       //   beta:  0 = +1, 1 = -1, 2 = general, 3 = no beta * C0 term
+  int escale;      // exponent shift of the recombined sum: 2 l1 - 2
+  int a_batched, b_batched;  // 0: the operand is shared by the whole batch (digitized once)
+  const int* active;
+  int* err;
+};
+// A product whose operands are digitised (on the preparing stream) and whose kernel parameters are
+// filled, ready to launch alone or with other products of the same variant.
+struct TcPrepared {
+  int variant = -1;  // gemm_tc_variant
+  int NBt = 0, MBt = 0;
+  long tiles = 0;    // output tiles: column tiles x row tiles x batch
+  TcParams p{};
+};
+// Kernel variant of a product: digits used and IO type; -1 for products split along K.
+int gemm_tc_variant(const TcArgs& a, int digits);
+// Digitise a product's operands on `st` (not one split along K) and fill *out.
+cudaError_t gemm_tc_prepare(const TcArgs& a, int digits, void* scratch, size_t scratch_bytes, int* err_flag,
+                            cudaStream_t st, TcPrepared* out);
+// One persistent launch over the tiles of 1..kTcMaxGroup prepared products of one variant (each
+// product's tiles computed exactly as in a launch of its own: the results are bit-identical).
+constexpr int kTcMaxGroup = 8;
+cudaError_t gemm_tc_launch(const TcPrepared* const* p, int n, cudaStream_t st, cudaEvent_t* ev = nullptr);
 // digit products (pairs i + j <= digits + 1) the engine issues per real product
 inline int tc_pairs(int digits) { return digits * (digits + 1) / 2; }
 size_t gemm_tc_scratch_bytes(int M, int N, int K, int batch, int digits);

@@ -12,9 +12,13 @@
 // safe here for the same reason it is safe between slices: the anti-Hermitian part of M,
 // eta S + Gamma/2, is positive definite, so every leading principal block and every Schur
 // complement is nonsingular.
+#include <chrono>
+#include <condition_variable>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
+#include <thread>
 #include <type_traits>
 #include <vector>
 
@@ -51,8 +55,12 @@ struct Layout {
 };
 }  // namespace
 
+struct qtx_rgf_group_s;
+
 struct qtx_rgf_plan_s {
   qtx_rgf_desc d{};
+  qtx_rgf_group_s* group = nullptr;  // set while the plan solves as a member of a group
+  int member = -1;
   int b = 0, nb = 0, Ec = 0;
   long bb = 0;
   size_t esz = 0;  // bytes per complex element of the sweep workspace
@@ -208,6 +216,10 @@ template <typename T>
 qtx_status gemm(qtx_rgf_plan_s* P, const GemmArgs<T>& g, cudaStream_t st, bool force_simt = false,
                 DigitHint hint = DigitHint{});
 
+// A tensor-core product of a plan that solves as a group member: posted to the group, launched
+// together with the other members' products (defined with the group below).
+cudaError_t group_gemm(qtx_rgf_plan_s* P, const TcArgs& a, int digits, cudaStream_t st);
+
 // The profiled product kernel is the plan's own: the SIMT GEMM in the FP64 / FP32 modes, the
 // tensor-core GEMM in the emulated modes (whose FP32 starting-guess inverse also calls GEMMs -- SIMT,
 // or the tensor cores' four-plane FP32 instance -- which are not counted).
@@ -245,6 +257,10 @@ qtx_status gemm<float>(qtx_rgf_plan_s* P, const GemmArgs<float>& g, cudaStream_t
     a.batch = g.batch; a.active = g.active;
     // in the FP32 mode these are the plan's own products (profiled); in the emulated mode they
     // belong to the starting inverse (not counted)
+    if (P->group && gemm_tc_variant(a, 4) >= 0) {
+      QTX_CK(group_gemm(P, a, 4, st));
+      return QTX_OK;
+    }
     cudaEvent_t* ev = (P->prof && P->d.precision == QTX_FP32) ? P->next_events() : nullptr;
     QTX_CK(gemm_tc(a, 4, P->ws + P->L.tc_scratch, P->L.tc_bytes, P->d_err_flag, st, ev));
     if (ev) {
@@ -284,6 +300,10 @@ qtx_status gemm<df>(qtx_rgf_plan_s* P, const GemmArgs<df>& g, cudaStream_t st, b
   a.C = g.C; a.ldc = g.ldc; a.sC = g.sC;
   a.alpha = g.alpha; a.beta = g.beta;
   a.batch = g.batch; a.active = g.active;
+  if (P->group && gemm_tc_variant(a, tc_digits(P->d)) >= 0) {
+    QTX_CK(group_gemm(P, a, tc_digits(P->d), st));
+    return QTX_OK;
+  }
   cudaEvent_t* ev = P->prof ? P->next_events() : nullptr;
   QTX_CK(gemm_tc(a, tc_digits(P->d), P->ws + P->L.tc_scratch, P->L.tc_bytes, P->d_err_flag, st, ev));
   if (ev) {
@@ -1357,6 +1377,228 @@ qtx_status qtx_lead_self_energy(int n, const void* H00, const void* H01, const d
   qtx_rgf_destroy(P);
   if (s == QTX_OK && e != cudaSuccess) s = QTX_ERR_CUDA;
   return s;
+}
+
+}  // extern "C"
+
+// ----------------------------------------------------------------------------- groups (uneven batches)
+// Several plans -- devices of different N_B and b, each with its own energies -- solved together:
+// every member's solve runs on its own host thread and stream.  A tensor-core product is digitised on
+// the member's stream; if it fills at least kPoolWaves waves of the GPU alone it is launched there
+// at once, otherwise it is pooled: the member posts it and waits, and the pending products are
+// launched together -- one persistent kernel over the union of their tiles, per kernel variant, at most
+// kTcMaxGroup products a launch -- on the group's stream once they fill kPoolWaves waves, once every
+// member still solving has posted one, or once the poster has waited kPoolWaitUs on the host.  Events
+// order each pooled launch after its members' preceding work and before their following work.  The
+// grouping only changes which launch computes a tile, never how, so every member's results equal
+// its plan's solo solve bit for bit; the launches are plain stream work joined back to the caller's
+// stream, so a group solve can be captured in a CUDA graph.
+constexpr int kPoolWaves = 2;
+constexpr int kPoolWaitUs = 50;
+
+struct qtx_rgf_group_s {
+  std::vector<qtx_rgf_plan_s*> plans;
+  std::vector<cudaStream_t> mst;     // member streams
+  std::vector<cudaEvent_t> ready;    // per member: its work up to the posted product
+  cudaStream_t gst = nullptr;        // launch stream of the pooled products
+  std::vector<cudaEvent_t> done;     // ring of launch events
+  size_t done_pos = 0;
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> join;
+  cudaEvent_t gjoin = nullptr;
+  long pool_tiles = 304;             // kPoolWaves x SMs
+  std::mutex mu;
+  std::condition_variable cv;
+  struct Req {
+    TcPrepared p;
+    int member = 0;
+    bool released = false;
+    cudaEvent_t after = nullptr;
+    cudaError_t status = cudaSuccess;
+  };
+  std::vector<Req*> pending;
+  long pending_tiles = 0;
+  int live = 0;
+  long long launches = 0, pooled_products = 0;
+  std::string err;
+
+  // with mu held: launch every pending product and release the posting threads
+  void launch_pending() {
+    cudaError_t e = cudaSuccess;
+    for (Req* r : pending)
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(gst, ready[r->member], 0);
+    std::vector<bool> taken(pending.size(), false);
+    for (size_t i = 0; i < pending.size() && e == cudaSuccess; ++i) {
+      if (taken[i]) continue;
+      const TcPrepared* p[kTcMaxGroup];
+      int n = 0;
+      for (size_t j = i; j < pending.size() && n < kTcMaxGroup; ++j) {
+        if (taken[j] || pending[j]->p.variant != pending[i]->p.variant) continue;
+        taken[j] = true;
+        p[n++] = &pending[j]->p;
+      }
+      e = gemm_tc_launch(p, n, gst);
+      ++launches;
+      pooled_products += n;
+    }
+    cudaEvent_t ev = done[done_pos++ % done.size()];
+    if (e == cudaSuccess) e = cudaEventRecord(ev, gst);
+    for (Req* r : pending) {
+      r->after = ev;
+      r->status = e;
+      r->released = true;
+    }
+    pending.clear();
+    pending_tiles = 0;
+    cv.notify_all();
+  }
+};
+
+namespace {
+
+cudaError_t group_gemm(qtx_rgf_plan_s* P, const TcArgs& a, int digits, cudaStream_t st) {
+  qtx_rgf_group_s* G = P->group;
+  qtx_rgf_group_s::Req r;
+  r.member = P->member;
+  cudaError_t e = gemm_tc_prepare(a, digits, P->ws + P->L.tc_scratch, P->L.tc_bytes, P->d_err_flag, st, &r.p);
+  if (e != cudaSuccess || r.p.tiles == 0) return e;
+  if (r.p.tiles >= G->pool_tiles) {  // fills the GPU alone
+    const TcPrepared* one[1] = {&r.p};
+    return gemm_tc_launch(one, 1, st);
+  }
+  if ((e = cudaEventRecord(G->ready[P->member], st)) != cudaSuccess) return e;
+  {
+    std::unique_lock<std::mutex> lk(G->mu);
+    G->pending.push_back(&r);
+    G->pending_tiles += r.p.tiles;
+    if (G->pending_tiles >= G->pool_tiles || (int)G->pending.size() == G->live) G->launch_pending();
+    while (!r.released)
+      if (!G->cv.wait_for(lk, std::chrono::microseconds(kPoolWaitUs), [&] { return r.released; }))
+        G->launch_pending();
+  }
+  if (r.status != cudaSuccess) return r.status;
+  return cudaStreamWaitEvent(st, r.after, 0);
+}
+
+// a member leaves the group when its solve has returned (successfully or not)
+void group_leave(qtx_rgf_group_s* G) {
+  std::unique_lock<std::mutex> lk(G->mu);
+  --G->live;
+  if (G->live > 0 && !G->pending.empty() && (int)G->pending.size() == G->live) G->launch_pending();
+}
+
+}  // namespace
+
+extern "C" {
+
+qtx_status qtx_rgf_group_create(int n_plans, const qtx_rgf_plan* plans, qtx_rgf_group* out) {
+  if (!out || n_plans < 1 || !plans) return QTX_ERR_INVALID_ARG;
+  *out = nullptr;
+  for (int m = 0; m < n_plans; ++m)
+    if (!plans[m] || plans[m]->group) return QTX_ERR_INVALID_ARG;
+  auto* G = new qtx_rgf_group_s();
+  G->plans.assign(plans, plans + n_plans);
+  int dev = 0, sms = 152;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  G->pool_tiles = (long)kPoolWaves * sms;
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&G->gst, cudaStreamNonBlocking);
+  G->mst.assign(n_plans, nullptr);
+  G->ready.assign(n_plans, nullptr);
+  G->join.assign(n_plans, nullptr);
+  G->done.assign(4, nullptr);
+  for (int m = 0; m < n_plans && e == cudaSuccess; ++m) {
+    e = cudaStreamCreateWithFlags(&G->mst[m], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&G->ready[m], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&G->join[m], cudaEventDisableTiming);
+  }
+  for (auto& ev : G->done)
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&G->fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&G->gjoin, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    g_create_error = std::string("group set-up: ") + cudaGetErrorString(e);
+    qtx_rgf_group_destroy(G);
+    return QTX_ERR_CUDA;
+  }
+  *out = G;
+  return QTX_OK;
+}
+
+qtx_status qtx_rgf_group_solve(qtx_rgf_group G, const qtx_rgf_inputs* const* in, const qtx_rgf_outputs* const* out,
+                               void* stream) {
+  if (!G || !in || !out) return QTX_ERR_INVALID_ARG;
+  const int n = (int)G->plans.size();
+  for (int m = 0; m < n; ++m)
+    if (!in[m] || !out[m] || !out[m]->status_per_energy) {
+      G->err = "group solves need inputs, outputs and a status_per_energy array for every member";
+      return QTX_ERR_INVALID_ARG;
+    }
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  G->err.clear();
+  if (cudaEventRecord(G->fork, st) != cudaSuccess) { G->err = "fork event"; return QTX_ERR_CUDA; }
+  for (int m = 0; m < n; ++m)
+    if (cudaStreamWaitEvent(G->mst[m], G->fork, 0) != cudaSuccess) { G->err = "fork wait"; return QTX_ERR_CUDA; }
+  // the group stream starts after the caller's earlier work too
+  if (cudaStreamWaitEvent(G->gst, G->fork, 0) != cudaSuccess) { G->err = "fork wait"; return QTX_ERR_CUDA; }
+  std::vector<qtx_status> res(n, QTX_OK);
+  G->live = n;
+  G->pending.clear();
+  for (int m = 0; m < n; ++m) {
+    G->plans[m]->group = G;
+    G->plans[m]->member = m;
+  }
+  std::vector<std::thread> th;
+  th.reserve(n);
+  for (int m = 0; m < n; ++m)
+    th.emplace_back([&, m] {
+      res[m] = qtx_rgf_solve(G->plans[m], in[m], out[m], G->mst[m]);
+      group_leave(G);
+    });
+  for (auto& t : th) t.join();
+  for (int m = 0; m < n; ++m) {
+    G->plans[m]->group = nullptr;
+    G->plans[m]->member = -1;
+  }
+  qtx_status worst = QTX_OK;
+  for (int m = 0; m < n; ++m)
+    if (res[m] != QTX_OK && worst == QTX_OK) {
+      worst = res[m];
+      G->err = std::string("member ") + std::to_string(m) + ": " + G->plans[m]->err;
+    }
+  // join every member stream and the group stream back into the caller's stream
+  for (int m = 0; m < n; ++m) {
+    if (cudaEventRecord(G->join[m], G->mst[m]) != cudaSuccess || cudaStreamWaitEvent(st, G->join[m], 0) != cudaSuccess) {
+      if (worst == QTX_OK) { worst = QTX_ERR_CUDA; G->err = "join"; }
+    }
+  }
+  if (cudaEventRecord(G->gjoin, G->gst) != cudaSuccess || cudaStreamWaitEvent(st, G->gjoin, 0) != cudaSuccess) {
+    if (worst == QTX_OK) { worst = QTX_ERR_CUDA; G->err = "join"; }
+  }
+  return worst;
+}
+
+long long qtx_rgf_group_launches(qtx_rgf_group G) { return G ? G->launches : 0; }
+
+long long qtx_rgf_group_pooled_products(qtx_rgf_group G) { return G ? G->pooled_products : 0; }
+
+const char* qtx_rgf_group_last_error(qtx_rgf_group G) { return G ? G->err.c_str() : g_create_error.c_str(); }
+
+qtx_status qtx_rgf_group_destroy(qtx_rgf_group G) {
+  if (!G) return QTX_OK;
+  for (auto s : G->mst)
+    if (s) cudaStreamDestroy(s);
+  if (G->gst) cudaStreamDestroy(G->gst);
+  for (auto e : G->ready)
+    if (e) cudaEventDestroy(e);
+  for (auto e : G->join)
+    if (e) cudaEventDestroy(e);
+  for (auto e : G->done)
+    if (e) cudaEventDestroy(e);
+  if (G->fork) cudaEventDestroy(G->fork);
+  if (G->gjoin) cudaEventDestroy(G->gjoin);
+  delete G;
+  return QTX_OK;
 }
 
 }  // extern "C"

@@ -167,24 +167,32 @@ __host__ __device__ constexpr int acc_of(int i, int j) { return (i + j <= 5) ? (
 __host__ __device__ constexpr int n_acc(int S) { return S + 1 >= 6 ? 5 : S; }
 
 // ------------------------------------------------------------------------------ GEMM kernel
-struct TcParams {
-  const unsigned char* pa;  // A plane tiles [batch'][S][M_pad/128][nks][TILE_A]
-  const unsigned char* pb;  // B plane sub-tiles [batch'][S][N_pad/48][K_pad/16][3][SUB_B]: Re, Im, -Im
-  const int* eA;   // [batch][M_pad] row exponents of op(A)
-  const int* eB;   // [batch][N_pad] column exponents of op(B)
-  int M_pad, N_pad, nks;  // nks: K-stages of 32 over the embedded K (2 * K_pad)
-  int M, N;
-  int bn_last;     // complex columns the last column tile computes: N - 48 (NBt - 1), rounded up to 8
-  void* C; long ldc, sC;         // cx<df>, or cx<float> for the FP32 products (IO = float)
-  const void* C0; long ldc0, sC0;
-  df alpha, beta;  // as df32 pairs; the kinds say how they enter the epilogue:
-  int akind;       //   alpha: 0 = +1, 1 = -1, 2 = general (df32 product)
-  int bkind;       //   beta:  0 = +1, 1 = -1, 2 = general, 3 = no beta * C0 term
-  int escale;      // exponent shift of the recombined sum: 2 l1 - 2
-  int a_batched, b_batched;  // 0: the operand is shared by the whole batch (digitized once)
-  const int* active;
-  int* err;
+// TcParams (per-product kernel parameters) is declared in kernels.cuh.
+
+
+// A launch covers the tiles of up to kMaxGroup independent products (a grouped launch: the products
+// of several devices of different shapes, one persistent kernel over the union of their tiles).
+// Problem q owns tiles [tile0[q], tile0[q+1]); within a problem, tiles are ordered column tile
+// fastest, then row tile, then batch entry.
+constexpr int kMaxGroup = kTcMaxGroup;
+struct TcGroup {
+  int n;
+  int tile0[kMaxGroup + 1];
+  int NBt[kMaxGroup], MBt[kMaxGroup];
+  TcParams p[kMaxGroup];
 };
+// problem of global tile t, and t's index within it
+template <bool GROUP>
+__device__ __forceinline__ int problem_of(const TcGroup& G, long t, long& lt) {
+  if (!GROUP) {
+    lt = t;
+    return 0;
+  }
+  int q = 0;
+  while (q + 1 < G.n && t >= G.tile0[q + 1]) ++q;
+  lt = t - G.tile0[q];
+  return q;
+}
 
 // Sum of the accumulators of one output value (acc0 largest) as df32, with TwoSum steps.
 template <int NACC>
@@ -235,8 +243,10 @@ template <> __device__ __forceinline__ cx<float> c_from_df<float>(cx<df> v) {
 __device__ __forceinline__ df df_of(df x) { return x; }
 __device__ __forceinline__ df df_of(float x) { return mkdf(x, 0.f); }
 
-template <int S, int NST, typename IO>
-__global__ void __launch_bounds__(320, 1) k_tc_gemm(TcParams p, int n_tiles, int NBt, int MBt) {
+// GROUP = false: a single product (problem 0; its parameters at fixed offsets); true: a grouped launch.
+template <int S, int NST, typename IO, bool GROUP>
+__global__ void __launch_bounds__(320, 1) k_tc_gemm(const __grid_constant__ TcGroup G) {
+  const int n_tiles = G.tile0[G.n];
   constexpr int STAGE = S * (TILE_A + TILE_B);
   constexpr int NACC = n_acc(S);
   extern __shared__ unsigned char smem_raw[];
@@ -250,7 +260,6 @@ __global__ void __launch_bounds__(320, 1) k_tc_gemm(TcParams p, int n_tiles, int
   __shared__ int s_got;
   __shared__ int s_eB[BNC];
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int per_e = NBt * MBt;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < NST; ++s) {
@@ -277,7 +286,11 @@ __global__ void __launch_bounds__(320, 1) k_tc_gemm(TcParams p, int n_tiles, int
       for (int k = 0; ok; ++k) {
         const long t = tile_at(k);
         if (t >= n_tiles) break;
-        const int e = (int)(t / per_e), mblk = (int)((t / NBt) % MBt), nblk = (int)(t % NBt);
+        long lt;
+        const int q = problem_of<GROUP>(G, t, lt);
+        const TcParams& p = G.p[q];
+        const int NBt = G.NBt[q], MBt = G.MBt[q];
+        const int e = (int)(lt / (NBt * MBt)), mblk = (int)((lt / NBt) % MBt), nblk = (int)(lt % NBt);
         if (p.active && !p.active[e]) continue;
         const long MB = p.M_pad / BM, NB = p.N_pad / BNC, nkb = p.nks / 2;
         const long ea = p.a_batched ? e : 0, eb = p.b_batched ? e : 0;
@@ -287,7 +300,7 @@ __global__ void __launch_bounds__(320, 1) k_tc_gemm(TcParams p, int n_tiles, int
         for (int ks = 0; ks < p.nks; ++ks, ++g) {
           const int s = (int)(g % NST);
           const uint32_t ph = (uint32_t)(g / NST) & 1u;
-          if (!mbar_wait(&empty[s], ph ^ 1u, p.err)) { ok = false; break; }
+          if (!mbar_wait(&empty[s], ph ^ 1u, G.p[0].err)) { ok = false; break; }
           mbar_expect_tx(&full[s], S * (TILE_A + 2 * sub));
           unsigned char* st = base + s * STAGE;
           // K-stages [0, nkb) meet A's real parts: B rows (Re, Im); stages [nkb, 2 nkb) meet A's
@@ -313,17 +326,21 @@ __global__ void __launch_bounds__(320, 1) k_tc_gemm(TcParams p, int n_tiles, int
       for (int k = 0; ok; ++k) {
         const long t = tile_at(k);
         if (t >= n_tiles) break;
-        const int e = (int)(t / per_e);
+        long lt;
+        const int q = problem_of<GROUP>(G, t, lt);
+        const TcParams& p = G.p[q];
+        const int NBt = G.NBt[q], MBt = G.MBt[q];
+        const int e = (int)(lt / (NBt * MBt));
         if (p.active && !p.active[e]) continue;
-        const uint32_t idesc = idesc_n(2 * (t % NBt == NBt - 1 ? p.bn_last : BNC));
+        const uint32_t idesc = idesc_n(2 * (lt % NBt == NBt - 1 ? p.bn_last : BNC));
         // TMEM is free once the epilogue has read the previous tile's accumulators
-        if (!mbar_wait(acce, ((uint32_t)j & 1u) ^ 1u, p.err)) break;
+        if (!mbar_wait(acce, ((uint32_t)j & 1u) ^ 1u, G.p[0].err)) break;
         fence_after();
         uint32_t started = 0;
         for (int ks = 0; ks < p.nks; ++ks, ++g) {
           const int s = (int)(g % NST);
           const uint32_t ph = (uint32_t)(g / NST) & 1u;
-          if (!mbar_wait(&full[s], ph, p.err)) { ok = false; break; }
+          if (!mbar_wait(&full[s], ph, G.p[0].err)) { ok = false; break; }
           fence_after();
           const uint32_t sa = su32(base + s * STAGE);
 #pragma unroll
@@ -354,7 +371,11 @@ __global__ void __launch_bounds__(320, 1) k_tc_gemm(TcParams p, int n_tiles, int
     for (int k = 0;; ++k) {
       const long t = tile_at(k);
       if (t >= n_tiles) break;
-      const int e = (int)(t / per_e), mblk = (int)((t / NBt) % MBt), nblk = (int)(t % NBt);
+      long lt;
+      const int q = problem_of<GROUP>(G, t, lt);
+      const TcParams& p = G.p[q];
+      const int NBt = G.NBt[q], MBt = G.MBt[q];
+      const int e = (int)(lt / (NBt * MBt)), mblk = (int)((lt / NBt) % MBt), nblk = (int)(lt % NBt);
       if (p.active && !p.active[e]) continue;
       // complex columns of this tile: Re parts in TMEM columns [0, bn), Im parts in [bn, 2 bn)
       const int bn = nblk == NBt - 1 ? p.bn_last : BNC;
@@ -365,7 +386,7 @@ __global__ void __launch_bounds__(320, 1) k_tc_gemm(TcParams p, int n_tiles, int
       asm volatile("bar.sync 1, 256;" ::: "memory");
       if (threadIdx.x >= 64 && threadIdx.x < 64 + BNC)
         s_eB[threadIdx.x - 64] = p.eB[(long)(p.b_batched ? e : 0) * p.N_pad + nblk * BNC + threadIdx.x - 64];
-      if (threadIdx.x == 64) s_got = mbar_wait(accf, (uint32_t)j & 1u, p.err) ? 1 : 0;
+      if (threadIdx.x == 64) s_got = mbar_wait(accf, (uint32_t)j & 1u, G.p[0].err) ? 1 : 0;
       __syncwarp();
       asm volatile("bar.sync 2, 256;" ::: "memory");
       if (!s_got) break;
@@ -712,29 +733,31 @@ cudaError_t digitize(const cx<TI>* X, long ldx, long sX, int opX, int side, int 
   }
 }
 
-template <int S, int NST, typename IO>
-cudaError_t launch(const TcArgs& a, void* scratch, size_t scratch_bytes, int* err_flag, cudaStream_t st,
-                   cudaEvent_t* ev) {
+// Digitise one product's operands (into the scratch, or a kept operand) and fill its kernel
+// parameters and tile counts.
+template <int S, typename IO>
+cudaError_t prepare(const TcArgs& a, void* scratch, size_t scratch_bytes, int* err_flag, cudaStream_t st,
+                    TcPrepared& out) {
+  TcParams& p = out.p;
   // operand and result pointers in the IO type (TcArgs carries the df32 ones; f32 products pass
   // FP32 arrays through the same fields)
   const cx<IO>* A = reinterpret_cast<const cx<IO>*>(a.A);
   const cx<IO>* B = reinterpret_cast<const cx<IO>*>(a.B);
   const Dims d = dims_of(a.M, a.N, a.K, S);
-  Scratch s = carve(scratch, d, a.batch, S);
-  if (s.bytes > scratch_bytes) return cudaErrorInvalidValue;
+  Scratch sc = carve(scratch, d, a.batch, S);
+  if (sc.bytes > scratch_bytes) return cudaErrorInvalidValue;
   cudaError_t e;
   const int ab = a.sA != 0, bb_ = a.sB != 0;
   // digit planes and exponents of each operand: in the scratch, or in a kept operand (digitised
   // there now, or reused as they are)
-  unsigned char* pa = a.opndA ? a.opndA->planes : s.pa;
-  unsigned char* pb = a.opndB ? a.opndB->planes : s.pb;
-  int* ea = a.opndA ? a.opndA->expo : s.ea;
-  int* eb = a.opndB ? a.opndB->expo : s.eb;
+  unsigned char* pa = a.opndA ? a.opndA->planes : sc.pa;
+  unsigned char* pb = a.opndB ? a.opndB->planes : sc.pb;
+  int* ea = a.opndA ? a.opndA->expo : sc.ea;
+  int* eb = a.opndB ? a.opndB->expo : sc.eb;
   if (!(a.opndA && a.opndA->mode == 2))
     if ((e = digitize<S, IO>(A, a.lda, a.sA, a.opA, 0, a.M, a.K, d, ea, pa, ab ? a.batch : 1, ab ? a.active : nullptr, st))) return e;
   if (!(a.opndB && a.opndB->mode == 2))
     if ((e = digitize<S, IO>(B, a.ldb, a.sB, a.opB, 1, a.N, a.K, d, eb, pb, bb_ ? a.batch : 1, bb_ ? a.active : nullptr, st))) return e;
-  TcParams p;
   p.pa = pa;
   p.pb = pb;
   p.eA = ea;
@@ -763,24 +786,47 @@ cudaError_t launch(const TcArgs& a, void* scratch, size_t scratch_bytes, int* er
   p.b_batched = bb_;
   p.active = a.active;
   p.err = err_flag;
+  out.NBt = d.N_pad / BNC;
+  out.MBt = d.M_pad / BM;
+  const int tail = a.N - (out.NBt - 1) * BNC;  // 1..48 complex columns in the last column tile
+  p.bn_last = (tail + 7) / 8 * 8;
+  out.tiles = (long)out.NBt * out.MBt * a.batch;
+  return cudaSuccess;
+}
+
+// One persistent launch over the tiles of n prepared products (n = 1: a plain product).
+template <int S, int NST, typename IO>
+cudaError_t launch(const TcPrepared* const* pp, int n, cudaStream_t st, cudaEvent_t* ev) {
+  if (n < 1 || n > kMaxGroup) return cudaErrorInvalidValue;
+  cudaError_t e;
   const size_t smem = (size_t)NST * S * (TILE_A + TILE_B) + OUT_BYTES + 1024 + 256;
   static bool attr = false;
   static int sms = 0;
   if (!attr) {
-    if ((e = cudaFuncSetAttribute(k_tc_gemm<S, NST, IO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
+    if ((e = cudaFuncSetAttribute(k_tc_gemm<S, NST, IO, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
+    if ((e = cudaFuncSetAttribute(k_tc_gemm<S, NST, IO, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
     int dev = 0;
     if ((e = cudaGetDevice(&dev))) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))) return e;
     attr = true;
   }
-  const int NBt = d.N_pad / BNC, MBt = d.M_pad / BM;
-  const int tail = a.N - (NBt - 1) * BNC;  // 1..48 complex columns in the last column tile
-  p.bn_last = (tail + 7) / 8 * 8;
-  const long tiles = (long)NBt * MBt * a.batch;
-  if (tiles > 0x7fffffffL) return cudaErrorInvalidValue;
-  const int grid = (int)(tiles < sms ? tiles : sms);  // one CTA per SM (the kernel holds 230 KB of smem)
+  TcGroup G;
+  G.n = n;
+  long total = 0;
+  for (int q = 0; q < n; ++q) {
+    G.p[q] = pp[q]->p;
+    G.NBt[q] = pp[q]->NBt;
+    G.MBt[q] = pp[q]->MBt;
+    G.tile0[q] = (int)total;
+    total += pp[q]->tiles;
+    if (total > 0x7fffffffL) return cudaErrorInvalidValue;
+  }
+  G.tile0[n] = (int)total;
+  if (total == 0) return cudaSuccess;
+  const int grid = (int)(total < sms ? total : sms);  // one CTA per SM (the kernel holds ~230 KB of smem)
   if (ev) cudaEventRecord(ev[0], st);
-  k_tc_gemm<S, NST, IO><<<grid, 320, smem, st>>>(p, (int)tiles, NBt, MBt);
+  if (n == 1) k_tc_gemm<S, NST, IO, false><<<grid, 320, smem, st>>>(G);
+  else k_tc_gemm<S, NST, IO, true><<<grid, 320, smem, st>>>(G);
   count_launch();
   if (ev) cudaEventRecord(ev[1], st);
   return cudaGetLastError();
@@ -836,6 +882,40 @@ TcOperand tc_operand_at(void* base, int side, int R, int K, int batch, int digit
   return o;
 }
 
+// Kernel variant of a product: digits actually used (effective_digits) and the IO type; -1 when the
+// product is split along K (it then runs as consecutive chunks and cannot be prepared on its own).
+int gemm_tc_variant(const TcArgs& a, int digits) {
+  if (k_chunks(a.K) > 1) return -1;
+  return effective_digits(digits, a.K) * 2 + (a.f32 ? 1 : 0);
+}
+
+cudaError_t gemm_tc_prepare(const TcArgs& a, int digits, void* scratch, size_t scratch_bytes, int* err_flag,
+                            cudaStream_t st, TcPrepared* out) {
+  out->variant = gemm_tc_variant(a, digits);
+  out->tiles = 0;
+  if (a.M <= 0 || a.N <= 0 || a.batch <= 0) return cudaSuccess;
+  switch (out->variant) {
+    case 4 * 2 + 1: return tc::prepare<4, float>(a, scratch, scratch_bytes, err_flag, st, *out);
+    case 7 * 2: return tc::prepare<7, df>(a, scratch, scratch_bytes, err_flag, st, *out);
+    case 6 * 2: return tc::prepare<6, df>(a, scratch, scratch_bytes, err_flag, st, *out);
+    case 2 * 2: return tc::prepare<2, df>(a, scratch, scratch_bytes, err_flag, st, *out);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t gemm_tc_launch(const TcPrepared* const* p, int n, cudaStream_t st, cudaEvent_t* ev) {
+  if (n < 1 || n > kTcMaxGroup) return cudaErrorInvalidValue;
+  for (int q = 1; q < n; ++q)
+    if (p[q]->variant != p[0]->variant) return cudaErrorInvalidValue;
+  switch (p[0]->variant) {
+    case 4 * 2 + 1: return tc::launch<4, 4, float>(p, n, st, ev);
+    case 7 * 2: return tc::launch<7, 2, df>(p, n, st, ev);
+    case 6 * 2: return tc::launch<6, 3, df>(p, n, st, ev);
+    case 2 * 2: return tc::launch<2, 8, df>(p, n, st, ev);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 cudaError_t gemm_tc(const TcArgs& a, int digits, void* scratch, size_t scratch_bytes, int* err_flag,
                     cudaStream_t st, cudaEvent_t* ev) {
   if (a.M <= 0 || a.N <= 0 || a.batch <= 0) return cudaSuccess;
@@ -865,12 +945,11 @@ cudaError_t gemm_tc(const TcArgs& a, int digits, void* scratch, size_t scratch_b
     if (ev) cudaEventRecord(ev[1], st);
     return cudaSuccess;
   }
-  digits = effective_digits(digits, a.K);
-  if (a.f32) return digits == 4 ? tc::launch<4, 4, float>(a, scratch, scratch_bytes, err_flag, st, ev) : cudaErrorInvalidValue;
-  if (digits == 7) return tc::launch<7, 2, df>(a, scratch, scratch_bytes, err_flag, st, ev);
-  if (digits == 6) return tc::launch<6, 3, df>(a, scratch, scratch_bytes, err_flag, st, ev);
-  if (digits == 2) return tc::launch<2, 8, df>(a, scratch, scratch_bytes, err_flag, st, ev);
-  return cudaErrorInvalidValue;
+  TcPrepared p;
+  cudaError_t e = gemm_tc_prepare(a, digits, scratch, scratch_bytes, err_flag, st, &p);
+  if (e != cudaSuccess) return e;
+  const TcPrepared* one[1] = {&p};
+  return gemm_tc_launch(one, 1, st, ev);
 }
 
 }  // namespace qtx

@@ -115,6 +115,29 @@ def test_uneven_batch_graph_replay(q, precision):
     ub.close()
 
 
+@pytest.mark.parametrize("precision", ["emu64", "fp32"])
+def test_group_solve_equals_solo_solves(q, precision):
+    """A group solve of the eight scaled uneven devices (their tensor-core products pooled into shared
+    persistent launches, each device on its own stream) equals the same plans solved one by one, bit
+    for bit, and pools: its pooled launches cover more products than there are launches."""
+    from paper_2606_25595_gb300.batch import UnevenBatch
+    devs = W.uneven_batch(n_energies=4, scale=0.25)
+    outs = ("GR_diag", "GL_diag", "current", "density", "integrals")
+    solo = UnevenBatch(devs, precision, chunks=[2] * len(devs), outputs=outs, grouped=False)
+    solo.launch()
+    r_solo = solo.results()
+    solo.close()
+    grp = UnevenBatch(devs, precision, chunks=[2] * len(devs), outputs=outs, grouped=True)
+    grp.launch()
+    r_grp = grp.results()
+    for a, b in zip(r_solo, r_grp):
+        assert np.all(a["status"] == 0)
+        for k in a:
+            assert np.array_equal(a[k], b[k]), k
+    assert 0 < grp.group.launches() < grp.group.pooled_products()
+    grp.close()
+
+
 @pytest.mark.slow
 def test_nrl_shape_streamed_sigma(q):
     """The paper's NR-L block shape, b = 3408 and N_B = 10 (Sec. V; split-K products with seven
