@@ -68,6 +68,17 @@ size_t qtx_fpx_bytes(int bits, long n);
 qtx_status qtx_fpx_compress(int bits, const double *x, long n, double cutoff, void *out, void *stream);
 qtx_status qtx_fpx_decompress(int bits, const void *in, long n, double *x, void *stream);
 
+/* Test switch of the bounded device-side waits (the paper has no counterpart; it exists to test the
+ * QTX_ERR_TIMEOUT path without faulting or hanging a GPU).  While enabled (enable != 0), every
+ * tensor-core product launch first makes its MMA-issuing thread wait on a barrier that nothing arrives
+ * at, with every wait of the launch limited to 100 us: the wait gives up before any MMA is issued,
+ * the launch raises its wait flag, drains the bulk copies it has issued, frees its tensor memory and
+ * returns, and the call that launched it reports QTX_ERR_TIMEOUT (qtx_zgemm_batched, or
+ * qtx_rgf_status after a solve; the products' outputs are then not valid).  The context stays usable
+ * and the next call after disabling the switch computes normally.  Process-wide; not for production
+ * use.  Always returns QTX_OK. */
+qtx_status qtx_tc_wait_test(int enable);
+
 /* Size in bytes of the fixed device array behind qtx_zgemm_emu64_noalloc (48 MiB per GPU). */
 #define QTX_NOALLOC_SCRATCH_BYTES ((size_t)48 << 20)
 

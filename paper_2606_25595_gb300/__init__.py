@@ -34,7 +34,8 @@ EXPORTED = ("qtx_rgf_plan_create", "qtx_rgf_solve", "qtx_rgf_status", "qtx_rgf_d
             "qtx_rgf_gemm_profile", "qtx_kernel_launches", "qtx_zgemm_emu64_noalloc",
             "qtx_fpx_bytes", "qtx_fpx_compress", "qtx_fpx_decompress", "qtx_w_assemble",
             "qtx_rgf_group_create", "qtx_rgf_group_solve", "qtx_rgf_group_destroy",
-            "qtx_rgf_group_last_error", "qtx_rgf_group_launches", "qtx_rgf_group_pooled_products")
+            "qtx_rgf_group_last_error", "qtx_rgf_group_launches", "qtx_rgf_group_pooled_products",
+            "qtx_tc_wait_test")
 
 
 class QtxError(RuntimeError):
@@ -145,6 +146,8 @@ def load() -> ctypes.CDLL:
     L.qtx_rgf_group_launches.restype = ctypes.c_longlong
     L.qtx_rgf_group_pooled_products.argtypes = [vp]
     L.qtx_rgf_group_pooled_products.restype = ctypes.c_longlong
+    L.qtx_tc_wait_test.argtypes = [i]
+    L.qtx_tc_wait_test.restype = i
     L.qtx_fpx_bytes.argtypes = [i, l]
     L.qtx_fpx_bytes.restype = ctypes.c_size_t
     L.qtx_fpx_compress.argtypes = [i, vp, l, d, vp, vp]

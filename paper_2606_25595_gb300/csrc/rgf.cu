@@ -1091,6 +1091,12 @@ qtx_status qtx_rgf_solve(qtx_rgf_plan P, const qtx_rgf_inputs* in, const qtx_rgf
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   P->last = st;
   P->worst = 0;
+  // the bounded-wait flag of the tensor-core launches starts clear for every solve
+  if (cudaMemsetAsync(P->d_err_flag, 0, sizeof(int), st) != cudaSuccess) {
+    P->err = "clearing the wait flag failed";
+    cudaGetLastError();
+    return QTX_ERR_CUDA;
+  }
   // the workspace is laid out for the plan's n_blocks; a shorter device uses its first slices
   P->nb = in->n_blocks ? in->n_blocks : P->d.n_blocks;
   qtx_status s;
@@ -1124,6 +1130,11 @@ qtx_status qtx_w_assemble(qtx_rgf_plan P, const qtx_w_inputs* in, const qtx_w_ou
   }
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   P->last = st;
+  if (cudaMemsetAsync(P->d_err_flag, 0, sizeof(int), st) != cudaSuccess) {
+    P->err = "clearing the wait flag failed";
+    cudaGetLastError();
+    return QTX_ERR_CUDA;
+  }
   for (int e0 = 0; e0 < in->n_energies; e0 += P->Ec) {
     const int ne = std::min(P->Ec, in->n_energies - e0);
     qtx_status s;

@@ -43,6 +43,7 @@
 // Every mbarrier wait is bounded (2 s of %globaltimer); on expiry the kernel sets *err and unwinds.
 #include <cuda_bf16.h>
 
+#include <atomic>
 #include <cstring>
 #include <mutex>
 
@@ -88,21 +89,34 @@ __device__ __forceinline__ uint64_t gtimer() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-// Bounded wait: gives up after ~2 s, raising *err.
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, int* err) {
+// Bounded wait: gives up after limit_ns of %globaltimer (2 s in normal launches), raising *err, or as
+// soon as another thread has raised it.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, int* err, uint64_t limit_ns) {
   if (mbar_try(b, parity)) return true;
   const uint64_t t0 = gtimer();
   while (true) {
     for (int i = 0; i < 64; ++i)
       if (mbar_try(b, parity)) return true;
     if (*((volatile int*)err)) return false;
-    if (gtimer() - t0 > 2000000000ull) {
+    if (gtimer() - t0 > limit_ns) {
       atomicExch(err, 1);
       return false;
     }
     __nanosleep(128);
   }
 }
+// Bounded wait for work this CTA has already issued (bulk copies, MMAs) to complete, used on the way
+// out after an error: it does not give up because *err is raised, only after limit_ns.
+__device__ __forceinline__ bool mbar_wait_drain(uint64_t* b, uint32_t parity, uint64_t limit_ns) {
+  const uint64_t t0 = gtimer();
+  while (!mbar_try(b, parity)) {
+    if (gtimer() - t0 > limit_ns) return false;
+    __nanosleep(64);
+  }
+  return true;
+}
+constexpr uint64_t kWaitLimitNs = 2000000000ull;   // bounded waits of normal launches
+constexpr uint64_t kWaitTestLimitNs = 100000ull;   // with the wait test switched on
 __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
   asm volatile(
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
@@ -177,6 +191,8 @@ __host__ __device__ constexpr int n_acc(int S) { return S + 1 >= 6 ? 5 : S; }
 constexpr int kMaxGroup = kTcMaxGroup;
 struct TcGroup {
   int n;
+  int hold;           // test switch: the MMA thread first waits on a barrier nothing arrives at
+  uint64_t limit_ns;  // limit of every bounded wait in this launch
   int tile0[kMaxGroup + 1];
   int NBt[kMaxGroup], MBt[kMaxGroup];
   TcParams p[kMaxGroup];
@@ -256,7 +272,9 @@ __global__ void __launch_bounds__(320, 1) k_tc_gemm(const __grid_constant__ TcGr
   uint64_t* empty = full + NST;
   uint64_t* accf = empty + NST;
   uint64_t* acce = accf + 1;
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(acce + 1);
+  uint64_t* holdbar = acce + 1;   // never arrived at (the wait test)
+  uint64_t* drainbar = acce + 2;  // the MMA thread's final commit
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(acce + 3);
   __shared__ int s_got;
   __shared__ int s_eB[BNC];
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -268,6 +286,8 @@ __global__ void __launch_bounds__(320, 1) k_tc_gemm(const __grid_constant__ TcGr
     }
     mbar_init(accf, 1);
     mbar_init(acce, 1);
+    mbar_init(holdbar, 1);
+    mbar_init(drainbar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -300,7 +320,7 @@ __global__ void __launch_bounds__(320, 1) k_tc_gemm(const __grid_constant__ TcGr
         for (int ks = 0; ks < p.nks; ++ks, ++g) {
           const int s = (int)(g % NST);
           const uint32_t ph = (uint32_t)(g / NST) & 1u;
-          if (!mbar_wait(&empty[s], ph ^ 1u, G.p[0].err)) { ok = false; break; }
+          if (!mbar_wait(&empty[s], ph ^ 1u, G.p[0].err, G.limit_ns)) { ok = false; break; }
           mbar_expect_tx(&full[s], S * (TILE_A + 2 * sub));
           unsigned char* st = base + s * STAGE;
           // K-stages [0, nkb) meet A's real parts: B rows (Re, Im); stages [nkb, 2 nkb) meet A's
@@ -316,6 +336,10 @@ __global__ void __launch_bounds__(320, 1) k_tc_gemm(const __grid_constant__ TcGr
           }
         }
       }
+      // the copies of the last stages issued (at most NST of them, one per slot) land before the
+      // CTA goes on to exit, also when a wait gave up and the MMA thread no longer consumes them
+      for (long gi = g > NST ? g - NST : 0; gi < g; ++gi)
+        mbar_wait_drain(&full[gi % NST], (uint32_t)(gi / NST) & 1u, kWaitLimitNs);
     }
     __syncwarp();
   } else if (warp == 1) {
@@ -323,6 +347,8 @@ __global__ void __launch_bounds__(320, 1) k_tc_gemm(const __grid_constant__ TcGr
       long g = 0;
       int j = 0;  // tiles processed by this CTA
       bool ok = true;
+      // wait test: a barrier nothing arrives at, so the wait gives up before any MMA is issued
+      if (G.hold && !mbar_wait(holdbar, 0u, G.p[0].err, G.limit_ns)) ok = false;
       for (int k = 0; ok; ++k) {
         const long t = tile_at(k);
         if (t >= n_tiles) break;
@@ -334,13 +360,13 @@ __global__ void __launch_bounds__(320, 1) k_tc_gemm(const __grid_constant__ TcGr
         if (p.active && !p.active[e]) continue;
         const uint32_t idesc = idesc_n(2 * (lt % NBt == NBt - 1 ? p.bn_last : BNC));
         // TMEM is free once the epilogue has read the previous tile's accumulators
-        if (!mbar_wait(acce, ((uint32_t)j & 1u) ^ 1u, G.p[0].err)) break;
+        if (!mbar_wait(acce, ((uint32_t)j & 1u) ^ 1u, G.p[0].err, G.limit_ns)) break;
         fence_after();
         uint32_t started = 0;
         for (int ks = 0; ks < p.nks; ++ks, ++g) {
           const int s = (int)(g % NST);
           const uint32_t ph = (uint32_t)(g / NST) & 1u;
-          if (!mbar_wait(&full[s], ph, G.p[0].err)) { ok = false; break; }
+          if (!mbar_wait(&full[s], ph, G.p[0].err, G.limit_ns)) { ok = false; break; }
           fence_after();
           const uint32_t sa = su32(base + s * STAGE);
 #pragma unroll
@@ -360,6 +386,10 @@ __global__ void __launch_bounds__(320, 1) k_tc_gemm(const __grid_constant__ TcGr
         mma_commit(accf);
         ++j;
       }
+      // every MMA this thread issued has completed before TMEM is freed (a commit tracks all of
+      // them; it arrives at once when none is outstanding)
+      mma_commit(drainbar);
+      mbar_wait_drain(drainbar, 0u, kWaitLimitNs);
     }
     __syncwarp();
   } else {
@@ -386,7 +416,7 @@ __global__ void __launch_bounds__(320, 1) k_tc_gemm(const __grid_constant__ TcGr
       asm volatile("bar.sync 1, 256;" ::: "memory");
       if (threadIdx.x >= 64 && threadIdx.x < 64 + BNC)
         s_eB[threadIdx.x - 64] = p.eB[(long)(p.b_batched ? e : 0) * p.N_pad + nblk * BNC + threadIdx.x - 64];
-      if (threadIdx.x == 64) s_got = mbar_wait(accf, (uint32_t)j & 1u, G.p[0].err) ? 1 : 0;
+      if (threadIdx.x == 64) s_got = mbar_wait(accf, (uint32_t)j & 1u, G.p[0].err, G.limit_ns) ? 1 : 0;
       __syncwarp();
       asm volatile("bar.sync 2, 256;" ::: "memory");
       if (!s_got) break;
@@ -660,6 +690,9 @@ __global__ void __launch_bounds__(32 * RPC) k_digitize_rows(const cx<TI>* X, lon
 }
 
 // ------------------------------------------------------------------------------ host side
+// Test switch of the bounded waits (qtx_tc_wait_test).
+std::atomic<int> g_wait_test{0};
+
 struct Dims {
   int M_pad, N_pad, K_pad, l1, P;
 };
@@ -812,6 +845,8 @@ cudaError_t launch(const TcPrepared* const* pp, int n, cudaStream_t st, cudaEven
   }
   TcGroup G;
   G.n = n;
+  G.hold = g_wait_test.load(std::memory_order_relaxed);
+  G.limit_ns = G.hold ? kWaitTestLimitNs : kWaitLimitNs;
   long total = 0;
   for (int q = 0; q < n; ++q) {
     G.p[q] = pp[q]->p;
@@ -953,3 +988,8 @@ cudaError_t gemm_tc(const TcArgs& a, int digits, void* scratch, size_t scratch_b
 }
 
 }  // namespace qtx
+
+extern "C" qtx_status qtx_tc_wait_test(int enable) {
+  qtx::tc::g_wait_test.store(enable ? 1 : 0, std::memory_order_relaxed);
+  return QTX_OK;
+}

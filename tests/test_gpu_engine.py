@@ -184,3 +184,39 @@ def test_lead_self_energy_matches_oracle(q):
         ref, _, _, kap = O.lead_self_energy(e, eta, s["leads"]["H00_L"], s["leads"]["H01_L"],
                                            track_cond=True)
         assert np.linalg.norm(SR[k] - ref) / np.linalg.norm(ref) < max(1e-12, 1e4 * kap * 2.0 ** -53)
+
+
+def test_bounded_wait_gives_up_and_the_context_stays_usable(q):
+    """The tensor-core kernel's waits are bounded.  With the test switch on (qtx_tc_wait_test), every
+    product launch's MMA thread first waits on a barrier nothing arrives at, limited to 100 us: the wait
+    gives up before any MMA is issued, the launch drains its copies and frees its tensor memory, and
+    the call reports QTX_ERR_TIMEOUT.  Nothing faults or hangs: afterwards the same GEMM and an RGF
+    solve on the same plan give the results they gave before (the plan's wait flag is cleared per
+    solve)."""
+    import torch
+    L = q.load()
+    rng = np.random.default_rng(8)
+    A = _t(rng.standard_normal((2, 96, 64)) + 1j * rng.standard_normal((2, 96, 64)))
+    B = _t(rng.standard_normal((2, 64, 80)) + 1j * rng.standard_normal((2, 64, 80)))
+    ref = q.zgemm_batched(A, B, "emu64").cpu().numpy()
+    dev = W.random_device(96, 3, n_energies=2, seed=5)
+    outs = ["GR_diag", "GL_diag", "current", "density"]
+    P = q.Plan(q.make_desc(3, 96, "emu64", 2, has_scattering=True, outputs=outs))
+    good = q.solve_device(dev, "emu64", outputs=outs, plan=P)
+    assert P.status() == 0
+    L.qtx_tc_wait_test(1)
+    try:
+        with pytest.raises(q.QtxError) as ei:
+            q.zgemm_batched(A, B, "emu64")
+        assert ei.value.status == 6  # QTX_ERR_TIMEOUT
+        q.solve_device(dev, "emu64", outputs=outs, plan=P)
+        assert P.status() == 6
+    finally:
+        L.qtx_tc_wait_test(0)
+    torch.cuda.synchronize()
+    assert np.array_equal(q.zgemm_batched(A, B, "emu64").cpu().numpy(), ref)
+    again = q.solve_device(dev, "emu64", outputs=outs, plan=P)
+    assert P.status() == 0
+    for k in outs:
+        assert np.array_equal(again[k], good[k]), k
+    P.close()
