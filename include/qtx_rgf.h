@@ -79,7 +79,13 @@ enum {
   QTX_OUT_CONTACT = 1u << 9,   /* I_L,R(E) = Re Tr[Sigma^<_c G^>_kk - Sigma^>_c G^<_kk]  [N_E][2]      */
   QTX_OUT_TRANSMISSION = 1u << 10, /* T(E) = Tr[Gam_L A_00] - Tr[Gam_L G_00 Gam_L G_00^H]  [N_E]    */
   QTX_OUT_INTEGRALS = 1u << 11,    /* sum_E w_E I_i(E) [N_B-1],  sum_E w_E n_i(E)/(2 pi) [N_B]     */
-  QTX_OUT_ALL = (1u << 12) - 1u
+  QTX_OUT_CONTINUITY = 1u << 12,   /* current-conservation residual per energy [N_E] (Sec. II-B):
+                                      max_i |I_{i-1} + J_i - I_i| / max_i s_i, J_i = Re Tr[Sigma^<_ii G^>_ii -
+                                      Sigma^>_ii G^<_ii] (scattering and broadening), I_{-1} = I_L, I_{N_B-1} =
+                                      -I_R with contacts, else 0; s_i = the absolute sums of the terms of J_i
+                                      and I_i (the size of what each balance cancels, so the residual is
+                                      ~kappa * eps of the arithmetic, ~eps for a well-conditioned FP64 solve) */
+  QTX_OUT_ALL = (1u << 13) - 1u
 };
 
 /* Shapes and numerics, fixed for the life of a plan. */
@@ -135,6 +141,14 @@ typedef struct {
                                   the first right-hand side -- e.g. X^> of the W system from B^>
                                   alongside X^< from B^<.  The plan then keeps one more set of
                                   left-connected blocks (N_B blocks per energy in flight) */
+  double escalate_tol;         /* > 0 (QTX_EMU64, QTX_FP32, QTX_BF16X3; block-diagonal Sigma, not
+                                  system_input or sigma_stream): after each chunk the continuity residual
+                                  (QTX_OUT_CONTINUITY) of every energy is checked, and energies whose
+                                  residual is not below escalate_tol are solved again in FP64 on the same
+                                  workspace; their outputs and integral contributions are replaced and
+                                  outputs->escalated marks them.  Needs one host synchronisation per
+                                  chunk (so such solves cannot be captured in a CUDA graph).  FP32 plans
+                                  then size their workspace for complex128 blocks.  0 = off */
 } qtx_rgf_desc;
 
 /* Device inputs (caller-owned, complex128 unless noted). */
@@ -173,6 +187,8 @@ typedef struct {
   double *current, *density, *contact, *transmission;
   double *current_int, *density_int;
   int *status_per_energy;  /* [N_E] qtx_status per energy */
+  double *continuity;      /* [N_E] QTX_OUT_CONTINUITY residual (of the accepted result) */
+  int *escalated;          /* [N_E] 1 where escalate_tol made the energy be solved again in FP64, else 0 */
 } qtx_rgf_outputs;
 
 typedef struct qtx_rgf_plan_s *qtx_rgf_plan;

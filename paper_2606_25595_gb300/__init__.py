@@ -25,7 +25,8 @@ STATUS = {0: "QTX_OK", 1: "QTX_ERR_INVALID_ARG", 2: "QTX_ERR_OOM", 3: "QTX_ERR_C
           7: "QTX_ERR_UNSUPPORTED"}
 OUT = {"GR_diag": 1 << 0, "GR_upper": 1 << 1, "GR_lower": 1 << 2, "GL_diag": 1 << 3,
        "GL_upper": 1 << 4, "GG_diag": 1 << 5, "GG_upper": 1 << 6, "current": 1 << 7,
-       "density": 1 << 8, "contact": 1 << 9, "transmission": 1 << 10, "integrals": 1 << 11}
+       "density": 1 << 8, "contact": 1 << 9, "transmission": 1 << 10, "integrals": 1 << 11,
+       "continuity": 1 << 12}
 BLOCK_OUTPUTS = ("GR_diag", "GR_upper", "GR_lower", "GL_diag", "GL_upper", "GG_diag", "GG_upper")
 # Every function the C ABI exports (checked by the CPU tests against include/*.h).
 EXPORTED = ("qtx_rgf_plan_create", "qtx_rgf_solve", "qtx_rgf_status", "qtx_rgf_destroy",
@@ -53,7 +54,8 @@ class Desc(ctypes.Structure):
                 ("decim_max_iter", ctypes.c_int), ("outputs", ctypes.c_uint),
                 ("offdiag_sigma", ctypes.c_int), ("storage_bits", ctypes.c_int),
                 ("sigma_stream", ctypes.c_int), ("system_input", ctypes.c_int),
-                ("refine_tol", ctypes.c_double), ("second_rhs", ctypes.c_int)]
+                ("refine_tol", ctypes.c_double), ("second_rhs", ctypes.c_int),
+                ("escalate_tol", ctypes.c_double)]
 
 
 class Inputs(ctypes.Structure):
@@ -86,7 +88,7 @@ class Outputs(ctypes.Structure):
     _fields_ = [(n, ctypes.c_void_p) for n in BLOCK_OUTPUTS] + \
                [(n, ctypes.c_void_p) for n in ("current", "density", "contact", "transmission",
                                                "current_int", "density_int",
-                                               "status_per_energy")]
+                                               "status_per_energy", "continuity", "escalated")]
 
 
 _lib = None
@@ -166,9 +168,9 @@ def make_desc(n_blocks, block_size, precision="fp64", max_energies_in_flight=64,
               refine_max_iter=2, has_S=False, has_scattering=True, energy_dependent_sigma=False,
               leads=False, decim_tol=1e-13, decim_max_iter=100, outputs=None,
               offdiag_sigma=False, storage_bits=0, sigma_stream=False, system_input=False,
-              refine_tol=0.0, second_rhs=False) -> Desc:
+              refine_tol=0.0, second_rhs=False, escalate_tol=0.0) -> Desc:
     if outputs is None:
-        outputs = (1 << 12) - 1
+        outputs = (1 << 12) - 1  # every output but the continuity residual
     elif not isinstance(outputs, int):
         mask = 0
         for name in outputs:
@@ -180,7 +182,7 @@ def make_desc(n_blocks, block_size, precision="fp64", max_energies_in_flight=64,
                 int(bool(energy_dependent_sigma)), int(bool(leads)), float(decim_tol),
                 int(decim_max_iter), int(outputs), int(bool(offdiag_sigma)), int(storage_bits),
                 int(bool(sigma_stream)), int(bool(system_input)), float(refine_tol),
-                int(bool(second_rhs)))
+                int(bool(second_rhs)), float(escalate_tol))
 
 
 def kernel_launches() -> int:
@@ -374,7 +376,8 @@ def has_offdiag_sigma(dev: dict) -> bool:
 
 def solve_device(dev: dict, precision: str = "fp64", outputs=None, max_energies_in_flight=64,
                  refine_max_iter=2, weights=None, energies=None, stream=None, plan=None,
-                 device_inputs=None, keep_on_device=False, storage_bits=0, sigma_stream=False):
+                 device_inputs=None, keep_on_device=False, storage_bits=0, sigma_stream=False,
+                 escalate_tol=0.0):
     """Solve a ``workloads``-style device dict on the GPU and return numpy arrays (or tensors).
 
     Marshalling only: inputs are copied to torch CUDA tensors (complex128), the C ABI is called on
@@ -387,14 +390,14 @@ def solve_device(dev: dict, precision: str = "fp64", outputs=None, max_energies_
     E = np.asarray(dev["energies"] if energies is None else energies, dtype=np.float64)
     ne = E.size
     din = device_inputs if device_inputs is not None else upload(dev, E, weights, sigma_host=sigma_stream)
-    want = list(outputs) if outputs is not None else list(OUT)
+    want = list(outputs) if outputs is not None else [k for k in OUT if k != "continuity"]
     if not dev.get("leads"):
         want = [w for w in want if w not in ("contact", "transmission")]
     desc = make_desc(nb, b, precision, min(max_energies_in_flight, ne), refine_max_iter,
                      has_S=dev.get("S_diag") is not None, has_scattering=dev.get("SigR") is not None,
                      energy_dependent_sigma=dev.get("SigR") is not None and dev["SigR"].shape[0] > 1,
                      leads=bool(dev.get("leads")), outputs=want, offdiag_sigma=has_offdiag_sigma(dev),
-                     storage_bits=storage_bits, sigma_stream=sigma_stream)
+                     storage_bits=storage_bits, sigma_stream=sigma_stream, escalate_tol=escalate_tol)
     P = plan if plan is not None else Plan(desc)
     cdev = torch.device("cuda")
     res = {}
@@ -402,7 +405,7 @@ def solve_device(dev: dict, precision: str = "fp64", outputs=None, max_energies_
               "GR_lower": (ne, nb - 1, b, b), "GL_diag": (ne, nb, b, b),
               "GL_upper": (ne, nb - 1, b, b), "GG_diag": (ne, nb, b, b),
               "GG_upper": (ne, nb - 1, b, b), "current": (ne, nb - 1), "density": (ne, nb),
-              "contact": (ne, 2), "transmission": (ne,), "integrals": None}
+              "contact": (ne, 2), "transmission": (ne,), "integrals": None, "continuity": (ne,)}
     o = Outputs()
     for k in want:
         if k == "integrals":
@@ -419,6 +422,9 @@ def solve_device(dev: dict, precision: str = "fp64", outputs=None, max_energies_
         setattr(o, k, res[k].data_ptr())
     res["status"] = torch.zeros(ne, dtype=torch.int32, device=cdev)
     o.status_per_energy = res["status"].data_ptr()
+    if escalate_tol > 0:
+        res["escalated"] = torch.zeros(ne, dtype=torch.int32, device=cdev)
+        o.escalated = res["escalated"].data_ptr()
     st = torch.cuda.current_stream().cuda_stream if stream is None else stream
     P.solve(din["_inputs"], o, st)
     torch.cuda.current_stream().synchronize()

@@ -93,6 +93,22 @@ cudaError_t obs_trace2(double* out, long ld, const cx<double>* X, long sX, const
 cudaError_t obs_frob_dot(double* out, long ld, const cx<double>* X, long sX, const cx<double>* Y,
                          long sY, double scale, int b, int batch, cudaStream_t st);
 
+// out[e * ld] = J = Re Tr[Sigma^< G^>] - Re Tr[Sigma^> G^<] of one slice (G^> = G^< + G - G^H,
+// Sigma^> = Sigma^< + Sigma^R - Sigma^R^H - 2 i eta I; SL, SR complex128 or null, batch stride sSig);
+// scale[e * ld] = the absolute sum of its terms plus, with GLu = G^<_{i,i+1} given, that of the
+// interface's current (Hu, Su: H_{i,i+1}, S_{i,i+1} or null; E the energies); gn[e * ld] = ||G_ii||_F^2,
+// hn[e * ld] = ||H_ii||_F + 2 ||H_{i,i+1}||_F (Hd = H_ii)
+template <typename T>
+cudaError_t obs_balance(double* out, double* scale, double* gn, double* hn, long ld, const cx<double>* SL,
+                        const cx<double>* SR, long sSig, const cx<T>* G, const cx<T>* GL, long sG, double eta, int b,
+                        int batch, cudaStream_t st, const cx<double>* Hd, const cx<double>* Hu, const cx<double>* Su,
+                        const double* E, const cx<T>* GLu);
+// res[e] = max_i |I_{i-1} + J_i - I_i| / max_i scale_i per energy (con: [ne][2] contact currents or
+// null); flag[e] = !(res[e] < tol) or !(kappa_est eps_mode < tol), kappa_est = (|E| + max hn) sqrt(max gn)
+cudaError_t continuity(const double* cur, long ldc, const double* J, const double* Js, const double* gn,
+                       const double* hn, long ldj, const double* con, const double* E, int nb, int ne, double tol,
+                       double eps_mode, double* res, int* flag, cudaStream_t st);
+
 // ---- lead post-processing: from Sigma^R (complex128) build Gamma, Sigma^<, Sigma^>
 cudaError_t lead_sigmas(const cx<double>* SR, cx<double>* Gam, cx<double>* SL, cx<double>* SG,
                         const double* E, double mu, double kT, int b, int batch, cudaStream_t st);

@@ -48,7 +48,7 @@ inline bool uv_per_energy(const qtx_rgf_desc& d) {
 }
 
 struct Layout {
-  size_t g, gl, gl2, gfx, glfx, fx_slot, sig_stage, opnd[3], opnd_bytes[3], refine_act, tmp, inv_tmp, U, V, ident, ident_df, ref, f32a, f32tmp, dec, lead, obs, flags, dscale,
+  size_t g, gl, gl2, gfx, glfx, fx_slot, sig_stage, opnd[3], opnd_bytes[3], refine_act, tmp, inv_tmp, U, V, ident, ident_df, ref, f32a, f32tmp, dec, lead, obs, flags, dscale, bal, bscale, bgn, bhn, cres, cflag,
       tc_scratch, total;
   int n_tmp, n_dec;
   size_t tc_bytes;
@@ -71,6 +71,7 @@ struct qtx_rgf_plan_s {
   int* d_err_flag = nullptr;    // tensor-core engine wait/limit flag
   int worst = 0;                // worst per-energy status after the last synchronising call
   int* h_status = nullptr;      // pinned host copy of the chunk status
+  int* h_flag = nullptr;        // pinned host copy of the chunk's escalation flags
   std::vector<int> status_host;
   const int* out_status = nullptr;  // caller's per-energy status array of the last solve
   int out_status_n = 0;
@@ -99,7 +100,9 @@ Layout make_layout(const qtx_rgf_desc& d) {
   Layout L{};
   const long b = d.block_size, nb = d.n_blocks, Ec = d.max_energies_in_flight;
   const size_t bb = (size_t)b * b;
-  const size_t es = d.precision == QTX_FP32 ? sizeof(cx<float>) : sizeof(cx<double>);
+  // FP32 plans that escalate energies to FP64 lay out complex128 blocks (the FP64 re-solve runs on
+  // the same workspace); df32 blocks are complex128-sized anyway
+  const size_t es = (d.precision == QTX_FP32 && !(d.escalate_tol > 0)) ? sizeof(cx<float>) : sizeof(cx<double>);
   Arena a;
   // 12, 13: Sigma^<_{i,i+1} in the sweep's type and g_i Sigma^<_{i,i+1}; 14: g_i B2_{i,i+1} (second_rhs)
   L.n_tmp = d.offdiag_sigma ? (d.second_rhs ? 15 : 14) : 12;
@@ -135,6 +138,14 @@ Layout make_layout(const qtx_rgf_desc& d) {
   L.obs = a.take((size_t)Ec * (2 * nb + 8) * sizeof(double));
   L.flags = a.take((size_t)Ec * 3 * sizeof(int) + 64);
   L.dscale = a.take(64);  // device scalars (the decimation's tolerance scale)
+  // continuity check: per-slice balances J [Ec][nb], residuals [Ec], escalation flags [Ec]
+  const bool cont = (d.outputs & QTX_OUT_CONTINUITY) || d.escalate_tol > 0;
+  L.bal = a.take(cont ? (size_t)Ec * nb * sizeof(double) : 0);
+  L.bscale = a.take(cont ? (size_t)Ec * nb * sizeof(double) : 0);
+  L.bgn = a.take(cont ? (size_t)Ec * nb * sizeof(double) : 0);
+  L.bhn = a.take(cont ? (size_t)Ec * nb * sizeof(double) : 0);
+  L.cres = a.take(cont ? (size_t)Ec * sizeof(double) : 0);
+  L.cflag = a.take(cont ? (size_t)Ec * sizeof(int) + 64 : 0);
   L.refine_act = a.take((size_t)Ec * 2 * sizeof(int) + 64);  // per-energy sweep masks (ping-pong)
   L.tc_bytes = 0;
   if (mixed) L.tc_bytes = gemm_tc_scratch_bytes((int)b, (int)b, (int)b, (int)Ec, d.precision == QTX_EMU64 ? 6 : 2);
@@ -717,6 +728,12 @@ qtx_status solve_chunk(qtx_rgf_plan_s* P, const qtx_rgf_inputs* in, const qtx_rg
   double* tra = con + (size_t)P->Ec * 2;       // [ne]
   const unsigned m = d.outputs;
   auto want = [&](unsigned bit, const void* p) { return (m & bit) && p; };
+  // current conservation (Sec. II-B): per-slice balances J_i, checked after the sweep
+  const bool cont = (m & QTX_OUT_CONTINUITY) || d.escalate_tol > 0;
+  double* bal = reinterpret_cast<double*>(P->ws + P->L.bal);        // [ne][nb]
+  double* bscale = reinterpret_cast<double*>(P->ws + P->L.bscale);  // [ne][nb]
+  double* bgn = reinterpret_cast<double*>(P->ws + P->L.bgn);        // [ne][nb]
+  double* bhn = reinterpret_cast<double*>(P->ws + P->L.bhn);        // [ne][nb]
   {
     const int i = nb - 1;
     if (want(QTX_OUT_GR_DIAG, out->GR_diag) && (s = emit<T>(P, out->GR_diag, nb, i, e0, c.g(i), b, ne, st))) return s;
@@ -726,6 +743,9 @@ qtx_status solve_chunk(qtx_rgf_plan_s* P, const qtx_rgf_inputs* in, const qtx_rg
                           : emit<T>(P, out->GG_diag, nb, i, e0, c.gl(i), b, ne, st, c.g(i), c.g(i))))
       return s;
     QTX_CK(obs_density<T>(den + i, nb, c.gl(i), bb, b, ne, st));
+    if (cont)
+      QTX_CK(obs_balance<T>(bal + i, bscale + i, bgn + i, bhn + i, nb, sigL(i), sigR(i), sSig, c.g(i), c.gl(i), bb,
+                            eta, b, ne, st, Hd + (long)i * bb, nullptr, nullptr, c.E, nullptr));
     if (d.leads) {  // right contact current on slice N_B-1:  G^> = G^< + G^R - G^A
       cx<T>* GG = c.tmp(0);
       Term<T> t0; t0.p = c.gl(i); t0.s = bb; t0.alpha = 1.0;
@@ -814,6 +834,9 @@ qtx_status solve_chunk(qtx_rgf_plan_s* P, const qtx_rgf_inputs* in, const qtx_rg
         QTX_CK(obs_current<T>(cur + i, ncur, Hu + (long)i * bb, Su ? Su + (long)i * bb : nullptr, GLu, bb, c.E, b, ne, st,
                               reinterpret_cast<double*>(c.tmp(0)), (long)ne * bb * (long)sizeof(cx<T>) / (long)sizeof(double)));
       QTX_CK(obs_density<T>(den + i, nb, gli, bb, b, ne, st));
+      if (cont)
+        QTX_CK(obs_balance<T>(bal + i, bscale + i, bgn + i, bhn + i, nb, sigL(i), sigR(i), sSig, gi, gli, bb, eta, b,
+                              ne, st, Hd + (long)i * bb, Hu + (long)i * bb, Su ? Su + (long)i * bb : nullptr, c.E, GLu));
     }
   }
   if (d.leads) {  // left contact current and transmission on slice 0
@@ -840,6 +863,20 @@ qtx_status solve_chunk(qtx_rgf_plan_s* P, const qtx_rgf_inputs* in, const qtx_rg
     if ((s = gemm<double>(P, gargs<double>(b, b, b, Gam_L, b, bb, OP_N, G64, b, bb, OP_N, nullptr, 0, 0, X1, b, bb, 1.0, 0.0, ne, nullptr), st, true))) return s;
     if ((s = gemm<double>(P, gargs<double>(b, b, b, G64, b, bb, OP_N, Gam_L, b, bb, OP_N, nullptr, 0, 0, X2, b, bb, 1.0, 0.0, ne, nullptr), st, true))) return s;
     QTX_CK(obs_frob_dot(tra, 1, X1, bb, X2, bb, -1.0, b, ne, st));
+  }
+  // ---- continuity residual per energy (and the escalation flags)
+  if (cont) {
+    double* cres = reinterpret_cast<double*>(P->ws + P->L.cres);
+    int* cflag = reinterpret_cast<int*>(P->ws + P->L.cflag);
+    // unit error of the products in this mode (Eq. 6: error ~ kappa eps): 6 (7) bf16 digits ~41 bits,
+    // 2 digits ~13 bits, complex64 24 bits, FP64 53
+    const double eps_mode = std::is_same<T, double>::value ? 0x1p-53
+                            : std::is_same<T, float>::value  ? 0x1p-24
+                            : (d.precision == QTX_BF16X3 ? 0x1p-13 : 0x1p-40);
+    QTX_CK(continuity(cur, ncur, bal, bscale, bgn, bhn, nb, d.leads ? con : nullptr, c.E, nb, ne,
+                      d.escalate_tol > 0 ? d.escalate_tol : 1e300, eps_mode, cres, cflag, st));
+    if (want(QTX_OUT_CONTINUITY, out->continuity))
+      QTX_CK(cudaMemcpyAsync(out->continuity + e0, cres, (size_t)ne * sizeof(double), cudaMemcpyDeviceToDevice, st));
   }
   // ---- 4. outputs of the per-energy observables and their integrals
   const int nbm1 = nb - 1;
@@ -874,8 +911,37 @@ qtx_status solve_all(qtx_rgf_plan_s* P, const qtx_rgf_inputs* in, const qtx_rgf_
     const int ne = std::min(P->Ec, in->n_energies - e0);
     int* status = out->status_per_energy ? out->status_per_energy + e0 : chunk_status;
     QTX_CK(cudaMemsetAsync(status, 0, (size_t)ne * sizeof(int), st));
+    if (out->escalated) QTX_CK(cudaMemsetAsync(out->escalated + e0, 0, (size_t)ne * sizeof(int), st));
     qtx_status s = solve_chunk<T>(P, in, out, e0, ne, status, st);
     if (s) return s;
+    if (!std::is_same<T, double>::value && P->d.escalate_tol > 0) {
+      // energies whose current is not conserved to escalate_tol are solved again in FP64
+      QTX_CK(cudaMemcpyAsync(P->h_flag, P->ws + P->L.cflag, sizeof(int) * ne, cudaMemcpyDeviceToHost, st));
+      QTX_CK(cudaStreamSynchronize(st));
+      std::vector<int> redo;
+      for (int k = 0; k < ne; ++k)
+        if (P->h_flag[k]) redo.push_back(k);
+      if (!redo.empty()) {
+        // take their integral contributions back out first (the chunk's per-energy values are still
+        // in the observable buffers; each FP64 re-solve adds its own)
+        const int nbm1 = nb - 1, ncur = nb > 1 ? nb - 1 : 1;
+        double* cur = reinterpret_cast<double*>(P->ws + P->L.obs);
+        double* den = cur + (size_t)P->Ec * ncur;
+        if ((m & QTX_OUT_INTEGRALS) && out->current_int && nbm1 > 0)
+          for (int k : redo)
+            QTX_CK(integrate_add(out->current_int, cur + (size_t)k * ncur, ncur, nbm1, in->weights, in->energies, e0 + k,
+                                 in->n_energies, 1, -1.0, st));
+        if ((m & QTX_OUT_INTEGRALS) && out->density_int)
+          for (int k : redo)
+            QTX_CK(integrate_add(out->density_int, den + (size_t)k * nb, nb, nb, in->weights, in->energies, e0 + k,
+                                 in->n_energies, 1, -1.0 / (2.0 * 3.14159265358979323846), st));
+        for (int k : redo) {
+          QTX_CK(cudaMemsetAsync(status + k, 0, sizeof(int), st));
+          if ((s = solve_chunk<double>(P, in, out, e0 + k, 1, status + k, st))) return s;
+          if (out->escalated) QTX_CK(fill_int(out->escalated + e0 + k, 1, 1, st));
+        }
+      }
+    }
     if (!out->status_per_energy) {
       // keep the worst chunk status without a host sync: fold into the error flag word
       QTX_CK(cudaMemcpyAsync(P->h_status, status, sizeof(int) * ne, cudaMemcpyDeviceToHost, st));
@@ -899,6 +965,11 @@ qtx_status validate(const qtx_rgf_desc* d, std::string& err) {
   if (d->storage_bits && !fpx_width_ok(d->storage_bits)) { err = "storage_bits must be 0, 56, 48, 40, 32, 24 or 16"; return QTX_ERR_INVALID_ARG; }
   if (d->sigma_stream && (!d->has_scattering || !d->energy_dependent_sigma || d->offdiag_sigma)) { err = "sigma_stream needs has_scattering and energy_dependent_sigma, without offdiag_sigma"; return QTX_ERR_INVALID_ARG; }
   if (d->second_rhs && (!d->system_input || d->storage_bits)) { err = "second_rhs needs system_input and storage_bits = 0"; return QTX_ERR_INVALID_ARG; }
+  if (!(d->escalate_tol >= 0.0)) { err = "escalate_tol must be >= 0"; return QTX_ERR_INVALID_ARG; }
+  if ((d->escalate_tol > 0 || (d->outputs & QTX_OUT_CONTINUITY)) && (d->offdiag_sigma || d->system_input || d->sigma_stream)) {
+    err = "the continuity check (escalate_tol, QTX_OUT_CONTINUITY) needs block-diagonal Sigma, no system_input and no sigma_stream";
+    return QTX_ERR_INVALID_ARG;
+  }
   if (d->system_input) {
     const unsigned bad = (d->second_rhs ? 0u : QTX_OUT_GG_DIAG | QTX_OUT_GG_UPPER) | QTX_OUT_CURRENT | QTX_OUT_CONTACT | QTX_OUT_TRANSMISSION | QTX_OUT_INTEGRALS;
     if (d->has_S || d->leads || d->sigma_stream) { err = "system_input needs has_S = 0, leads = 0, sigma_stream = 0"; return QTX_ERR_INVALID_ARG; }
@@ -1049,6 +1120,7 @@ qtx_status qtx_rgf_plan_create(const qtx_rgf_desc* desc, qtx_rgf_plan* out) {
   e = cudaMalloc(&P->d_err_flag, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(P->d_err_flag, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMallocHost(&P->h_status, sizeof(int) * P->Ec);
+  if (e == cudaSuccess && desc->escalate_tol > 0) e = cudaMallocHost(&P->h_flag, sizeof(int) * P->Ec);
   // identity block for the refinement residual
   if (e == cudaSuccess) {
     std::vector<cx<double>> I((size_t)P->bb, mk<double>(0, 0));
@@ -1065,6 +1137,7 @@ qtx_status qtx_rgf_plan_create(const qtx_rgf_desc* desc, qtx_rgf_plan* out) {
     cudaFree(P->ws);
     if (P->d_err_flag) cudaFree(P->d_err_flag);
     if (P->h_status) cudaFreeHost(P->h_status);
+    if (P->h_flag) cudaFreeHost(P->h_flag);
     delete P;
     return QTX_ERR_CUDA;
   }
@@ -1201,6 +1274,7 @@ qtx_status qtx_rgf_destroy(qtx_rgf_plan P) {
   if (P->ws) cudaFree(P->ws);
   if (P->d_err_flag) cudaFree(P->d_err_flag);
   if (P->h_status) cudaFreeHost(P->h_status);
+  if (P->h_flag) cudaFreeHost(P->h_flag);
   delete P;
   return QTX_OK;
 }

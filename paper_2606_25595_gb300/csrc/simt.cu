@@ -887,6 +887,132 @@ template cudaError_t obs_trace2<double>(double*, long, const cx<double>*, long, 
 template cudaError_t obs_trace2<float>(double*, long, const cx<double>*, long, const cx<float>*, long, const cx<double>*, long, const cx<float>*, long, int, int, cudaStream_t, int, double);
 template cudaError_t obs_trace2<df>(double*, long, const cx<double>*, long, const cx<df>*, long, const cx<double>*, long, const cx<df>*, long, int, int, cudaStream_t, int, double);
 
+// Local current balance of slice i (current conservation, Sec. II-B):
+//   J = Re Tr[Sigma^< G^>] - Re Tr[Sigma^> G^<],  G^> = G^< + G - G^H,
+//   Sigma^> = Sigma^< + Sigma^R - Sigma^R^H - 2 i eta I  (the broadening acts as a sink),
+// with Tr[X Y] = sum_jk X_jk Y_kj; Sigma pointers may be null (no scattering), sSig their batch stride.
+// scale = the absolute sum of J's terms, sum_jk |Sigma^<_jk| |G^>_kj| + |Sigma^>_jk| |G^<_kj|, plus,
+// when the interface (i, i+1) exists (GLu = G^<_{i,i+1} non-null), that of its current,
+// 2 sum_jk |(H - E S)_{i,i+1, jk}| |G^<_{i,i+1, jk}|: the size of the terms each balance cancels, hence
+// the scale of its rounding error.
+// gn[e * ld] = ||G_ii||_F^2 and hn[e * ld] = ||H_ii||_F + 2 ||H_{i,i+1}||_F (Hd = H_ii, Hu may be null): the
+// pieces of the condition estimate ||M|| ||G|| of the escalation check.
+template <typename T>
+__global__ void __launch_bounds__(256) k_obs_balance(double* out, double* scale, double* gn, double* hn, long ld,
+                                                     const cx<double>* SL, const cx<double>* SR, long sSig,
+                                                     const cx<T>* G, const cx<T>* GL, long sG, double eta, int b,
+                                                     const cx<double>* Hd, const cx<double>* Hu,
+                                                     const cx<double>* Su, const double* E, const cx<T>* GLu) {
+  const int e = blockIdx.x;
+  const long bb = (long)b * b;
+  const cx<T>* Ge = G + (long)e * sG;
+  const cx<T>* GLe = GL + (long)e * sG;
+  double s = 0.0, a = 0.0, g2 = 0.0, hd2 = 0.0, hu2 = 0.0;
+  for (long idx = threadIdx.x; idx < bb; idx += blockDim.x) {
+    const int j = (int)(idx / b), k = (int)(idx % b);
+    const long kj = (long)k * b + j;
+    const cx<double> gl = cvt<double>(GLe[kj]);
+    const cx<double> gkj = cvt<double>(Ge[kj]), gjk = cvt<double>(Ge[idx]);
+    const cx<double> gg = mk<double>(gl.re + gkj.re - gjk.re, gl.im + gkj.im + gjk.im);  // G^>_kj
+    cx<double> sl = mk<double>(0.0, 0.0), sg = mk<double>(0.0, j == k ? -2.0 * eta : 0.0);
+    if (SL) {
+      sl = SL[(long)e * sSig + idx];
+      sg.re += sl.re;
+      sg.im += sl.im;
+    }
+    if (SR) {
+      const cx<double> rjk = SR[(long)e * sSig + idx], rkj = SR[(long)e * sSig + kj];
+      sg.re += rjk.re - rkj.re;  // Sigma^R - Sigma^R^H
+      sg.im += rjk.im + rkj.im;
+    }
+    s += (sl.re * gg.re - sl.im * gg.im) - (sg.re * gl.re - sg.im * gl.im);
+    a += hypot(sl.re, sl.im) * hypot(gg.re, gg.im) + hypot(sg.re, sg.im) * hypot(gl.re, gl.im);
+    g2 += gjk.re * gjk.re + gjk.im * gjk.im;
+    const cx<double> hd = Hd[idx];
+    hd2 += hd.re * hd.re + hd.im * hd.im;
+    if (Hu) hu2 += Hu[idx].re * Hu[idx].re + Hu[idx].im * Hu[idx].im;
+    if (GLu) {
+      const cx<double> u = cvt<double>(GLu[(long)e * sG + idx]);
+      cx<double> h = Hu[idx];
+      if (Su) {
+        const double Ee = E[e];
+        h.re -= Ee * Su[idx].re;
+        h.im -= Ee * Su[idx].im;
+      }
+      a += 2.0 * hypot(h.re, h.im) * hypot(u.re, u.im);
+    }
+  }
+  s = block_sum(s);
+  a = block_sum(a);
+  g2 = block_sum(g2);
+  hd2 = block_sum(hd2);
+  hu2 = block_sum(hu2);
+  if (threadIdx.x == 0) {
+    out[(long)e * ld] = s;
+    scale[(long)e * ld] = a;
+    gn[(long)e * ld] = g2;
+    hn[(long)e * ld] = sqrt(hd2) + 2.0 * sqrt(hu2);
+  }
+}
+template <typename T>
+cudaError_t obs_balance(double* out, double* scale, double* gn, double* hn, long ld, const cx<double>* SL,
+                        const cx<double>* SR, long sSig, const cx<T>* G, const cx<T>* GL, long sG, double eta, int b,
+                        int batch, cudaStream_t st, const cx<double>* Hd, const cx<double>* Hu, const cx<double>* Su,
+                        const double* E, const cx<T>* GLu) {
+  k_obs_balance<T><<<batch, 256, 0, st>>>(out, scale, gn, hn, ld, SL, SR, sSig, G, GL, sG, eta, b, Hd, Hu, Su, E, GLu);
+  count_launch();
+  return cudaGetLastError();
+}
+#define QTX_BAL(T)                                                                                                   \
+  template cudaError_t obs_balance<T>(double*, double*, double*, double*, long, const cx<double>*,                \
+                                      const cx<double>*, long, const cx<T>*, const cx<T>*, long, double, int, int,  \
+                                      cudaStream_t, const cx<double>*, const cx<double>*, const cx<double>*,        \
+                                      const double*, const cx<T>*);
+QTX_BAL(double)
+QTX_BAL(float)
+QTX_BAL(df)
+#undef QTX_BAL
+
+// Continuity residual per energy: the largest violation of I_{i-1} + J_i = I_i over the slices
+// (I_{-1} = I_L, I_{N_B-1} = -I_R with contacts, else 0), relative to the largest balance scale
+// (k_obs_balance).  flag[e] = 1 when it is not below tol (NaN included), or when the condition
+// estimate kappa = (|E| + max_i hn_i) max_i ||G_ii||_F times eps_mode (the arithmetic's unit error,
+// Eq. 6's model error ~ kappa eps) is not below tol.  One thread per energy.
+__global__ void k_continuity(const double* cur, long ldc, const double* J, const double* Js, const double* gn,
+                             const double* hn, long ldj, const double* con, const double* E, int nb, int ne, double tol,
+                             double eps_mode, double* res, int* flag) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= ne) return;
+  const double* I = cur + (long)e * ldc;
+  const double* Je = J + (long)e * ldj;
+  const double* Se = Js + (long)e * ldj;
+  const double IL = con ? con[2L * e] : 0.0, IR = con ? con[2L * e + 1] : 0.0;
+  double worst = 0.0, scale = 0.0;
+  for (int i = 0; i < nb; ++i) {
+    const double prev = i == 0 ? IL : I[i - 1];
+    const double next = i == nb - 1 ? -IR : I[i];
+    const double r = fabs(prev + Je[i] - next);
+    worst = (r > worst || r != r) ? r : worst;
+    scale = fmax(scale, Se[i]);
+  }
+  const double rel = worst / (scale > 0.0 ? scale : 1.0);
+  double g2 = 0.0, h = 0.0;
+  for (int i = 0; i < nb; ++i) {
+    g2 = fmax(g2, gn[(long)e * ldj + i]);
+    h = fmax(h, hn[(long)e * ldj + i]);
+  }
+  const double kest = (fabs(E[e]) + h) * sqrt(g2);
+  res[e] = rel;
+  flag[e] = (rel < tol && kest * eps_mode < tol) ? 0 : 1;
+}
+cudaError_t continuity(const double* cur, long ldc, const double* J, const double* Js, const double* gn,
+                       const double* hn, long ldj, const double* con, const double* E, int nb, int ne, double tol,
+                       double eps_mode, double* res, int* flag, cudaStream_t st) {
+  k_continuity<<<(ne + 127) / 128, 128, 0, st>>>(cur, ldc, J, Js, gn, hn, ldj, con, E, nb, ne, tol, eps_mode, res, flag);
+  count_launch();
+  return cudaGetLastError();
+}
+
 __global__ void __launch_bounds__(256) k_obs_frob_dot(double* out, long ld, const cx<double>* X, long sX,
                                                       const cx<double>* Y, long sY, double scale, int b) {
   const int e = blockIdx.x;

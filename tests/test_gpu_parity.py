@@ -498,3 +498,70 @@ def test_sigma_streamed_from_host(q, precision):
         assert np.array_equal(a[k], b[k]), k
     if precision == "fp64":
         _check(b, O.solve(dev), 1e-10, 1e-10, keys=("GR_diag", "GR_upper", "GL_diag", "GL_upper"))
+
+
+def _resonant_device():
+    """Weakly broadened device (scattering 1e-7, eta = 1e-12) with one energy exactly at an eigenvalue
+    of H: kappa(M) = 2.5e7 there, ~250 at the two other energies."""
+    dev = W.random_device(16, 4, n_energies=3, seed=21, sigma_scale=1e-7, eta=1e-12)
+    nb, b = 4, 16
+    H = np.zeros((nb * b, nb * b), complex)
+    for i in range(nb):
+        H[i * b:(i + 1) * b, i * b:(i + 1) * b] = dev["H_diag"][i]
+        if i + 1 < nb:
+            H[i * b:(i + 1) * b, (i + 1) * b:(i + 2) * b] = dev["H_upper"][i]
+            H[(i + 1) * b:(i + 2) * b, i * b:(i + 1) * b] = dev["H_upper"][i].conj().T
+    lam = np.linalg.eigvalsh(H)
+    dev["energies"] = np.array([-0.5, lam[np.argmin(np.abs(lam - 0.2))], 0.37])
+    return dev
+
+
+def test_escalation_by_continuity_and_by_condition(q):
+    """Per-energy a-posteriori checks and escalation to FP64 (escalate_tol = 1e-6), on a weakly broadened
+    device (scattering 1e-7, eta = 1e-12):
+    * E = -0.5: G^> = G^< + G^R - G^A cancels to ~1e-7 of its terms there, and the emulated solve's
+      G^< breaks current conservation (Sec. II-B) by more than 1e-6 of the balances' scale;
+    * E at an eigenvalue of H (kappa(M) = 2.5e7): the emulated solve conserves current to 1e-8 -- its
+      error acts as a perturbation of M -- but is off by more than 1e-6; the condition estimate
+      ||M|| max_i ||G_ii||_F (Eq. 6: error ~ kappa eps) times 2^-40 exceeds the tolerance;
+    * E = 0.37 passes both checks.
+    The two flagged energies are solved again in FP64: then current and density are within 1e-6 of the
+    oracle (densities relative to each energy's largest, currents relative to the absolute sum of
+    their trace terms -- they are ~1e-12 differences of ~1e-4 terms off resonance), the energy
+    integrals too (the escalated energies' contributions are replaced), and the energy that passed
+    keeps the emulated solve's own results."""
+    dev = _resonant_device()
+    ref = O.solve(dev)
+    outs = ["GR_diag", "GL_diag", "current", "density", "integrals", "continuity"]
+    plain = q.solve_device(dev, "emu64", outputs=outs)
+    c = plain["continuity"]
+    assert c[0] > 1e-6 and c[1] < 1e-8 and c[2] < 1e-8, c
+    assert np.abs(plain["current"][1] - ref["current"][1]).max() > 1e-6 * np.abs(ref["current"][1]).max()
+    res = q.solve_device(dev, "emu64", outputs=outs, escalate_tol=1e-6)
+    assert res["escalated"].tolist() == [1, 1, 0]
+    assert np.all(res["status"] == 0)
+    assert np.all(res["continuity"] < 1e-6), res["continuity"]
+    for e in range(3):
+        assert np.abs(res["density"][e] - ref["density"][e]).max() < 1e-6 * np.abs(ref["density"][e]).max()
+        for i in range(dev["n_blocks"] - 1):
+            absum = 2 * np.sum(np.abs(dev["H_upper"][i]) * np.abs(ref["GL_upper"][e][i]))
+            assert abs(res["current"][e][i] - ref["current"][e][i]) < 1e-6 * absum, (e, i)
+    assert np.abs(res["current"][1] - ref["current"][1]).max() < 1e-6 * np.abs(ref["current"][1]).max()
+    for k in ("current_int", "density_int"):
+        assert np.abs(res[k] - ref[k]).max() < 1e-6 * np.abs(ref[k]).max(), k
+    # the energy that passed keeps the emulated solve's own results
+    for k in ("current", "density", "GR_diag"):
+        assert np.array_equal(res[k][2], plain[k][2]), k
+
+
+def test_fp32_plan_escalates_every_energy_to_fp64(q):
+    """An FP32 plan with escalate_tol far below the FP32 mode's continuity residual solves every
+    energy again in FP64 (its workspace is then laid out for complex128 blocks): FP64 parity."""
+    dev = W.random_device(64, 5, n_energies=4, seed=6)
+    ref = O.solve(dev)
+    res = q.solve_device(dev, "fp32", outputs=["GR_diag", "GL_diag", "current", "density", "integrals",
+                                               "continuity"], escalate_tol=1e-12, max_energies_in_flight=3)
+    assert res["escalated"].tolist() == [1, 1, 1, 1]
+    _check(res, ref, 1e-10, 1e-10, keys=("GR_diag", "GL_diag"))
+    assert _obs_err(res["current_int"], ref["current_int"]) < 1e-10
+    assert _obs_err(res["density_int"], ref["density_int"]) < 1e-10
