@@ -5,9 +5,13 @@ runs in the library's kernels through the C ABI).
   bias-point solve on the first ``n_blocks`` slices of one model, with its own energy grid, contact
   chemical potentials and precision.
 * Plans (device workspaces) are pooled per (block size, precision) and sized for the model's full
-  length; a pool grows only when its HBM footprint (``qtx_rgf_footprint``) fits the budget.
-* Each of ``slots`` CUDA streams runs one request at a time; requests that arrive while others are on
-  the GPU are admitted as soon as a slot, a plan and memory are free, so their work overlaps on the
+  length; a pool grows only when its HBM footprint (``qtx_rgf_footprint``) fits the budget.  A request
+  whose plan could never fit the budget is refused when it is submitted (its result says why).
+* Each of ``slots`` CUDA streams runs one batch at a time: the queued requests admitted together
+  (up to ``group_size``, each with a plan of its own) are solved as one ``qtx_rgf_group``, so their
+  small tensor-core products share persistent kernel launches while every request keeps its own
+  outputs -- results equal to solving it alone, bit for bit.  Requests that arrive while others are on
+  the GPU are admitted as soon as a slot, plans and memory are free, so their work overlaps on the
   device.  Completion is detected by polling CUDA events; latency = completion - arrival.
 """
 from __future__ import annotations
@@ -17,7 +21,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import Inputs, Outputs, Plan, footprint, make_desc
+from . import Group, Inputs, Outputs, Plan, footprint, make_desc
 
 __all__ = ["DeviceModel", "Request", "Server"]
 
@@ -66,11 +70,15 @@ class Server:
     """Admit requests as they arrive and overlap their solves on ``slots`` CUDA streams."""
 
     def __init__(self, models: dict, slots: int = 4, hbm_budget: int | None = None,
-                 chunk_by_b: dict | None = None, refine_max_iter: int = 2):
+                 chunk_by_b: dict | None = None, refine_max_iter: int = 2, group_size: int = 4):
         import torch
         self.models = models
         self.streams = [torch.cuda.Stream() for _ in range(slots)]
-        self.busy: list = [None] * slots  # (request, plan, event, buffers)
+        self.busy: list = [None] * slots  # (batch of (request, plan, buffers), group, event)
+        self.group_size = max(1, min(int(group_size), 8))
+        self.rejected: list = []
+        self.batches = 0
+        self.largest_batch = 0
         free, _ = torch.cuda.mem_get_info()
         self.budget = hbm_budget if hbm_budget is not None else int(free * 0.6)
         self.used = 0
@@ -111,20 +119,26 @@ class Server:
 
     # ------------------------------------------------------------------ request lifecycle
     def submit(self, req: Request):
+        """Queue a request, or refuse it at once when its plan could never fit the HBM budget."""
+        m = self.models[req.model]
+        need = footprint(self._desc(m, req.precision, 1 << 30))
+        if need > self.budget:
+            req.result = {"rejected": f"plan footprint {need} bytes exceeds the HBM budget {self.budget}"}
+            req.t_done = time.perf_counter()
+            self.rejected.append(req)
+            return
         self.queue.append(req)
 
-    def _start(self, slot: int, req: Request, plan: Plan):
+    def _buffers(self, req: Request, plan: Plan):
         import torch
         m = self.models[req.model]
         nb, ne = req.n_blocks, len(req.energies)
-        st = self.streams[slot]
-        with torch.cuda.stream(st):
-            E = torch.as_tensor(req.energies, dtype=torch.float64).cuda(non_blocking=False)
-            cur = torch.empty((ne, max(nb - 1, 1)), dtype=torch.float64, device="cuda")
-            den = torch.empty((ne, nb), dtype=torch.float64, device="cuda")
-            cint = torch.zeros(max(nb - 1, 1), dtype=torch.float64, device="cuda")
-            dint = torch.zeros(nb, dtype=torch.float64, device="cuda")
-            stat = torch.zeros(ne, dtype=torch.int32, device="cuda")
+        E = torch.as_tensor(req.energies, dtype=torch.float64).cuda(non_blocking=False)
+        cur = torch.empty((ne, max(nb - 1, 1)), dtype=torch.float64, device="cuda")
+        den = torch.empty((ne, nb), dtype=torch.float64, device="cuda")
+        cint = torch.zeros(max(nb - 1, 1), dtype=torch.float64, device="cuda")
+        dint = torch.zeros(nb, dtype=torch.float64, device="cuda")
+        stat = torch.zeros(ne, dtype=torch.int32, device="cuda")
         inp = Inputs()
         inp.H_diag = m.H_diag.data_ptr()
         inp.H_upper = m.H_upper.data_ptr()
@@ -140,24 +154,49 @@ class Server:
         out.current_int = cint.data_ptr() if nb > 1 else None
         out.density_int = dint.data_ptr()
         out.status_per_energy = stat.data_ptr()
-        plan.solve(inp, out, st.cuda_stream)
+        return inp, out, (E, cur, den, cint, dint, stat)
+
+    def _start(self, slot: int, batch: list):
+        """Solve a batch of (request, plan) on one slot: one plan solve, or one group solve whose
+        members' small products share launches."""
+        import torch
+        st = self.streams[slot]
+        items = []
+        with torch.cuda.stream(st):
+            for req, plan in batch:
+                inp, out, bufs = self._buffers(req, plan)
+                items.append((req, plan, inp, out, bufs))
+        group = None
+        if len(items) == 1:
+            items[0][1].solve(items[0][2], items[0][3], st.cuda_stream)
+        else:
+            group = Group([it[1] for it in items])
+            group.solve([it[2] for it in items], [it[3] for it in items], st.cuda_stream)
         ev = torch.cuda.Event()
         ev.record(st)
-        req.t_start = time.perf_counter()
-        self.busy[slot] = (req, plan, ev, (E, cur, den, cint, dint, stat))
+        now = time.perf_counter()
+        for it in items:
+            it[0].t_start = now
+        self.batches += 1
+        self.largest_batch = max(self.largest_batch, len(items))
+        self.busy[slot] = ([(it[0], it[1], it[4]) for it in items], group, ev)
 
     def _finish(self, slot: int):
-        req, plan, ev, (E, cur, den, cint, dint, stat) = self.busy[slot]
-        req.t_done = time.perf_counter()
-        req.result = {"current": cur.cpu().numpy() if req.n_blocks > 1 else np.zeros((len(req.energies), 0)),
-                      "density": den.cpu().numpy(), "current_int": cint.cpu().numpy(),
-                      "density_int": dint.cpu().numpy(), "status": stat.cpu().numpy()}
-        self.pools[plan.key].append(plan)
+        batch, group, ev = self.busy[slot]
+        t = time.perf_counter()
+        for req, plan, (E, cur, den, cint, dint, stat) in batch:
+            req.t_done = t
+            req.result = {"current": cur.cpu().numpy() if req.n_blocks > 1 else np.zeros((len(req.energies), 0)),
+                          "density": den.cpu().numpy(), "current_int": cint.cpu().numpy(),
+                          "density_int": dint.cpu().numpy(), "status": stat.cpu().numpy()}
+            self.pools[plan.key].append(plan)
+            self.done.append(req)
+        if group is not None:
+            group.close()
         self.busy[slot] = None
-        self.done.append(req)
 
     def poll(self) -> bool:
-        """Retire finished requests and admit queued ones; returns True if anything changed."""
+        """Retire finished batches and admit queued requests; returns True if anything changed."""
         changed = False
         for s, item in enumerate(self.busy):
             if item is not None and item[2].query():
@@ -166,14 +205,19 @@ class Server:
         for s in range(len(self.busy)):
             if self.busy[s] is not None or not self.queue:
                 continue
-            # FIFO with skip-ahead: the first queued request whose plan is available or fits
-            for qi, req in enumerate(self.queue):
+            # FIFO with skip-ahead: the first queued requests whose plans are available or fit
+            batch = []
+            for req in list(self.queue):
                 plan = self._take_plan(self.models[req.model], req.precision)
-                if plan is not None:
-                    self.queue.pop(qi)
-                    self._start(s, req, plan)
-                    changed = True
+                if plan is None:
+                    continue
+                self.queue.remove(req)
+                batch.append((req, plan))
+                if len(batch) == self.group_size:
                     break
+            if batch:
+                self._start(s, batch)
+                changed = True
         return changed
 
     def run(self, requests: list, time_limit: float = 600.0) -> dict:
@@ -195,7 +239,9 @@ class Server:
         done = [r for r in self.done if r in requests]
         lat = np.array([r.latency for r in done]) if done else np.zeros(0)
         pts = sum(len(r.energies) for r in done)
-        return {"completed": len(done), "submitted": len(requests), "wall_s": t1 - t0,
+        return {"completed": len(done), "submitted": len(requests),
+                "rejected": len([r for r in self.rejected if r in requests]), "wall_s": t1 - t0,
+                "batches": self.batches, "largest_batch": self.largest_batch,
                 "energy_points_per_s": pts / (t1 - t0) if t1 > t0 else 0.0,
                 "requests_per_s": len(done) / (t1 - t0) if t1 > t0 else 0.0,
                 "p50_s": float(np.percentile(lat, 50)) if lat.size else None,

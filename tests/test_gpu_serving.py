@@ -1,4 +1,5 @@
-"""Serving loop: results are the same alone and in the mix; prefix solves match the oracle."""
+"""Serving loop: results are the same alone, in the mix and in a merged batch; prefix solves match the
+oracle; requests that can never fit the HBM budget are refused."""
 import numpy as np
 import pytest
 
@@ -49,6 +50,44 @@ def test_results_identical_alone_and_in_the_mix(env):
         assert np.all(r.result["status"] == 0)
         for k in ("current", "density", "current_int", "density_int"):
             assert np.array_equal(r.result[k], alone[r.rid][k]), (r.rid, k)
+
+
+def test_merged_batch_equals_solo_runs(env):
+    """Four requests queued together on one slot run as one merged batch (a group solve: their small
+    products share persistent launches), and each one's current, density and integrals equal its solo
+    run bit for bit."""
+    serve, devs, models = env
+    alone = {}
+    for r in _requests(serve):
+        srv = serve.Server(models, slots=1, group_size=1)
+        r.t_arrival = 0.0
+        srv.run([r])
+        alone[r.rid] = r.result
+    srv = serve.Server(models, slots=1, group_size=4)
+    reqs = _requests(serve)
+    for r in reqs:
+        r.t_arrival = 0.0
+    stats = srv.run(reqs)
+    assert stats["completed"] == 4 and stats["largest_batch"] == 4 and stats["batches"] == 1, stats
+    for r in reqs:
+        assert np.all(r.result["status"] == 0)
+        for k in ("current", "density", "current_int", "density_int"):
+            assert np.array_equal(r.result[k], alone[r.rid][k]), (r.rid, k)
+
+
+def test_request_beyond_the_budget_is_refused(env):
+    """A request whose plan footprint exceeds the HBM budget is refused at submit with a reason;
+    the others complete."""
+    serve, devs, models = env
+    from paper_2606_25595_gb300 import footprint, make_desc
+    small = footprint(make_desc(16, 64, "fp32", 128, 2, has_scattering=True,
+                                outputs=["current", "density", "integrals"]))
+    srv = serve.Server(models, slots=2, hbm_budget=small + 1)
+    reqs = [serve.Request(0, "b64", 16, np.linspace(-1, 1, 5), "fp32", 0.0, 0.0, 0.0),
+            serve.Request(1, "b128", 12, np.linspace(-1, 1, 5), "emu64", 0.0, 0.0, 0.0)]
+    stats = srv.run(reqs, time_limit=60.0)
+    assert stats["completed"] == 1 and stats["rejected"] == 1, stats
+    assert "rejected" in reqs[1].result and np.all(reqs[0].result["status"] == 0)
 
 
 def test_prefix_solve_matches_oracle(env):
