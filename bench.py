@@ -57,6 +57,8 @@ def parse():
                          "nrl: b=3408 N_B=10 (the paper's NR-L shape), per-energy self-energies streamed from host; "
                          "wsolve: screened-Coulomb system b=256 N_B=32, 64 energies (assembly + one selected solve for B^< and B^>)")
     ap.add_argument("--requests", type=int, default=40)
+    ap.add_argument("--group", type=int, default=4, help="serving: requests admitted together as one group solve")
+    ap.add_argument("--serving-solo", action="store_true", help="serving: also run the stream without batching")
     ap.add_argument("--refine-tol", type=float, default=2.0 ** -12,
                     help="mixed workloads: an energy stops its Newton sweeps once ||I - A X||_F <= this "
                          "(the next residual is then <= its square, 2^-24, below the digit products' error); "
@@ -462,21 +464,23 @@ def run_serving(args, q, W):
             r.t_arrival -= t0
         return out
 
-    srv = serve.Server(models, slots=4)
-    srv.warm(("emu64", "fp32"))
-    # warm every kernel once
-    srv.run([serve.Request(0, "b64", 16, np.linspace(-1, 1, 4), "emu64"),
-             serve.Request(1, "b64", 16, np.linspace(-1, 1, 4), "fp32")])
-    sat = srv.run(reqs(args.requests, 200.0, 1))
+    def server(group):
+        srv = serve.Server(models, slots=4, group_size=group)
+        srv.warm(("emu64", "fp32"), per_key=group)
+        # warm every kernel once
+        srv.run([serve.Request(0, "b64", 16, np.linspace(-1, 1, 4), "emu64"),
+                 serve.Request(1, "b64", 16, np.linspace(-1, 1, 4), "fp32")])
+        return srv
+
+    sat = server(args.group).run(reqs(args.requests, 200.0, 1), time_limit=3600.0)
+    solo = server(1).run(reqs(args.requests, 200.0, 1), time_limit=3600.0) if (args.group > 1 and args.serving_solo) else None
     lam = max(0.7 * sat["requests_per_s"], 0.05)
-    srv2 = serve.Server(models, slots=4)
-    srv2.warm(("emu64", "fp32"))
-    sub = srv2.run(reqs(max(args.requests // 2, 10), lam, 2))
+    sub = server(args.group).run(reqs(max(args.requests // 2, 10), lam, 2), time_limit=3600.0)
     _line(args, sat["energy_points_per_s"], 1e3 * sat["wall_s"],
           "served RGF requests: Poisson arrivals, b in {64,128,256,512}, N_B~U[16,96], N_E in "
           "{32,64,128}, complex64/emulated-FP64 tags", "emu64",
           {"serving": {"saturated_200_per_s": sat, f"at_0.7_capacity_{lam:.2f}_per_s": sub,
-                       "slots": 4}})
+                       "saturated_without_batching": solo, "slots": 4, "group_size": args.group}})
 
 
 def main():
