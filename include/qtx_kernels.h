@@ -23,7 +23,7 @@ enum { QTX_OP_N = 0, QTX_OP_C = 1 /* conjugate transpose */ };
  * op(A) is M x K, op(B) is K x N, C and C0 are M x N.  lda/ldb/ldc0/ldc are row strides and
  * strideA/B/C0/C batch strides in complex elements (0 shares one matrix across the batch).
  * precision: QTX_FP64 / QTX_FP32 on the CUDA cores; QTX_EMU64 / QTX_BF16X3 on the tcgen05 tensor cores
- * with 6 (7 when K > 512) / 2 bf16 digit planes per operand (Ozaki-style slicing, Sec. II-C), inputs
+ * with 6 (7 when K > 512) / 2 bf16 digit planes per operand (Ozaki-style slicing, Sec. II-D), inputs
  * and outputs rounded to df32 (hi + lo FP32 pairs) on the way in and out; alpha and beta are applied as
  * df32 pairs as well (~48 bits: a scalar such as 0.1 adds no FP32-sized error).  C0 may be NULL when beta == 0; C may
  * alias C0 (same layout).  Errors: QTX_ERR_INVALID_ARG (sizes < 0, NULL operands),

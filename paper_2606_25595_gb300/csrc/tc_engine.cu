@@ -2,7 +2,7 @@
 //
 // C[e] = alpha * op(A[e]) * op(B[e]) + beta * C0[e]   (complex, df32 storage, e = batch index)
 //
-// Method (Ozaki-style slicing, paper Sec. II-C: operands are split into lower-precision slices whose
+// Method (Ozaki-style slicing, paper Sec. II-D: operands are split into lower-precision slices whose
 // partial products are recombined): every row of op(A) and every column of op(B) is scaled by a
 // power of two 2^(P - e) (e: exponent of its largest entry) and rounded to a P-bit integer v, which is
 // written as S balanced base-128 digits  v = sum_i d_i 128^(S-i),  |d_1| <= 2^(l1-1), |d_i| <= 64.
