@@ -448,9 +448,16 @@ qtx_status block_inverse<df>(qtx_rgf_plan_s* P, cx<df>* A, int n, int batch, con
       next = masks + (it & 1) * P->Ec;
       QTX_CK(residual_mask(R, nn, n, batch, P->d.refine_tol, act, next, st));
     }
-    if ((s = gemm<df>(P, gargs<df>(n, n, n, A, n, nn, OP_N, R, n, nn, OP_N, A, n, nn, Xn, n, nn, 1.0, 1.0, batch, act), st))) return s;
-    Term<df> tXn; tXn.p = Xn; tXn.s = nn; tXn.alpha = 1.0;
-    QTX_CK((combine<df, df>(A, nn, tXn, none, none, n, batch, nullptr, 0.0, 0.0, act, st)));
+    if (n <= 1024) {
+      // X <- X + X R in place: the product reads X only through its digit planes (made before the
+      // launch) and, element by element in the epilogue, as C0 right before writing C
+      if ((s = gemm<df>(P, gargs<df>(n, n, n, A, n, nn, OP_N, R, n, nn, OP_N, A, n, nn, A, n, nn, 1.0, 1.0, batch, act), st))) return s;
+    } else {
+      // split along K: a later K-chunk digitises columns of X an earlier chunk would have overwritten
+      if ((s = gemm<df>(P, gargs<df>(n, n, n, A, n, nn, OP_N, R, n, nn, OP_N, A, n, nn, Xn, n, nn, 1.0, 1.0, batch, act), st))) return s;
+      Term<df> tXn; tXn.p = Xn; tXn.s = nn; tXn.alpha = 1.0;
+      QTX_CK((combine<df, df>(A, nn, tXn, none, none, n, batch, nullptr, 0.0, 0.0, act, st)));
+    }
     if (next) act = next;
   }
   return QTX_OK;
