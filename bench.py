@@ -67,6 +67,8 @@ def parse():
                     help="mixed workloads: other precision modes timed on the same workload after the headline "
                          "(one solve each, all energies), with their error against the oracle sample")
     ap.add_argument("--no-modes", action="store_true")
+    ap.add_argument("--no-others", action="store_true",
+                    help="mixed workload: skip the secondary strip (config 1) and uneven (config 3) measurements")
     ap.add_argument("--storage-bits", type=int, default=0,
                     help="mixed workloads: keep the left-connected blocks in FPX of this many bits (0 = off)")
     return ap.parse_args()
@@ -260,6 +262,45 @@ def _timed(step, steps, warmup):
     e1.record(st)
     torch.cuda.synchronize()
     return e0.elapsed_time(e1)
+
+
+# energies in flight per device of the uneven workload, as the autotuner picks them on this GPU
+UNEVEN_CHUNKS = [128, 128, 128, 128, 64, 128, 128, 128]
+
+
+def secondary_workloads(q, W, steps=3, warmup=2):
+    """The W=16 strip (FP64, contacts) and the uneven 8-device batch (FP32 products on the tensor
+    cores, one group solve replayed from a CUDA graph), each timed with CUDA events after warm-up,
+    with the strip's error against the CPU oracle (all 64 energies)."""
+    import numpy as np
+    import torch
+    import oracle as O
+    from paper_2606_25595_gb300.batch import UnevenBatch
+    out = {}
+    dev = W.strip(**W.STRIP_CFG)
+    plan, din, o, bufs = _solve_setup(q, dev, "fp64", 64, ["current", "density", "contact", "transmission",
+                                                            "integrals"])
+    st = torch.cuda.current_stream()
+    ms = _timed(lambda: plan.solve(din["_inputs"], o, st.cuda_stream), 5, 3)
+    ref = O.solve(dev, keep_blocks=False)
+    out["strip_config1_fp64"] = {
+        "value": 64 * 5 / (ms / 1e3), "unit": UNIT,
+        "workload": "W=16 strip b=16 N_B=32 N_E=64 [-3.5,3.5] eta=1e-6, Sancho-Rubio contacts",
+        "error_vs_oracle": {k: float(np.abs(bufs[k].cpu().numpy() - ref[k]).max() / np.abs(ref[k]).max())
+                            for k in ("current", "density", "contact", "transmission")}}
+    plan.close()
+    devs = W.uneven_batch(n_energies=128)
+    ub = UnevenBatch(devs, "fp32", UNEVEN_CHUNKS)
+    ub.capture()
+    ms = _timed(ub.replay, steps, warmup)
+    out["uneven_config3_fp32"] = {
+        "value": ub.n_energies * steps / (ms / 1e3), "unit": UNIT,
+        "workload": "8 random BT devices (N_B, b) = " + ", ".join(f"({d['n_blocks']},{d['block_size']})" for d in devs)
+                    + ", 128 energies each, one group solve replayed from a CUDA graph",
+        "status_ok": all(bool(np.all(r["status"] == 0)) for r in ub.results())}
+    ub.close()
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_strip(args, q, W):
@@ -677,6 +718,12 @@ def main():
     else:
         cur_host, den_host = cur.cpu().numpy(), den.cpu().numpy()
 
+    # ---------------------------------------------------------------- the strip and uneven workloads
+    # (secondary measurements, so that every benchmarked configuration appears in the one line)
+    others = {}
+    if not args.no_others and args.precision == "emu64":
+        others = secondary_workloads(q, W)
+
     # ---------------------------------------------------------------- CPU oracle sample + error
     cpu = None
     err = None
@@ -721,6 +768,7 @@ def main():
                 "status_ok": status_ok,
                 "gpu_launches": int(launches),
                 "clocks": clocks, "roofline": roofline, "e2e": e2e, "fp64_path": fp64, "other_modes": modes,
+                "other_workloads": others,
                 "cpu_baseline": cpu, "error_vs_oracle": err}
         print(json.dumps(line), flush=True)
     if ws > 1:
