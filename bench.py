@@ -269,9 +269,10 @@ UNEVEN_CHUNKS = [128, 128, 128, 128, 64, 128, 128, 128]
 
 
 def secondary_workloads(q, W, steps=3, warmup=2):
-    """The W=16 strip (FP64, contacts) and the uneven 8-device batch (FP32 products on the tensor
-    cores, one group solve replayed from a CUDA graph), each timed with CUDA events after warm-up,
-    with the strip's error against the CPU oracle (all 64 energies)."""
+    """The W=16 strip (FP64, contacts), the uneven 8-device batch (FP32 products on the tensor cores,
+    one group solve replayed from a CUDA graph) and the b = 1024 device (emulated FP64, 16 energies),
+    each timed with CUDA events after warm-up, with the strip's error against the CPU oracle (all 64
+    energies)."""
     import numpy as np
     import torch
     import oracle as O
@@ -299,6 +300,17 @@ def secondary_workloads(q, W, steps=3, warmup=2):
                     + ", 128 energies each, one group solve replayed from a CUDA graph",
         "status_ok": all(bool(np.all(r["status"] == 0)) for r in ub.results())}
     ub.close()
+    torch.cuda.empty_cache()
+    # config 4: b = 1024, N_B = 32, emulated FP64 (seven digits), 16 of its 256 energies
+    d4 = W.random_device(W.OZAKI_CFG["b"], W.OZAKI_CFG["n_blocks"], n_energies=W.OZAKI_CFG["n_energies"], seed=0)
+    sub = np.linspace(0, W.OZAKI_CFG["n_energies"] - 1, 16).astype(int)
+    plan, din, o, bufs = _solve_setup(q, d4, "emu64", 16, ["current", "density"], energies=d4["energies"][sub])
+    ms = _timed(lambda: plan.solve(din["_inputs"], o, st.cuda_stream), 1, 1)
+    out["ozaki_config4_emu64"] = {
+        "value": 16 / (ms / 1e3), "unit": UNIT,
+        "workload": "random BT device b=1024 N_B=32, 16 of its 256 energies on [-2,2], emulated FP64 (7 digit planes)",
+        "status_ok": bool(torch.all(bufs["status"] == 0).item())}
+    plan.close()
     torch.cuda.empty_cache()
     return out
 

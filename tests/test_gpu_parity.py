@@ -286,23 +286,26 @@ def _dense_M(dev, E, k=0):
 
 def _check_kappa_eps(q, dev, precision, eps_mode):
     """Error bars from Eq. 6's model (error ~ kappa * eps_m), with kappa = kappa_2(M(E)) of the dense
-    device matrix per energy: G blocks (relative Frobenius) and density (relative to max_i |n_i(E)|)
-    within 4 kappa eps_m; the current, a trace of products whose terms largely cancel, within
+    device matrix per energy and a constant that grows like sqrt(b) (the rounding of length-b sums):
+    G blocks (relative Frobenius) and density (relative to max_i |n_i(E)|) within
+    4 sqrt(b/64) kappa eps_m; the current, a trace of products whose terms largely cancel, within
     kappa eps_m times the absolute sum of its terms, 2 sum_jk |H_{i,i+1}|_jk |G^<_{i,i+1}|_jk.
-    (Measured on these devices: at most 2.9, 1.7 and 0.16 of the respective bars.)"""
+    (Measured: blocks and density at most 2.9 kappa eps_m for b <= 128 and 4.7 for b = 384, 512; the
+    current at most 0.16 of its bar.)"""
     ref = O.solve(dev)
     res = q.solve_device(dev, precision, refine_max_iter=2)
     assert np.all(res["status"] == 0)
     nb = dev["n_blocks"]
+    grow = np.sqrt(max(dev["block_size"], 64) / 64.0)
     for e, E in enumerate(dev["energies"]):
-        ke = np.linalg.cond(_dense_M(dev, E)) * eps_mode
+        ke = np.linalg.cond(_dense_M(dev, E)) * eps_mode * grow
         for k in ("GR_diag", "GL_diag", "GR_upper", "GL_upper"):
             err = np.linalg.norm(res[k][e] - ref[k][e]) / np.linalg.norm(ref[k][e])
             assert err < 4 * ke, (k, E, err, ke)
         assert np.abs(res["density"][e] - ref["density"][e]).max() < 4 * ke * np.abs(ref["density"][e]).max()
         for i in range(nb - 1):
             absum = 2 * np.sum(np.abs(dev["H_upper"][i]) * np.abs(ref["GL_upper"][e][i]))
-            assert abs(res["current"][e][i] - ref["current"][e][i]) < ke * absum, (E, i)
+            assert abs(res["current"][e][i] - ref["current"][e][i]) < ke / grow * absum, (E, i)
 
 
 @pytest.mark.parametrize("b,nb,ne,seed", [(64, 16, 6, 2), (128, 8, 4, 3)])
@@ -565,3 +568,11 @@ def test_fp32_plan_escalates_every_energy_to_fp64(q):
     _check(res, ref, 1e-10, 1e-10, keys=("GR_diag", "GL_diag"))
     assert _obs_err(res["current_int"], ref["current_int"]) < 1e-10
     assert _obs_err(res["density_int"], ref["density_int"]) < 1e-10
+
+
+@pytest.mark.parametrize("b", [384, 512])
+def test_fp32_at_the_uneven_workloads_block_sizes(q, b):
+    """FP32 mode (products on the tensor cores from four digit planes; recursive inverse down to
+    64-leaves) at the uneven workload's largest block sizes, three slices, two energies: within the
+    kappa * 2^-24 bars of _check_kappa_eps."""
+    _check_kappa_eps(q, W.random_device(b, 3, n_energies=2, seed=b), "fp32", 2.0 ** -24)
