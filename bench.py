@@ -71,6 +71,10 @@ def parse():
                     help="mixed workload: skip the secondary strip (config 1) and uneven (config 3) measurements")
     ap.add_argument("--storage-bits", type=int, default=0,
                     help="mixed workloads: keep the left-connected blocks in FPX of this many bits (0 = off)")
+    ap.add_argument("--tc-stages", type=int, default=0,
+                    help="mixed workloads: pipeline stages of the tensor-core product kernel (0 = its default)")
+    ap.add_argument("--tc-ctas", type=int, default=0,
+                    help="mixed workloads: persistent CTAs per product launch (0 = one per SM)")
     return ap.parse_args()
 
 
@@ -472,13 +476,15 @@ def run_uneven(args, q, W):
     from paper_2606_25595_gb300.batch import UnevenBatch
     prec = args.precision if args.precision != "emu64" else "fp32"
     devs = W.uneven_batch(n_energies=128)
-    chunks = []
+    chunks, stages = [], []
     for dev in devs:
         din = q.upload(dev)
         chunks.append(autotune.best_chunk(din, dev["block_size"], dev["n_blocks"], prec, 128,
                                           budget_bytes=24 << 30))
+        stages.append(autotune.best_stages(din, dev["block_size"], dev["n_blocks"], prec, chunks[-1]))
         del din
-    ub = UnevenBatch(devs, prec, chunks)
+    ub = UnevenBatch(devs, prec, chunks, stages=stages)
+    pool = autotune.best_pool_waves(ub)
     captured = True
     try:
         ub.capture()
@@ -493,7 +499,8 @@ def run_uneven(args, q, W):
     _line(args, ne_total * args.steps / (ms / 1e3), ms / args.steps,
           "8 random BT devices (N_B, b) = " + ", ".join(f"({d['n_blocks']},{d['block_size']})" for d in devs)
           + ", 128 energies each", prec,
-          {"status_ok": ok, "cuda_graph": captured, "energies_in_flight": chunks})
+          {"status_ok": ok, "cuda_graph": captured, "energies_in_flight": chunks, "tc_stages": stages,
+           "pool_waves": pool})
 
 
 def run_serving(args, q, W):
@@ -567,7 +574,7 @@ def main():
     outs = ["GR_diag", "GL_diag", "current", "density", "integrals"]
     desc = q.make_desc(nb, b, args.precision, min(args.chunk, ne), refine_max_iter=2,
                        has_scattering=True, outputs=outs, offdiag_sigma=bt, storage_bits=args.storage_bits,
-                       refine_tol=args.refine_tol)
+                       refine_tol=args.refine_tol, tc_stages=args.tc_stages, tc_ctas=args.tc_ctas)
     plan = q.Plan(desc)
     cd = torch.device("cuda")
     GR = torch.empty((ne, nb, b, b), dtype=torch.complex128, device=cd)
@@ -774,6 +781,7 @@ def main():
                            "global_batch": ne * ws, "precision": args.precision,
                            "energies_in_flight": min(args.chunk, ne),
                            "storage_bits": args.storage_bits,
+                           "tc_stages": args.tc_stages, "tc_ctas": args.tc_ctas,
                            "refine_max_iter": 2, "refine_tol": args.refine_tol,
                            "plan_bytes_per_energy_in_flight": q.footprint(desc) // min(args.chunk, ne),
                            "l2": "inputs and working set (>= 16 GB) larger than L2; no flush"},

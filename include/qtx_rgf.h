@@ -149,6 +149,11 @@ typedef struct {
                                   outputs->escalated marks them.  Needs one host synchronisation per
                                   chunk (so such solves cannot be captured in a CUDA graph).  FP32 plans
                                   then size their workspace for complex128 blocks.  0 = off */
+  int tc_stages;               /* schedule of the tensor-core product kernel: pipeline stages (0 = the
+                                  default; 6 digit planes take 2 or 3, 4 planes 3 or 4, 2 planes 4 or 8,
+                                  7 planes 2; other values give the default) */
+  int tc_ctas;                 /* schedule: persistent CTAs per product launch (0 = one per SM; fewer
+                                  leave SMs to products of other plans running concurrently) */
 } qtx_rgf_desc;
 
 /* Device inputs (caller-owned, complex128 unless noted). */
@@ -266,6 +271,10 @@ qtx_status qtx_rgf_group_solve(qtx_rgf_group group, const qtx_rgf_inputs *const 
                                const qtx_rgf_outputs *const *outputs, void *stream);
 qtx_status qtx_rgf_group_destroy(qtx_rgf_group group);
 const char *qtx_rgf_group_last_error(qtx_rgf_group group);
+/* Schedule of the pooling: a product is pooled when it fills fewer than `waves` waves of the GPU
+ * (tiles < waves x SMs) and pooled products are launched once they fill that many; 0 = never pool.
+ * Default 2. */
+qtx_status qtx_rgf_group_set_pool_waves(qtx_rgf_group group, int waves);
 /* Pooled product-kernel launches this group has issued, and the products they covered (monotonic;
  * for tests and profiling). */
 long long qtx_rgf_group_launches(qtx_rgf_group group);

@@ -36,7 +36,7 @@ EXPORTED = ("qtx_rgf_plan_create", "qtx_rgf_solve", "qtx_rgf_status", "qtx_rgf_d
             "qtx_fpx_bytes", "qtx_fpx_compress", "qtx_fpx_decompress", "qtx_w_assemble",
             "qtx_rgf_group_create", "qtx_rgf_group_solve", "qtx_rgf_group_destroy",
             "qtx_rgf_group_last_error", "qtx_rgf_group_launches", "qtx_rgf_group_pooled_products",
-            "qtx_tc_wait_test")
+            "qtx_tc_wait_test", "qtx_rgf_group_set_pool_waves")
 
 
 class QtxError(RuntimeError):
@@ -55,7 +55,7 @@ class Desc(ctypes.Structure):
                 ("offdiag_sigma", ctypes.c_int), ("storage_bits", ctypes.c_int),
                 ("sigma_stream", ctypes.c_int), ("system_input", ctypes.c_int),
                 ("refine_tol", ctypes.c_double), ("second_rhs", ctypes.c_int),
-                ("escalate_tol", ctypes.c_double)]
+                ("escalate_tol", ctypes.c_double), ("tc_stages", ctypes.c_int), ("tc_ctas", ctypes.c_int)]
 
 
 class Inputs(ctypes.Structure):
@@ -146,6 +146,8 @@ def load() -> ctypes.CDLL:
     L.qtx_rgf_group_last_error.restype = ctypes.c_char_p
     L.qtx_rgf_group_launches.argtypes = [vp]
     L.qtx_rgf_group_launches.restype = ctypes.c_longlong
+    L.qtx_rgf_group_set_pool_waves.argtypes = [vp, i]
+    L.qtx_rgf_group_set_pool_waves.restype = i
     L.qtx_rgf_group_pooled_products.argtypes = [vp]
     L.qtx_rgf_group_pooled_products.restype = ctypes.c_longlong
     L.qtx_tc_wait_test.argtypes = [i]
@@ -168,7 +170,7 @@ def make_desc(n_blocks, block_size, precision="fp64", max_energies_in_flight=64,
               refine_max_iter=2, has_S=False, has_scattering=True, energy_dependent_sigma=False,
               leads=False, decim_tol=1e-13, decim_max_iter=100, outputs=None,
               offdiag_sigma=False, storage_bits=0, sigma_stream=False, system_input=False,
-              refine_tol=0.0, second_rhs=False, escalate_tol=0.0) -> Desc:
+              refine_tol=0.0, second_rhs=False, escalate_tol=0.0, tc_stages=0, tc_ctas=0) -> Desc:
     if outputs is None:
         outputs = (1 << 12) - 1  # every output but the continuity residual
     elif not isinstance(outputs, int):
@@ -182,7 +184,7 @@ def make_desc(n_blocks, block_size, precision="fp64", max_energies_in_flight=64,
                 int(bool(energy_dependent_sigma)), int(bool(leads)), float(decim_tol),
                 int(decim_max_iter), int(outputs), int(bool(offdiag_sigma)), int(storage_bits),
                 int(bool(sigma_stream)), int(bool(system_input)), float(refine_tol),
-                int(bool(second_rhs)), float(escalate_tol))
+                int(bool(second_rhs)), float(escalate_tol), int(tc_stages), int(tc_ctas))
 
 
 def kernel_launches() -> int:
@@ -262,6 +264,11 @@ class Group:
         s = L.qtx_rgf_group_solve(self._h, ia, oa, ctypes.c_void_p(stream))
         if s != 0:
             raise QtxError(s, L.qtx_rgf_group_last_error(self._h).decode())
+
+    def set_pool_waves(self, waves: int) -> None:
+        s = load().qtx_rgf_group_set_pool_waves(self._h, int(waves))
+        if s != 0:
+            raise QtxError(s, "qtx_rgf_group_set_pool_waves")
 
     def launches(self) -> int:
         return int(load().qtx_rgf_group_launches(self._h))

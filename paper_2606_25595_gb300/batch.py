@@ -22,10 +22,13 @@ class UnevenBatch:
     """Resident inputs, plans and outputs of a list of ``workloads``-style device dicts.
 
     ``chunks``: energies in flight per device (default: all of the device's energies).
+    ``stages``, ``ctas``: per-device schedule of the tensor-core product kernel (``make_desc``'s
+    ``tc_stages``, ``tc_ctas``; default 0 = the kernel's own).
     ``outputs``: names as in ``make_desc``; per-energy arrays and integrals are kept on the device."""
 
     def __init__(self, devs: list, precision: str = "fp32", chunks=None, refine_max_iter: int = 2,
-                 refine_tol: float = 0.0, outputs=("current", "density", "integrals"), grouped: bool = True):
+                 refine_tol: float = 0.0, outputs=("current", "density", "integrals"), grouped: bool = True,
+                 stages=None, ctas=None):
         import torch
         self.devs = devs
         self.grouped = grouped
@@ -40,7 +43,9 @@ class UnevenBatch:
             din = upload(dev, E)
             desc = make_desc(nb, b, precision, ec, refine_max_iter, has_S=dev.get("S_diag") is not None,
                              has_scattering=dev.get("SigR") is not None, leads=bool(dev.get("leads")),
-                             outputs=want, refine_tol=refine_tol)
+                             outputs=want, refine_tol=refine_tol,
+                             tc_stages=0 if stages is None else int(stages[k]),
+                             tc_ctas=0 if ctas is None else int(ctas[k]))
             plan = Plan(desc)
             o = Outputs()
             bufs = {}

@@ -215,6 +215,9 @@ struct TcArgs {
   TcOperand* opndA = nullptr;  // optional kept / reused digit planes of op(A), op(B)
   TcOperand* opndB = nullptr;
   bool f32 = false;            // A, B, C0, C point to cx<float> arrays (four digit planes only)
+  int stages = 0;              // schedule: pipeline stages of the product kernel (0 = the variant's
+                               // default; only sizes its shared memory allows are taken)
+  int ctas = 0;                // schedule: persistent CTAs per launch (0 = one per SM)
 };
 
 }  // namespace qtx

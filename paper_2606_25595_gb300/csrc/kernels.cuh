@@ -166,11 +166,12 @@ struct TcParams {
 // filled, ready to launch alone or with other products of the same variant.
 struct TcPrepared {
   int variant = -1;  // gemm_tc_variant
+  int ctas = 0;      // persistent CTAs of its launch (0 = one per SM)
   int NBt = 0, MBt = 0;
   long tiles = 0;    // output tiles: column tiles x row tiles x batch
   TcParams p{};
 };
-// Kernel variant of a product: digits used and IO type; -1 for products split along K.
+// Kernel variant of a product: digits used, IO type and pipeline stages; -1 for products split along K.
 int gemm_tc_variant(const TcArgs& a, int digits);
 // Digitise a product's operands on `st` (not one split along K) and fill *out.
 cudaError_t gemm_tc_prepare(const TcArgs& a, int digits, void* scratch, size_t scratch_bytes, int* err_flag,

@@ -266,6 +266,7 @@ qtx_status gemm<float>(qtx_rgf_plan_s* P, const GemmArgs<float>& g, cudaStream_t
     a.C = reinterpret_cast<cx<df>*>(g.C); a.ldc = g.ldc; a.sC = g.sC;
     a.alpha = g.alpha; a.beta = g.beta;
     a.batch = g.batch; a.active = g.active;
+    a.stages = P->d.tc_stages; a.ctas = P->d.tc_ctas;
     // in the FP32 mode these are the plan's own products (profiled); in the emulated mode they
     // belong to the starting inverse (not counted)
     if (P->group && gemm_tc_variant(a, 4) >= 0) {
@@ -311,6 +312,7 @@ qtx_status gemm<df>(qtx_rgf_plan_s* P, const GemmArgs<df>& g, cudaStream_t st, b
   a.C = g.C; a.ldc = g.ldc; a.sC = g.sC;
   a.alpha = g.alpha; a.beta = g.beta;
   a.batch = g.batch; a.active = g.active;
+  a.stages = P->d.tc_stages; a.ctas = P->d.tc_ctas;
   if (P->group && gemm_tc_variant(a, tc_digits(P->d)) >= 0) {
     QTX_CK(group_gemm(P, a, tc_digits(P->d), st));
     return QTX_OK;
@@ -973,6 +975,7 @@ qtx_status validate(const qtx_rgf_desc* d, std::string& err) {
   if (d->sigma_stream && (!d->has_scattering || !d->energy_dependent_sigma || d->offdiag_sigma)) { err = "sigma_stream needs has_scattering and energy_dependent_sigma, without offdiag_sigma"; return QTX_ERR_INVALID_ARG; }
   if (d->second_rhs && (!d->system_input || d->storage_bits)) { err = "second_rhs needs system_input and storage_bits = 0"; return QTX_ERR_INVALID_ARG; }
   if (!(d->escalate_tol >= 0.0)) { err = "escalate_tol must be >= 0"; return QTX_ERR_INVALID_ARG; }
+  if (d->tc_stages < 0 || d->tc_ctas < 0) { err = "tc_stages and tc_ctas must be >= 0"; return QTX_ERR_INVALID_ARG; }
   if ((d->escalate_tol > 0 || (d->outputs & QTX_OUT_CONTINUITY)) && (d->offdiag_sigma || d->system_input || d->sigma_stream)) {
     err = "the continuity check (escalate_tol, QTX_OUT_CONTINUITY) needs block-diagonal Sigma, no system_input and no sigma_stream";
     return QTX_ERR_INVALID_ARG;
@@ -1485,7 +1488,7 @@ qtx_status qtx_lead_self_energy(int n, const void* H00, const void* H01, const d
 // grouping only changes which launch computes a tile, never how, so every member's results equal
 // its plan's solo solve bit for bit; the launches are plain stream work joined back to the caller's
 // stream, so a group solve can be captured in a CUDA graph.
-constexpr int kPoolWaves = 2;
+constexpr int kPoolWaves = 2;  // default pooling threshold (qtx_rgf_group_set_pool_waves)
 constexpr int kPoolWaitUs = 50;
 
 struct qtx_rgf_group_s {
@@ -1498,7 +1501,8 @@ struct qtx_rgf_group_s {
   cudaEvent_t fork = nullptr;
   std::vector<cudaEvent_t> join;
   cudaEvent_t gjoin = nullptr;
-  long pool_tiles = 304;             // kPoolWaves x SMs
+  long pool_tiles = 304;             // pooling threshold in tiles: waves x SMs
+  int sms = 152;
   std::mutex mu;
   std::condition_variable cv;
   struct Req {
@@ -1554,7 +1558,7 @@ cudaError_t group_gemm(qtx_rgf_plan_s* P, const TcArgs& a, int digits, cudaStrea
   r.member = P->member;
   cudaError_t e = gemm_tc_prepare(a, digits, P->ws + P->L.tc_scratch, P->L.tc_bytes, P->d_err_flag, st, &r.p);
   if (e != cudaSuccess || r.p.tiles == 0) return e;
-  if (r.p.tiles >= G->pool_tiles) {  // fills the GPU alone
+  if (r.p.tiles >= G->pool_tiles) {  // fills the GPU alone (or pooling is off)
     const TcPrepared* one[1] = {&r.p};
     return gemm_tc_launch(one, 1, st);
   }
@@ -1594,6 +1598,7 @@ qtx_status qtx_rgf_group_create(int n_plans, const qtx_rgf_plan* plans, qtx_rgf_
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   G->pool_tiles = (long)kPoolWaves * sms;
+  G->sms = sms;
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&G->gst, cudaStreamNonBlocking);
   G->mst.assign(n_plans, nullptr);
   G->ready.assign(n_plans, nullptr);
@@ -1668,6 +1673,12 @@ qtx_status qtx_rgf_group_solve(qtx_rgf_group G, const qtx_rgf_inputs* const* in,
     if (worst == QTX_OK) { worst = QTX_ERR_CUDA; G->err = "join"; }
   }
   return worst;
+}
+
+qtx_status qtx_rgf_group_set_pool_waves(qtx_rgf_group G, int waves) {
+  if (!G || waves < 0) return QTX_ERR_INVALID_ARG;
+  G->pool_tiles = (long)waves * G->sms;  // 0: every product fills "0 waves", so none is pooled
+  return QTX_OK;
 }
 
 long long qtx_rgf_group_launches(qtx_rgf_group G) { return G ? G->launches : 0; }

@@ -858,7 +858,11 @@ cudaError_t launch(const TcPrepared* const* pp, int n, cudaStream_t st, cudaEven
   }
   G.tile0[n] = (int)total;
   if (total == 0) return cudaSuccess;
-  const int grid = (int)(total < sms ? total : sms);  // one CTA per SM (the kernel holds ~230 KB of smem)
+  // one CTA per SM (the kernel holds up to ~230 KB of smem), or the schedule's CTA count
+  int ctas = sms;
+  for (int q = 0; q < n; ++q)
+    if (pp[q]->ctas > 0 && pp[q]->ctas < ctas) ctas = pp[q]->ctas;
+  const int grid = (int)(total < ctas ? total : ctas);
   if (ev) cudaEventRecord(ev[0], st);
   if (n == 1) k_tc_gemm<S, NST, IO, false><<<grid, 320, smem, st>>>(G);
   else k_tc_gemm<S, NST, IO, true><<<grid, 320, smem, st>>>(G);
@@ -917,19 +921,32 @@ TcOperand tc_operand_at(void* base, int side, int R, int K, int batch, int digit
   return o;
 }
 
-// Kernel variant of a product: digits actually used (effective_digits) and the IO type; -1 when the
-// product is split along K (it then runs as consecutive chunks and cannot be prepared on its own).
+// Pipeline stages of a kernel variant: the requested count if shared memory allows it (beside the
+// 98 KB epilogue staging: 6 digit planes take 43 KB a stage, 7 take 50 KB, 4 take 29 KB, 2 take
+// 14 KB), else the default.
+static int resolve_stages(int S, bool f32, int want) {
+  if (f32) return (want == 3) ? 3 : 4;          // S = 4: 3 or 4 stages
+  if (S == 6) return (want == 2) ? 2 : 3;       // 2 or 3
+  if (S == 7) return 2;
+  return (want == 4) ? 4 : 8;                   // S = 2: 4 or 8
+}
+
+// Kernel variant of a product: digits actually used (effective_digits), the IO type and the stages;
+// -1 when the product is split along K (it then runs as consecutive chunks and cannot be prepared on
+// its own).
 int gemm_tc_variant(const TcArgs& a, int digits) {
   if (k_chunks(a.K) > 1) return -1;
-  return effective_digits(digits, a.K) * 2 + (a.f32 ? 1 : 0);
+  const int S = effective_digits(digits, a.K);
+  return S * 2 + (a.f32 ? 1 : 0) + 100 * resolve_stages(S, a.f32, a.stages);
 }
 
 cudaError_t gemm_tc_prepare(const TcArgs& a, int digits, void* scratch, size_t scratch_bytes, int* err_flag,
                             cudaStream_t st, TcPrepared* out) {
   out->variant = gemm_tc_variant(a, digits);
+  out->ctas = a.ctas;
   out->tiles = 0;
   if (a.M <= 0 || a.N <= 0 || a.batch <= 0) return cudaSuccess;
-  switch (out->variant) {
+  switch (out->variant % 100) {
     case 4 * 2 + 1: return tc::prepare<4, float>(a, scratch, scratch_bytes, err_flag, st, *out);
     case 7 * 2: return tc::prepare<7, df>(a, scratch, scratch_bytes, err_flag, st, *out);
     case 6 * 2: return tc::prepare<6, df>(a, scratch, scratch_bytes, err_flag, st, *out);
@@ -943,10 +960,13 @@ cudaError_t gemm_tc_launch(const TcPrepared* const* p, int n, cudaStream_t st, c
   for (int q = 1; q < n; ++q)
     if (p[q]->variant != p[0]->variant) return cudaErrorInvalidValue;
   switch (p[0]->variant) {
-    case 4 * 2 + 1: return tc::launch<4, 4, float>(p, n, st, ev);
-    case 7 * 2: return tc::launch<7, 2, df>(p, n, st, ev);
-    case 6 * 2: return tc::launch<6, 3, df>(p, n, st, ev);
-    case 2 * 2: return tc::launch<2, 8, df>(p, n, st, ev);
+    case 400 + 4 * 2 + 1: return tc::launch<4, 4, float>(p, n, st, ev);
+    case 300 + 4 * 2 + 1: return tc::launch<4, 3, float>(p, n, st, ev);
+    case 200 + 7 * 2: return tc::launch<7, 2, df>(p, n, st, ev);
+    case 300 + 6 * 2: return tc::launch<6, 3, df>(p, n, st, ev);
+    case 200 + 6 * 2: return tc::launch<6, 2, df>(p, n, st, ev);
+    case 800 + 2 * 2: return tc::launch<2, 8, df>(p, n, st, ev);
+    case 400 + 2 * 2: return tc::launch<2, 4, df>(p, n, st, ev);
     default: return cudaErrorInvalidValue;
   }
 }

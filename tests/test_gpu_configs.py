@@ -138,6 +138,43 @@ def test_group_solve_equals_solo_solves(q, precision):
     grp.close()
 
 
+@pytest.mark.parametrize("precision,stages", [("emu64", 2), ("fp32", 3), ("bf16x3", 4)])
+def test_schedule_knobs_leave_results_unchanged(q, precision, stages):
+    """The product kernel's schedule (pipeline stages, persistent CTAs per launch) and the group's
+    pooling threshold change only the order tiles are taken in, never a tile's arithmetic: the scaled
+    uneven devices solved with the non-default stage count and 37 CTAs per launch, and as a group at
+    every pooling threshold the autotuner searches, equal the default schedule bit for bit."""
+    from paper_2606_25595_gb300 import autotune
+    from paper_2606_25595_gb300.batch import UnevenBatch
+    devs = W.uneven_batch(n_energies=4, scale=0.25)
+    outs = ("GR_diag", "GL_diag", "current", "density")
+    n = len(devs)
+    ref = UnevenBatch(devs, precision, chunks=[2] * n, outputs=outs, grouped=False)
+    ref.launch()
+    r_ref = ref.results()
+    ref.close()
+    alt = UnevenBatch(devs, precision, chunks=[2] * n, outputs=outs, grouped=False,
+                      stages=[stages] * n, ctas=[37] * n)
+    alt.launch()
+    r_alt = alt.results()
+    alt.close()
+    for a, b in zip(r_ref, r_alt):
+        assert np.all(a["status"] == 0)
+        for k in a:
+            assert np.array_equal(a[k], b[k]), k
+    grp = UnevenBatch(devs, precision, chunks=[2] * n, outputs=outs, grouped=True, stages=[stages] * n)
+    for w in (0, 1, 2, 4):
+        grp.group.set_pool_waves(w)
+        grp.launch()
+        for a, b in zip(r_ref, grp.results()):
+            for k in a:
+                assert np.array_equal(a[k], b[k]), (w, k)
+    best = autotune.best_pool_waves(grp, refresh=True)
+    assert best in (0, 1, 2, 4)
+    grp.close()
+    assert stages in autotune.STAGE_CHOICES[precision]
+
+
 @pytest.mark.slow
 def test_nrl_shape_streamed_sigma(q):
     """The paper's NR-L block shape, b = 3408 and N_B = 10 (Sec. V; split-K products with seven
