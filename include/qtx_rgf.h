@@ -273,7 +273,7 @@ qtx_status qtx_rgf_group_destroy(qtx_rgf_group group);
 const char *qtx_rgf_group_last_error(qtx_rgf_group group);
 /* Schedule of the pooling: a product is pooled when it fills fewer than `waves` waves of the GPU
  * (tiles < waves x SMs) and pooled products are launched once they fill that many; 0 = never pool.
- * Default 2. */
+ * Default 0: the members' streams then overlap on the GPU without holding one another in step. */
 qtx_status qtx_rgf_group_set_pool_waves(qtx_rgf_group group, int waves);
 /* Pooled product-kernel launches this group has issued, and the products they covered (monotonic;
  * for tests and profiling). */

@@ -1478,17 +1478,19 @@ qtx_status qtx_lead_self_energy(int n, const void* H00, const void* H01, const d
 
 // ----------------------------------------------------------------------------- groups (uneven batches)
 // Several plans -- devices of different N_B and b, each with its own energies -- solved together:
-// every member's solve runs on its own host thread and stream.  A tensor-core product is digitised on
-// the member's stream; if it fills at least kPoolWaves waves of the GPU alone it is launched there
-// at once, otherwise it is pooled: the member posts it and waits, and the pending products are
-// launched together -- one persistent kernel over the union of their tiles, per kernel variant, at most
-// kTcMaxGroup products a launch -- on the group's stream once they fill kPoolWaves waves, once every
-// member still solving has posted one, or once the poster has waited kPoolWaitUs on the host.  Events
-// order each pooled launch after its members' preceding work and before their following work.  The
+// every member's solve runs on its own host thread and stream, so the streams' launches overlap on
+// the GPU.  With a pooling threshold of w > 0 waves, a tensor-core product is digitised on the
+// member's stream; if it fills at least w waves of the GPU alone it is launched there at once,
+// otherwise it is pooled: the member posts it and waits, and the pending products are launched
+// together -- one persistent kernel over the union of their tiles, per kernel variant, at most
+// kTcMaxGroup products a launch -- on the group's stream once they fill w waves, once every member
+// still solving has posted one, or once the poster has waited kPoolWaitUs on the host.  Events order
+// each pooled launch after its members' preceding work and before their following work.  The
 // grouping only changes which launch computes a tile, never how, so every member's results equal
 // its plan's solo solve bit for bit; the launches are plain stream work joined back to the caller's
-// stream, so a group solve can be captured in a CUDA graph.
-constexpr int kPoolWaves = 2;  // default pooling threshold (qtx_rgf_group_set_pool_waves)
+// stream, so a group solve can be captured in a CUDA graph.  Pooling is off by default: its events
+// hold the members in step, which costs more than the merged launches save.
+constexpr int kPoolWaves = 0;  // default pooling threshold (qtx_rgf_group_set_pool_waves)
 constexpr int kPoolWaitUs = 50;
 
 struct qtx_rgf_group_s {

@@ -8,9 +8,10 @@ runs in the library's kernels through the C ABI).
   length; a pool grows only when its HBM footprint (``qtx_rgf_footprint``) fits the budget.  A request
   whose plan could never fit the budget is refused when it is submitted (its result says why).
 * Each of ``slots`` CUDA streams runs one batch at a time: the queued requests admitted together
-  (up to ``group_size``, each with a plan of its own) are solved as one ``qtx_rgf_group``, so their
-  small tensor-core products share persistent kernel launches while every request keeps its own
-  outputs -- results equal to solving it alone, bit for bit.  Requests that arrive while others are on
+  (up to ``group_size``, each with a plan of its own) are solved as one ``qtx_rgf_group``: each
+  request's solve is enqueued from its own host thread onto its own stream, so their launches overlap
+  on the device, while every request keeps its own outputs -- results equal to solving it alone, bit
+  for bit.  Requests that arrive while others are on
   the GPU are admitted as soon as a slot, plans and memory are free, so their work overlaps on the
   device.  Completion is detected by polling CUDA events; latency = completion - arrival.
 """
@@ -158,7 +159,7 @@ class Server:
 
     def _start(self, slot: int, batch: list):
         """Solve a batch of (request, plan) on one slot: one plan solve, or one group solve whose
-        members' small products share launches."""
+        members are enqueued concurrently, each on its own stream."""
         import torch
         st = self.streams[slot]
         items = []

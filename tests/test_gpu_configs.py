@@ -117,9 +117,10 @@ def test_uneven_batch_graph_replay(q, precision):
 
 @pytest.mark.parametrize("precision", ["emu64", "fp32"])
 def test_group_solve_equals_solo_solves(q, precision):
-    """A group solve of the eight scaled uneven devices (their tensor-core products pooled into shared
-    persistent launches, each device on its own stream) equals the same plans solved one by one, bit
-    for bit, and pools: its pooled launches cover more products than there are launches."""
+    """A group solve of the eight scaled uneven devices (each device on its own stream and host
+    thread) equals the same plans solved one by one, bit for bit, without pooling (the default) and
+    with the tensor-core products pooled into shared persistent launches at a two-wave threshold,
+    where its pooled launches cover more products than there are launches."""
     from paper_2606_25595_gb300.batch import UnevenBatch
     devs = W.uneven_batch(n_energies=4, scale=0.25)
     outs = ("GR_diag", "GL_diag", "current", "density", "integrals")
@@ -130,10 +131,15 @@ def test_group_solve_equals_solo_solves(q, precision):
     grp = UnevenBatch(devs, precision, chunks=[2] * len(devs), outputs=outs, grouped=True)
     grp.launch()
     r_grp = grp.results()
-    for a, b in zip(r_solo, r_grp):
+    assert grp.group.launches() == 0
+    grp.group.set_pool_waves(2)
+    grp.launch()
+    r_pool = grp.results()
+    for a, b, c in zip(r_solo, r_grp, r_pool):
         assert np.all(a["status"] == 0)
         for k in a:
             assert np.array_equal(a[k], b[k]), k
+            assert np.array_equal(a[k], c[k]), k
     assert 0 < grp.group.launches() < grp.group.pooled_products()
     grp.close()
 
