@@ -210,20 +210,31 @@ __device__ __forceinline__ int problem_of(const TcGroup& G, long t, long& lt) {
   return q;
 }
 
-// Sum of the accumulators of one output value (acc0 largest) as df32, with TwoSum steps.
+// Sum of the accumulators of one output value as df32.  The exact groups acc0..acc3 (all of them
+// when NACC < 5) hold multiples of 1, 2^-7, 2^-14, 2^-21 with |acc0| <= 2^21 (Keff L^2 for every
+// l1 of dims_of) and |acc_g| < 2^(24 - 7 g); acc4 is the rounded tail, below 2^-2.  So:
+//   T = acc0 + acc1 + acc2 + acc3 in FP32 has |T| < 2^22 and is within 3 * 2^-3 of their exact sum
+//     S4 (three roundings of at most half an ulp of 2^-2);
+//   H = T rounded to an integer (adding and subtracting 1.5 * 2^23) is within 7/8 of S4;
+//   r = ((acc0 - H) + acc1) + acc2 + acc3 is exact step by step: acc0 - H is an integer below 2^23,
+//     and each later partial sum equals S4 - H minus the groups still to come, below 2^11 on the grid
+//     of its finest term (at most 18 significant bits);
+//   adding acc4 rounds once, by at most 2^-25 (acc4's own accumulation error is far larger);
+//   |r| < 1 <= |H| unless H = 0, so (H, r) renormalises with one Fast2Sum.
+// 13 FP32 additions for five accumulators, against 31 for a chain of TwoSum steps.
 template <int NACC>
 __device__ __forceinline__ df sum_acc(const uint32_t (&v)[NACC][8], int c) {
-  float s = __uint_as_float(v[0][c]), e = 0.f;
+  constexpr int NEX = NACC < 5 ? NACC : 4;  // exact groups
+  const float a0 = __uint_as_float(v[0][c]);
+  float t = a0;
 #pragma unroll
-  for (int g = 1; g < NACC; ++g) {
-    const float x = __uint_as_float(v[g][c]);
-    const float t = s + x;
-    const float bv = t - s;
-    e += (s - (t - bv)) + (x - bv);
-    s = t;
-  }
-  const float h = s + e;
-  return mkdf(h, e - (h - s));
+  for (int g = 1; g < NEX; ++g) t = __fadd_rn(t, __uint_as_float(v[g][c]));
+  const float H = __fsub_rn(__fadd_rn(t, 12582912.f), 12582912.f);
+  float r = __fsub_rn(a0, H);
+#pragma unroll
+  for (int g = 1; g < NACC; ++g) r = __fadd_rn(r, __uint_as_float(v[g][c]));
+  const float hi = __fadd_rn(H, r);
+  return mkdf(hi, __fsub_rn(r, __fsub_rn(hi, H)));
 }
 
 // Tile of round k for this CTA.  Round k covers tiles [k G, (k + 1) G) (G = gridDim.x; column tile
