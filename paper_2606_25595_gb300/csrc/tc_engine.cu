@@ -14,8 +14,8 @@
 // of the leading digit shrinks with K to guarantee it), so their FP32 sums are exact whatever
 // rounding the tensor core's accumulator applies; only acc4, at ~2^-24 of the product, is rounded
 // (the accumulation truncates, so its error grows with the number of MMA steps: ~2^-38 at K = 256).
-// The epilogue adds the five with error-free FP32 TwoSum steps (the exact groups are summed exactly up
-// to the final df32 rounding), applies the row/column scales and writes df32.
+// The epilogue adds the five into df32 (the exact groups exactly: their FP32 sum rounded to an integer
+// plus the remainder formed term by term, see sum_acc), applies the row/column scales and writes df32.
 // With S = 6 digits (21 digit products) the products carry ~41 bits for K <= 256 (the "emulated FP64"
 // mode); for K > 512, where l1 = 5, that mode takes S = 7 (28 digit products, ~44 bits) instead.
 // With S = 2 (3 digit products) they carry ~13 bits ("BF16x3").
@@ -37,9 +37,9 @@
 //            pairs), tcgen05.commit's each stage back to the producer and each finished tile to the
 //            epilogue, and waits for the epilogue to release TMEM before the next tile;
 //   warps 2-9 epilogue (two warps per TMEM lane quarter, one per column half): tcgen05.ld of the
-//            accumulators, TwoSum recombination into df32, row/column scaling into a staging area,
-//            release of TMEM, then coalesced stores with the beta * C0 term -- overlapping the next
-//            tile's mainloop.
+//            accumulators and their recombination into df32 in a staging area, release of TMEM, then
+//            the row/column scaling, the alpha and beta * C0 terms and coalesced stores --
+//            overlapping the next tile's mainloop.
 // Every mbarrier wait is bounded (2 s of %globaltimer); on expiry the kernel sets *err and unwinds.
 #include <cuda_bf16.h>
 
@@ -288,6 +288,7 @@ __global__ void __launch_bounds__(320, 1) k_tc_gemm(const __grid_constant__ TcGr
   uint32_t* tslot = reinterpret_cast<uint32_t*>(acce + 3);
   __shared__ int s_got;
   __shared__ int s_eB[BNC];
+  __shared__ int s_eA[BM];
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
 
   if (threadIdx.x == 0) {
@@ -420,13 +421,13 @@ __global__ void __launch_bounds__(320, 1) k_tc_gemm(const __grid_constant__ TcGr
       if (p.active && !p.active[e]) continue;
       // complex columns of this tile: Re parts in TMEM columns [0, bn), Im parts in [bn, 2 bn)
       const int bn = nblk == NBt - 1 ? p.bn_last : BNC;
-      const int m = mblk * BM + r;
-      const int eAm = p.eA[(long)(p.a_batched ? e : 0) * p.M_pad + m];
       // every epilogue thread is done with the previous tile's staging area and exponents
       __syncwarp();
       asm volatile("bar.sync 1, 256;" ::: "memory");
       if (threadIdx.x >= 64 && threadIdx.x < 64 + BNC)
         s_eB[threadIdx.x - 64] = p.eB[(long)(p.b_batched ? e : 0) * p.N_pad + nblk * BNC + threadIdx.x - 64];
+      if (threadIdx.x >= 128 && threadIdx.x < 128 + BM)
+        s_eA[threadIdx.x - 128] = p.eA[(long)(p.a_batched ? e : 0) * p.M_pad + mblk * BM + threadIdx.x - 128];
       if (threadIdx.x == 64) s_got = mbar_wait(accf, (uint32_t)j & 1u, G.p[0].err, G.limit_ns) ? 1 : 0;
       __syncwarp();
       asm volatile("bar.sync 2, 256;" ::: "memory");
@@ -442,23 +443,12 @@ __global__ void __launch_bounds__(320, 1) k_tc_gemm(const __grid_constant__ TcGr
           tmem_ld8(trow + gq * ACC_COLS + bn + c0, vi[gq]);
         }
         tmem_wait_ld();
+        // only the recombination runs while the tile holds TMEM; scaling waits for the store phase
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
-          int Es = eAm + s_eB[c0 + c] - p.escale;
-          Es = Es < -250 ? -250 : (Es > 250 ? 250 : Es);
-          const float f1 = __int_as_float((Es / 2 + 127) << 23), f2 = __int_as_float((Es - Es / 2 + 127) << 23);
-          const df sr = sum_acc<NACC>(vr, c), si = sum_acc<NACC>(vi, c);
-          // the scales are powers of two: exact (barring over/underflow)
           cx<df> o;
-          o.re = mkdf(sr.hi * f1 * f2, sr.lo * f1 * f2);
-          o.im = mkdf(si.hi * f1 * f2, si.lo * f1 * f2);
-          if (p.akind == 1) {
-            o.re = df_neg(o.re);
-            o.im = df_neg(o.im);
-          } else if (p.akind == 2) {
-            o.re = df_mul(o.re, p.alpha);
-            o.im = df_mul(o.im, p.alpha);
-          }
+          o.re = sum_acc<NACC>(vr, c);
+          o.im = sum_acc<NACC>(vi, c);
           out[r * OUT_LD + c0 + c] = o;
         }
       }
@@ -474,6 +464,19 @@ __global__ void __launch_bounds__(320, 1) k_tc_gemm(const __grid_constant__ TcGr
         const int mm = mblk * BM + rr, nn = nblk * BNC + cc;
         if (mm < p.M && nn < p.N) {
           cx<df> v = out[rr * OUT_LD + cc];
+          int Es = s_eA[rr] + s_eB[cc] - p.escale;
+          Es = Es < -250 ? -250 : (Es > 250 ? 250 : Es);
+          const float f1 = __int_as_float((Es / 2 + 127) << 23), f2 = __int_as_float((Es - Es / 2 + 127) << 23);
+          // the scales are powers of two: exact (barring over/underflow)
+          v.re = mkdf(v.re.hi * f1 * f2, v.re.lo * f1 * f2);
+          v.im = mkdf(v.im.hi * f1 * f2, v.im.lo * f1 * f2);
+          if (p.akind == 1) {
+            v.re = df_neg(v.re);
+            v.im = df_neg(v.im);
+          } else if (p.akind == 2) {
+            v.re = df_mul(v.re, p.alpha);
+            v.im = df_mul(v.im, p.alpha);
+          }
           if (C0e && p.bkind != 3) {
             const cx<IO> c0v = C0e[(long)mm * p.ldc0 + nn];
             df c0r = df_of(c0v.re), c0i = df_of(c0v.im);
