@@ -49,9 +49,10 @@ cudaError_t convert_strided(const cx<Tin>* in, long ldi, long si, cx<Tout>* out,
 // X[e] += I
 template <typename T>
 cudaError_t add_identity(cx<T>* X, long sX, int n, int batch, const int* active, cudaStream_t st);
-// next[e] = active[e] (1 when active is nullptr) and ||R[e]||_F > tol, from the hi parts in FP32
+// next[e] = active[e] (1 when active is nullptr) and ||R[e]||_F > tol, from the hi parts in FP32; a
+// non-finite norm also sets status[e] = QTX_ERR_SINGULAR (status may be nullptr)
 cudaError_t residual_mask(const cx<df>* R, long sR, int n, int batch, double tol, const int* active, int* next,
-                          cudaStream_t st);
+                          int* status, cudaStream_t st);
 
 // ---- assemble a diagonal block of M (step 1 of the sweep), in T precision from complex128 inputs:
 //   out[e] = (E[e] + i eta) S - H - SigR[e] - lead[e]     (S == nullptr => identity)

@@ -448,7 +448,7 @@ qtx_status block_inverse<df>(qtx_rgf_plan_s* P, cx<df>* A, int n, int batch, con
     int* next = nullptr;
     if (P->d.refine_tol > 0.0 && it + 1 < P->d.refine_max_iter) {
       next = masks + (it & 1) * P->Ec;
-      QTX_CK(residual_mask(R, nn, n, batch, P->d.refine_tol, act, next, st));
+      QTX_CK(residual_mask(R, nn, n, batch, P->d.refine_tol, act, next, status, st));
     }
     if (n <= 1024) {
       // X <- X + X R in place: the product reads X only through its digit planes (made before the

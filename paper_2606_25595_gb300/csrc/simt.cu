@@ -660,7 +660,7 @@ template cudaError_t assemble_offdiag<float>(cx<float>*, cx<float>*, const cx<do
 template cudaError_t assemble_offdiag<df>(cx<df>*, cx<df>*, const cx<double>*, const cx<double>*, const double*, double, int, int, cudaStream_t, const cx<double>*, const cx<double>*, long);
 
 __global__ void __launch_bounds__(256) k_residual_mask(const cx<df>* R, long sR, long nn, float tol2,
-                                                       const int* active, int* next) {
+                                                       const int* active, int* next, int* status) {
   const int e = blockIdx.x;
   if (active && !active[e]) {
     if (threadIdx.x == 0) next[e] = 0;
@@ -675,13 +675,15 @@ __global__ void __launch_bounds__(256) k_residual_mask(const cx<df>* R, long sR,
   __syncthreads();
   if (threadIdx.x == 0) {
     for (int w = 1; w < 8; ++w) s += red[w];
-    // a NaN or infinite norm compares false against tol2: such an energy keeps refining
+    // a NaN or infinite norm compares false against tol2: such an energy keeps refining, and its
+    // block inverse has failed, so it is reported singular
     next[e] = (s <= tol2) ? 0 : 1;
+    if (status && !(s <= 3.0e38f)) atomicCAS(status + e, 0, (int)QTX_ERR_SINGULAR);
   }
 }
 cudaError_t residual_mask(const cx<df>* R, long sR, int n, int batch, double tol, const int* active, int* next,
-                          cudaStream_t st) {
-  k_residual_mask<<<batch, 256, 0, st>>>(R, sR, (long)n * n, (float)(tol * tol), active, next);
+                          int* status, cudaStream_t st) {
+  k_residual_mask<<<batch, 256, 0, st>>>(R, sR, (long)n * n, (float)(tol * tol), active, next, status);
   count_launch();
   return cudaGetLastError();
 }

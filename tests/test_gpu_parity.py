@@ -14,6 +14,8 @@ import workloads as W
 
 pytestmark = pytest.mark.gpu
 
+QTX_ERR_SINGULAR = 4  # qtx_status (include/qtx_rgf.h)
+
 BLOCKS = ("GR_diag", "GR_upper", "GR_lower", "GL_diag", "GL_upper", "GG_diag", "GG_upper")
 
 
@@ -555,6 +557,31 @@ def test_escalation_by_continuity_and_by_condition(q):
     # the energy that passed keeps the emulated solve's own results
     for k in ("current", "density", "GR_diag"):
         assert np.array_equal(res[k][2], plain[k][2]), k
+
+
+@pytest.mark.parametrize("precision", ["emu64", "fp64"])
+def test_non_finite_energy_is_reported_singular(q, precision):
+    """An energy that is NaN or infinite makes its diagonal blocks non-finite: its block inverse fails
+    (the leaf inverse's pivot check; in the emulated mode with refine_tol > 0 also the refinement's
+    residual norm), status_per_energy reports QTX_ERR_SINGULAR for it, and the other energies of the
+    same chunk come out bit for bit as in a solve without it (energies never mix)."""
+    dev = W.random_device(64, 3, n_energies=2, seed=5)
+    outs = ["GR_diag", "GL_diag", "current", "density"]
+
+    def run(E):
+        desc = q.make_desc(3, 64, precision, E.size, 2, has_scattering=True, outputs=outs,
+                           refine_tol=2.0 ** -12 if precision == "emu64" else 0.0)
+        plan = q.Plan(desc)
+        r = q.solve_device(dev, precision, outputs=outs, energies=E, plan=plan, max_energies_in_flight=E.size)
+        plan.close()
+        return r
+
+    good = run(np.array([-0.4, 0.6]))
+    mixed = run(np.array([-0.4, np.nan, 0.6, np.inf]))
+    assert good["status"].tolist() == [0, 0]
+    assert mixed["status"].tolist() == [0, QTX_ERR_SINGULAR, 0, QTX_ERR_SINGULAR]
+    for k in outs:
+        assert np.array_equal(good[k], mixed[k][[0, 2]]), k
 
 
 def test_fp32_plan_escalates_every_energy_to_fp64(q):
