@@ -150,7 +150,7 @@ typedef struct {
                                   chunk (so such solves cannot be captured in a CUDA graph).  FP32 plans
                                   then size their workspace for complex128 blocks.  0 = off */
   int tc_stages;               /* schedule of the tensor-core product kernel: pipeline stages (0 = the
-                                  default; 6 digit planes take 2 or 3, 4 planes 3 or 4, 2 planes 4 or 8,
+                                  default; 6 digit planes take 2 or 3, 4 planes 2 or 3, 2 planes 4 or 6,
                                   7 planes 2; other values give the default) */
   int tc_ctas;                 /* schedule: persistent CTAs per product launch (0 = one per SM; fewer
                                   leave SMs to products of other plans running concurrently) */

@@ -115,7 +115,7 @@ def _time_plan(desc, dev_inputs, n_blocks, ec, repeats=1):
 
 
 # pipeline stages the product kernel can take per precision (the first is the default)
-STAGE_CHOICES = {"emu64": (3, 2), "fp32": (4, 3), "bf16x3": (8, 4)}
+STAGE_CHOICES = {"emu64": (3, 2), "fp32": (3, 2), "bf16x3": (6, 4)}
 
 
 def best_stages(dev_inputs: dict, b: int, n_blocks: int, precision: str, chunk: int,

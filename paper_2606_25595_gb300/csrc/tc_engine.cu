@@ -8,8 +8,9 @@
 // written as S balanced base-128 digits  v = sum_i d_i 128^(S-i),  |d_1| <= 2^(l1-1), |d_i| <= 64.
 // Digit i is stored pre-scaled as d_i * 2^(-7(i-1)) in a bf16 "digit plane" (exact: <= 7 significant
 // bits).  The products of digit planes i, j with i + j <= S + 1 run on the tensor cores (kind::f16,
-// bf16 inputs, FP32 accumulation in TMEM) into five accumulators (480 of the 512 TMEM columns):
-//     acc0..acc3: i + j = 2, 3, 4, 5,     acc4: i + j >= 6.
+// bf16 inputs, FP32 accumulation in TMEM) into one accumulator per digit group:
+//     acc0..acc3: i + j = 2, 3, 4, 5,     acc4: i + j >= 6 (6 and 7 planes; 4 planes stop at i + j = 5,
+//     2 planes at i + j = 3, with every group exact).
 // acc0..acc3 hold integers times 2^(-7 (i+j-2)) whose magnitudes stay below 2^24 units (the bound l1
 // of the leading digit shrinks with K to guarantee it), so their FP32 sums are exact whatever
 // rounding the tensor core's accumulator applies; only acc4, at ~2^-24 of the product, is rounded
@@ -22,13 +23,14 @@
 //
 // Complex arithmetic uses the real embedding (4M form):
 //     [D_re | D_im] = [A_re | A_im] * [[B_re, B_im], [-B_im, B_re]]
-// so one MMA chain with N = 96 real columns produces 48 complex columns (the last column tile of a
-// product takes only its N - 48 (tiles - 1) columns rounded up to 8, with a narrower MMA N).  The right operand's
-// digit planes are stored transposed (N x K, K-major) as three 48-row sub-tiles per block of 48
-// columns and 16 complex k -- Re B, Im B and -Im B -- which the producer pairs into the 96 rows the
-// MMA reads: (Re, Im) against A's real parts, (-Im, Re) against its imaginary parts.
+// so one MMA chain with N = 2 BNC real columns produces BNC complex columns (BNC = 48 for 6 and 7
+// digit planes, 64 for 4 and 2: bnc_of; the last column tile of a product takes only its
+// N - BNC (tiles - 1) columns rounded up to 8, with a narrower MMA N).  The right operand's digit
+// planes are stored transposed (N x K, K-major) as three BNC-row sub-tiles per block of BNC columns
+// and 16 complex k -- Re B, Im B and -Im B -- which the producer pairs into the 2 BNC rows the MMA
+// reads: (Re, Im) against A's real parts, (-Im, Re) against its imaginary parts.
 //
-// Kernel structure (persistent: one CTA per SM walking 128 x 48 complex output tiles, 10 warps):
+// Kernel structure (persistent: one CTA per SM walking 128 x BNC complex output tiles, 10 warps):
 //   warp 0   producer: one bulk asynchronous copy (cp.async.bulk, mbarrier complete-tx) per plane
 //            tile of one K-stage (16 K-elements; the digitiser stores every tile contiguously, already
 //            in the 32-byte-swizzled K-major layout the MMA descriptors expect), a ring of 2-8 stages
@@ -55,15 +57,22 @@ namespace qtx {
 namespace tc {
 
 constexpr int BM = 128;        // output rows per CTA (TMEM lanes)
-constexpr int BNC = 48;        // complex output columns per CTA
-constexpr int BNR = 2 * BNC;   // real (embedded) columns per CTA = MMA N
 constexpr int BKS = 16;        // bf16 K elements per stage (32-byte rows, 32B swizzle) = one MMA K
 constexpr int TILE_A = BM * BKS * 2;   // bytes of one A-plane tile (128 rows x 32 B)
-constexpr int TILE_B = BNR * BKS * 2;  // bytes of one B-plane tile in shared memory (96 rows x 32 B)
-constexpr int SUB_B = BNC * BKS * 2;   // bytes of one 48-row sub-tile of the right operand's planes
-constexpr int ACC_COLS = BNR;  // TMEM columns per accumulator
-constexpr int OUT_LD = BNC + 1;  // row stride (complex elements) of the epilogue's smem staging
 constexpr int DW = 7;          // bits per digit below the leading one
+// Complex output columns per CTA (BNC; the MMA's N is 2 BNC real columns, one TMEM accumulator is
+// 2 BNC columns wide): 48 for 6 and 7 digit planes, whose five accumulators take 480 of the 512 TMEM
+// columns; 64 for 4 and 2 planes, whose digit groups all stay exact in at most four accumulators
+// (4 x 128 columns), so a tile covers a third more columns at N = 128.
+__host__ __device__ constexpr int bnc_of(int S) { return S >= 6 ? 48 : 64; }
+// bytes of one B-plane tile in shared memory (2 BNC rows x 32 B) and of one BNC-row sub-tile
+__host__ __device__ constexpr int tile_b_of(int S) { return 2 * bnc_of(S) * BKS * 2; }
+__host__ __device__ constexpr int sub_b_of(int S) { return bnc_of(S) * BKS * 2; }
+// the epilogue's staging area: BM x BNC df32 complex values (16 bytes), the 16-byte column index
+// XOR-swizzled by the row's low three bits, so rows written by consecutive lanes and columns read by
+// consecutive threads both fall in distinct bank groups
+__host__ __device__ constexpr int out_bytes_of(int S) { return BM * bnc_of(S) * 16; }
+__host__ __device__ constexpr int out_at(int r, int c, int S) { return r * bnc_of(S) + (c ^ (r & 7)); }
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -257,8 +266,7 @@ __device__ __forceinline__ long tile_at(int k) {
 // registers and the staging area).  So the producer's loads and the MMAs of tile j+1 overlap the
 // epilogue's global stores of tile j, and the prologue (TMEM allocation, barrier set-up, first
 // loads) is paid once per SM rather than once per tile.  The staging area is separate from the
-// stage ring (NST = 3 stages fit beside it for 6 digit planes).
-constexpr int OUT_BYTES = BM * OUT_LD * (int)sizeof(cx<df>);
+// stage ring (NST = 3 stages fit beside it for 6 and 4 digit planes, 6 for 2).
 
 // IO: element type of C and C0 -- df (the emulated-FP64 products) or float (the products of the
 // FP32 starting inverse, four digit planes: ~27-bit products, all digit groups exact).
@@ -274,11 +282,13 @@ __device__ __forceinline__ df df_of(float x) { return mkdf(x, 0.f); }
 template <int S, int NST, typename IO, bool GROUP>
 __global__ void __launch_bounds__(320, 1) k_tc_gemm(const __grid_constant__ TcGroup G) {
   const int n_tiles = G.tile0[G.n];
+  constexpr int BNC = bnc_of(S), TILE_B = tile_b_of(S), SUB_B = sub_b_of(S), ACC_COLS = 2 * BNC;
+  constexpr int OUT_BYTES = out_bytes_of(S);
   constexpr int STAGE = S * (TILE_A + TILE_B);
   constexpr int NACC = n_acc(S);
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  cx<df>* out = reinterpret_cast<cx<df>*>(base + NST * STAGE);  // [BM][OUT_LD] staging
+  cx<df>* out = reinterpret_cast<cx<df>*>(base + NST * STAGE);  // [BM][BNC] staging (out_at)
   uint64_t* full = reinterpret_cast<uint64_t*>(base + NST * STAGE + OUT_BYTES);
   uint64_t* empty = full + NST;
   uint64_t* accf = empty + NST;
@@ -326,7 +336,7 @@ __global__ void __launch_bounds__(320, 1) k_tc_gemm(const __grid_constant__ TcGr
         if (p.active && !p.active[e]) continue;
         const long MB = p.M_pad / BM, NB = p.N_pad / BNC, nkb = p.nks / 2;
         const long ea = p.a_batched ? e : 0, eb = p.b_batched ? e : 0;
-        // rows taken from each 48-row sub-tile: all of them, or the last tile's first bn_last (a
+        // rows taken from each BNC-row sub-tile: all of them, or the last tile's first bn_last (a
         // multiple of 8 rows = whole 256-byte swizzle groups, so the pair stays in the MMA layout)
         const uint32_t sub = (uint32_t)(nblk == NBt - 1 ? p.bn_last : BNC) * BKS * 2;
         for (int ks = 0; ks < p.nks; ++ks, ++g) {
@@ -449,7 +459,7 @@ __global__ void __launch_bounds__(320, 1) k_tc_gemm(const __grid_constant__ TcGr
           cx<df> o;
           o.re = sum_acc<NACC>(vr, c);
           o.im = sum_acc<NACC>(vi, c);
-          out[r * OUT_LD + c0 + c] = o;
+          out[out_at(r, c0 + c, S)] = o;
         }
       }
       // accumulators read (tcgen05.wait::ld above): hand TMEM back to the MMA thread
@@ -463,7 +473,7 @@ __global__ void __launch_bounds__(320, 1) k_tc_gemm(const __grid_constant__ TcGr
         const int rr = idx / bn, cc = idx % bn;
         const int mm = mblk * BM + rr, nn = nblk * BNC + cc;
         if (mm < p.M && nn < p.N) {
-          cx<df> v = out[rr * OUT_LD + cc];
+          cx<df> v = out[out_at(rr, cc, S)];
           int Es = s_eA[rr] + s_eB[cc] - p.escale;
           Es = Es < -250 ? -250 : (Es > 250 ? 250 : Es);
           const float f1 = __int_as_float((Es / 2 + 127) << 23), f2 = __int_as_float((Es - Es / 2 + 127) << 23);
@@ -632,9 +642,10 @@ __global__ void __launch_bounds__(32 * RPC) k_digitize_rows(const cx<TI>* X, lon
   if (t < RPC && r0 + t < R_pad) eout[(long)e * R_pad + r0 + t] = s_ex[t];
   // ---- digits: item = (row rr, complex k = 8 kc .. 8 kc + 7)
   // left operand: [row_block of 128][k_stage of 16 embedded k][128 x 32 B] tiles, embedded k' = k for
-  // Re, K_pad + k for Im.  right operand: [col_block of 48][k_block of 16 complex k][3][48 x 32 B]
+  // Re, K_pad + k for Im.  right operand: [col_block of BNC][k_block of 16 complex k][3][BNC x 32 B]
   // sub-tiles holding Re, Im and -Im (the producer pairs them into the (Re, Im) and (-Im, Re) rows).
   const long nks = 2L * K_pad / BKS, nkb = K_pad / BKS;
+  constexpr int BNC = bnc_of(S), SUB_B = sub_b_of(S);
   const long plane_bytes = side == 0 ? (rows_plane / BM) * nks * (long)TILE_A : (long)(R_pad / BNC) * nkb * 3 * SUB_B;
   unsigned char* pe = planes + (long)e * S * plane_bytes;
   const int nkc = K_pad / 8;
@@ -713,7 +724,7 @@ struct Dims {
 inline Dims dims_of(int M, int N, int K, int S) {
   Dims d;
   d.M_pad = (M + BM - 1) / BM * BM;
-  d.N_pad = (N + BNC - 1) / BNC * BNC;
+  d.N_pad = (N + bnc_of(S) - 1) / bnc_of(S) * bnc_of(S);
   d.K_pad = (K + 31) / 32 * 32;
   // Leading digit bound L = 2^(l1-1), others 64: per K term the exact groups are bounded by
   //   i+j=2: L^2,  3: 2 L 64,  4: 2 L 64 + 64^2,  5: 2 L 64 + 2 * 64^2
@@ -734,7 +745,7 @@ inline Scratch carve(void* base, const Dims& d, int batch, int S) {
   Scratch s;
   unsigned char* p = reinterpret_cast<unsigned char*>(base);
   const size_t a = al((size_t)batch * S * d.M_pad * 2 * d.K_pad * sizeof(__nv_bfloat16));
-  const size_t b = al((size_t)batch * S * (d.N_pad / BNC) * (d.K_pad / BKS) * 3 * SUB_B);  // Re, Im, -Im sub-tiles
+  const size_t b = al((size_t)batch * S * (d.N_pad / bnc_of(S)) * (d.K_pad / BKS) * 3 * sub_b_of(S));  // Re, Im, -Im sub-tiles
   const size_t ea = al((size_t)batch * d.M_pad * sizeof(int));
   const size_t eb = al((size_t)batch * d.N_pad * sizeof(int));
   s.pa = p;
@@ -833,9 +844,9 @@ cudaError_t prepare(const TcArgs& a, void* scratch, size_t scratch_bytes, int* e
   p.b_batched = bb_;
   p.active = a.active;
   p.err = err_flag;
-  out.NBt = d.N_pad / BNC;
+  out.NBt = d.N_pad / bnc_of(S);
   out.MBt = d.M_pad / BM;
-  const int tail = a.N - (out.NBt - 1) * BNC;  // 1..48 complex columns in the last column tile
+  const int tail = a.N - (out.NBt - 1) * bnc_of(S);  // 1..BNC complex columns in the last column tile
   p.bn_last = (tail + 7) / 8 * 8;
   out.tiles = (long)out.NBt * out.MBt * a.batch;
   return cudaSuccess;
@@ -846,7 +857,7 @@ template <int S, int NST, typename IO>
 cudaError_t launch(const TcPrepared* const* pp, int n, cudaStream_t st, cudaEvent_t* ev) {
   if (n < 1 || n > kMaxGroup) return cudaErrorInvalidValue;
   cudaError_t e;
-  const size_t smem = (size_t)NST * S * (TILE_A + TILE_B) + OUT_BYTES + 1024 + 256;
+  const size_t smem = (size_t)NST * S * (TILE_A + tile_b_of(S)) + out_bytes_of(S) + 1024 + 256;
   static bool attr = false;
   static int sms = 0;
   if (!attr) {
@@ -916,7 +927,7 @@ static size_t al1k(size_t x) { return (x + 1023) & ~size_t(1023); }
 // digit-plane bytes of one operand (as carve lays them out)
 static size_t plane_bytes_of(int side, const tc::Dims& d, int batch, int S) {
   return side == 0 ? (size_t)batch * S * d.M_pad * 2 * d.K_pad * 2
-                   : (size_t)batch * S * (d.N_pad / tc::BNC) * (d.K_pad / tc::BKS) * 3 * tc::SUB_B;
+                   : (size_t)batch * S * (d.N_pad / tc::bnc_of(S)) * (d.K_pad / tc::BKS) * 3 * tc::sub_b_of(S);
 }
 
 size_t gemm_tc_operand_bytes(int side, int R, int K, int batch, int digits) {
@@ -935,14 +946,14 @@ TcOperand tc_operand_at(void* base, int side, int R, int K, int batch, int digit
   return o;
 }
 
-// Pipeline stages of a kernel variant: the requested count if shared memory allows it (beside the
-// 98 KB epilogue staging: 6 digit planes take 43 KB a stage, 7 take 50 KB, 4 take 29 KB, 2 take
-// 14 KB), else the default.
+// Pipeline stages of a kernel variant: the requested count if shared memory allows it, else the
+// default.  Beside the 96 KB epilogue staging of 48-column tiles, 6 digit planes take 42 KB a stage
+// and 7 take 49 KB; beside the 128 KB staging of 64-column tiles, 4 planes take 32 KB and 2 take 16 KB.
 static int resolve_stages(int S, bool f32, int want) {
-  if (f32) return (want == 3) ? 3 : 4;          // S = 4: 3 or 4 stages
+  if (f32) return (want == 2) ? 2 : 3;          // S = 4: 2 or 3 stages
   if (S == 6) return (want == 2) ? 2 : 3;       // 2 or 3
   if (S == 7) return 2;
-  return (want == 4) ? 4 : 8;                   // S = 2: 4 or 8
+  return (want == 4) ? 4 : 6;                   // S = 2: 4 or 6
 }
 
 // Kernel variant of a product: digits actually used (effective_digits), the IO type and the stages;
@@ -974,12 +985,12 @@ cudaError_t gemm_tc_launch(const TcPrepared* const* p, int n, cudaStream_t st, c
   for (int q = 1; q < n; ++q)
     if (p[q]->variant != p[0]->variant) return cudaErrorInvalidValue;
   switch (p[0]->variant) {
-    case 400 + 4 * 2 + 1: return tc::launch<4, 4, float>(p, n, st, ev);
     case 300 + 4 * 2 + 1: return tc::launch<4, 3, float>(p, n, st, ev);
+    case 200 + 4 * 2 + 1: return tc::launch<4, 2, float>(p, n, st, ev);
     case 200 + 7 * 2: return tc::launch<7, 2, df>(p, n, st, ev);
     case 300 + 6 * 2: return tc::launch<6, 3, df>(p, n, st, ev);
     case 200 + 6 * 2: return tc::launch<6, 2, df>(p, n, st, ev);
-    case 800 + 2 * 2: return tc::launch<2, 8, df>(p, n, st, ev);
+    case 600 + 2 * 2: return tc::launch<2, 6, df>(p, n, st, ev);
     case 400 + 2 * 2: return tc::launch<2, 4, df>(p, n, st, ev);
     default: return cudaErrorInvalidValue;
   }

@@ -144,7 +144,7 @@ def test_group_solve_equals_solo_solves(q, precision):
     grp.close()
 
 
-@pytest.mark.parametrize("precision,stages", [("emu64", 2), ("fp32", 3), ("bf16x3", 4)])
+@pytest.mark.parametrize("precision,stages", [("emu64", 2), ("fp32", 2), ("bf16x3", 4)])
 def test_schedule_knobs_leave_results_unchanged(q, precision, stages):
     """The product kernel's schedule (pipeline stages, persistent CTAs per launch) and the group's
     pooling threshold change only the order tiles are taken in, never a tile's arithmetic: the scaled

@@ -31,26 +31,33 @@ def _op(X, op):
     return X if op == "N" else np.conj(np.swapaxes(X, -1, -2))
 
 
-# N covers every kind of last column tile (48 columns per tile): 16 (64, 16, 256), 22 -> 24 (70),
-# 8 (200), a full 48 (96), 41 -> 48 and a single column; the last shape has 400 tiles, so the
-# persistent CTAs run several rounds and a partial one
+# N covers every kind of last column tile.  With 48 columns per tile (6 and 7 digit planes): 16 (64,
+# 16, 256), 22 -> 24 (70), 8 (200), a full 48 (96), 41 -> 48 and a single column; with 64 (2 and 4
+# planes): a full 64 (64, 128, 256), 6 -> 8 (70), 8 (200), 32 (96), 41 -> 48, 16 and a single column.
+# The last shape has 400 (48) or 320 (64) tiles, so the persistent CTAs run several rounds and a
+# partial one
 SHAPES = [(128, 64, 32, 1), (130, 70, 50, 3), (16, 16, 16, 4), (256, 256, 256, 2), (33, 200, 300, 2),
           (64, 96, 48, 2), (40, 41, 24, 3), (17, 1, 16, 2), (256, 200, 64, 40)]
 
 
 @pytest.mark.parametrize("M,N,K,batch", SHAPES)
 @pytest.mark.parametrize("opA,opB", [("N", "N"), ("C", "N"), ("N", "C"), ("C", "C")])
-def test_emu64_integer_inputs_are_exact(q, M, N, K, batch, opA, opB):
+@pytest.mark.parametrize("prec", ["emu64", "bf16x3"])
+def test_integer_inputs_are_exact(q, M, N, K, batch, opA, opB, prec):
     """Integer operands: every digit product is exact, so the result equals the integer product
-    bit for bit (pins digits, scales, the complex embedding, the TMA/UMMA layouts and the epilogue)."""
+    bit for bit (pins digits, scales, the complex embedding, the TMA/UMMA layouts and the epilogue).
+    BF16x3 (64-column tiles) keeps the products of planes i + j <= 3 only, so its operands are
+    multiples of 16 below 500: with the row scaled to 12 or 13 bits they are whole multiples of the
+    leading digit's unit, the second digits are zero and nothing dropped was nonzero."""
     rng = np.random.default_rng(M * 7 + N * 3 + K)
     sa = (batch, M, K) if opA == "N" else (batch, K, M)
     sb = (batch, K, N) if opB == "N" else (batch, N, K)
-    A = rng.integers(-500, 501, sa) + 1j * rng.integers(-500, 501, sa)
-    B = rng.integers(-500, 501, sb) + 1j * rng.integers(-500, 501, sb)
+    lo, unit = (-500, 1) if prec == "emu64" else (-31, 16)
+    A = unit * (rng.integers(lo, -lo + 1, sa) + 1j * rng.integers(lo, -lo + 1, sa))
+    B = unit * (rng.integers(lo, -lo + 1, sb) + 1j * rng.integers(lo, -lo + 1, sb))
     C0 = rng.integers(-1000, 1001, (batch, M, N)) + 1j * rng.integers(-1000, 1001, (batch, M, N))
     ref = -(_op(A, opA) @ _op(B, opB)) + C0
-    got = q.zgemm_batched(_t(A), _t(B), "emu64", opA, opB, alpha=-1.0, beta=1.0, C0=_t(C0)).cpu().numpy()
+    got = q.zgemm_batched(_t(A), _t(B), prec, opA, opB, alpha=-1.0, beta=1.0, C0=_t(C0)).cpu().numpy()
     assert np.array_equal(got, ref)
 
 
