@@ -65,6 +65,10 @@ template <typename T>
 cudaError_t axpby_from64(cx<T>* out, long sOut, const cx<double>* X, long sX, double c1,
                          const cx<double>* Y, long sY, double c2, int b, int batch,
                          cudaStream_t st);
+// out[e] = src + (E[e] + i eta) on the diagonal, for e < batch (src one shared block; E may be nullptr)
+template <typename T>
+cudaError_t broadcast_diag(cx<T>* out, long sOut, const cx<T>* src, int b, const double* E, double eta, int batch,
+                           cudaStream_t st);
 // off-diagonal rows of M: U[e] = z_e S_up - H_up - SRu[e],  V[e] = z_e S_up^H - H_up^H - SRl[e]
 // (S_up, SRu, SRl may be nullptr; SRu/SRl advance by sSR per batch entry, 0 = shared)
 template <typename T>

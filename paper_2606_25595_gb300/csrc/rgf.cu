@@ -48,7 +48,7 @@ inline bool uv_per_energy(const qtx_rgf_desc& d) {
 }
 
 struct Layout {
-  size_t g, gl, gl2, gfx, glfx, fx_slot, sig_stage, opnd[3], opnd_bytes[3], refine_act, tmp, inv_tmp, U, V, ident, ident_df, ref, f32a, f32tmp, dec, lead, obs, flags, dscale, bal, bscale, bgn, bhn, cres, cflag,
+  size_t g, gl, gl2, gfx, glfx, fx_slot, sig_stage, opnd[3], opnd_bytes[3], refine_act, tmp, inv_tmp, U, V, ident, ident_df, shared_blk, ref, f32a, f32tmp, dec, lead, obs, flags, dscale, bal, bscale, bgn, bhn, cres, cflag,
       tc_scratch, total;
   int n_tmp, n_dec;
   size_t tc_bytes;
@@ -127,6 +127,8 @@ Layout make_layout(const qtx_rgf_desc& d) {
   L.V = a.take(ou);
   L.ident = a.take(bb * sizeof(cx<double>));
   L.ident_df = a.take(bb * sizeof(cx<double>));
+  // one block shared by every energy (the slice's -(H + Sigma^R) or Sigma^<, converted once)
+  L.shared_blk = a.take(d.precision == QTX_FP64 ? 0 : bb * sizeof(cx<double>));
   const bool mixed = d.precision == QTX_EMU64 || d.precision == QTX_BF16X3;
   L.ref = a.take((mixed || b > kLeafMax) ? 3 * Ec * bb * sizeof(cx<double>) : 0);
   L.f32a = a.take(mixed ? Ec * bb * sizeof(cx<float>) : 0);
@@ -657,8 +659,14 @@ qtx_status solve_chunk(qtx_rgf_plan_s* P, const qtx_rgf_inputs* in, const qtx_rg
       sLi = stL;
       sS = bb;
     }
+    cx<T>* shared_blk = reinterpret_cast<cx<T>*>(P->ws + P->L.shared_blk);
     if (d.system_input) QTX_CK(axpby_from64<T>(gi, bb, Md + (long)i * bb, (long)nb * bb, 1.0, nullptr, 0, 0.0, b, ne, st));
-    else QTX_CK(assemble_diag<T>(gi, Hd + (long)i * bb, Sd ? Sd + (long)i * bb : nullptr, sRi, sS, lead, bb, c.E, eta, b, ne, st));
+    else if (!std::is_same<T, double>::value && !Sd && (sS == 0 || !sRi) && !lead) {
+      // Sigma^R shared by the energies: -(H_ii + Sigma^R_ii) converted once, then E + i eta added
+      // on each energy's diagonal
+      QTX_CK(axpby_from64<T>(shared_blk, 0, Hd + (long)i * bb, 0, -1.0, sRi, 0, -1.0, b, 1, st));
+      QTX_CK(broadcast_diag<T>(gi, bb, shared_blk, b, c.E, eta, ne, st));
+    } else QTX_CK(assemble_diag<T>(gi, Hd + (long)i * bb, Sd ? Sd + (long)i * bb : nullptr, sRi, sS, lead, bb, c.E, eta, b, ne, st));
     if (d.leads && nb == 1) {  // one slice touches both contacts
       Term<T> tg; tg.p = gi; tg.s = bb; tg.alpha = 1.0;
       QTX_CK((combine<T, T>(c.tmp(0), bb, tg, none, none, b, ne, nullptr, 0, 0, nullptr, st)));
@@ -687,7 +695,10 @@ qtx_status solve_chunk(qtx_rgf_plan_s* P, const qtx_rgf_inputs* in, const qtx_rg
       const cx<double>* lsl = nullptr;
       if (k == 0 && d.leads && i == 0) lsl = SL_L;
       else if (k == 0 && d.leads && i == nb - 1) lsl = SL_R;
-      if (sl) QTX_CK(axpby_from64<T>(SLi, bb, sl, sS, 1.0, lsl, bb, 1.0, b, ne, st));
+      if (sl && !lsl && sS == 0 && !std::is_same<T, double>::value) {  // shared: converted once
+        QTX_CK(axpby_from64<T>(shared_blk, 0, sl, 0, 1.0, nullptr, 0, 0.0, b, 1, st));
+        QTX_CK(broadcast_diag<T>(SLi, bb, shared_blk, b, nullptr, 0.0, ne, st));
+      } else if (sl) QTX_CK(axpby_from64<T>(SLi, bb, sl, sS, 1.0, lsl, bb, 1.0, b, ne, st));
       else if (lsl) QTX_CK(axpby_from64<T>(SLi, bb, lsl, bb, 1.0, nullptr, 0, 0.0, b, ne, st));
       else QTX_CK(cudaMemsetAsync(SLi, 0, (size_t)ne * bb * sizeof(cx<T>), st));
       if (k == 0 && d.leads && nb == 1) {

@@ -479,6 +479,57 @@ __global__ void __launch_bounds__(256) k_combine(cx<Tout>* out, long sOut, Term<
   }
 }
 
+// Without transposed terms every operand and the output are read and written in the same
+// row-major order: one flat grid-stride pass per energy, with more bytes in flight per thread than
+// the 32 x 32 tiles above (the tiled pass runs the output conversions at about half the HBM rate).
+template <typename Tin, typename Tout>
+__global__ void __launch_bounds__(256) k_combine_flat(cx<Tout>* out, long sOut, Term<Tin> t0, Term<Tin> t1,
+                                                      Term<Tin> t2, int b, const double* E, double eta,
+                                                      double diag_coef, int has_diag, const int* active) {
+  using Acc = typename AccSel<Tin, Tout>::type;
+  const int e = blockIdx.y;
+  if (active && !active[e]) return;
+  const int bb = b * b;
+  const cx<Tin>* X0 = t0.p ? t0.p + (long)e * t0.s : nullptr;
+  const cx<Tin>* X1 = t1.p ? t1.p + (long)e * t1.s : nullptr;
+  const cx<Tin>* X2 = t2.p ? t2.p + (long)e * t2.s : nullptr;
+  cx<Tout>* O = out + (long)e * sOut;
+  const double dre = has_diag ? (E ? diag_coef * E[e] : 0.0) : 0.0, dim_ = has_diag ? diag_coef * eta : 0.0;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < bb; idx += gridDim.x * blockDim.x) {
+    Acc ar, ai;
+    acc_zero(ar);
+    acc_zero(ai);
+    if (X0) {
+      const cx<Tin> v = X0[idx];
+      acc_axpy_k(ar, t0.kind, t0.alpha_f, t0.alpha, v.re);
+      acc_axpy_k(ai, t0.kind, t0.alpha_f, t0.alpha, v.im);
+    }
+    if (X1) {
+      const cx<Tin> v = X1[idx];
+      acc_axpy_k(ar, t1.kind, t1.alpha_f, t1.alpha, v.re);
+      acc_axpy_k(ai, t1.kind, t1.alpha_f, t1.alpha, v.im);
+    }
+    if (X2) {
+      const cx<Tin> v = X2[idx];
+      acc_axpy_k(ar, t2.kind, t2.alpha_f, t2.alpha, v.re);
+      acc_axpy_k(ai, t2.kind, t2.alpha_f, t2.alpha, v.im);
+    }
+    if (has_diag && idx % (b + 1) == 0) {  // row == column
+      acc_add_d(ar, dre);
+      acc_add_d(ai, dim_);
+    }
+    cx<Tout> o;
+    o.re = acc_out<Tout>(ar);
+    o.im = acc_out<Tout>(ai);
+    O[idx] = o;
+  }
+}
+// CTAs along one energy's elements: about eight per SM over the whole batch, at least one per energy
+static unsigned flat_ctas(long bb, int batch) {
+  const long want = (8L * 152 + batch - 1) / batch, most = (bb + 255) / 256;
+  return (unsigned)(want < 1 ? 1 : (want > most ? most : want));
+}
+
 template <typename Tin, typename Tout>
 cudaError_t combine(cx<Tout>* out, long sOut, Term<Tin> t0, Term<Tin> t1, Term<Tin> t2, int b,
                     int batch, const double* E, double eta, double diag_coef, const int* active,
@@ -490,6 +541,13 @@ cudaError_t combine(cx<Tout>* out, long sOut, Term<Tin> t0, Term<Tin> t1, Term<T
   classify(t0);
   classify(t1);
   classify(t2);
+  if (t0.op != OP_C && t1.op != OP_C && t2.op != OP_C) {
+    dim3 fgrid(flat_ctas((long)b * b, batch), batch);
+    k_combine_flat<Tin, Tout><<<fgrid, 256, 0, st>>>(out, sOut, t0, t1, t2, b, E, eta, diag_coef, diag_coef != 0.0,
+                                                     active);
+    count_launch();
+    return cudaGetLastError();
+  }
   dim3 grid((b + 31) / 32, (b + 31) / 32, batch);
   k_combine<Tin, Tout><<<grid, 256, 0, st>>>(out, sOut, t0, t1, t2, b, E, eta, diag_coef, diag_coef != 0.0, active);
   count_launch();
@@ -601,6 +659,42 @@ cudaError_t axpby_from64(cx<T>* out, long sOut, const cx<double>* X, long sX, do
 template cudaError_t axpby_from64<double>(cx<double>*, long, const cx<double>*, long, double, const cx<double>*, long, double, int, int, cudaStream_t);
 template cudaError_t axpby_from64<float>(cx<float>*, long, const cx<double>*, long, double, const cx<double>*, long, double, int, int, cudaStream_t);
 template cudaError_t axpby_from64<df>(cx<df>*, long, const cx<double>*, long, double, const cx<double>*, long, double, int, int, cudaStream_t);
+
+// out[e] = src (one block shared by every energy) plus E[e] + i eta on the diagonal (E may be
+// nullptr: no diagonal term).  The sweep's per-energy copy of a block whose FP64 -> df32 / FP32
+// conversion was done once; only the writes remain.
+__device__ __forceinline__ df add_t(df a, df c) { return df_add(a, c); }
+__device__ __forceinline__ float add_t(float a, float c) { return a + c; }
+template <typename T>
+__global__ void __launch_bounds__(256) k_broadcast_diag(cx<T>* out, long sOut, const cx<T>* src, int b,
+                                                        const double* E, double eta) {
+  const int e = blockIdx.y;
+  const int bb = b * b;
+  cx<T> z;
+  if (E) {
+    z.re = from_d<T>(E[e]);
+    z.im = from_d<T>(eta);
+  }
+  cx<T>* O = out + (long)e * sOut;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < bb; idx += gridDim.x * blockDim.x) {
+    cx<T> v = src[idx];
+    if (E && idx % (b + 1) == 0) {  // row == column
+      v.re = add_t(v.re, z.re);
+      v.im = add_t(v.im, z.im);
+    }
+    O[idx] = v;
+  }
+}
+template <typename T>
+cudaError_t broadcast_diag(cx<T>* out, long sOut, const cx<T>* src, int b, const double* E, double eta, int batch,
+                           cudaStream_t st) {
+  dim3 grid(flat_ctas((long)b * b, batch), batch);
+  k_broadcast_diag<T><<<grid, 256, 0, st>>>(out, sOut, src, b, E, eta);
+  count_launch();
+  return cudaGetLastError();
+}
+template cudaError_t broadcast_diag<float>(cx<float>*, long, const cx<float>*, int, const double*, double, int, cudaStream_t);
+template cudaError_t broadcast_diag<df>(cx<df>*, long, const cx<df>*, int, const double*, double, int, cudaStream_t);
 
 template <typename T>
 __global__ void k_assemble_offdiag(cx<T>* U, cx<T>* V, const cx<double>* Hup, const cx<double>* Sup,
