@@ -68,7 +68,7 @@ def parse():
                          "(one solve each, all energies), with their error against the oracle sample")
     ap.add_argument("--no-modes", action="store_true")
     ap.add_argument("--no-others", action="store_true",
-                    help="mixed workload: skip the secondary strip (config 1) and uneven (config 3) measurements")
+                    help="mixed workload: skip the secondary measurements (strip, uneven batch, b = 1024 device, serving)")
     ap.add_argument("--storage-bits", type=int, default=0,
                     help="mixed workloads: keep the left-connected blocks in FPX of this many bits (0 = off)")
     ap.add_argument("--tc-stages", type=int, default=0,
@@ -274,9 +274,9 @@ UNEVEN_CHUNKS = [128, 128, 128, 128, 64, 128, 128, 128]
 
 def secondary_workloads(q, W, steps=3, warmup=2):
     """The W=16 strip (FP64, contacts, one solve replayed from a CUDA graph), the uneven 8-device batch
-    (FP32 products on the tensor cores, one group solve replayed from a CUDA graph) and the b = 1024
+    (FP32 products on the tensor cores, one group solve replayed from a CUDA graph), the b = 1024
     device (emulated FP64, 16 energies), each timed with CUDA events after warm-up, with the strip's
-    error against the CPU oracle (all 64 energies)."""
+    error against the CPU oracle (all 64 energies); and a short serving run (config 5, wall clock)."""
     import numpy as np
     import torch
     import oracle as O
@@ -320,6 +320,16 @@ def secondary_workloads(q, W, steps=3, warmup=2):
         "workload": "random BT device b=1024 N_B=32, 16 of its 256 energies on [-2,2], emulated FP64 (7 digit planes)",
         "status_ok": bool(torch.all(bufs["status"] == 0).item())}
     plan.close()
+    torch.cuda.empty_cache()
+    # config 5: 40 requests at 200/s (saturating), then 20 at 0.7 x the measured capacity
+    sat, sub, lam, _ = serving_runs(q, W, 40, 4)
+    keep = ("completed", "rejected", "requests_per_s", "energy_points_per_s", "p50_s", "p99_s", "wall_s")
+    out["serving_config5"] = {
+        "value": sat["energy_points_per_s"], "unit": UNIT,
+        "workload": "40 Poisson requests at 200/s (b in {64,128,256,512}, N_B~U[16,96], N_E in {32,64,128}, "
+                    "complex64 / emulated-FP64), admitted in groups of 4 on 4 streams",
+        "saturated": {k: sat[k] for k in keep if k in sat},
+        f"at_0.7_capacity_{lam:.2f}_per_s": {k: sub[k] for k in keep if k in sub}}
     torch.cuda.empty_cache()
     return out
 
@@ -513,9 +523,11 @@ def run_uneven(args, q, W):
            "pool_waves": pool})
 
 
-def run_serving(args, q, W):
+def serving_runs(q, W, n_requests, group, solo=False):
     """Poisson request stream (mean 200/s): b in {64,128,256,512}, N_B ~ U[16,96], N_E in {32,64,128},
-    complex64 / emulated-FP64 tags; then the same at 0.7 x the measured capacity."""
+    complex64 / emulated-FP64 tags; then the same at 0.7 x the measured capacity.  Returns the
+    saturated run, the run at 0.7 x capacity with its rate, and (solo) the saturated run without
+    batching."""
     import numpy as np
     from paper_2606_25595_gb300 import serve
     models = {}
@@ -542,10 +554,16 @@ def run_serving(args, q, W):
                  serve.Request(1, "b64", 16, np.linspace(-1, 1, 4), "fp32")])
         return srv
 
-    sat = server(args.group).run(reqs(args.requests, 200.0, 1), time_limit=3600.0)
-    solo = server(1).run(reqs(args.requests, 200.0, 1), time_limit=3600.0) if (args.group > 1 and args.serving_solo) else None
+    sat = server(group).run(reqs(n_requests, 200.0, 1), time_limit=3600.0)
+    alone = server(1).run(reqs(n_requests, 200.0, 1), time_limit=3600.0) if (group > 1 and solo) else None
     lam = max(0.7 * sat["requests_per_s"], 0.05)
-    sub = server(args.group).run(reqs(max(args.requests // 2, 10), lam, 2), time_limit=3600.0)
+    sub = server(group).run(reqs(max(n_requests // 2, 10), lam, 2), time_limit=3600.0)
+    return sat, sub, lam, alone
+
+
+def run_serving(args, q, W):
+    """Config 5 alone (see serving_runs)."""
+    sat, sub, lam, solo = serving_runs(q, W, args.requests, args.group, args.serving_solo)
     _line(args, sat["energy_points_per_s"], 1e3 * sat["wall_s"],
           "served RGF requests: Poisson arrivals, b in {64,128,256,512}, N_B~U[16,96], N_E in "
           "{32,64,128}, complex64/emulated-FP64 tags", "emu64",
