@@ -151,6 +151,8 @@ Layout make_layout(const qtx_rgf_desc& d) {
   L.refine_act = a.take((size_t)Ec * 2 * sizeof(int) + 64);  // per-energy sweep masks (ping-pong)
   L.tc_bytes = 0;
   if (mixed) L.tc_bytes = gemm_tc_scratch_bytes((int)b, (int)b, (int)b, (int)Ec, d.precision == QTX_EMU64 ? 6 : 2);
+  if (d.precision == QTX_EMU64)  // the Newton correction's four-plane products
+    L.tc_bytes = std::max(L.tc_bytes, gemm_tc_scratch_bytes((int)b, (int)b, (int)b, (int)Ec, 4));
   // the FP32 mode's products of 96 and more (four digit planes; the recursive inverse's halves too)
   if (d.precision == QTX_FP32 && b >= 96 && b <= 1024) L.tc_bytes = gemm_tc_scratch_bytes((int)b, (int)b, (int)b, (int)Ec, 4);
   L.tc_scratch = a.take(L.tc_bytes);
@@ -220,10 +222,12 @@ GemmArgs<T> gargs(int M, int N, int K, const cx<T>* A, long lda, long sA, int op
 enum { DG_NONE = 0, DG_KEEP = 1, DG_REUSE = 2 };
 struct DigitHint {
   int a_slot = -1, a_mode = DG_NONE, b_slot = -1, b_mode = DG_NONE;
+  int digits = 0;  // digit planes of a tensor-core product (0: the plan's)
 };
 inline DigitHint keepA(int slot) { DigitHint h; h.a_slot = slot; h.a_mode = DG_KEEP; return h; }
 inline DigitHint reuseA(int slot) { DigitHint h; h.a_slot = slot; h.a_mode = DG_REUSE; return h; }
 inline DigitHint keepB(int slot) { DigitHint h; h.b_slot = slot; h.b_mode = DG_KEEP; return h; }
+inline DigitHint planes(int digits) { DigitHint h; h.digits = digits; return h; }
 
 template <typename T>
 qtx_status gemm(qtx_rgf_plan_s* P, const GemmArgs<T>& g, cudaStream_t st, bool force_simt = false,
@@ -294,9 +298,10 @@ inline int tc_digits(const qtx_rgf_desc& d) { return d.precision == QTX_EMU64 ? 
 template <>
 qtx_status gemm<df>(qtx_rgf_plan_s* P, const GemmArgs<df>& g, cudaStream_t st, bool, DigitHint hint) {
   TcArgs a;
-  // kept operands: only for the plan's b x b x b products, when slots exist
+  const int digits = hint.digits > 0 ? hint.digits : tc_digits(P->d);
+  // kept operands: only for the plan's b x b x b products at the plan's digit count, when slots exist
   TcOperand oa, ob;
-  const bool square = g.M == P->b && g.N == P->b && g.K == P->b && g.batch <= P->Ec;
+  const bool square = g.M == P->b && g.N == P->b && g.K == P->b && g.batch <= P->Ec && digits == tc_digits(P->d);
   if (square && hint.a_mode != DG_NONE && P->L.opnd_bytes[hint.a_slot]) {
     oa = tc_operand_at(P->ws + P->L.opnd[hint.a_slot], 0, P->b, P->b, P->Ec, tc_digits(P->d));
     oa.mode = hint.a_mode;
@@ -315,15 +320,16 @@ qtx_status gemm<df>(qtx_rgf_plan_s* P, const GemmArgs<df>& g, cudaStream_t st, b
   a.alpha = g.alpha; a.beta = g.beta;
   a.batch = g.batch; a.active = g.active;
   a.stages = P->d.tc_stages; a.ctas = P->d.tc_ctas;
-  if (P->group && gemm_tc_variant(a, tc_digits(P->d)) >= 0) {
-    QTX_CK(group_gemm(P, a, tc_digits(P->d), st));
+  if (P->group && gemm_tc_variant(a, digits) >= 0) {
+    QTX_CK(group_gemm(P, a, digits, st));
     return QTX_OK;
   }
-  cudaEvent_t* ev = P->prof ? P->next_events() : nullptr;
-  QTX_CK(gemm_tc(a, tc_digits(P->d), P->ws + P->L.tc_scratch, P->L.tc_bytes, P->d_err_flag, st, ev));
+  // the profile times the products at the plan's digit count (one kernel instance)
+  cudaEvent_t* ev = (P->prof && digits == tc_digits(P->d)) ? P->next_events() : nullptr;
+  QTX_CK(gemm_tc(a, digits, P->ws + P->L.tc_scratch, P->L.tc_bytes, P->d_err_flag, st, ev));
   if (ev) {
     const double f = 8.0 * g.M * g.N * g.K * g.batch;
-    P->pipe_flops += f * tc_pairs(tc_digits(P->d));
+    P->pipe_flops += f * tc_pairs(digits);
     P->useful_flops += f;
   }
   return QTX_OK;
@@ -452,13 +458,20 @@ qtx_status block_inverse<df>(qtx_rgf_plan_s* P, cx<df>* A, int n, int batch, con
       next = masks + (it & 1) * P->Ec;
       QTX_CK(residual_mask(R, nn, n, batch, P->d.refine_tol, act, next, status, st));
     }
+    // The correction X R is small (||R|| <= 2^-12 once an energy is refined, and typically near the
+    // FP32 inverse's kappa 2^-24), so four digit planes (~27-bit operands, every digit group exact)
+    // keep its error near 2^-27 |X| |R|, far below the 2^-40 the sweep keeps; R itself, where A X
+    // cancels against I, takes the plan's six.
+    const DigitHint xr = tc_digits(P->d) == 6 ? planes(4) : DigitHint{};
     if (n <= 1024) {
       // X <- X + X R in place: the product reads X only through its digit planes (made before the
       // launch) and, element by element in the epilogue, as C0 right before writing C
-      if ((s = gemm<df>(P, gargs<df>(n, n, n, A, n, nn, OP_N, R, n, nn, OP_N, A, n, nn, A, n, nn, 1.0, 1.0, batch, act), st))) return s;
+      if ((s = gemm<df>(P, gargs<df>(n, n, n, A, n, nn, OP_N, R, n, nn, OP_N, A, n, nn, A, n, nn, 1.0, 1.0, batch, act), st,
+                        false, xr))) return s;
     } else {
       // split along K: a later K-chunk digitises columns of X an earlier chunk would have overwritten
-      if ((s = gemm<df>(P, gargs<df>(n, n, n, A, n, nn, OP_N, R, n, nn, OP_N, A, n, nn, Xn, n, nn, 1.0, 1.0, batch, act), st))) return s;
+      if ((s = gemm<df>(P, gargs<df>(n, n, n, A, n, nn, OP_N, R, n, nn, OP_N, A, n, nn, Xn, n, nn, 1.0, 1.0, batch, act), st,
+                        false, xr))) return s;
       Term<df> tXn; tXn.p = Xn; tXn.s = nn; tXn.alpha = 1.0;
       QTX_CK((combine<df, df>(A, nn, tXn, none, none, n, batch, nullptr, 0.0, 0.0, act, st)));
     }

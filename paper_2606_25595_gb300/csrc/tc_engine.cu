@@ -950,8 +950,8 @@ TcOperand tc_operand_at(void* base, int side, int R, int K, int batch, int digit
 // default.  Beside the 96 KB epilogue staging of 48-column tiles, 6 digit planes take 42 KB a stage
 // and 7 take 49 KB; beside the 128 KB staging of 64-column tiles, 4 planes take 32 KB and 2 take 16 KB.
 static int resolve_stages(int S, bool f32, int want) {
-  if (f32) return (want == 2) ? 2 : 3;          // S = 4: 2 or 3 stages
-  if (S == 6) return (want == 2) ? 2 : 3;       // 2 or 3
+  if (f32 || S == 4) return (want == 2) ? 2 : 3;  // S = 4 (complex64 or df32 in and out): 2 or 3
+  if (S == 6) return (want == 2) ? 2 : 3;         // 2 or 3
   if (S == 7) return 2;
   return (want == 4) ? 4 : 6;                   // S = 2: 4 or 6
 }
@@ -973,6 +973,7 @@ cudaError_t gemm_tc_prepare(const TcArgs& a, int digits, void* scratch, size_t s
   if (a.M <= 0 || a.N <= 0 || a.batch <= 0) return cudaSuccess;
   switch (out->variant % 100) {
     case 4 * 2 + 1: return tc::prepare<4, float>(a, scratch, scratch_bytes, err_flag, st, *out);
+    case 4 * 2: return tc::prepare<4, df>(a, scratch, scratch_bytes, err_flag, st, *out);
     case 7 * 2: return tc::prepare<7, df>(a, scratch, scratch_bytes, err_flag, st, *out);
     case 6 * 2: return tc::prepare<6, df>(a, scratch, scratch_bytes, err_flag, st, *out);
     case 2 * 2: return tc::prepare<2, df>(a, scratch, scratch_bytes, err_flag, st, *out);
@@ -987,6 +988,8 @@ cudaError_t gemm_tc_launch(const TcPrepared* const* p, int n, cudaStream_t st, c
   switch (p[0]->variant) {
     case 300 + 4 * 2 + 1: return tc::launch<4, 3, float>(p, n, st, ev);
     case 200 + 4 * 2 + 1: return tc::launch<4, 2, float>(p, n, st, ev);
+    case 300 + 4 * 2: return tc::launch<4, 3, df>(p, n, st, ev);
+    case 200 + 4 * 2: return tc::launch<4, 2, df>(p, n, st, ev);
     case 200 + 7 * 2: return tc::launch<7, 2, df>(p, n, st, ev);
     case 300 + 6 * 2: return tc::launch<6, 3, df>(p, n, st, ev);
     case 200 + 6 * 2: return tc::launch<6, 2, df>(p, n, st, ev);
