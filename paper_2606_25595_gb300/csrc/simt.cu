@@ -541,7 +541,8 @@ cudaError_t combine(cx<Tout>* out, long sOut, Term<Tin> t0, Term<Tin> t1, Term<T
   classify(t0);
   classify(t1);
   classify(t2);
-  if (t0.op != OP_C && t1.op != OP_C && t2.op != OP_C) {
+  auto direct = [](const Term<Tin>& t) { return !t.p || t.op != OP_C; };  // absent terms count as direct
+  if (direct(t0) && direct(t1) && direct(t2)) {
     dim3 fgrid(flat_ctas((long)b * b, batch), batch);
     k_combine_flat<Tin, Tout><<<fgrid, 256, 0, st>>>(out, sOut, t0, t1, t2, b, E, eta, diag_coef, diag_coef != 0.0,
                                                      active);
