@@ -9,8 +9,9 @@ Per device shape (b, N_B) and precision it picks:
 Per group of devices it picks the pooling threshold: products of fewer than that many waves of tiles
 are pooled into shared persistent launches (``best_pool_waves``).
 
-The tensor-core tile itself (128 rows x 48 complex columns) is fixed by the hardware mapping: TMEM
-holds five accumulators of 96 columns.
+The tensor-core tile itself is fixed by the hardware mapping: 128 rows x 48 complex columns for 6
+and 7 digit planes (TMEM holds their five accumulators of 96 columns), x 64 for 4 and 2 planes
+(at most four accumulators of 128).
 """
 from __future__ import annotations
 
