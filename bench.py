@@ -774,9 +774,10 @@ def main():
         cur_host, den_host = cur.cpu().numpy(), den.cpu().numpy()
 
     # ---------------------------------------------------------------- the strip and uneven workloads
-    # (secondary measurements, so that every benchmarked configuration appears in the one line)
+    # (secondary single-GPU measurements, so that every benchmarked configuration appears in the one
+    # line; rank 0 alone runs them, after every collective of the timed legs)
     others = {}
-    if not args.no_others and args.precision == "emu64":
+    if not args.no_others and args.precision == "emu64" and rank == 0:
         others = secondary_workloads(q, W)
 
     # ---------------------------------------------------------------- CPU oracle sample + error
