@@ -93,21 +93,32 @@ def max_over_ranks(x, ws):
     return D.max_over_ranks(x, ws)
 
 
+def source_hash(path):
+    """First 16 hex digits of the SHA-256 of a CUDA source with its comments and blank lines removed
+    (a comment edit leaves the kernel, and so the counters taken on it, unchanged)."""
+    import hashlib
+    import re
+    text = open(path).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    lines = [re.sub(r"//.*$", "", l).rstrip() for l in text.splitlines()]
+    code = "\n".join(l for l in lines if l.strip())
+    return hashlib.sha256(code.encode()).hexdigest()[:16]
+
+
 def captured_traffic(energies_per_launch):
     """DRAM bytes per product-kernel launch from the committed ncu capture, scaled by the energies a
     launch processes (traffic grows in proportion: each energy's planes are read once).  None when
     the kernel source changed since the capture."""
-    import hashlib
     cap = os.path.join(ROOT, "profiles", "k_tc_gemm_emu64_b256_e64.txt")
     src = os.path.join(ROOT, "paper_2606_25595_gb300", "csrc", "tc_engine.cu")
     if not (os.path.exists(cap) and os.path.exists(src)):
         return None, None
     txt = open(cap).read()
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    h = source_hash(src)
     per = None
     same = False
     for line in txt.splitlines():
-        if line.startswith("source_sha256_16:"):
+        if line.startswith("source_code_sha256_16:"):
             same = line.split()[1] == h
         if line.startswith("dram_bytes_per_energy:"):
             per = float(line.split()[1])

@@ -33,7 +33,7 @@
 // Kernel structure (persistent: one CTA per SM walking 128 x BNC complex output tiles, 10 warps):
 //   warp 0   producer: one bulk asynchronous copy (cp.async.bulk, mbarrier complete-tx) per plane
 //            tile of one K-stage (16 K-elements; the digitiser stores every tile contiguously, already
-//            in the 32-byte-swizzled K-major layout the MMA descriptors expect), a ring of 2-8 stages
+//            in the 32-byte-swizzled K-major layout the MMA descriptors expect), a ring of 2-6 stages
 //            that runs on across tiles;
 //   warp 1   allocates 512 TMEM columns once; one thread issues the tcgen05.mma's (2 K16 steps x
 //            pairs), tcgen05.commit's each stage back to the producer and each finished tile to the
