@@ -48,7 +48,7 @@ inline bool uv_per_energy(const qtx_rgf_desc& d) {
 }
 
 struct Layout {
-  size_t g, gl, gl2, gfx, glfx, fx_slot, sig_stage, opnd[3], opnd_bytes[3], refine_act, tmp, inv_tmp, U, V, ident, ident_df, shared_blk, ref, f32a, f32tmp, dec, lead, obs, flags, dscale, bal, bscale, bgn, bhn, cres, cflag,
+  size_t g, gl, gl2, zk, gfx, glfx, fx_slot, sig_stage, opnd[3], opnd_bytes[3], refine_act, tmp, inv_tmp, U, V, ident, ident_df, shared_blk, ref, f32a, f32tmp, dec, lead, obs, flags, dscale, bal, bscale, bgn, bhn, cres, cflag,
       tc_scratch, total;
   int n_tmp, n_dec;
   size_t tc_bytes;
@@ -119,6 +119,9 @@ Layout make_layout(const qtx_rgf_desc& d) {
     L.gl = a.take(nb * Ec * bb * es);
   }
   L.gl2 = a.take(d.second_rhs ? nb * Ec * bb * es : 0);  // left-connected blocks of the second right-hand side
+  // Z_i = V_i g_i of every slice but the last, formed in the forward sweep and kept for the
+  // backward one (without FPX storage, whose point is to keep fewer full blocks)
+  L.zk = a.take(!d.storage_bits && nb > 1 ? (nb - 1) * Ec * bb * es : 0);
   L.tmp = a.take((size_t)L.n_tmp * Ec * bb * es);
   L.sig_stage = a.take(d.sigma_stream ? 2 * Ec * bb * sizeof(cx<double>) : 0);  // Sigma^R_ii, Sigma^<_ii
   L.inv_tmp = a.take(Ec * bb * es + 4096);
@@ -197,6 +200,9 @@ struct Ctx {
   cx<T>* gl(int i) const { return blk(P->L.gl, P->d.storage_bits ? i % 2 : i); }
   // lesser-type blocks of right-hand side k (k = 1: second_rhs, never FPX-stored)
   cx<T>* glk(int k, int i) const { return k ? blk(P->L.gl2, i) : gl(i); }
+  // Z_i = V_i g_i kept from the forward sweep (nullptr without: FPX storage or one slice)
+  bool keep_z() const { return !P->d.storage_bits && P->nb > 1; }
+  cx<T>* zk(int i) const { return blk(P->L.zk, i); }
   void* gfx(int i) const { return P->ws + P->L.gfx + (size_t)i * P->L.fx_slot; }
   void* glfx(int i) const { return P->ws + P->L.glfx + (size_t)i * P->L.fx_slot; }
 };
@@ -688,7 +694,14 @@ qtx_status solve_chunk(qtx_rgf_plan_s* P, const qtx_rgf_inputs* in, const qtx_rg
       Term<T> t1; t1.p = c.tmp(1); t1.s = bb; t1.alpha = 1.0;
       QTX_CK((combine<T, T>(gi, bb, t0, t1, none, b, ne, nullptr, 0, 0, nullptr, st)));
     }
-    if (i > 0) {
+    if (i > 0 && c.keep_z()) {
+      // V g U as (V g) U: Z_{i-1} = V_{i-1} g_{i-1} is kept for the backward sweep
+      // (G_{i,i-1} = -G_ii Z_{i-1}), which then needs one product less per slice
+      cx<T>* Zp = c.zk(i - 1);
+      if ((s = gemm<T>(P, gargs<T>(b, b, b, V(i - 1), b, sUV, OP_N, c.g(i - 1), b, bb, OP_N, nullptr, 0, 0, Zp, b, bb, 1.0, 0.0, ne, nullptr), st)))
+        return s;
+      if ((s = gemm<T>(P, gargs<T>(b, b, b, Zp, b, bb, OP_N, U(i - 1), b, sUV, OP_N, gi, b, bb, gi, b, bb, -1.0, 1.0, ne, nullptr), st))) return s;
+    } else if (i > 0) {
       cx<T>* Tm = c.tmp(0);
       // g_{i-1} was the left operand of the previous slice's g_{i-1} Sigma^<: its digit planes are kept
       if ((s = gemm<T>(P, gargs<T>(b, b, b, c.g(i - 1), b, bb, OP_N, U(i - 1), b, sUV, OP_N, nullptr, 0, 0, Tm, b, bb, 1.0, 0.0, ne, nullptr), st,
@@ -697,8 +710,8 @@ qtx_status solve_chunk(qtx_rgf_plan_s* P, const qtx_rgf_inputs* in, const qtx_rg
     }
     if ((s = block_inverse<T>(P, gi, b, ne, nullptr, status, st))) return s;
     // block-tridiagonal right-hand sides: V_{i-1} g_{i-1} of the cross term, shared by both
-    cx<T>* Zf = c.tmp(2);
-    if (i > 0 && odg &&
+    cx<T>* Zf = i > 0 && c.keep_z() ? c.zk(i - 1) : c.tmp(2);
+    if (i > 0 && odg && !c.keep_z() &&
         (s = gemm<T>(P, gargs<T>(b, b, b, V(i - 1), b, sUV, OP_N, c.g(i - 1), b, bb, OP_N, nullptr, 0, 0, Zf, b, bb, 1.0, 0.0, ne, nullptr), st)))
       return s;
     for (int k = 0; k < nrhs; ++k) {
@@ -791,7 +804,7 @@ qtx_status solve_chunk(qtx_rgf_plan_s* P, const qtx_rgf_inputs* in, const qtx_rg
   for (int i = nb - 2; i >= 0; --i) {
     cx<T>* GRn = c.g(i + 1);
     cx<T>* Pm = c.tmp(2);
-    cx<T>* Z = c.tmp(3);
+    cx<T>* Z = c.keep_z() ? c.zk(i) : c.tmp(3);  // V_i g_i
     cx<T>* GRl = c.tmp(4);
     cx<T>* GRu = c.tmp(5);
     cx<T>* Q = c.tmp(6);
@@ -813,7 +826,7 @@ qtx_status solve_chunk(qtx_rgf_plan_s* P, const qtx_rgf_inputs* in, const qtx_rg
     DigitHint x2;
     x2.a_slot = 1; x2.a_mode = DG_REUSE; x2.b_slot = 2; x2.b_mode = DG_REUSE;
     if ((s = MM(gi, bb, OP_N, U(i), sUV, OP_N, nullptr, Pm, 1.0, 0.0))) return s;
-    if ((s = MM(V(i), sUV, OP_N, gi, bb, OP_N, nullptr, Z, 1.0, 0.0))) return s;
+    if (!c.keep_z() && (s = MM(V(i), sUV, OP_N, gi, bb, OP_N, nullptr, Z, 1.0, 0.0))) return s;
     // block-tridiagonal right-hand side k: g_i L_k with L_k its upper block (g_i still left-connected)
     auto Rl = [&](int k) { return odg ? c.tmp(13 + k) : nullptr; };
     if (odg) {

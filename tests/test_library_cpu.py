@@ -77,7 +77,8 @@ def test_block_tridiagonal_sigma_descriptor(libpath):
 
 def test_fpx_storage_descriptor(libpath):
     """storage_bits must be one of the FPX widths; it replaces the N_B left-connected blocks per kind
-    in the sweep's type by two working blocks plus N_B compressed slots."""
+    in the sweep's type by two working blocks plus N_B compressed slots, and such plans keep no
+    Z_i = V_i g_i blocks from the forward sweep (N_B - 1 more full blocks without FPX storage)."""
     import paper_2606_25595_gb300 as q
     h = ctypes.c_void_p()
     bad = q.make_desc(8, 32, "fp64", 4, storage_bits=33)
@@ -87,7 +88,7 @@ def test_fpx_storage_descriptor(libpath):
     base = q.footprint(q.make_desc(nb, b, "emu64", ec))
     for bits in (48, 40, 24):
         fx = q.footprint(q.make_desc(nb, b, "emu64", ec, storage_bits=bits))
-        saved = 2 * (nb - 2) * ec * b * b * 16 - 2 * nb * ec * (2 * b * b) * bits // 8
+        saved = 2 * (nb - 2) * ec * b * b * 16 - 2 * nb * ec * (2 * b * b) * bits // 8 + (nb - 1) * ec * b * b * 16
         assert abs((base - fx) - saved) < 1 << 20, (bits, base - fx, saved)
     assert q.load().qtx_fpx_bytes(40, 10) == 80
 
