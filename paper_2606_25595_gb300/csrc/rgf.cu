@@ -48,7 +48,7 @@ inline bool uv_per_energy(const qtx_rgf_desc& d) {
 }
 
 struct Layout {
-  size_t g, gl, gl2, zk, gfx, glfx, fx_slot, sig_stage, opnd[3], opnd_bytes[3], refine_act, tmp, inv_tmp, U, V, ident, ident_df, shared_blk, ref, f32a, f32tmp, dec, lead, obs, flags, dscale, bal, bscale, bgn, bhn, cres, cflag,
+  size_t g, gl, gl2, zk, xk, gfx, glfx, fx_slot, sig_stage, opnd[3], opnd_bytes[3], refine_act, tmp, inv_tmp, U, V, ident, ident_df, shared_blk, ref, f32a, f32tmp, dec, lead, obs, flags, dscale, bal, bscale, bgn, bhn, cres, cflag,
       tc_scratch, total;
   int n_tmp, n_dec;
   size_t tc_bytes;
@@ -122,6 +122,8 @@ Layout make_layout(const qtx_rgf_desc& d) {
   // Z_i = V_i g_i of every slice but the last, formed in the forward sweep and kept for the
   // backward one (without FPX storage, whose point is to keep fewer full blocks)
   L.zk = a.take(!d.storage_bits && nb > 1 ? (nb - 1) * Ec * bb * es : 0);
+  // and X_i = V_i g^<_i of every right-hand side, the backward sweep's Q_i
+  L.xk = a.take(!d.storage_bits && nb > 1 ? (size_t)(d.second_rhs ? 2 : 1) * (nb - 1) * Ec * bb * es : 0);
   L.tmp = a.take((size_t)L.n_tmp * Ec * bb * es);
   L.sig_stage = a.take(d.sigma_stream ? 2 * Ec * bb * sizeof(cx<double>) : 0);  // Sigma^R_ii, Sigma^<_ii
   L.inv_tmp = a.take(Ec * bb * es + 4096);
@@ -203,6 +205,8 @@ struct Ctx {
   // Z_i = V_i g_i kept from the forward sweep (nullptr without: FPX storage or one slice)
   bool keep_z() const { return !P->d.storage_bits && P->nb > 1; }
   cx<T>* zk(int i) const { return blk(P->L.zk, i); }
+  // X_i = V_i g^<_i of right-hand side k, kept from the forward sweep as the backward sweep's Q_i
+  cx<T>* xk(int k, int i) const { return blk(P->L.xk, (long)k * (P->nb - 1) + i); }
   void* gfx(int i) const { return P->ws + P->L.gfx + (size_t)i * P->L.fx_slot; }
   void* glfx(int i) const { return P->ws + P->L.glfx + (size_t)i * P->L.fx_slot; }
 };
@@ -734,7 +738,7 @@ qtx_status solve_chunk(qtx_rgf_plan_s* P, const qtx_rgf_inputs* in, const qtx_rg
         QTX_CK((combine<T, T>(SLi, bb, t0, t1, none, b, ne, nullptr, 0, 0, nullptr, st)));
       }
       if (i > 0) {
-        cx<T>* X = c.tmp(0);
+        cx<T>* X = c.keep_z() ? c.xk(k, i - 1) : c.tmp(0);  // V_{i-1} g^<_{i-1}
         if ((s = gemm<T>(P, gargs<T>(b, b, b, V(i - 1), b, sUV, OP_N, c.glk(k, i - 1), b, bb, OP_N, nullptr, 0, 0, X, b, bb, 1.0, 0.0, ne, nullptr), st))) return s;
         if ((s = gemm<T>(P, gargs<T>(b, b, b, X, b, bb, OP_N, V(i - 1), b, sUV, OP_C, SLi, b, bb, SLi, b, bb, 1.0, 1.0, ne, nullptr), st))) return s;
         if (odg) {  // block-tridiagonal Sigma^<: bracket += -Y + Y^H, Y = V_{i-1} g_{i-1} Sigma^<_{i-1,i}
@@ -807,7 +811,7 @@ qtx_status solve_chunk(qtx_rgf_plan_s* P, const qtx_rgf_inputs* in, const qtx_rg
     cx<T>* Z = c.keep_z() ? c.zk(i) : c.tmp(3);  // V_i g_i
     cx<T>* GRl = c.tmp(4);
     cx<T>* GRu = c.tmp(5);
-    cx<T>* Q = c.tmp(6);
+    cx<T>* Qw = c.tmp(6);
     cx<T>* K = c.tmp(7);
     cx<T>* PGL = c.tmp(8);
     cx<T>* X2 = c.tmp(9);
@@ -846,7 +850,9 @@ qtx_status solve_chunk(qtx_rgf_plan_s* P, const qtx_rgf_inputs* in, const qtx_rg
     for (int k = 0; k < nrhs; ++k) {
       cx<T>* gli = c.glk(k, i);
       cx<T>* GLn = c.glk(k, i + 1);
-      if ((s = MM(V(i), sUV, OP_N, gli, bb, OP_N, nullptr, Q, 1.0, 0.0))) return s;
+      // Q = V_i g^<_i: the forward sweep's X of slice i + 1 when kept
+      cx<T>* Q = c.keep_z() ? c.xk(k, i) : Qw;
+      if (!c.keep_z() && (s = MM(V(i), sUV, OP_N, gli, bb, OP_N, nullptr, Q, 1.0, 0.0))) return s;
       if (odg) {  // Q = V_i g^<_i + (g_i Sigma^<_{i,i+1})^H
         Term<T> t0; t0.p = Q; t0.s = bb; t0.alpha = 1.0;
         Term<T> t1; t1.p = Rl(k); t1.s = bb; t1.alpha = 1.0; t1.op = OP_C;

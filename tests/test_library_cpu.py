@@ -78,7 +78,8 @@ def test_block_tridiagonal_sigma_descriptor(libpath):
 def test_fpx_storage_descriptor(libpath):
     """storage_bits must be one of the FPX widths; it replaces the N_B left-connected blocks per kind
     in the sweep's type by two working blocks plus N_B compressed slots, and such plans keep no
-    Z_i = V_i g_i blocks from the forward sweep (N_B - 1 more full blocks without FPX storage)."""
+    Z_i = V_i g_i and X_i = V_i g^<_i blocks from the forward sweep (2 (N_B - 1) more full blocks
+    without FPX storage)."""
     import paper_2606_25595_gb300 as q
     h = ctypes.c_void_p()
     bad = q.make_desc(8, 32, "fp64", 4, storage_bits=33)
@@ -88,7 +89,7 @@ def test_fpx_storage_descriptor(libpath):
     base = q.footprint(q.make_desc(nb, b, "emu64", ec))
     for bits in (48, 40, 24):
         fx = q.footprint(q.make_desc(nb, b, "emu64", ec, storage_bits=bits))
-        saved = 2 * (nb - 2) * ec * b * b * 16 - 2 * nb * ec * (2 * b * b) * bits // 8 + (nb - 1) * ec * b * b * 16
+        saved = 2 * (nb - 2) * ec * b * b * 16 - 2 * nb * ec * (2 * b * b) * bits // 8 + 2 * (nb - 1) * ec * b * b * 16
         assert abs((base - fx) - saved) < 1 << 20, (bits, base - fx, saved)
     assert q.load().qtx_fpx_bytes(40, 10) == 80
 
@@ -103,8 +104,9 @@ def test_refine_tol_validation(libpath):
 
 def test_second_rhs_descriptor(libpath):
     """second_rhs needs system_input and no FPX storage; it keeps one more set of left-connected
-    blocks (N_B per energy in flight) and, with block-tridiagonal right-hand sides, one more work
-    block; GG outputs are then allowed on a system_input plan."""
+    blocks (N_B per energy in flight), one more set of the forward sweep's X_i = V_i g^<_i
+    (N_B - 1) and, with block-tridiagonal right-hand sides, one more work block; GG outputs are then
+    allowed on a system_input plan."""
     import paper_2606_25595_gb300 as q
     h = ctypes.c_void_p()
     lib = q.load()
@@ -120,4 +122,4 @@ def test_second_rhs_descriptor(libpath):
     one = q.footprint(q.make_desc(nb, b, "fp64", ec, outputs=["GR_diag", "GL_diag"], **kw))
     two = q.footprint(q.make_desc(nb, b, "fp64", ec, outputs=["GR_diag", "GL_diag", "GG_diag"],
                                   second_rhs=True, **kw))
-    assert two - one == (nb + 1) * ec * b * b * 16
+    assert two - one == (nb + 1) * ec * b * b * 16 + (nb - 1) * ec * b * b * 16
