@@ -565,10 +565,16 @@ def serving_runs(q, W, n_requests, group, solo=False):
                  serve.Request(1, "b64", 16, np.linspace(-1, 1, 4), "fp32")])
         return srv
 
-    sat = server(group).run(reqs(n_requests, 200.0, 1), time_limit=3600.0)
-    alone = server(1).run(reqs(n_requests, 200.0, 1), time_limit=3600.0) if (group > 1 and solo) else None
+    def run(group, requests):
+        srv = server(group)
+        stats = srv.run(requests, time_limit=300.0)
+        srv.close()
+        return stats
+
+    sat = run(group, reqs(n_requests, 200.0, 1))
+    alone = run(1, reqs(n_requests, 200.0, 1)) if (group > 1 and solo) else None
     lam = max(0.7 * sat["requests_per_s"], 0.05)
-    sub = server(group).run(reqs(max(n_requests // 2, 10), lam, 2), time_limit=3600.0)
+    sub = run(group, reqs(max(n_requests // 2, 10), lam, 2))
     return sat, sub, lam, alone
 
 

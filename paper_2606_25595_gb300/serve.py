@@ -5,7 +5,9 @@ runs in the library's kernels through the C ABI).
   bias-point solve on the first ``n_blocks`` slices of one model, with its own energy grid, contact
   chemical potentials and precision.
 * Plans (device workspaces) are pooled per (block size, precision) and sized for the model's full
-  length; a pool grows only when its HBM footprint (``qtx_rgf_footprint``) fits the budget.  A request
+  length (``PlanPool``); a pool grows only when its HBM footprint (``qtx_rgf_footprint``) fits the
+  budget, and when it does not, idle plans of other keys are closed to make room, so that a request
+  whose plan fits the budget alone is always admitted once the batches ahead of it finish.  A request
   whose plan could never fit the budget is refused when it is submitted (its result says why).
 * Each of ``slots`` CUDA streams runs one batch at a time: the queued requests admitted together
   (up to ``group_size``, each with a plan of its own) are solved as one ``qtx_rgf_group``: each
@@ -24,7 +26,7 @@ import numpy as np
 
 from . import Group, Inputs, Outputs, Plan, footprint, make_desc
 
-__all__ = ["DeviceModel", "Request", "Server"]
+__all__ = ["DeviceModel", "PlanPool", "Request", "Server"]
 
 
 class DeviceModel:
@@ -67,6 +69,85 @@ class Request:
         return self.t_done - self.t_arrival
 
 
+class PlanPool:
+    """Idle plans per key within an HBM budget (host bookkeeping only; ``create(key)`` makes a plan,
+    whose ``close()`` frees its workspace).
+
+    ``take`` hands out an idle plan of the key, else creates one if ``used + need`` fits the budget.
+    Failing both, a key that has plans in use waits for one of them to come back (None), while a key
+    with no plan at all first closes idle plans of other keys (the largest first) until its plan fits.
+    Plans in use are never closed, so a key without plans waits only while the plans in use hold too
+    much of the budget; once they are given back it is served for any ``need`` <= budget.  Without
+    the eviction step a key that found the budget filled by other keys' idle plans would wait for
+    ever; evicting only for keys without plans keeps the device synchronisation of a close off the
+    common path."""
+
+    def __init__(self, budget: int, create):
+        self.budget = int(budget)
+        self.create = create
+        self.used = 0
+        self.idle: dict = {}              # key -> list of (plan, bytes)
+        self.size: dict = {}              # id(plan) -> (key, bytes) of every plan the pool made
+        self.count: dict = {}             # key -> plans of the key, idle or in use
+        self.evicted = 0
+
+    def _evict_for(self, key, need: int) -> bool:
+        while self.used + need > self.budget:
+            victims = [(b, k) for k, lst in self.idle.items() if k != key for _, b in lst]
+            if not victims:
+                return False
+            b, k = max(victims, key=lambda v: v[0])
+            lst = self.idle[k]
+            i = next(j for j, (_, bj) in enumerate(lst) if bj == b)
+            plan, _ = lst.pop(i)
+            self._drop(plan, k, b)
+            self.evicted += 1
+        return True
+
+    def _make(self, key, need: int):
+        plan = self.create(key)
+        self.size[id(plan)] = (key, int(need))
+        self.count[key] = self.count.get(key, 0) + 1
+        self.used += int(need)
+        return plan
+
+    def _drop(self, plan, key, b: int):
+        del self.size[id(plan)]
+        self.count[key] -= 1
+        plan.close()
+        self.used -= b
+
+    def take(self, key, need: int):
+        lst = self.idle.setdefault(key, [])
+        if lst:
+            return lst.pop()[0]
+        if need > self.budget:
+            return None
+        if self.used + need > self.budget and (self.count.get(key, 0) or not self._evict_for(key, need)):
+            return None
+        return self._make(key, need)
+
+    def give(self, plan):
+        key, b = self.size[id(plan)]
+        self.idle.setdefault(key, []).append((plan, b))
+
+    def warm(self, wanted: list, per_key: int = 1):
+        """Create up to ``per_key`` idle plans for each (key, need) of ``wanted``, one round over all
+        keys at a time, so that every key gets a plan before any key gets a second; never evicts."""
+        for r in range(per_key):
+            for key, need in wanted:
+                lst = self.idle.setdefault(key, [])
+                if len(lst) <= r and self.used + need <= self.budget:
+                    lst.append((self._make(key, need), int(need)))
+
+    def close(self):
+        """Close the idle plans (plans still handed out stay open and counted)."""
+        for key, lst in self.idle.items():
+            for plan, b in lst:
+                self._drop(plan, key, b)
+        self.idle.clear()
+
+
 class Server:
     """Admit requests as they arrive and overlap their solves on ``slots`` CUDA streams."""
 
@@ -82,47 +163,42 @@ class Server:
         self.largest_batch = 0
         free, _ = torch.cuda.mem_get_info()
         self.budget = hbm_budget if hbm_budget is not None else int(free * 0.6)
-        self.used = 0
-        self.pools: dict = {}             # (b, nb_max, precision) -> list of idle plans
+        self.plans = PlanPool(self.budget, self._create)   # keys (b, nb_max, scattering, precision)
         self.chunk_by_b = chunk_by_b or {64: 128, 128: 64, 256: 32, 512: 16, 1024: 8}
         self.refine = refine_max_iter
         self.queue: list = []
         self.done: list = []
 
     # ------------------------------------------------------------------ plans
-    def _desc(self, m: DeviceModel, precision: str, n_e: int):
-        ec = min(self.chunk_by_b.get(m.b, 16), n_e)
-        return make_desc(m.n_blocks, m.b, precision, ec, self.refine, has_scattering=m.SigR is not None,
+    def _key(self, m: DeviceModel, precision: str):
+        return (m.b, m.n_blocks, m.SigR is not None, precision)
+
+    def _desc(self, key):
+        b, nb, scat, precision = key
+        return make_desc(nb, b, precision, self.chunk_by_b.get(b, 16), self.refine, has_scattering=scat,
                          outputs=["current", "density", "integrals"])
 
-    def _take_plan(self, m: DeviceModel, precision: str):
-        key = (m.b, m.n_blocks, precision)
-        pool = self.pools.setdefault(key, [])
-        if pool:
-            return pool.pop()
-        d = self._desc(m, precision, 1 << 30)
-        need = footprint(d)
-        if self.used + need > self.budget:
-            return None
-        p = Plan(d)
-        p.key, p.bytes = key, need
-        self.used += need
+    def _create(self, key):
+        p = Plan(self._desc(key))
+        p.key = key
         return p
 
+    def _take_plan(self, m: DeviceModel, precision: str):
+        key = self._key(m, precision)
+        return self.plans.take(key, footprint(self._desc(key)))
+
     def warm(self, precisions=("emu64", "fp32"), per_key: int = 1):
-        """Create plans ahead of time (plan creation allocates and would stall the loop)."""
-        for m in self.models.values():
-            for prec in precisions:
-                plans = [self._take_plan(m, prec) for _ in range(per_key)]
-                for p in plans:
-                    if p is not None:
-                        self.pools[p.key].append(p)
+        """Create plans ahead of time (plan creation allocates and would stall the loop): up to
+        ``per_key`` per (model, precision), every key served once before any key twice."""
+        keys = dict.fromkeys(self._key(m, prec) for m in self.models.values() for prec in precisions)
+        wanted = [(k, footprint(self._desc(k))) for k in keys]
+        self.plans.warm(wanted, per_key)
 
     # ------------------------------------------------------------------ request lifecycle
     def submit(self, req: Request):
         """Queue a request, or refuse it at once when its plan could never fit the HBM budget."""
         m = self.models[req.model]
-        need = footprint(self._desc(m, req.precision, 1 << 30))
+        need = footprint(self._desc(self._key(m, req.precision)))
         if need > self.budget:
             req.result = {"rejected": f"plan footprint {need} bytes exceeds the HBM budget {self.budget}"}
             req.t_done = time.perf_counter()
@@ -190,7 +266,7 @@ class Server:
             req.result = {"current": cur.cpu().numpy() if req.n_blocks > 1 else np.zeros((len(req.energies), 0)),
                           "density": den.cpu().numpy(), "current_int": cint.cpu().numpy(),
                           "density_int": dint.cpu().numpy(), "status": stat.cpu().numpy()}
-            self.pools[plan.key].append(plan)
+            self.plans.give(plan)
             self.done.append(req)
         if group is not None:
             group.close()
@@ -221,6 +297,10 @@ class Server:
                 changed = True
         return changed
 
+    def close(self):
+        """Free the pooled plans (call once no batch is in flight)."""
+        self.plans.close()
+
     def run(self, requests: list, time_limit: float = 600.0) -> dict:
         """Replay ``requests`` (their ``t_arrival`` are offsets in seconds from now) to completion."""
         pending = sorted(requests, key=lambda r: r.t_arrival)
@@ -247,4 +327,4 @@ class Server:
                 "requests_per_s": len(done) / (t1 - t0) if t1 > t0 else 0.0,
                 "p50_s": float(np.percentile(lat, 50)) if lat.size else None,
                 "p99_s": float(np.percentile(lat, 99)) if lat.size else None,
-                "hbm_plans_bytes": int(self.used)}
+                "hbm_plans_bytes": int(self.plans.used), "plans_evicted": self.plans.evicted}
