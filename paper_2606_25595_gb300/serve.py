@@ -19,6 +19,7 @@ runs in the library's kernels through the C ABI).
 """
 from __future__ import annotations
 
+import functools
 import time
 from dataclasses import dataclass, field
 
@@ -148,6 +149,18 @@ class PlanPool:
         self.idle.clear()
 
 
+def _serving_desc(key, chunk_by_b: dict, refine: int):
+    b, nb, scat, precision = key
+    return make_desc(nb, b, precision, chunk_by_b.get(b, 16), refine, has_scattering=scat,
+                     outputs=["current", "density", "integrals"])
+
+
+def _new_plan(key, chunk_by_b: dict, refine: int):
+    p = Plan(_serving_desc(key, chunk_by_b, refine))
+    p.key = key
+    return p
+
+
 class Server:
     """Admit requests as they arrive and overlap their solves on ``slots`` CUDA streams."""
 
@@ -163,9 +176,12 @@ class Server:
         self.largest_batch = 0
         free, _ = torch.cuda.mem_get_info()
         self.budget = hbm_budget if hbm_budget is not None else int(free * 0.6)
-        self.plans = PlanPool(self.budget, self._create)   # keys (b, nb_max, scattering, precision)
-        self.chunk_by_b = chunk_by_b or {64: 128, 128: 64, 256: 32, 512: 16, 1024: 8}
+        self.chunk_by_b = dict(chunk_by_b or {64: 128, 128: 64, 256: 32, 512: 16, 1024: 8})
         self.refine = refine_max_iter
+        # keys (b, nb_max, scattering, precision); the factory holds no reference to the server, so
+        # the plans are freed as soon as the server is dropped
+        self.plans = PlanPool(self.budget, functools.partial(_new_plan, chunk_by_b=self.chunk_by_b,
+                                                             refine=self.refine))
         self.queue: list = []
         self.done: list = []
 
@@ -174,14 +190,7 @@ class Server:
         return (m.b, m.n_blocks, m.SigR is not None, precision)
 
     def _desc(self, key):
-        b, nb, scat, precision = key
-        return make_desc(nb, b, precision, self.chunk_by_b.get(b, 16), self.refine, has_scattering=scat,
-                         outputs=["current", "density", "integrals"])
-
-    def _create(self, key):
-        p = Plan(self._desc(key))
-        p.key = key
-        return p
+        return _serving_desc(key, self.chunk_by_b, self.refine)
 
     def _take_plan(self, m: DeviceModel, precision: str):
         key = self._key(m, precision)
