@@ -109,10 +109,14 @@ typedef struct {
                                   cross terms of the lesser recursions (forward: -V g L + (V g L)^H in
                                   the bracket of g^<_i; backward: Q = V g^< + (g L)^H) */
   int storage_bits;            /* 0: the left-connected blocks g_i, g^<_i of the forward sweep are kept
-                                  in the sweep's own type until the backward sweep reads them; X in
-                                  {56, 48, 40, 32, 24, 16}: they are kept in the FPX format of X bits
-                                  (qtx_kernels.h, Sec. V), with two working blocks per kind in the
-                                  sweep's type, which shrinks the footprint per energy in flight */
+                                  in the sweep's own type until the backward sweep reads them, and so
+                                  are the forward sweep's products V_i g_i and V_i g^<_i (one per
+                                  right-hand side), which the backward sweep needs again (Sec. II-A:
+                                  two block products fewer per slice, N_B - 1 blocks more per kind and
+                                  energy in flight); X in {56, 48, 40, 32, 24, 16}: g_i, g^<_i are
+                                  kept in the FPX format of X bits (qtx_kernels.h, Sec. V), with two
+                                  working blocks per kind in the sweep's type, and the products are
+                                  formed again, which shrinks the footprint per energy in flight */
   int sigma_stream;            /* 1 (needs has_scattering and energy_dependent_sigma, not offdiag_sigma):
                                   SigR_diag and SigL_diag are HOST arrays [N_E][N_B][b][b] (pinned, or
                                   the copies are synchronous); each slice's blocks for the energies of
