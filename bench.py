@@ -334,7 +334,8 @@ def secondary_workloads(q, W, steps=3, warmup=2):
     torch.cuda.empty_cache()
     # config 5: 40 requests at 200/s (saturating), then 20 at 0.7 x the measured capacity
     sat, sub, lam, _ = serving_runs(q, W, 40, 4)
-    keep = ("completed", "rejected", "requests_per_s", "energy_points_per_s", "p50_s", "p99_s", "wall_s")
+    keep = ("completed", "submitted", "rejected", "requests_per_s", "energy_points_per_s", "p50_s", "p99_s", "wall_s",
+            "plans_evicted")
     out["serving_config5"] = {
         "value": sat["energy_points_per_s"], "unit": UNIT,
         "workload": "40 Poisson requests at 200/s (b in {64,128,256,512}, N_B~U[16,96], N_E in {32,64,128}, "
