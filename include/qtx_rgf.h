@@ -44,7 +44,7 @@ typedef enum {
   QTX_ERR_SINGULAR = 4,      /* a pivot of a block inverse was zero (per energy) */
   QTX_ERR_NOT_CONVERGED = 5, /* lead decimation hit decim_max_iter (per energy) */
   QTX_ERR_TIMEOUT = 6,       /* a bounded device-side wait expired (per energy / per launch) */
-  QTX_ERR_UNSUPPORTED = 7    /* valid request this build or GPU does not provide */
+  QTX_ERR_UNSUPPORTED = 7    /* valid request the compiled library or the GPU does not provide */
 } qtx_status;
 
 /* Arithmetic of the block products and inverses (Sec. IV, V-A of the paper: the solve of Eq. 2 is

@@ -1029,7 +1029,7 @@ qtx_status validate(const qtx_rgf_desc* d, std::string& err) {
     if (d->outputs & bad) { err = "system_input produces no G^> (without second_rhs), current, contact, transmission or integrals outputs"; return QTX_ERR_INVALID_ARG; }
   }
   if ((d->precision == QTX_EMU64 || d->precision == QTX_BF16X3) && !tc_available()) {
-    err = "tensor-core engine not available in this build";
+    err = "tensor-core engine not compiled into the library";
     return QTX_ERR_UNSUPPORTED;
   }
   return QTX_OK;
