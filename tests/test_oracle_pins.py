@@ -286,6 +286,47 @@ def test_exact_current_continuity():
         assert abs(I[nb - 2] + J[nb - 1] + IR) < 1e-11 * scale
 
 
+def test_exact_current_continuity_with_overlap():
+    """With a non-orthogonal basis the bond current is 2 Re Tr[(H - E S)_{i,i+1} G^<_{i+1,i}] and the
+    broadening enters as the block-tridiagonal sink -i eta S.  From M G^< - G^< M^H =
+    Sigma^< G^A - G^R Sigma^< (M = z S - H - Sigma^R, Sigma^< without an eta part), the trace of the
+    (i, i) block gives I_{i-1} + J_i = I_i with
+        J_i = Re Tr[Sigma^<_ii G^>_ii - Sigma^>_ii G^<_ii]          (scattering, Sigma^> = Sigma^< + Sigma^R - Sigma^A)
+            + Re { i eta sum_{j=i-1..i+1} (Tr[S_ij G^<_ji] + Tr[S_ji G^<_ij]) }   (the eta sink),
+    and the contacts close the chain as in the orthogonal case."""
+    rng = np.random.default_rng(37)
+    dev = _with_leads_and_overlap(W.random_device(5, 6, n_energies=4, seed=37), rng, overlap=True)
+    nb, b = dev["n_blocks"], dev["block_size"]
+    eta = dev["eta"]
+    Sd, Su = dev["S_diag"], dev["S_upper"]
+
+    def S(i, j):
+        return Sd[i] if i == j else (Su[i] if j == i + 1 else Su[j].conj().T)
+
+    for E in (-0.5, 0.6):
+        r = O.rgf_energy(E, dev)
+        GLu = r["GL_upper"]
+
+        def GL(i, j):
+            return r["GL_diag"][i] if i == j else (GLu[i] if j == i + 1 else -GLu[j].conj().T)
+
+        J = np.zeros(nb)
+        for i in range(nb):
+            SL = dev["SigL"][0, i]
+            SR = dev["SigR"][0, i]
+            SG = SL + SR - SR.conj().T
+            sink = sum(np.trace(S(i, j) @ GL(j, i)) + np.trace(S(j, i) @ GL(i, j))
+                       for j in range(max(i - 1, 0), min(i + 2, nb)))
+            J[i] = np.real(np.trace(SL @ r["GG_diag"][i] - SG @ r["GL_diag"][i]) + 1j * eta * sink)
+        I = r["current"]
+        IL, IR = r["contact"]
+        scale = np.abs(I).max()
+        assert abs(IL + J[0] - I[0]) < 1e-11 * scale
+        for i in range(1, nb - 1):
+            assert abs(I[i - 1] + J[i] - I[i]) < 1e-11 * scale
+        assert abs(I[nb - 2] + J[nb - 1] + IR) < 1e-11 * scale
+
+
 def test_equilibrium_fluctuation_dissipation():
     """mu_L = mu_R and every Sigma^< = -f (Sigma^R - Sigma^A) (eta reservoir included) =>
     G^< = -f (G^R - G^A), zero current, n_i(E) = f Tr A_ii."""
